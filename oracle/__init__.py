@@ -1,0 +1,211 @@
+"""ctypes wrapper of the CPU oracle (oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU-baseline leg.  The CUDA library never imports or links it.
+
+`build()` compiles oracle.cpp with g++ into oracle/_build/liboracle.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "_build", "liboracle.so")
+UNKNOWN = 0xFFFFFFFF
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(HERE, "oracle.cpp")
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(LIB), exist_ok=True)
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = load(LIB)
+    return _lib
+
+
+def load(path: str):
+    """Load and type an oracle library built from oracle.cpp at `path`."""
+    L = C.CDLL(path)
+    vp, u64, u32, i32 = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int
+    L.orc_attribute.restype = vp
+    L.orc_attribute.argtypes = [u64, vp, vp, vp, u64, vp, vp, vp, vp, u32, u32]
+    L.orc_inclusive_structure.restype = vp
+    L.orc_inclusive_structure.argtypes = [u32, vp, u64, vp, vp, vp, vp]
+    L.orc_inclusive_cct.restype = i32
+    L.orc_inclusive_cct.argtypes = [u32, vp, u32, u64, vp, vp, vp, vp]
+    L.orc_derive.restype = vp
+    L.orc_derive.argtypes = [u32, vp, vp, vp, vp, vp, u32, u32, u32]
+    L.orc_apportion.restype = vp
+    L.orc_apportion.argtypes = [u32, vp, u32, u32, vp, vp, vp, u32, u64, vp, vp, vp, vp, u32, vp]
+    for name in ("orc_status", "orc_apportion_status"):
+        getattr(L, name).restype = i32; getattr(L, name).argtypes = [vp]
+    for name in ("orc_bad", "orc_size", "orc_derive_size"):
+        getattr(L, name).restype = u64; getattr(L, name).argtypes = [vp]
+    L.orc_apportion_V.restype = u32; L.orc_apportion_V.argtypes = [vp]
+    L.orc_fetch.argtypes = [vp] * 7
+    L.orc_derive_fetch.argtypes = [vp] * 14
+    L.orc_apportion_fetch.argtypes = [vp] * 5
+    for name in ("orc_free", "orc_derive_free", "orc_apportion_free"):
+        getattr(L, name).argtypes = [vp]
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+@dataclass
+class KeyList:
+    """Sorted (ctx, node, stall) -> value list."""
+    ctx: np.ndarray
+    node: np.ndarray
+    stall: np.ndarray
+    val: np.ndarray
+    total: np.ndarray | None = None
+    unknown: np.ndarray | None = None
+    status: int = 0
+    bad: int = 0
+
+    def __len__(self):
+        return int(self.val.shape[0])
+
+
+def _take(L, h, n_stall, with_totals):
+    st, bad, n = L.orc_status(h), L.orc_bad(h), L.orc_size(h)
+    ctx = np.empty(n, np.uint32); node = np.empty(n, np.uint32)
+    stall = np.empty(n, np.uint8); val = np.empty(n, np.uint64)
+    tot = np.zeros(n_stall, np.uint64) if with_totals else None
+    unk = np.zeros(n_stall, np.uint64) if with_totals else None
+    L.orc_fetch(h, _p(ctx), _p(node), _p(stall), _p(val), _p(tot), _p(unk))
+    L.orc_free(h)
+    return KeyList(ctx, node, stall, val, tot, unk, st, bad)
+
+
+def attribute(binary, pc, ctx, stall, count, n_ctx: int, n_stall: int) -> KeyList:
+    """Attribution + raw-metric aggregation (Sections 4.2, 4.5, 5)."""
+    L = lib()
+    lo, hi, nd = _c(binary.range_lo, np.uint64), _c(binary.range_hi, np.uint64), _c(binary.range_node, np.uint32)
+    pc = _c(np.asarray(pc).view(np.uint64) if np.asarray(pc).dtype == np.int64 else pc, np.uint64)
+    ctx = _c(np.asarray(ctx).view(np.uint32) if np.asarray(ctx).dtype == np.int32 else ctx, np.uint32)
+    stall = _c(stall, np.uint8)
+    if count is not None:
+        count = _c(np.asarray(count).view(np.uint32) if np.asarray(count).dtype == np.int32 else count, np.uint32)
+    h = L.orc_attribute(lo.shape[0], _p(lo), _p(hi), _p(nd), pc.shape[0], _p(pc), _p(ctx),
+                        _p(stall), _p(count), n_ctx, n_stall)
+    return _take(L, h, n_stall, True)
+
+
+def attribute_samples(binary, s) -> KeyList:
+    """attribute() on a synth.Samples (moved to host)."""
+    return attribute(binary, s.pc.cpu().numpy(), s.ctx.cpu().numpy(), s.stall.cpu().numpy(),
+                     None if s.count is None else s.count.cpu().numpy(), s.n_ctx, s.n_stall)
+
+
+def inclusive_structure(node_parent, keys: KeyList) -> KeyList:
+    """Inclusive metrics over the structure tree within each context (Section 6.1)."""
+    L = lib()
+    par = _c(node_parent, np.uint32)
+    k = [_c(keys.ctx, np.uint32), _c(keys.node, np.uint32), _c(keys.stall, np.uint8), _c(keys.val, np.uint64)]
+    h = L.orc_inclusive_structure(par.shape[0], _p(par), k[0].shape[0], *[_p(x) for x in k])
+    return _take(L, h, 0, False)
+
+
+def inclusive_cct(cct_parent, n_stall: int, keys: KeyList) -> np.ndarray:
+    """Inclusive per-stall totals over the host calling-context tree (Section 6.1)."""
+    L = lib()
+    par = _c(cct_parent, np.uint32)
+    out = np.zeros((par.shape[0], n_stall), np.uint64)
+    k = [_c(keys.ctx, np.uint32), _c(keys.stall, np.uint8), _c(keys.val, np.uint64)]
+    st = L.orc_inclusive_cct(par.shape[0], _p(par), n_stall, k[0].shape[0], *[_p(x) for x in k], _p(out))
+    if st:
+        raise ValueError(f"oracle inclusive_cct status {st}")
+    return out
+
+
+@dataclass
+class Derived:
+    ctx: np.ndarray
+    node: np.ndarray
+    stall: np.ndarray
+    sum: np.ndarray
+    min: np.ndarray
+    max: np.ndarray
+    mean: np.ndarray
+    std: np.ndarray
+    cov: np.ndarray
+    S: np.ndarray
+    S_issued: np.ndarray
+    W: np.ndarray
+    frac: np.ndarray
+
+
+def derive(profiles, n_ctx: int, n_stall: int, issued_mask: int = 1) -> Derived:
+    """Cross-profile statistics (Section 4.5) and warp issue rate (Section 7)."""
+    L = lib()
+    P = len(profiles)
+    ks = [[_c(p.ctx, np.uint32), _c(p.node, np.uint32), _c(p.stall, np.uint8), _c(p.val, np.uint64)] for p in profiles]
+    nk = np.array([k[0].shape[0] for k in ks], np.uint64)
+    ptrs = [np.array([k[j].ctypes.data for k in ks], np.uint64) for j in range(4)]
+    h = L.orc_derive(P, _p(nk), *[_p(x) for x in ptrs], n_ctx, n_stall, issued_mask)
+    n = L.orc_derive_size(h)
+    d = Derived(np.empty(n, np.uint32), np.empty(n, np.uint32), np.empty(n, np.uint8), np.empty(n, np.uint64),
+                *[np.empty(n, np.float64) for _ in range(5)],
+                np.empty(n_ctx, np.uint64), np.empty(n_ctx, np.uint64), np.empty(n_ctx, np.float64),
+                np.empty((n_ctx, n_stall), np.float64))
+    L.orc_derive_fetch(h, _p(d.ctx), _p(d.node), _p(d.stall), _p(d.sum), _p(d.min), _p(d.max), _p(d.mean),
+                       _p(d.std), _p(d.cov), _p(d.S), _p(d.S_issued), _p(d.W), _p(d.frac))
+    L.orc_derive_free(h)
+    del ks
+    return d
+
+
+@dataclass
+class GpuCct:
+    V: int
+    cnode_of_func: np.ndarray    # uint32[F]
+    incl: np.ndarray             # float64[n_req, V, n_stall + 1]
+    a: np.ndarray                # float64[n_req, E, n_stall + 1]
+    flags: np.ndarray            # uint8[n_req, E]
+
+
+def apportion(binary, n_stall: int, keys: KeyList, req_ctx) -> GpuCct:
+    """Approximate GPU calling context tree, Section 6.3 steps 1-4."""
+    L = lib()
+    nf = _c(binary.node_func, np.uint32)
+    cc, ce, cn = _c(binary.cs_caller, np.uint32), _c(binary.cs_callee, np.uint32), _c(binary.cs_node, np.uint32)
+    k = [_c(keys.ctx, np.uint32), _c(keys.node, np.uint32), _c(keys.stall, np.uint8), _c(keys.val, np.uint64)]
+    rq = _c(req_ctx, np.uint32)
+    F, E = int(binary.n_funcs), int(cc.shape[0])
+    h = L.orc_apportion(nf.shape[0], _p(nf), F, E, _p(cc), _p(ce), _p(cn), n_stall,
+                        k[0].shape[0], *[_p(x) for x in k], rq.shape[0], _p(rq))
+    st = L.orc_apportion_status(h)
+    if st:
+        L.orc_apportion_free(h)
+        raise ValueError(f"oracle apportion status {st}")
+    V = L.orc_apportion_V(h)
+    M = n_stall + 1
+    g = GpuCct(V, np.empty(F, np.uint32), np.empty((rq.shape[0], V, M)), np.empty((rq.shape[0], E, M)),
+               np.empty((rq.shape[0], E), np.uint8))
+    L.orc_apportion_fetch(h, _p(g.cnode_of_func), _p(g.incl), _p(g.a), _p(g.flags))
+    L.orc_apportion_free(h)
+    return g

@@ -1,0 +1,482 @@
+// CPU oracle for GPU PC-sample analysis (arXiv 2109.06931).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, single-threaded
+// statement of what the CUDA library computes.  Only the test suite, the
+// smoke check and the benchmark's CPU-baseline leg may load it; the library
+// never calls it and shares no code, header or table with it.
+//
+// Every function follows one passage of the paper, cited beside it:
+//   Section 4.2   a PC sample = (instruction address, stall reason, count);
+//                 it becomes a GPU-instruction node under the kernel's context.
+//   Section 4.5   a raw metric is the sum of all measured values of a kind
+//                 in a context; post-mortem derived metrics are sum, min,
+//                 mean, max, std. deviation and coefficient of variation.
+//   Section 5     instructions map to lines, loops, inlined code, functions.
+//   Section 6.1   statistic generation propagates values up the calling
+//                 context tree (inclusive metrics).
+//   Section 6.3   GPU calling context tree, steps 1-4 (call-graph weights,
+//                 zero-weight fix-up, SCC collapse, gprof-style splitting).
+//   Section 7     warp issue rate W = (S - S_stall) / S.
+// Readings of points the paper leaves open are stated where they are used.
+//
+// Floating point is double precision throughout; counts are exact uint64.
+// Parity status: every entry point is pinned by tests against brute force,
+// closed forms or hand-computed cases (no "parity unpinned" function).
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <set>
+#include <tuple>
+#include <vector>
+#include <algorithm>
+
+namespace {
+
+const uint32_t UNKNOWN = 0xFFFFFFFFu;   // attribution of a PC in no range
+const uint32_t NO_PARENT = 0xFFFFFFFFu;
+
+const int OK = 0, INVALID_ARG = 1, INVALID_SAMPLE = 3;
+
+typedef std::tuple<uint32_t, uint32_t, uint32_t> Key;   // (ctx, node, stall)
+
+// A sorted key -> value list handed back to the caller.
+struct KeyList {
+    std::vector<uint32_t> ctx, node, stall;
+    std::vector<uint64_t> val;
+    std::vector<uint64_t> total, unknown;   // per stall reason (attribution only)
+    int status = OK;
+    uint64_t bad = 0;
+};
+
+}  // namespace
+
+extern "C" {
+
+// ---------------------------------------------------------------------------
+// O1 + O2: attribution (Section 4.2, Section 5) and raw-metric aggregation
+// (Section 4.5).
+//
+// O1: for each sample, the range is the last one with lo <= pc (ranges are
+//     sorted by lo and disjoint); the sample belongs to that range's node if
+//     pc < hi (half-open ranges), else to UNKNOWN.
+// O2: raw metric of key (ctx, node, stall) = sum of the counts of its samples;
+//     a missing count array means every record counts 1; keys whose sum is 0
+//     are omitted.  Any record with ctx >= n_ctx or stall >= n_stall fails the
+//     whole call (status INVALID_SAMPLE, number of bad records in `bad`).
+void* orc_attribute(uint64_t n_ranges, const uint64_t* range_lo, const uint64_t* range_hi,
+                    const uint32_t* range_node, uint64_t n, const uint64_t* pc,
+                    const uint32_t* ctx, const uint8_t* stall, const uint32_t* count,
+                    uint32_t n_ctx, uint32_t n_stall) {
+    KeyList* out = new KeyList();
+    out->total.assign(n_stall, 0);
+    out->unknown.assign(n_stall, 0);
+    for (uint64_t i = 0; i < n; ++i)
+        if (ctx[i] >= n_ctx || stall[i] >= n_stall) out->bad++;
+    if (out->bad) { out->status = INVALID_SAMPLE; return out; }
+
+    std::map<Key, uint64_t> agg;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t* it = std::upper_bound(range_lo, range_lo + n_ranges, pc[i]);
+        uint32_t node = UNKNOWN;
+        if (it != range_lo) {
+            uint64_t j = (uint64_t)(it - range_lo) - 1;
+            if (pc[i] < range_hi[j]) node = range_node[j];
+        }
+        uint64_t c = count ? count[i] : 1;
+        agg[Key(ctx[i], node, stall[i])] += c;
+        out->total[stall[i]] += c;
+        if (node == UNKNOWN) out->unknown[stall[i]] += c;
+    }
+    for (auto& kv : agg) {
+        if (kv.second == 0) continue;
+        out->ctx.push_back(std::get<0>(kv.first));
+        out->node.push_back(std::get<1>(kv.first));
+        out->stall.push_back(std::get<2>(kv.first));
+        out->val.push_back(kv.second);
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// O4(a): inclusive metrics over the program-structure tree inside each
+// context (Section 6.1, statistic generation: values propagate up the tree).
+// Every key's value is added to its node and to every ancestor of that node
+// up to the function node (node_parent == NO_PARENT).  UNKNOWN has no
+// ancestors and keeps its own value.  Output sorted by (ctx, node, stall).
+void* orc_inclusive_structure(uint32_t n_nodes, const uint32_t* node_parent, uint64_t k,
+                              const uint32_t* kctx, const uint32_t* knode,
+                              const uint8_t* kstall, const uint64_t* kval) {
+    KeyList* out = new KeyList();
+    std::map<Key, uint64_t> agg;
+    for (uint64_t i = 0; i < k; ++i) {
+        uint32_t n = knode[i];
+        if (n == UNKNOWN) { agg[Key(kctx[i], n, kstall[i])] += kval[i]; continue; }
+        if (n >= n_nodes) { out->status = INVALID_ARG; return out; }
+        uint32_t steps = 0;
+        while (n != NO_PARENT) {
+            agg[Key(kctx[i], n, kstall[i])] += kval[i];
+            n = node_parent[n];
+            if (++steps > n_nodes) { out->status = INVALID_ARG; return out; }
+        }
+    }
+    for (auto& kv : agg) {
+        out->ctx.push_back(std::get<0>(kv.first));
+        out->node.push_back(std::get<1>(kv.first));
+        out->stall.push_back(std::get<2>(kv.first));
+        out->val.push_back(kv.second);
+    }
+    return out;
+}
+
+// O4(b): inclusive metrics over the host calling-context tree (Section 6.1).
+// Launch context c is CCT node c.  host[h][r] = sum of the values of all keys
+// (UNKNOWN included) whose context lies in the subtree of h: each key's value
+// is added to its context and to every ancestor.  `host` is n_cct x n_stall.
+int orc_inclusive_cct(uint32_t n_cct, const uint32_t* cct_parent, uint32_t n_stall, uint64_t k,
+                      const uint32_t* kctx, const uint8_t* kstall, const uint64_t* kval,
+                      uint64_t* host) {
+    std::memset(host, 0, sizeof(uint64_t) * (size_t)n_cct * n_stall);
+    for (uint64_t i = 0; i < k; ++i) {
+        uint32_t h = kctx[i];
+        if (h >= n_cct || kstall[i] >= n_stall) return INVALID_ARG;
+        uint32_t steps = 0;
+        while (h != NO_PARENT) {
+            host[(size_t)h * n_stall + kstall[i]] += kval[i];
+            h = cct_parent[h];
+            if (++steps > n_cct) return INVALID_ARG;
+        }
+    }
+    return OK;
+}
+
+// ---------------------------------------------------------------------------
+// O5: derived metrics across P profiles (Section 4.5) and warp issue rate
+// (Section 7).
+//
+// For every key in the union of the P profiles, x_p is the profile's value or
+// 0 where the key is absent: sum, min, max, mean = sum / P, population std
+// sqrt(sum (x_p - mean)^2 / P) by two passes, CoV = std / mean.
+// Per context, over the sum of all profiles: S = all samples, S_issued = the
+// samples whose stall reason is in issued_mask (not stalled),
+// W = (S - S_stall) / S = S_issued / S (NaN when S = 0), and the fraction of
+// S in each stall reason (NaN when S = 0).
+struct Derived {
+    std::vector<uint32_t> ctx, node, stall;
+    std::vector<uint64_t> sum;
+    std::vector<double> mn, mx, mean, sd, cov;
+    std::vector<uint64_t> S, S_issued;
+    std::vector<double> W, frac;
+};
+
+void* orc_derive(uint32_t P, const uint64_t* nkeys, const uint32_t* const* kctx,
+                 const uint32_t* const* knode, const uint8_t* const* kstall,
+                 const uint64_t* const* kval, uint32_t n_ctx, uint32_t n_stall,
+                 uint32_t issued_mask) {
+    Derived* d = new Derived();
+    std::map<Key, std::vector<uint64_t>> u;
+    for (uint32_t p = 0; p < P; ++p)
+        for (uint64_t i = 0; i < nkeys[p]; ++i) {
+            auto& v = u[Key(kctx[p][i], knode[p][i], kstall[p][i])];
+            if (v.empty()) v.assign(P, 0);
+            v[p] += kval[p][i];
+        }
+    d->S.assign(n_ctx, 0);
+    d->S_issued.assign(n_ctx, 0);
+    for (auto& kv : u) {
+        const std::vector<uint64_t>& x = kv.second;
+        uint64_t s = 0, lo = x[0], hi = x[0];
+        for (uint32_t p = 0; p < P; ++p) { s += x[p]; lo = std::min(lo, x[p]); hi = std::max(hi, x[p]); }
+        double mean = (double)s / P;
+        double ss = 0;
+        for (uint32_t p = 0; p < P; ++p) { double e = (double)x[p] - mean; ss += e * e; }
+        double sd = std::sqrt(ss / P);
+        d->ctx.push_back(std::get<0>(kv.first));
+        d->node.push_back(std::get<1>(kv.first));
+        d->stall.push_back(std::get<2>(kv.first));
+        d->sum.push_back(s);
+        d->mn.push_back((double)lo);
+        d->mx.push_back((double)hi);
+        d->mean.push_back(mean);
+        d->sd.push_back(sd);
+        d->cov.push_back(sd / mean);
+        uint32_t c = std::get<0>(kv.first), r = std::get<2>(kv.first);
+        if (c < n_ctx) {
+            d->S[c] += s;
+            if (r < 32 && ((issued_mask >> r) & 1u)) d->S_issued[c] += s;
+        }
+    }
+    d->W.assign(n_ctx, NAN);
+    d->frac.assign((size_t)n_ctx * n_stall, NAN);
+    std::vector<uint64_t> per((size_t)n_ctx * n_stall, 0);
+    for (auto& kv : u) {
+        uint32_t c = std::get<0>(kv.first), r = std::get<2>(kv.first);
+        if (c < n_ctx && r < n_stall) {
+            uint64_t s = 0;
+            for (uint64_t v : kv.second) s += v;
+            per[(size_t)c * n_stall + r] += s;
+        }
+    }
+    for (uint32_t c = 0; c < n_ctx; ++c) {
+        if (d->S[c] == 0) continue;
+        d->W[c] = (double)d->S_issued[c] / (double)d->S[c];
+        for (uint32_t r = 0; r < n_stall; ++r)
+            d->frac[(size_t)c * n_stall + r] = (double)per[(size_t)c * n_stall + r] / (double)d->S[c];
+    }
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// O3: approximate GPU calling context tree (Section 6.3, steps 1-4), per
+// launch context c.
+//
+// Step 1: static call graph from the call sites (one edge per call
+//   instruction).  w(e) = samples at e's call instruction (node cs_node[e]),
+//   summed over stall reasons, in context c.  excl(f)[r] = samples of c in
+//   nodes of f (UNKNOWN excluded); S(f) = sum_r excl(f)[r], which includes
+//   f's own call instructions.
+// Step 2 ("a function has samples and none of its incoming edges has a
+//   non-zero weight ... repeat through callers"): Z0 = {f : S(f) > 0,
+//   indeg(f) >= 1, every measured w(in(f)) = 0}; a caller g of a member of Z
+//   joins Z when indeg(g) >= 1 and every measured w(in(g)) = 0.  Every edge
+//   into a member of Z gets weight 1 (flag FIXUP).  Roots (indeg 0) stop it.
+// Step 3: Tarjan's SCCs; a non-trivial SCC (>= 2 members or a self-call) is
+//   one condensed node whose exclusive cost is the sum of its members'; its
+//   internal edges are dropped (flag INTRA_SCC, a = 0).  Reading for a
+//   condensed node left with zero incoming weight although it has cost or
+//   holds a member of Z (step 2 precedes step 3 and cannot see this): apply
+//   the step-2 rule again on the condensed graph (flag FIXUP2).
+// Step 4 (gprof assumption): r(e) = w(e) / W(head), W(v) = incoming weight of
+//   v (r = 0 when W = 0); bottom-up over the condensed DAG
+//   incl(v) = excl(v) + sum_{e out of v} r(e) incl(head(e)), and
+//   a(e) = r(e) incl(head(e)).  Cost that cannot be passed up stays at roots.
+//
+// Output layout, per requested context (dense): condensed node ids are
+// f for a function in a trivial SCC and F + k for the k-th non-trivial SCC
+// (SCCs ordered by smallest member); incl[V][n_stall + 1] (last column is the
+// total over stall reasons), a[E][n_stall + 1], flags[E].  Rows of functions
+// that belong to a non-trivial SCC stay zero.
+struct GpuCct {
+    uint32_t V = 0;
+    std::vector<uint32_t> cnode_of_func;
+    std::vector<double> incl, a;
+    std::vector<uint8_t> flags;
+    int status = OK;
+};
+
+enum { F_FIXUP = 1, F_FIXUP2 = 2, F_INTRA = 4 };
+
+// Tarjan's strongly connected components, iterative form of the published
+// recursive algorithm (Tarjan 1972).  Returns comp[f] and the components in
+// the order Tarjan completes them (every component after all components it
+// reaches: reverse topological order of the condensed graph).
+static void tarjan(uint32_t F, const std::vector<std::vector<uint32_t>>& succ,
+                   std::vector<uint32_t>& comp, std::vector<std::vector<uint32_t>>& comps) {
+    std::vector<int64_t> index(F, -1), low(F, 0);
+    std::vector<char> on(F, 0);
+    std::vector<uint32_t> st;
+    comp.assign(F, 0);
+    comps.clear();
+    int64_t next = 0;
+    std::vector<std::pair<uint32_t, size_t>> call;   // (vertex, next successor position)
+    for (uint32_t s = 0; s < F; ++s) {
+        if (index[s] >= 0) continue;
+        call.push_back({s, 0});
+        index[s] = low[s] = next++; st.push_back(s); on[s] = 1;
+        while (!call.empty()) {
+            uint32_t v = call.back().first;
+            size_t& pos = call.back().second;
+            if (pos < succ[v].size()) {
+                uint32_t w = succ[v][pos++];
+                if (index[w] < 0) {
+                    index[w] = low[w] = next++; st.push_back(w); on[w] = 1;
+                    call.push_back({w, 0});
+                } else if (on[w]) {
+                    low[v] = std::min(low[v], index[w]);
+                }
+            } else {
+                if (low[v] == index[v]) {
+                    std::vector<uint32_t> c;
+                    uint32_t w;
+                    do { w = st.back(); st.pop_back(); on[w] = 0; comp[w] = (uint32_t)comps.size(); c.push_back(w); } while (w != v);
+                    comps.push_back(c);
+                }
+                call.pop_back();
+                if (!call.empty()) { uint32_t u = call.back().first; low[u] = std::min(low[u], low[v]); }
+            }
+        }
+    }
+}
+
+void* orc_apportion(uint32_t n_nodes, const uint32_t* node_func, uint32_t F, uint32_t E,
+                    const uint32_t* cs_caller, const uint32_t* cs_callee, const uint32_t* cs_node,
+                    uint32_t n_stall, uint64_t k, const uint32_t* kctx, const uint32_t* knode,
+                    const uint8_t* kstall, const uint64_t* kval,
+                    uint32_t n_req, const uint32_t* req_ctx) {
+    GpuCct* g = new GpuCct();
+    const uint32_t M = n_stall + 1;
+    // static graph, step 1 / step 3 parts that do not depend on the context
+    std::vector<std::vector<uint32_t>> succ(F), in_edges(F);
+    std::vector<int64_t> call_of_node(n_nodes, -1);
+    for (uint32_t e = 0; e < E; ++e) {
+        if (cs_caller[e] >= F || cs_callee[e] >= F || cs_node[e] >= n_nodes) { g->status = INVALID_ARG; return g; }
+        succ[cs_caller[e]].push_back(cs_callee[e]);
+        in_edges[cs_callee[e]].push_back(e);
+        call_of_node[cs_node[e]] = e;
+    }
+    std::vector<uint32_t> comp;
+    std::vector<std::vector<uint32_t>> comps;
+    tarjan(F, succ, comp, comps);
+    const uint32_t C = (uint32_t)comps.size();
+    std::vector<char> nontrivial(C, 0);
+    for (uint32_t c = 0; c < C; ++c) if (comps[c].size() >= 2) nontrivial[c] = 1;
+    for (uint32_t e = 0; e < E; ++e) if (cs_caller[e] == cs_callee[e]) nontrivial[comp[cs_caller[e]]] = 1;
+    // canonical condensed ids
+    std::vector<std::pair<uint32_t, uint32_t>> nt;   // (smallest member, comp)
+    for (uint32_t c = 0; c < C; ++c)
+        if (nontrivial[c]) nt.push_back({*std::min_element(comps[c].begin(), comps[c].end()), c});
+    std::sort(nt.begin(), nt.end());
+    std::vector<uint32_t> cid(C);
+    for (uint32_t c = 0; c < C; ++c) if (!nontrivial[c]) cid[c] = comps[c][0];
+    for (uint32_t i = 0; i < nt.size(); ++i) cid[nt[i].second] = F + i;
+    g->V = F + (uint32_t)nt.size();
+    g->cnode_of_func.resize(F);
+    for (uint32_t f = 0; f < F; ++f) g->cnode_of_func[f] = cid[comp[f]];
+
+    g->incl.assign((size_t)n_req * g->V * M, 0.0);
+    g->a.assign((size_t)n_req * E * M, 0.0);
+    g->flags.assign((size_t)n_req * E, 0);
+
+    for (uint32_t q = 0; q < n_req; ++q) {
+        const uint32_t c = req_ctx[q];
+        // step 1: exclusive costs and measured call weights in context c
+        std::vector<std::vector<double>> excl(F, std::vector<double>(n_stall, 0.0));
+        std::vector<uint64_t> S(F, 0), w(E, 0);
+        for (uint64_t i = 0; i < k; ++i) {
+            if (kctx[i] != c || knode[i] == UNKNOWN) continue;
+            if (knode[i] >= n_nodes || kstall[i] >= n_stall) { g->status = INVALID_ARG; return g; }
+            uint32_t f = node_func[knode[i]];
+            excl[f][kstall[i]] += (double)kval[i];
+            S[f] += kval[i];
+            if (call_of_node[knode[i]] >= 0) w[call_of_node[knode[i]]] += kval[i];
+        }
+        std::vector<char> measured_in(F, 0);
+        for (uint32_t f = 0; f < F; ++f)
+            for (uint32_t e : in_edges[f]) if (w[e] > 0) measured_in[f] = 1;
+        // step 2: zero-weight fix-up, closure through callers
+        std::vector<double> wt(E);
+        for (uint32_t e = 0; e < E; ++e) wt[e] = (double)w[e];
+        std::vector<uint8_t> fl(E, 0);
+        std::vector<char> inZ(F, 0);
+        std::vector<uint32_t> work;
+        for (uint32_t f = 0; f < F; ++f)
+            if (S[f] > 0 && !in_edges[f].empty() && !measured_in[f]) { inZ[f] = 1; work.push_back(f); }
+        while (!work.empty()) {
+            uint32_t f = work.back(); work.pop_back();
+            for (uint32_t e : in_edges[f]) {
+                wt[e] = 1.0; fl[e] |= F_FIXUP;
+                uint32_t h = cs_caller[e];
+                if (!inZ[h] && !in_edges[h].empty() && !measured_in[h]) { inZ[h] = 1; work.push_back(h); }
+            }
+        }
+        // step 3: condensation
+        std::vector<std::vector<double>> cex(C, std::vector<double>(n_stall, 0.0));
+        std::vector<char> cneed(C, 0);
+        for (uint32_t f = 0; f < F; ++f) {
+            for (uint32_t r = 0; r < n_stall; ++r) cex[comp[f]][r] += excl[f][r];
+            if (S[f] > 0 || inZ[f]) cneed[comp[f]] = 1;
+        }
+        std::vector<std::vector<uint32_t>> cin(C), cout_(C);
+        for (uint32_t e = 0; e < E; ++e) {
+            uint32_t a = comp[cs_caller[e]], b = comp[cs_callee[e]];
+            if (a == b) { fl[e] |= F_INTRA; wt[e] = 0.0; continue; }
+            cin[b].push_back(e); cout_[a].push_back(e);
+        }
+        std::vector<double> W(C, 0.0);
+        for (uint32_t v = 0; v < C; ++v) for (uint32_t e : cin[v]) W[v] += wt[e];
+        // reading: step-2 rule again on the condensed graph
+        std::vector<char> inZ2(C, 0);
+        for (uint32_t v = 0; v < C; ++v)
+            if (cneed[v] && !cin[v].empty() && W[v] == 0.0) { inZ2[v] = 1; work.push_back(v); }
+        while (!work.empty()) {
+            uint32_t v = work.back(); work.pop_back();
+            for (uint32_t e : cin[v]) {
+                wt[e] = 1.0; fl[e] |= F_FIXUP2;
+                uint32_t u = comp[cs_caller[e]];
+                if (!inZ2[u] && !cin[u].empty() && W[u] == 0.0) { inZ2[u] = 1; work.push_back(u); }
+            }
+        }
+        for (uint32_t v = 0; v < C; ++v) { W[v] = 0.0; for (uint32_t e : cin[v]) W[v] += wt[e]; }
+        // step 4: bottom-up in Tarjan completion order (callees first)
+        std::vector<std::vector<double>> incl(C, std::vector<double>(n_stall, 0.0));
+        double* A = &g->a[(size_t)q * E * M];
+        for (uint32_t v = 0; v < C; ++v) {
+            for (uint32_t r = 0; r < n_stall; ++r) incl[v][r] = cex[v][r];
+            for (uint32_t e : cout_[v]) {
+                uint32_t h = comp[cs_callee[e]];
+                double ratio = W[h] > 0.0 ? wt[e] / W[h] : 0.0;
+                double tot = 0.0;
+                for (uint32_t r = 0; r < n_stall; ++r) {
+                    double x = ratio * incl[h][r];
+                    incl[v][r] += x;
+                    A[(size_t)e * M + r] = x;
+                    tot += x;
+                }
+                A[(size_t)e * M + n_stall] = tot;
+            }
+        }
+        double* I = &g->incl[(size_t)q * g->V * M];
+        for (uint32_t v = 0; v < C; ++v) {
+            double tot = 0.0;
+            for (uint32_t r = 0; r < n_stall; ++r) { I[(size_t)cid[v] * M + r] = incl[v][r]; tot += incl[v][r]; }
+            I[(size_t)cid[v] * M + n_stall] = tot;
+        }
+        std::memcpy(&g->flags[(size_t)q * E], fl.data(), E);
+    }
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// result access (ctypes marshalling)
+int orc_status(void* p) { return ((KeyList*)p)->status; }
+uint64_t orc_bad(void* p) { return ((KeyList*)p)->bad; }
+uint64_t orc_size(void* p) { return ((KeyList*)p)->val.size(); }
+void orc_fetch(void* p, uint32_t* ctx, uint32_t* node, uint8_t* stall, uint64_t* val,
+               uint64_t* total, uint64_t* unknown) {
+    KeyList* k = (KeyList*)p;
+    for (size_t i = 0; i < k->val.size(); ++i) {
+        ctx[i] = k->ctx[i]; node[i] = k->node[i]; stall[i] = (uint8_t)k->stall[i]; val[i] = k->val[i];
+    }
+    if (total) for (size_t r = 0; r < k->total.size(); ++r) total[r] = k->total[r];
+    if (unknown) for (size_t r = 0; r < k->unknown.size(); ++r) unknown[r] = k->unknown[r];
+}
+void orc_free(void* p) { delete (KeyList*)p; }
+
+uint64_t orc_derive_size(void* p) { return ((Derived*)p)->sum.size(); }
+void orc_derive_fetch(void* p, uint32_t* ctx, uint32_t* node, uint8_t* stall, uint64_t* sum,
+                      double* mn, double* mx, double* mean, double* sd, double* cov,
+                      uint64_t* S, uint64_t* S_issued, double* W, double* frac) {
+    Derived* d = (Derived*)p;
+    for (size_t i = 0; i < d->sum.size(); ++i) {
+        ctx[i] = d->ctx[i]; node[i] = d->node[i]; stall[i] = (uint8_t)d->stall[i]; sum[i] = d->sum[i];
+        mn[i] = d->mn[i]; mx[i] = d->mx[i]; mean[i] = d->mean[i]; sd[i] = d->sd[i]; cov[i] = d->cov[i];
+    }
+    for (size_t c = 0; c < d->S.size(); ++c) { S[c] = d->S[c]; S_issued[c] = d->S_issued[c]; W[c] = d->W[c]; }
+    for (size_t i = 0; i < d->frac.size(); ++i) frac[i] = d->frac[i];
+}
+void orc_derive_free(void* p) { delete (Derived*)p; }
+
+int orc_apportion_status(void* p) { return ((GpuCct*)p)->status; }
+uint32_t orc_apportion_V(void* p) { return ((GpuCct*)p)->V; }
+void orc_apportion_fetch(void* p, uint32_t* cnode_of_func, double* incl, double* a, uint8_t* flags) {
+    GpuCct* g = (GpuCct*)p;
+    std::copy(g->cnode_of_func.begin(), g->cnode_of_func.end(), cnode_of_func);
+    std::copy(g->incl.begin(), g->incl.end(), incl);
+    std::copy(g->a.begin(), g->a.end(), a);
+    std::copy(g->flags.begin(), g->flags.end(), flags);
+}
+void orc_apportion_free(void* p) { delete (GpuCct*)p; }
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+"""The pins are strong enough: each test compiles a copy of oracle.cpp with
+one plausible mistake planted (a wrong boundary, a dropped term, a wrong
+index or divisor) and checks that some pin now fails.  Mistakes are planted
+in a private copy of the oracle on the CPU only."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_apportion as TA
+import test_oracle_attribution as TT
+import test_oracle_inclusive_derive as TI
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")
+
+MUTATIONS = [
+    ("closed-range", "if (pc[i] < range_hi[j]) node", "if (pc[i] <= range_hi[j]) node",
+     [lambda o: TT.test_golden_fixture(o)]),
+    ("keep-zero-keys", "if (kv.second == 0) continue;", "",
+     [lambda o: TT.test_golden_fixture(o)]),
+    ("no-unknown-total", "if (node == UNKNOWN) out->unknown[stall[i]] += c;", "",
+     [lambda o: TT.test_golden_fixture(o)]),
+    ("step2-no-callers", "if (!inZ[h] && !in_edges[h].empty() && !measured_in[h]) { inZ[h] = 1; work.push_back(h); }", "",
+     [lambda o: TA.test_golden(o, "gpucct_fig5.json")]),
+    ("ratio-of-tail", "double ratio = W[h] > 0.0 ? wt[e] / W[h] : 0.0;", "double ratio = W[v] > 0.0 ? wt[e] / W[v] : 0.0;",
+     [lambda o: TA.test_golden(o, "gpucct_fig5.json"), lambda o: TA.test_path_enumeration(o, 1, False)]),
+    ("no-fixup2", "if (cneed[v] && !cin[v].empty() && W[v] == 0.0) { inZ2[v] = 1; work.push_back(v); }", "",
+     [lambda o: TA.test_golden(o, "gpucct_fig5.json")]),
+    ("scc-excl-dropped", "for (uint32_t r = 0; r < n_stall; ++r) cex[comp[f]][r] += excl[f][r];",
+     "for (uint32_t r = 0; r < n_stall; ++r) cex[comp[f]][r] = excl[f][r];",
+     [lambda o: TA.test_golden(o, "gpucct_fig5.json")]),
+    ("sample-std", "double sd = std::sqrt(ss / P);", "double sd = std::sqrt(ss / (P > 1 ? P - 1 : 1));",
+     [lambda o: TI.test_derive_vs_numpy(o)]),
+    ("incl-stops-below-func", "while (n != NO_PARENT) {\n            agg[Key(kctx[i], n, kstall[i])] += kval[i];",
+     "while (node_parent[n] != NO_PARENT) {\n            agg[Key(kctx[i], n, kstall[i])] += kval[i];",
+     [lambda o: TI.test_structure_inclusive_brute(o)]),
+    ("cct-skip-self", "while (h != NO_PARENT) {\n            host", "h = cct_parent[h];\n        while (h != NO_PARENT) {\n            host",
+     [lambda o: TI.test_cct_inclusive(o)]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, pins):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mut = tmp_path / "oracle_mut.cpp"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-o", str(so), str(mut)])
+    saved = oracle._lib
+    oracle._lib = oracle.load(str(so))
+    try:
+        caught = 0
+        for pin in pins:
+            try:
+                pin(oracle)
+            except (AssertionError, ValueError, KeyError):
+                caught += 1
+        assert caught >= 1, f"planted mistake '{name}' passed every pin"
+    finally:
+        oracle._lib = saved
