@@ -1,0 +1,285 @@
+/* hpa.h -- GPU PC-sample analysis on one GB300 (sm_103a).
+ *
+ * C ABI of libhpa.so.  The library attributes GPU PC samples to the program
+ * structure of a GPU binary, aggregates them into exact raw metrics per
+ * (launch context, structure node, stall reason), splits GPU function costs
+ * among call sites to form approximate GPU calling context trees, propagates
+ * inclusive metrics, and derives cross-profile statistics.  The operations
+ * follow "Measurement and Analysis of GPU-accelerated Applications with
+ * HPCToolkit" (Zhou et al., arXiv 2109.06931); each entry point cites the
+ * section that defines it.
+ *
+ * Conventions
+ *  - Every call returns an hpa_status.  No call aborts, traps or throws.
+ *  - Device work is enqueued on the handle's CUDA stream and runs
+ *    asynchronously.  Errors found on the host return at once; errors found
+ *    by a kernel (an invalid sample, a full output, a timed-out wait) are
+ *    recorded in a device status word and returned by hpa_sync().
+ *  - "device" arrays live in the handle's GPU memory and are owned by the
+ *    caller; they must stay valid until hpa_sync() returns.  "host" arrays
+ *    are read or written before the call returns.
+ *  - Identifiers: launch-context ids are uint32 in [0, n_ctx); structure node
+ *    ids are uint32 in [0, n_nodes); function ids in [0, n_funcs).
+ *  - One handle per host thread.
+ */
+#ifndef HPA_H
+#define HPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hpa_status;
+#define HPA_OK                0
+#define HPA_E_INVALID_ARG     1  /* bad pointer, size or option                    */
+#define HPA_E_INVALID_TABLE   2  /* structure / call graph / CCT fails validation   */
+#define HPA_E_INVALID_SAMPLE  3  /* a record has ctx >= n_ctx or stall >= n_stall   */
+#define HPA_E_CAPACITY        4  /* an output array is too small; *needed is set   */
+#define HPA_E_OOM             5  /* device memory could not be reserved             */
+#define HPA_E_CUDA            6  /* a CUDA runtime call failed                      */
+#define HPA_E_TIMEOUT         7  /* a bounded device wait gave up                   */
+#define HPA_E_INTERNAL        8  /* internal invariant violated (a bug)             */
+
+#define HPA_UNKNOWN_NODE 0xFFFFFFFFu  /* node of a PC covered by no range          */
+#define HPA_NO_PARENT    0xFFFFFFFFu  /* parent of a root                          */
+#define HPA_MAX_STALL    32u          /* stall reasons per sample: [0, 32)         */
+
+/* structure node kinds (Section 5: functions, inlined code, loops, lines) */
+enum { HPA_NODE_FUNC = 0, HPA_NODE_INLINE = 1, HPA_NODE_LOOP = 2, HPA_NODE_LINE = 3, HPA_NODE_CALL = 4 };
+
+/* call-edge flags of the GPU calling context tree (Section 6.3) */
+enum { HPA_EDGE_FIXUP = 1,      /* weight 1 assigned by the step-2 zero-weight rule          */
+       HPA_EDGE_FIXUP2 = 2,     /* weight 1 assigned by the same rule on the SCC-collapsed graph */
+       HPA_EDGE_INTRA_SCC = 4   /* edge inside one recursive SCC: removed, share 0          */ };
+
+typedef struct hpa_handle hpa_handle;
+
+/* Options of a handle.  Zero-initialised fields take their defaults. */
+typedef struct {
+    uint32_t issued_mask;   /* stall reasons that count as "issued" (not stalled) in the warp
+                               issue rate W; default 0x1 (reason 0)                        */
+    uint32_t leaf_capacity; /* records per shared-memory leaf of the aggregation; 0 = chosen
+                               per call by the tuner (hpa_tune)                             */
+    uint32_t timeout_iters; /* iteration limit of every bounded device wait; 0 = 1<<22     */
+    uint32_t reserved[5];
+} hpa_options;
+
+/* Program structure of one GPU binary (Section 5).  HOST arrays, copied into
+ * library-owned device memory by hpa_load_structure.
+ *  - ranges: half-open [range_lo[i], range_hi[i]) of relocated, binary-wide
+ *    unique instruction addresses (Section 5: each GPU function is relocated
+ *    to a unique address), sorted by lo, non-empty and pairwise disjoint
+ *    (overlapping functions are split into disjoint ranges, Section 5).
+ *    range_hi[n-1] - range_lo[0] must be < 2^32.  range_node[i] is the
+ *    structure node (usually a LINE or CALL node) that owns the range.
+ *  - nodes: a forest; node_parent[v] is HPA_NO_PARENT exactly for FUNC nodes,
+ *    otherwise a node of the same function; node_func[v] is v's function.
+ *    (n_nodes + 1) * n_stall must be <= 2^32.
+ *  - call sites (Section 6.3 step 1): one per call instruction; cs_node[e] is
+ *    the CALL node whose range is that instruction, cs_caller[e] its function,
+ *    cs_callee[e] the called function.                                         */
+typedef struct {
+    uint64_t n_ranges;
+    const uint64_t* range_lo;
+    const uint64_t* range_hi;
+    const uint32_t* range_node;
+    uint32_t n_nodes;
+    const uint32_t* node_parent;
+    const uint8_t* node_kind;
+    const uint32_t* node_func;
+    uint32_t n_funcs;
+    uint32_t n_calls;
+    const uint32_t* cs_caller;
+    const uint32_t* cs_callee;
+    const uint32_t* cs_node;
+} hpa_structure;
+
+/* Static facts of a loaded binary. */
+typedef struct {
+    uint32_t n_nodes, n_funcs, n_calls;
+    uint32_t n_cnodes;       /* condensed call-graph nodes V = n_funcs + non-trivial SCCs       */
+    uint32_t n_scc;          /* non-trivial SCCs (>= 2 functions or a self-call)                */
+    uint32_t cdag_levels;    /* levels of the condensed DAG                                      */
+    uint64_t n_ranges;
+} hpa_binary_info;
+
+/* One buffer of PC samples (Section 4.2: instruction address, stall reason,
+ * count; plus the launch calling context the kernel ran in).  DEVICE arrays
+ * (HOST arrays for the *_host entry points).  count may be NULL: every record
+ * then counts 1.  Valid ids: ctx < n_ctx, stall < n_stall <= HPA_MAX_STALL.   */
+typedef struct {
+    uint64_t n;
+    const uint64_t* pc;
+    const uint32_t* ctx;
+    const uint8_t* stall;
+    const uint32_t* count;
+    uint32_t n_ctx;
+    uint32_t n_stall;
+} hpa_samples;
+
+/* Raw-metric profile: unique keys ascending by (ctx, node, stall) with their
+ * exact sums.  Caller-allocated DEVICE arrays of `capacity` entries (K <= n
+ * always holds, so capacity = n is always enough).  n_keys is a device uint64:
+ * the number of keys written, or -- with status HPA_E_CAPACITY from hpa_sync --
+ * the number needed.  total / unknown (device uint64[n_stall], may be NULL)
+ * receive the per-stall sum of all counts and of the UNKNOWN ones.
+ * n_ctx / n_stall are filled in by the producing call.                        */
+typedef struct {
+    uint64_t capacity;
+    uint32_t* key_ctx;
+    uint32_t* key_node;
+    uint8_t* key_stall;
+    uint64_t* val;
+    uint64_t* n_keys;
+    uint64_t* total;
+    uint64_t* unknown;
+    uint32_t n_ctx;
+    uint32_t n_stall;
+} hpa_profile;
+
+/* Approximate GPU calling context trees of requested launch contexts
+ * (Section 6.3), dense per context.  DEVICE arrays:
+ *   req_ctx[n_req]                     contexts to reconstruct
+ *   incl[n_req][n_cnodes][n_stall + 1] inclusive cost of each condensed node
+ *                                      (last column: total over stall reasons);
+ *                                      a function inside a non-trivial SCC has
+ *                                      a zero row, its SCC row is n_funcs + k
+ *   a[n_req][n_calls][n_stall + 1]     share of the callee's inclusive cost
+ *                                      apportioned to each call site
+ *   flags[n_req][n_calls]              HPA_EDGE_* bits                         */
+typedef struct {
+    uint32_t n_req;
+    const uint32_t* req_ctx;
+    float* incl;
+    float* a;
+    uint8_t* flags;
+} hpa_gpucct;
+
+/* Host calling context tree: DEVICE parent array (parent[v] < n_nodes or
+ * HPA_NO_PARENT).  Launch context c is CCT node c (n_ctx <= n_nodes).        */
+typedef struct {
+    uint32_t n_nodes;
+    const uint32_t* parent;
+} hpa_cct;
+
+/* Cross-profile derived metrics (Section 4.5) and warp issue rate
+ * (Section 7).  DEVICE arrays.  Per key of the union of the profiles
+ * (ascending (ctx, node, stall), `capacity` entries, count in *n_keys): sum,
+ * min, max (absent = 0) and mean, population std, coefficient of variation.
+ * Per context over the summed profiles: S, S_issued, W = S_issued / S and
+ * frac[ctx][stall] = share of S per stall reason (NaN where S = 0).          */
+typedef struct {
+    uint64_t capacity;
+    uint32_t* key_ctx;
+    uint32_t* key_node;
+    uint8_t* key_stall;
+    uint64_t* sum;
+    uint64_t* min;
+    uint64_t* max;
+    float* mean;
+    float* std;
+    float* cov;
+    uint64_t* n_keys;
+    uint32_t n_ctx;          /* contexts of the per-context arrays below */
+    uint64_t* S;             /* [n_ctx] */
+    uint64_t* S_issued;      /* [n_ctx] */
+    float* W;                /* [n_ctx] */
+    float* frac;             /* [n_ctx][n_stall] */
+} hpa_derived;
+
+/* ---- handle ------------------------------------------------------------- */
+
+/* Create a handle on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  opt may be NULL.      */
+hpa_status hpa_create(hpa_handle** h, int device, void* cuda_stream, const hpa_options* opt);
+/* Free every library-owned device allocation of the handle. */
+hpa_status hpa_destroy(hpa_handle* h);
+/* Message of the last failed call on this handle ("" if none).  The string
+ * stays valid until the next call on the handle.                            */
+const char* hpa_last_error(hpa_handle* h);
+/* Wait for the handle's stream, then return and clear the first status a
+ * kernel recorded.  *bad (may be NULL) receives the number of invalid sample
+ * records when the status is HPA_E_INVALID_SAMPLE.                            */
+hpa_status hpa_sync(hpa_handle* h, uint64_t* bad);
+/* Reserve scratch for calls of up to max_samples records and max_groups
+ * contexts (summed over a batch), so that later calls allocate nothing (as
+ * stream capture requires).  Calls grow the scratch themselves otherwise.     */
+hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t max_groups);
+/* Number of kernels the handle has launched so far. */
+uint64_t hpa_kernel_launches(hpa_handle* h);
+
+/* ---- structure (Section 5, Section 6.3 steps 1 and 3) ------------------- */
+
+/* Validate and load one binary's structure; *binary_id names it afterwards.
+ * Validation: ranges sorted, non-empty, disjoint, span < 2^32; parents
+ * in range and of the same function, FUNC nodes exactly the roots, no cycle;
+ * call sites name existing functions and CALL nodes of the caller.
+ * Failure: HPA_E_INVALID_TABLE with a message.  The call also finds the
+ * call graph's strongly connected components (Tarjan's algorithm) and the
+ * level order of the condensed graph, which every context shares.            */
+hpa_status hpa_load_structure(hpa_handle* h, const hpa_structure* s, uint32_t* binary_id);
+hpa_status hpa_unload_structure(hpa_handle* h, uint32_t binary_id);
+/* Facts of a loaded binary; cnode_of_func (host uint32[n_funcs], may be NULL)
+ * receives each function's condensed node id.                                */
+hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t binary_id, hpa_binary_info* info,
+                               uint32_t* cnode_of_func);
+
+/* ---- the hot path ------------------------------------------------------- */
+
+/* Attribute every sample to the structure node whose range holds its PC
+ * (UNKNOWN if none; Sections 4.2 and 5) and sum the counts per
+ * (ctx, node, stall) into the raw metrics of `out` (Section 4.5).
+ * in: DEVICE arrays; out: DEVICE arrays (see hpa_profile).  An invalid record
+ * makes the whole call fail at hpa_sync with HPA_E_INVALID_SAMPLE and
+ * *n_keys = 0.  Counts are exact (uint64 sums).                             */
+hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
+                                 hpa_profile* out);
+
+/* Same as hpa_attribute_samples with HOST input and output arrays: copies the
+ * samples to the device, runs, copies the keys back and synchronises.
+ * out->n_keys, total and unknown are host pointers here.  Returns the final
+ * status (the hpa_sync status included).                                      */
+hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
+                                      hpa_profile* out);
+
+/* Many sample buffers of uneven sizes, each against its own binary, in one
+ * captured CUDA graph (the analogue of streaming aggregation over profiles,
+ * Section 6.1).  outs[i] receives exactly what hpa_attribute_samples would
+ * give for in[i] alone.  in/outs/binary_ids are HOST arrays of descriptors
+ * whose data pointers are DEVICE arrays.  Status per buffer: hpa_sync reports
+ * the first failure.                                                          */
+hpa_status hpa_attribute_batch(hpa_handle* h, uint32_t n, const uint32_t* binary_ids,
+                               const hpa_samples* in, hpa_profile* outs);
+
+/* Approximate GPU calling context tree per requested context (Section 6.3,
+ * steps 1-4): call-site weights from the samples of call instructions, the
+ * step-2 zero-weight fix-up, SCC collapse, and gprof-style apportioning of
+ * each condensed node's inclusive cost among its call sites.  p: a profile of
+ * this binary produced by hpa_attribute_samples (device keys).  FP32 results
+ * from FP64 accumulation of exact integer counts.                            */
+hpa_status hpa_apportion_callgraph(hpa_handle* h, uint32_t binary_id, const hpa_profile* p,
+                                   hpa_gpucct* out);
+
+/* Inclusive metrics (Section 6.1, statistic generation).
+ *  tree_out (may be NULL): for every key of p, its value is added to its node
+ *    and every structure ancestor up to the function node; output keys
+ *    ascending by (ctx, node, stall) with exact sums, capacity rules of
+ *    hpa_profile (capacity = p's key count * (tree depth + 1) is enough).
+ *  cct, cct_out (may be NULL): cct_out[v][stall] (DEVICE uint64[n_nodes][n_stall])
+ *    = sum of p's values whose context lies in CCT node v's subtree.        */
+hpa_status hpa_propagate_inclusive(hpa_handle* h, uint32_t binary_id, const hpa_profile* p,
+                                   hpa_profile* tree_out, const hpa_cct* cct, uint64_t* cct_out);
+
+/* Derived metrics over n_profiles profiles (Section 4.5) and the warp issue
+ * rate per context (Section 7, W = (S - S_stall) / S with the handle's
+ * issued_mask).  ps: HOST array of profile descriptors with DEVICE data.    */
+hpa_status hpa_derive_metrics(hpa_handle* h, const hpa_profile* const* ps, uint32_t n_profiles,
+                              hpa_derived* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPA_H */

@@ -1,0 +1,661 @@
+// Attribution (Sections 4.2, 5) and raw-metric aggregation (Section 4.5) of
+// GPU PC samples on sm_103a.
+//
+// Pipeline over one or many sample buffers (a "group" is one launch context
+// of one buffer; records of a group are aggregated together):
+//   k_grp_hist       records per group (reads ctx only)
+//   scan             group offsets
+//   k_item_flags,    groups are packed into items of <= cap records (runs of
+//   k_items, ...     small groups, or one group); a group with more than cap
+//                    records becomes a "big" item split into 2^h sub-bins
+//   k_attr_scatter   reads every sample once, attributes its PC to a
+//                    structure node, packs (node, stall) into a subkey and
+//                    scatters (subkey, count) into its group's segment
+//   k_big_partition  splits big groups by the subkey's top h bits
+//   k_leaf           per leaf: shared-memory radix sort + run reduction (or a
+//                    dense shared-memory window for oversized sub-bins)
+//   scan + k_emit    leaves are in key order; their run counts give every
+//                    key's output position
+//   k_finalize       per-buffer key counts and status
+// Counts are summed exactly in 64-bit integers; keys come out ascending by
+// (ctx, node, stall).
+
+#include <algorithm>
+
+#include "hpa_internal.h"
+
+namespace hpa {
+
+// ------------------------------------------------------------------ scans
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* in, uint64_t n, uint32_t* part) {
+    __shared__ uint32_t sw[33];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_EPT;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_EPT; ++i)
+        if (base + i < n) s += in[base + i];
+    s = warp_sum(s);
+    if (lane_id() == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < SCAN_THREADS / 32 ? sw[threadIdx.x] : 0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* part, uint32_t nb) {
+    __shared__ uint32_t sw[33];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? part[i] : 0;
+        uint32_t tot;
+        const uint32_t e = block_exclusive_scan<uint32_t, 1024>(v, sw, &tot);
+        if (i < nb) part[i] = carry + e;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) part[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, uint32_t* out, uint64_t n,
+                                                            const uint32_t* part, uint32_t nb) {
+    __shared__ uint32_t sw[33];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_EPT;
+    uint32_t v[SCAN_EPT];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_EPT; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        s += v[i];
+    }
+    uint32_t tot;
+    uint32_t pre = block_exclusive_scan<uint32_t, SCAN_THREADS>(s, sw, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_EPT; ++i) {
+        if (base + i < n) out[base + i] = pre;
+        pre += v[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = part[nb];
+}
+
+size_t scan_tmp_words(uint64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 2; }
+
+void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cudaStream_t s, uint64_t* launches) {
+    const uint32_t nb = (uint32_t)std::max<uint64_t>(1, (n + SCAN_TILE - 1) / SCAN_TILE);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, tmp);
+    k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb);
+    k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, tmp, nb);
+    *launches += 3;
+}
+
+// ------------------------------------------------------------------ helpers
+// largest b with pre[b] <= x (pre is non-decreasing, pre[0] = 0)
+template <typename T>
+__device__ __forceinline__ uint32_t upper_index(const T* pre, uint32_t n, T x) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (pre[m] <= x) lo = m; else hi = m;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t big_bits(uint32_t n, uint32_t cap, uint32_t sbits) {
+    // 2^h sub-bins of about cap / 2 records each
+    const uint32_t want = (uint32_t)((2ull * n + cap - 1) / cap);
+    uint32_t h = ceil_log2_u64(want);
+    h = max(h, 1u);
+    h = min(h, min(12u, sbits));
+    return h;
+}
+
+// ------------------------------------------------------------------ K1: records per group
+__global__ void __launch_bounds__(256) k_grp_hist(AggWork w) {
+    __shared__ uint32_t sh[2048];
+    for (uint64_t t = blockIdx.x; t < w.n_tiles; t += gridDim.x) {
+        const uint32_t b = upper_index<uint64_t>(w.buf_tile, w.n_buf, t);
+        const BufDev B = w.bufs[b];
+        const uint64_t i0 = (t - B.tile_base) * TILE;
+        const uint64_t i1 = min(i0 + TILE, B.n);
+        const bool priv = B.n_ctx <= 2048;
+        if (priv) {
+            for (uint32_t c = threadIdx.x; c < B.n_ctx; c += blockDim.x) sh[c] = 0;
+            __syncthreads();
+        }
+        uint32_t bad = 0;
+        for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const uint32_t c = __ldg(&B.ctx[i]);
+            if (c >= B.n_ctx) { ++bad; continue; }
+            if (priv) atomicAdd(&sh[c], 1u);
+            else atomicAdd(&w.grp_hist[B.grp_base + c], 1u);
+        }
+        if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
+        if (priv) {
+            __syncthreads();
+            for (uint32_t c = threadIdx.x; c < B.n_ctx; c += blockDim.x)
+                if (sh[c]) atomicAdd(&w.grp_hist[B.grp_base + c], sh[c]);
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K3..K8: items and leaves
+__global__ void k_item_flags(AggWork w) {
+    const uint32_t* seg = w.grp_hist;
+    const uint32_t span_mask = (w.span_log >= 32) ? 0xFFFFFFFFu : ((1u << w.span_log) - 1);
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < w.G; g += gridDim.x * blockDim.x) {
+        const uint32_t s0 = seg[g];
+        uint32_t f = 0;
+        if (g == 0) {
+            f = 1;
+        } else {
+            const uint32_t sp = seg[g - 1];
+            const uint32_t ng = seg[g + 1] - s0, np = s0 - sp;
+            if (ng > w.q || np > w.q) f = 1;
+            if (s0 / w.q != sp / w.q) f = 1;
+            if ((g & span_mask) == 0) f = 1;
+            if (w.n_buf > 1) {
+                const uint32_t b = upper_index<uint32_t>(w.buf_grp, w.n_buf, g);
+                if (w.buf_grp[b] == g) f = 1;
+            }
+        }
+        w.item_id[g] = f;
+        w.grp_cursor[g] = s0;
+    }
+}
+
+__global__ void k_items(AggWork w) {
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < w.G; g += gridDim.x * blockDim.x)
+        if (w.item_id[g + 1] != w.item_id[g]) w.item_grp0[w.item_id[g]] = g;
+}
+
+__global__ void k_items_size(AggWork w) {
+    const uint32_t n_items = w.item_id[w.G];
+    const uint32_t* seg = w.grp_hist;
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < w.G; it += gridDim.x * blockDim.x) {
+        uint32_t nl = 0;
+        if (it < n_items) {
+            const uint32_t g0 = w.item_grp0[it];
+            const uint32_t g1 = (it + 1 < n_items) ? w.item_grp0[it + 1] : w.G;
+            const uint32_t n = seg[g1] - seg[g0];
+            nl = (n > w.cap) ? (1u << big_bits(n, w.cap, w.sbits)) : 1u;
+        }
+        w.item_nleaf[it] = nl;
+    }
+}
+
+__global__ void k_leaves(AggWork w) {
+    const uint32_t n_items = w.item_id[w.G];
+    const uint32_t* seg = w.grp_hist;
+    const uint32_t* leaf_base = w.item_nleaf;
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < n_items; it += gridDim.x * blockDim.x) {
+        const uint32_t g0 = w.item_grp0[it];
+        const uint32_t g1 = (it + 1 < n_items) ? w.item_grp0[it + 1] : w.G;
+        const uint32_t n = seg[g1] - seg[g0];
+        const uint32_t l = leaf_base[it];
+        const uint32_t b = upper_index<uint32_t>(w.buf_grp, w.n_buf, g0);
+        if (w.buf_grp[b] == g0) w.buf_first_leaf[b] = l;
+        if (n <= w.cap) {
+            w.leaf_start[l] = seg[g0];
+            w.leaf_end[l] = seg[g1];
+            w.leaf_grp0[l] = g0;
+            w.leaf_info[l] = b << 8;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.buf_first_leaf[w.n_buf] = leaf_base[w.G];
+}
+
+// ------------------------------------------------------------------ K9: attribute + scatter
+template <bool HAS_CNT, int U>
+__global__ void __launch_bounds__(256) k_attr_scatter(AggWork w) {
+    extern __shared__ unsigned long long acc[];          // [n_stall_max][256] per-thread totals
+    __shared__ unsigned long long unk[HPA_MAX_STALL_DEV];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;       // stall slots per thread
+    for (uint32_t r = 0; r < nsm; ++r) acc[r * 256 + tid] = 0;
+    if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
+    __syncthreads();
+    uint32_t cur_b = 0xFFFFFFFFu;
+
+    auto flush = [&](uint32_t b) {
+        __syncthreads();
+        if (b != 0xFFFFFFFFu) {
+            const BufDev& B = w.bufs[b];
+            for (uint32_t r = tid >> 5; r < nsm; r += 8) {
+                unsigned long long v = 0;
+                for (uint32_t t = lane_id(); t < 256; t += 32) v += acc[r * 256 + t];
+                v = warp_sum(v);
+                if (lane_id() == 0 && v && B.total) atomicAdd((unsigned long long*)&B.total[r], v);
+                if (lane_id() == 0 && unk[r] && B.unknown) atomicAdd((unsigned long long*)&B.unknown[r], unk[r]);
+            }
+        }
+        __syncthreads();
+        for (uint32_t r = 0; r < nsm; ++r) acc[r * 256 + tid] = 0;
+        if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
+        __syncthreads();
+    };
+
+    for (uint64_t t = blockIdx.x; t < w.n_tiles; t += gridDim.x) {
+        const uint32_t b = upper_index<uint64_t>(w.buf_tile, w.n_buf, t);
+        if (b != cur_b) { flush(cur_b); cur_b = b; }
+        const BufDev B = w.bufs[b];
+        const DevBinary bin = w.bins[B.bin];
+        const uint64_t i0 = (t - B.tile_base) * TILE;
+        const uint64_t i1 = min(i0 + TILE, B.n);
+        const uint32_t M = bin.n_nodes;
+        uint32_t bad = 0;
+        for (uint64_t base = i0 + tid; base < i1; base += 256 * U) {
+            uint64_t pc[U];
+            uint32_t c[U], st[U], cnt[U], off[U], lo[U], hi[U], nd[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint64_t i = base + (uint64_t)u * 256;
+                ok[u] = i < i1;
+                if (ok[u]) {
+                    c[u] = __ldg(&B.ctx[i]);
+                    st[u] = __ldg(&B.stall[i]);
+                    pc[u] = __ldg((const unsigned long long*)&B.pc[i]);
+                    cnt[u] = (HAS_CNT && B.count) ? __ldg(&B.count[i]) : 1u;
+                    ok[u] = c[u] < B.n_ctx;
+                }
+            }
+            // attribution, all U lookups in lockstep (Section 4.2: PC -> structure node)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                nd[u] = M;
+                lo[u] = hi[u] = 0;
+                if (ok[u]) {
+                    const uint64_t o = pc[u] - bin.pc_base;
+                    if (o < bin.span) {
+                        off[u] = (uint32_t)o;
+                        const uint32_t bk = off[u] >> bin.dshift;
+                        lo[u] = __ldg(&bin.dir[bk]);
+                        hi[u] = __ldg(&bin.dir[bk + 1]);
+                        nd[u] = 0xFFFFFFFEu;    // search pending
+                    }
+                }
+            }
+            for (int it = 0; it < 40; ++it) {
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (nd[u] == 0xFFFFFFFEu && lo[u] < hi[u]) {
+                        const uint32_t m = (lo[u] + hi[u]) >> 1;
+                        if (__ldg(&bin.rng[m].y) > off[u]) hi[u] = m; else lo[u] = m + 1;
+                        any = true;
+                    }
+                }
+                if (!any) break;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (nd[u] == 0xFFFFFFFEu) {
+                    nd[u] = M;
+                    if (lo[u] < bin.n_ranges) {
+                        const uint4 r = __ldg(&bin.rng[lo[u]]);
+                        if (r.x <= off[u]) nd[u] = r.z;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!ok[u]) continue;
+                const bool bad_stall = st[u] >= B.n_stall;
+                const uint32_t slot = atomicAdd(&w.grp_cursor[B.grp_base + c[u]], 1u);
+                w.rec_sub[slot] = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
+                if (HAS_CNT) w.rec_cnt[slot] = bad_stall ? 0u : cnt[u];
+                if (bad_stall) {
+                    ++bad;
+                } else {
+                    acc[st[u] * 256 + tid] += cnt[u];
+                    if (nd[u] == M) atomicAdd(&unk[st[u]], (unsigned long long)cnt[u]);
+                }
+            }
+        }
+        if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
+    }
+    flush(cur_b);
+}
+
+// ------------------------------------------------------------------ K10: split big groups
+__global__ void __launch_bounds__(256) k_big_partition(AggWork w) {
+    __shared__ uint32_t hist[4096 + 1];
+    __shared__ uint32_t sw[33];
+    const uint32_t n_items = w.item_id[w.G];
+    const uint32_t* seg = w.grp_hist;
+    const uint32_t* leaf_base = w.item_nleaf;
+    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const uint32_t g0 = w.item_grp0[it];
+        const uint32_t g1 = (it + 1 < n_items) ? w.item_grp0[it + 1] : w.G;
+        const uint32_t s0 = seg[g0], s1 = seg[g1];
+        const uint32_t n = s1 - s0;
+        if (n <= w.cap) continue;                 // uniform across the block
+        const uint32_t h = big_bits(n, w.cap, w.sbits);
+        const uint32_t nb = 1u << h;
+        const uint32_t shift = w.sbits - h;
+        for (uint32_t j = threadIdx.x; j <= nb; j += blockDim.x) hist[j] = 0;
+        __syncthreads();
+        for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x)
+            atomicAdd(&hist[w.rec_sub[i] >> shift], 1u);
+        __syncthreads();
+        block_scan_array<uint32_t, 256, 17>(hist, nb + 1, sw);
+        const uint32_t l0 = leaf_base[it];
+        const uint32_t b = upper_index<uint32_t>(w.buf_grp, w.n_buf, g0);
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+            w.leaf_start[l0 + j] = s0 + hist[j];
+            w.leaf_end[l0 + j] = s0 + (j + 1 < nb ? hist[j + 1] : n);
+            w.leaf_grp0[l0 + j] = g0;
+            w.leaf_info[l0 + j] = (b << 8) | 1u;
+        }
+        __syncthreads();
+        for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+            const uint32_t sub = w.rec_sub[i];
+            const uint32_t p = s0 + atomicAdd(&hist[sub >> shift], 1u);
+            w.rec2_sub[p] = sub;
+            if (w.has_cnt) w.rec2_cnt[p] = w.rec_cnt[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ K11: leaves
+template <int THREADS, int CAP, bool HAS_CNT>
+struct LeafCfg {
+    using Sort = BlockRadix<THREADS, CAP, 8, uint32_t, HAS_CNT>;
+    static constexpr int EPT = (CAP + THREADS - 1) / THREADS;
+    static constexpr size_t SORT_BYTES = sizeof(typename Sort::Smem);
+    static constexpr int WD = 8192;                              // dense window (uint64 counters)
+    static constexpr size_t DENSE_BYTES = (size_t)WD * 8;
+    static constexpr size_t SMEM = SORT_BYTES > DENSE_BYTES ? SORT_BYTES : DENSE_BYTES;
+};
+
+struct SegPair { uint32_t f; unsigned long long s; };
+
+__device__ __forceinline__ SegPair seg_combine(SegPair a, SegPair b) {
+    return SegPair{a.f | b.f, b.f ? b.s : a.s + b.s};
+}
+
+// exclusive segmented scan across the block (one pair per thread)
+template <int THREADS>
+__device__ __forceinline__ unsigned long long block_seg_carry(SegPair x, SegPair* sw) {
+    constexpr int W = THREADS / 32;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    SegPair inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        SegPair y;
+        y.f = __shfl_up_sync(0xffffffffu, inc.f, o);
+        y.s = __shfl_up_sync(0xffffffffu, inc.s, o);
+        if (lane >= o) inc = seg_combine(y, inc);
+    }
+    SegPair exc;
+    exc.f = __shfl_up_sync(0xffffffffu, inc.f, 1);
+    exc.s = __shfl_up_sync(0xffffffffu, inc.s, 1);
+    if (lane == 0) exc = SegPair{0, 0};
+    if (lane == 31) sw[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SegPair run{0, 0};
+        for (int i = 0; i < W; ++i) {
+            SegPair t = sw[i];
+            sw[i] = run;
+            run = seg_combine(run, t);
+        }
+    }
+    __syncthreads();
+    const SegPair pre = seg_combine(sw[warp], exc);
+    __syncthreads();
+    return pre.s;
+}
+
+template <int THREADS, int CAP, bool HAS_CNT>
+__global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
+    using Cfg = LeafCfg<THREADS, CAP, HAS_CNT>;
+    using Sort = typename Cfg::Sort;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename Sort::Smem& S = *reinterpret_cast<typename Sort::Smem*>(smem_raw);
+    __shared__ uint32_t sw[33];
+    __shared__ SegPair sws[32];
+    __shared__ uint32_t gb[1025];
+    __shared__ unsigned long long red[2];
+    const uint32_t n_leaves = w.item_nleaf[w.G];
+    const uint32_t* seg = w.grp_hist;
+
+    for (uint32_t l = blockIdx.x; l < n_leaves; l += gridDim.x) {
+        const uint32_t start = w.leaf_start[l], end = w.leaf_end[l];
+        const uint32_t info = w.leaf_info[l];
+        const uint32_t n = end - start;
+        const uint32_t* src_sub = (info & 1u) ? w.rec2_sub : w.rec_sub;
+        const uint32_t* src_cnt = (info & 1u) ? w.rec2_cnt : w.rec_cnt;
+        if (n == 0) {
+            if (threadIdx.x == 0) w.leaf_d[l] = 0;
+            continue;
+        }
+        if (n <= (uint32_t)CAP) {
+            // groups of this leaf: a sub-bin holds one group; an item holds the
+            // groups whose records lie in [start, end)
+            const uint32_t g0 = w.leaf_grp0[l];
+            uint32_t ng = 1;
+            if (!(info & 1u)) {
+                // count groups: last group g with seg[g] < end
+                uint32_t lo = g0, hi = min(w.G, g0 + 1024u);
+                while (hi - lo > 1) {
+                    const uint32_t m = (lo + hi) >> 1;
+                    if (seg[m] < end) lo = m; else hi = m;
+                }
+                ng = lo - g0 + 1;
+            }
+            const uint32_t gbits = ng > 1 ? ceil_log2_u64(ng) : 0;
+            if (ng > 1) {
+                for (uint32_t j = threadIdx.x; j <= ng; j += THREADS) gb[j] = seg[g0 + j] - start;
+                __syncthreads();
+            }
+            for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
+                S.key[0][i] = src_sub[start + i];
+                if constexpr (HAS_CNT) S.val[0][i] = src_cnt[start + i];
+            }
+            __syncthreads();
+            if (ng > 1) {
+                // tag each record with its group inside the leaf
+                for (uint32_t j = threadIdx.x; j < ng; j += THREADS) {
+                    const uint32_t a = gb[j], e = min(gb[j + 1], n);
+                    for (uint32_t i = a; i < e; ++i) S.key[0][i] |= j << w.sbits;
+                }
+                __syncthreads();
+            }
+            const int cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
+            // runs of equal keys: heads, then a segmented carry across threads
+            const int c0 = threadIdx.x * Cfg::EPT;
+            const int c1 = min((int)n, c0 + Cfg::EPT);
+            uint32_t heads = 0;
+            SegPair mine{0, 0};
+            for (int i = c0; i < c1; ++i) {
+                const uint32_t k = S.key[cur][i];
+                const bool h = (i == 0) || (k != S.key[cur][i - 1]);
+                unsigned long long v = 1;
+                if constexpr (HAS_CNT) v = S.val[cur][i];
+                if (h) { ++heads; mine.f = 1; mine.s = 0; }
+                mine.s += v;
+            }
+            uint32_t n_runs;
+            const uint32_t rid0 = block_exclusive_scan<uint32_t, THREADS>(heads, sw, &n_runs);
+            const unsigned long long carry = block_seg_carry<THREADS>(mine, sws);
+            int run = (int)rid0 - 1;
+            unsigned long long a = carry;
+            for (int i = c0; i < c1; ++i) {
+                const uint32_t k = S.key[cur][i];
+                if (i == 0 || k != S.key[cur][i - 1]) { ++run; a = 0; }
+                unsigned long long v = 1;
+                if constexpr (HAS_CNT) v = S.val[cur][i];
+                a += v;
+                if (i == (int)n - 1 || S.key[cur][i + 1] != k) {
+                    w.tmp_key[start + run] = k;
+                    w.tmp_val[start + run] = a;
+                }
+            }
+            if (threadIdx.x == 0) w.leaf_d[l] = n_runs;
+            __syncthreads();
+        } else {
+            // oversized sub-bin (one group): dense shared-memory windows over
+            // the subkey range, each compacted in key order
+            unsigned long long* dense = reinterpret_cast<unsigned long long*>(smem_raw);
+            uint32_t mn = 0xFFFFFFFFu, mx = 0;
+            for (uint32_t i = start + threadIdx.x; i < end; i += THREADS) {
+                const uint32_t k = src_sub[i];
+                mn = min(mn, k); mx = max(mx, k);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if (threadIdx.x == 0) { red[0] = 0xFFFFFFFFull; red[1] = 0; }
+            __syncthreads();
+            if (lane_id() == 0) {
+                atomicMin(&red[0], (unsigned long long)mn);
+                atomicMax(&red[1], (unsigned long long)mx);
+            }
+            __syncthreads();
+            const uint32_t kmin = (uint32_t)red[0], kmax = (uint32_t)red[1];
+            __syncthreads();
+            uint32_t out = 0;
+            constexpr int WD = Cfg::WD;
+            constexpr int DEPT = WD / THREADS;
+            for (uint64_t wlo = kmin; wlo <= kmax; wlo += WD) {
+                for (int j = threadIdx.x; j < WD; j += THREADS) dense[j] = 0;
+                __syncthreads();
+                for (uint32_t i = start + threadIdx.x; i < end; i += THREADS) {
+                    const uint32_t k = src_sub[i];
+                    if (k >= wlo && (uint64_t)k < wlo + WD) {
+                        unsigned long long v = 1;
+                        if constexpr (HAS_CNT) v = src_cnt[i];
+                        atomicAdd(&dense[k - wlo], v);
+                    }
+                }
+                __syncthreads();
+                const int b0 = threadIdx.x * DEPT;
+                uint32_t nz = 0;
+                for (int j = 0; j < DEPT; ++j) nz += dense[b0 + j] != 0;
+                uint32_t tot;
+                uint32_t pos = block_exclusive_scan<uint32_t, THREADS>(nz, sw, &tot);
+                for (int j = 0; j < DEPT; ++j) {
+                    const unsigned long long v = dense[b0 + j];
+                    if (v) {
+                        w.tmp_key[start + out + pos] = (uint32_t)(wlo + b0 + j);
+                        w.tmp_val[start + out + pos] = v;
+                        ++pos;
+                    }
+                }
+                out += tot;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) w.leaf_d[l] = out;
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K13: emit
+__global__ void __launch_bounds__(256) k_emit(AggWork w) {
+    const uint32_t n_leaves = w.item_nleaf[w.G];
+    const uint32_t* leaf_out = w.leaf_d;
+    const uint32_t smask = (w.sbits >= 32) ? 0xFFFFFFFFu : ((1u << w.sbits) - 1);
+    const uint32_t stmask = (1u << w.sb) - 1;
+    for (uint32_t l = blockIdx.x; l < n_leaves; l += gridDim.x) {
+        const uint32_t d = leaf_out[l + 1] - leaf_out[l];
+        if (d == 0) continue;
+        const uint32_t info = w.leaf_info[l];
+        const uint32_t b = info >> 8;
+        const BufDev& B = w.bufs[b];
+        if (w.buf_bad[b]) continue;
+        const uint32_t M = w.bins[B.bin].n_nodes;
+        const uint32_t start = w.leaf_start[l];
+        const uint32_t g0 = w.leaf_grp0[l];
+        const uint64_t o0 = (uint64_t)leaf_out[l] - leaf_out[w.buf_first_leaf[b]];
+        const uint32_t gctx0 = g0 - B.grp_base;
+        for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+            const uint64_t pos = o0 + i;
+            if (pos >= B.capacity) break;
+            const uint32_t k = w.tmp_key[start + i];
+            const uint32_t sub = k & smask;
+            const uint32_t gl = (w.sbits >= 32) ? 0u : (k >> w.sbits);
+            const uint32_t node = sub >> w.sb;
+            B.key_ctx[pos] = gctx0 + gl;
+            B.key_node[pos] = (node == M) ? UNKNOWN : node;
+            B.key_stall[pos] = (uint8_t)(sub & stmask);
+            B.val[pos] = w.tmp_val[start + i];
+        }
+    }
+}
+
+__global__ void k_finalize(AggWork w) {
+    const uint32_t* leaf_out = w.leaf_d;
+    for (uint32_t b = threadIdx.x; b < w.n_buf; b += blockDim.x) {
+        const BufDev& B = w.bufs[b];
+        const uint64_t K = (uint64_t)leaf_out[w.buf_first_leaf[b + 1]] - leaf_out[w.buf_first_leaf[b]];
+        const unsigned long long bad = w.buf_bad[b];
+        if (bad) {
+            *B.n_keys = 0;
+            atomicAdd(&w.status->bad, bad);
+            raise_status(w.status, 3 /* HPA_E_INVALID_SAMPLE */, (int32_t)b);
+        } else {
+            *B.n_keys = K;
+            if (K > B.capacity) raise_status(w.status, 4 /* HPA_E_CAPACITY */, (int32_t)b);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ driver
+template <int THREADS, int CAP, bool HAS_CNT>
+static void launch_leaf(const AggWork& w, cudaStream_t s, int sms, int per_sm) {
+    using Cfg = LeafCfg<THREADS, CAP, HAS_CNT>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_leaf<THREADS, CAP, HAS_CNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg::SMEM);
+        attr_set = true;
+    }
+    k_leaf<THREADS, CAP, HAS_CNT><<<sms * per_sm, THREADS, Cfg::SMEM, s>>>(w);
+}
+
+void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
+    cudaMemsetAsync(w.grp_hist, 0, sizeof(uint32_t) * ((size_t)w.G + 1), s);
+    cudaMemsetAsync(w.leaf_d, 0, sizeof(uint32_t) * ((size_t)w.L_max + 1), s);
+    cudaMemsetAsync(w.buf_bad, 0, sizeof(unsigned long long) * w.n_buf, s);
+    const int gblocks = (int)std::min<uint64_t>((w.G + 255) / 256, (uint64_t)sms * 16);
+    const int hist_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 8));
+    k_grp_hist<<<hist_blocks, 256, 0, s>>>(w);
+    scan_u32(w.grp_hist, w.grp_hist, w.G, w.scan_tmp, s, launches);
+    k_item_flags<<<std::max(gblocks, 1), 256, 0, s>>>(w);
+    scan_u32(w.item_id, w.item_id, w.G, w.scan_tmp, s, launches);
+    k_items<<<std::max(gblocks, 1), 256, 0, s>>>(w);
+    k_items_size<<<std::max(gblocks, 1), 256, 0, s>>>(w);
+    scan_u32(w.item_nleaf, w.item_nleaf, w.G, w.scan_tmp, s, launches);
+    k_leaves<<<std::max(gblocks, 1), 256, 0, s>>>(w);
+    *launches += 5;
+    const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;
+    const size_t acc_bytes = (size_t)nsm * 256 * 8;
+    const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
+    if (w.has_cnt) {
+        cudaFuncSetAttribute(k_attr_scatter<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
+        k_attr_scatter<true, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
+    } else {
+        cudaFuncSetAttribute(k_attr_scatter<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
+        k_attr_scatter<false, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
+    }
+    k_big_partition<<<sms * 4, 256, 0, s>>>(w);
+    if (w.cap == LEAF_CAP_LARGE) {
+        if (w.has_cnt) launch_leaf<512, LEAF_CAP_LARGE, true>(w, s, sms, 1);
+        else launch_leaf<512, LEAF_CAP_LARGE, false>(w, s, sms, 1);
+    } else {
+        if (w.has_cnt) launch_leaf<256, LEAF_CAP_SMALL, true>(w, s, sms, 2);
+        else launch_leaf<256, LEAF_CAP_SMALL, false>(w, s, sms, 2);
+    }
+    scan_u32(w.leaf_d, w.leaf_d, w.L_max, w.scan_tmp, s, launches);
+    k_emit<<<sms * 8, 256, 0, s>>>(w);
+    k_finalize<<<1, 256, 0, s>>>(w);
+    *launches += 5;
+}
+
+}  // namespace hpa

@@ -1,0 +1,205 @@
+// Device-side helpers shared by the hpa kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hpa {
+
+constexpr uint32_t UNKNOWN = 0xFFFFFFFFu;
+constexpr uint32_t NO_PARENT = 0xFFFFFFFFu;
+constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
+
+// Device status word of a handle.  Kernels only ever raise it (atomicCAS from
+// 0), the host reads and clears it in hpa_sync.
+struct DevStatus {
+    int32_t code;           // first hpa_status raised by a kernel
+    int32_t where;          // kernel-specific detail (which wait gave up, ...)
+    unsigned long long bad; // invalid sample records
+};
+
+__device__ __forceinline__ void raise_status(DevStatus* st, int32_t code, int32_t where = 0) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+}
+
+// Program structure of one binary as the attribution kernels read it.
+//   rng[i] = {lo - pc_base, hi - pc_base, node, 0}, sorted, disjoint.
+//   dir[b] = first range whose hi - pc_base > b << dshift  (b in [0, n_dir]).
+// A PC p belongs to range i iff lo_i <= p < hi_i (half-open); ranges are
+// disjoint, so the only candidate is the first range with hi > p, which lies
+// between dir[b] and dir[b + 1] for p's bucket b.
+struct DevBinary {
+    uint64_t pc_base;
+    uint64_t span;          // range_hi[R-1] - pc_base (< 2^32)
+    uint32_t dshift;
+    uint32_t n_dir;
+    uint32_t n_ranges;
+    uint32_t n_nodes;       // M: UNKNOWN is coded as node M inside subkeys
+    const uint32_t* dir;
+    const uint4* rng;
+};
+
+// Section 4.2 / Section 5: the structure node of one PC (M if none).
+__device__ __forceinline__ uint32_t attribute_pc(const DevBinary& b, uint64_t pc) {
+    const uint64_t off64 = pc - b.pc_base;    // wraps to a huge value below the segment
+    if (off64 >= b.span) return b.n_nodes;
+    const uint32_t off = (uint32_t)off64;
+    const uint32_t bk = off >> b.dshift;
+    uint32_t i = __ldg(&b.dir[bk]);
+    uint32_t j = __ldg(&b.dir[bk + 1]);
+    // first range in [i, j] with hi > off; j itself qualifies (or is R)
+    while (i < j) {
+        const uint32_t m = (i + j) >> 1;
+        if (__ldg(&b.rng[m].y) > off) j = m; else i = m + 1;
+    }
+    if (i < b.n_ranges) {
+        const uint4 r = __ldg(&b.rng[i]);
+        if (r.x <= off) return r.z;
+    }
+    return b.n_nodes;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T x) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane_id() >= o) x += y;
+    }
+    return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Block-wide exclusive scan of one value per thread.  `sw` holds >= 33
+// entries of shared scratch.  Returns the exclusive prefix; *total gets the sum.
+template <typename T, int THREADS>
+__device__ __forceinline__ T block_exclusive_scan(T x, T* sw, T* total) {
+    constexpr int W = THREADS / 32;
+    const int warp = threadIdx.x >> 5;
+    T inc = warp_inclusive_scan(x);
+    if (lane_id() == 31) sw[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T v = (int)lane_id() < W ? sw[lane_id()] : T(0);
+        T vi = warp_inclusive_scan(v);
+        if ((int)lane_id() < W) sw[lane_id()] = vi - v;
+        if (lane_id() == W - 1) sw[32] = vi;
+    }
+    __syncthreads();
+    T r = sw[warp] + inc - x;
+    *total = sw[32];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive scan, in place, of n <= THREADS * EPT values held in shared
+// memory; each thread owns EPT consecutive entries.  Returns the total.
+template <typename T, int THREADS, int EPT>
+__device__ __forceinline__ T block_scan_array(T* a, int n, T* sw) {
+    const int base = threadIdx.x * EPT;
+    T loc[EPT];
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+        loc[i] = (base + i < n) ? a[base + i] : T(0);
+        s += loc[i];
+    }
+    T tot;
+    T pre = block_exclusive_scan<T, THREADS>(s, sw, &tot);
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+        if (base + i < n) a[base + i] = pre;
+        pre += loc[i];
+    }
+    __syncthreads();
+    return tot;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide stable LSD radix sort of n <= CAP (key, value) pairs held in
+// shared memory.  Each warp owns a contiguous chunk and walks it 32 elements
+// at a time in order, so equal digits keep their order (stability):
+//   pass A: warp-private digit counts and each element's rank among the
+//           equal digits before it in its warp's chunk (__match_any_sync);
+//   scan  : digit-major, warp-minor exclusive scan of the counts;
+//   pass B: scatter to scan offset + rank.
+// Digits are RB bits wide; `bits` is the key width to sort.
+template <int THREADS, int CAP, int RB, typename V, bool HAS_V>
+struct BlockRadix {
+    static constexpr int W = THREADS / 32;
+    static constexpr int BINS = 1 << RB;
+    static constexpr int SCAN_EPT = BINS * W / THREADS;   // entries per thread in the count scan
+    static_assert(SCAN_EPT * THREADS == BINS * W, "bins x warps must tile the block");
+
+    struct Smem {
+        uint32_t key[2][CAP];
+        V val[HAS_V ? 2 : 1][HAS_V ? CAP : 1];
+        uint16_t rank[CAP];
+        uint32_t cnt[W * BINS];       // digit-major: cnt[d * W + w]
+        uint32_t sw[33];
+    };
+
+    // Sorts s.key[0][0..n) (and s.val[0]) by their low `bits` bits.
+    // Returns the buffer index (0 or 1) that holds the result.
+    __device__ static int sort(Smem& s, int n, int bits) {
+        const int warp = threadIdx.x >> 5;
+        const int lane = lane_id();
+        const int chunk = ((n + W - 1) / W + 31) & ~31;
+        const int lo = warp * chunk;
+        const int hi = min(n, lo + chunk);
+        int cur = 0;
+        for (int shift = 0; shift < bits; shift += RB) {
+            const uint32_t dmask = (bits - shift >= RB) ? (BINS - 1) : ((1u << (bits - shift)) - 1);
+            for (int i = threadIdx.x; i < W * BINS; i += THREADS) s.cnt[i] = 0;
+            __syncthreads();
+            // pass A
+            for (int base = lo; base < lo + chunk; base += 32) {
+                const int i = base + lane;
+                const bool ok = i < hi;
+                const uint32_t d = ok ? ((s.key[cur][i] >> shift) & dmask) : 0xFFFFFFFFu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                if (ok) {
+                    const uint32_t before = s.cnt[d * W + warp];
+                    s.rank[i] = (uint16_t)(before + __popc(peers & lanemask_lt()));
+                }
+                __syncwarp();
+                if (ok && (peers & lanemask_lt()) == 0) s.cnt[d * W + warp] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            block_scan_array<uint32_t, THREADS, SCAN_EPT>(s.cnt, W * BINS, s.sw);
+            // pass B
+            for (int i = lo + lane; i < hi; i += 32) {
+                const uint32_t k = s.key[cur][i];
+                const uint32_t d = (k >> shift) & dmask;
+                const uint32_t pos = s.cnt[d * W + warp] + s.rank[i];
+                s.key[cur ^ 1][pos] = k;
+                if constexpr (HAS_V) s.val[cur ^ 1][pos] = s.val[cur][i];
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        return cur;
+    }
+};
+
+__host__ __device__ inline uint32_t ceil_log2_u64(uint64_t x) {
+    uint32_t b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+}  // namespace hpa

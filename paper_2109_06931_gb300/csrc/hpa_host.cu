@@ -1,0 +1,562 @@
+// C ABI of libhpa.so: handles, structure loading and validation, scratch
+// management and the launch sequences of every entry point declared in
+// include/hpa.h.
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hpa.h"
+#include "hpa_internal.h"
+#include "hpa_host.h"
+
+using namespace hpa;
+
+// ------------------------------------------------------------------ handle helpers
+hpa_status hpa_handle::fail(hpa_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return st;
+}
+
+hpa_status hpa_handle::cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return HPA_OK;
+    cudaGetLastError();
+    return fail(HPA_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool hpa_handle::capturing() const {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+hpa_status hpa_handle::ensure_scratch(size_t bytes) {
+    if (bytes <= scratch_cap) return HPA_OK;
+    if (capturing())
+        return fail(HPA_E_OOM, "scratch of %zu bytes needed during stream capture; call hpa_reserve first", bytes);
+    hpa_status st = cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    if (st) return st;
+    if (scratch) cudaFree(scratch);
+    scratch = nullptr;
+    scratch_cap = 0;
+    size_t want = bytes + bytes / 8 + (1 << 20);
+    if (cudaMalloc(&scratch, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HPA_E_OOM, "cannot allocate %zu bytes of device scratch", want);
+    }
+    scratch_cap = want;
+    ++scratch_epoch;
+    return HPA_OK;
+}
+
+hpa_status hpa_handle::ensure_staging(size_t bytes) {
+    if (bytes <= staging_cap) {
+        if (staging_event_live) {
+            hpa_status st = cuda(cudaEventSynchronize(staging_event), "cudaEventSynchronize");
+            if (st) return st;
+        }
+        return HPA_OK;
+    }
+    if (capturing()) return fail(HPA_E_OOM, "descriptor staging must grow during stream capture");
+    if (staging_event_live) cudaEventSynchronize(staging_event);
+    if (staging) cudaFreeHost(staging);
+    if (d_staging) cudaFree(d_staging);
+    staging = nullptr; d_staging = nullptr; staging_cap = 0;
+    size_t want = std::max<size_t>(bytes, 64 << 10);
+    if (cudaMallocHost(&staging, want) != cudaSuccess || cudaMalloc(&d_staging, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HPA_E_OOM, "cannot allocate %zu bytes of descriptor staging", want);
+    }
+    staging_cap = want;
+    ++scratch_epoch;
+    return HPA_OK;
+}
+
+// upload the staged descriptors; the host must not touch `staging` until the
+// event has completed (ensure_staging waits for it)
+hpa_status hpa_handle::upload_staging(size_t bytes) {
+    hpa_status st = cuda(cudaMemcpyAsync(d_staging, staging, bytes, cudaMemcpyHostToDevice, stream), "upload descriptors");
+    if (st) return st;
+    st = cuda(cudaEventRecord(staging_event, stream), "cudaEventRecord");
+    staging_event_live = true;
+    return st;
+}
+
+Binary* hpa_handle::binary(uint32_t id) {
+    if (id >= bins.size() || !bins[id]) return nullptr;
+    return bins[id];
+}
+
+// Arena carve-out helper
+struct Carve {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+// ------------------------------------------------------------------ create / destroy
+extern "C" hpa_status hpa_create(hpa_handle** out, int device, void* cuda_stream, const hpa_options* opt) {
+    if (!out) return HPA_E_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HPA_E_CUDA;
+    }
+    hpa_handle* h = new hpa_handle();
+    h->device = device;
+    h->stream = (cudaStream_t)cuda_stream;
+    if (opt) h->opt = *opt;
+    if (!h->opt.issued_mask) h->opt.issued_mask = 1u;
+    if (!h->opt.timeout_iters) h->opt.timeout_iters = 1u << 22;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&h->d_status, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMemset(h->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->staging_event, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return HPA_E_CUDA;
+    }
+    *out = h;
+    return HPA_OK;
+}
+
+hpa_handle::~hpa_handle() {
+    cudaStreamSynchronize(stream);
+    for (Binary* b : bins) delete b;
+    if (scratch) cudaFree(scratch);
+    if (staging) cudaFreeHost(staging);
+    if (d_staging) cudaFree(d_staging);
+    if (d_status) cudaFree(d_status);
+    if (d_bins) cudaFree(d_bins);
+    if (staging_event) cudaEventDestroy(staging_event);
+    for (auto& g : graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (host_io) cudaFree(host_io);
+    if (pinned_io) cudaFreeHost(pinned_io);
+}
+
+extern "C" hpa_status hpa_destroy(hpa_handle* h) {
+    if (!h) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    delete h;
+    return HPA_OK;
+}
+
+extern "C" const char* hpa_last_error(hpa_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+extern "C" uint64_t hpa_kernel_launches(hpa_handle* h) { return h ? h->launches : 0; }
+
+extern "C" hpa_status hpa_sync(hpa_handle* h, uint64_t* bad) {
+    if (!h) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    hpa_status st = h->cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (st) return st;
+    DevStatus ds;
+    st = h->cuda(cudaMemcpy(&ds, h->d_status, sizeof ds, cudaMemcpyDeviceToHost), "read device status");
+    if (st) return st;
+    if (bad) *bad = ds.bad;
+    if (ds.code) {
+        cudaMemset(h->d_status, 0, sizeof(DevStatus));
+        const char* what = ds.code == HPA_E_INVALID_SAMPLE ? "invalid sample records"
+                         : ds.code == HPA_E_CAPACITY ? "output capacity too small (n_keys holds the size needed)"
+                         : ds.code == HPA_E_TIMEOUT ? "a bounded device wait gave up"
+                         : "device error";
+        return h->fail(ds.code, "%s (detail %d, bad records %llu)", what, ds.where, (unsigned long long)ds.bad);
+    }
+    return HPA_OK;
+}
+
+// ------------------------------------------------------------------ structure
+static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B);
+
+extern "C" hpa_status hpa_load_structure(hpa_handle* h, const hpa_structure* s, uint32_t* binary_id) {
+    if (!h || !s || !binary_id) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    Binary* B = new Binary();
+    hpa_status st = load_binary(h, s, B);
+    if (st) { delete B; return st; }
+    uint32_t id = 0;
+    while (id < h->bins.size() && h->bins[id]) ++id;
+    if (id == h->bins.size()) h->bins.push_back(nullptr);
+    h->bins[id] = B;
+    st = h->refresh_bin_table();
+    if (st) { h->bins[id] = nullptr; delete B; return st; }
+    *binary_id = id;
+    return HPA_OK;
+}
+
+extern "C" hpa_status hpa_unload_structure(hpa_handle* h, uint32_t id) {
+    if (!h) return HPA_E_INVALID_ARG;
+    Binary* B = h->binary(id);
+    if (!B) return h->fail(HPA_E_INVALID_ARG, "no binary %u", id);
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    delete B;
+    h->bins[id] = nullptr;
+    return h->refresh_bin_table();
+}
+
+hpa_status hpa_handle::refresh_bin_table() {
+    std::vector<DevBinary> t(std::max<size_t>(1, bins.size()));
+    for (size_t i = 0; i < bins.size(); ++i)
+        if (bins[i]) t[i] = bins[i]->dev;
+    hpa_status st = cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    if (st) return st;
+    if (t.size() > d_bins_cap) {
+        if (d_bins) cudaFree(d_bins);
+        d_bins = nullptr;
+        if (cudaMalloc(&d_bins, t.size() * sizeof(DevBinary)) != cudaSuccess) {
+            cudaGetLastError();
+            d_bins_cap = 0;
+            return fail(HPA_E_OOM, "binary table");
+        }
+        d_bins_cap = t.size();
+        ++scratch_epoch;
+    }
+    return cuda(cudaMemcpy(d_bins, t.data(), t.size() * sizeof(DevBinary), cudaMemcpyHostToDevice), "binary table");
+}
+
+Binary::~Binary() {
+    for (void* p : dev_allocs) cudaFree(p);
+}
+
+static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B) {
+    const uint64_t R = s->n_ranges;
+    const uint32_t M = s->n_nodes, F = s->n_funcs, E = s->n_calls;
+    if (R == 0 || !s->range_lo || !s->range_hi || !s->range_node)
+        return h->fail(HPA_E_INVALID_ARG, "structure needs at least one range");
+    if (M == 0 || !s->node_parent || !s->node_kind || !s->node_func)
+        return h->fail(HPA_E_INVALID_ARG, "structure needs node tables");
+    if (R >= 0xFFFFFFFFull) return h->fail(HPA_E_INVALID_TABLE, "too many ranges");
+    if (M >= 0x7FFFFFFFu) return h->fail(HPA_E_INVALID_TABLE, "too many nodes");
+    if (E && (!s->cs_caller || !s->cs_callee || !s->cs_node))
+        return h->fail(HPA_E_INVALID_ARG, "call-site tables missing");
+    // ranges: sorted, non-empty, disjoint, span < 2^32
+    for (uint64_t i = 0; i < R; ++i) {
+        if (s->range_hi[i] <= s->range_lo[i])
+            return h->fail(HPA_E_INVALID_TABLE, "range %llu is empty", (unsigned long long)i);
+        if (i && s->range_lo[i] < s->range_hi[i - 1])
+            return h->fail(HPA_E_INVALID_TABLE, "range %llu overlaps or is out of order", (unsigned long long)i);
+        if (s->range_node[i] >= M)
+            return h->fail(HPA_E_INVALID_TABLE, "range %llu names node %u >= n_nodes", (unsigned long long)i, s->range_node[i]);
+    }
+    const uint64_t base = s->range_lo[0];
+    const uint64_t span = s->range_hi[R - 1] - base;
+    if (span >= (1ull << 32)) return h->fail(HPA_E_INVALID_TABLE, "ranges span %llu bytes (limit 2^32)", (unsigned long long)span);
+    // nodes: FUNC exactly the roots, parents of the same function, no cycles
+    for (uint32_t v = 0; v < M; ++v) {
+        const uint32_t p = s->node_parent[v];
+        if (s->node_func[v] >= F) return h->fail(HPA_E_INVALID_TABLE, "node %u names function %u >= n_funcs", v, s->node_func[v]);
+        if (s->node_kind[v] > HPA_NODE_CALL) return h->fail(HPA_E_INVALID_TABLE, "node %u has kind %u", v, s->node_kind[v]);
+        const bool root = p == HPA_NO_PARENT;
+        if (root != (s->node_kind[v] == HPA_NODE_FUNC))
+            return h->fail(HPA_E_INVALID_TABLE, "node %u: FUNC nodes must be exactly the roots", v);
+        if (!root) {
+            if (p >= M) return h->fail(HPA_E_INVALID_TABLE, "node %u has parent %u >= n_nodes", v, p);
+            if (s->node_func[p] != s->node_func[v]) return h->fail(HPA_E_INVALID_TABLE, "node %u and its parent belong to different functions", v);
+        }
+    }
+    std::vector<uint32_t> depth(M, 0xFFFFFFFFu);
+    std::vector<uint32_t> func_node(F, HPA_NO_PARENT);
+    for (uint32_t v = 0; v < M; ++v) {
+        if (s->node_parent[v] == HPA_NO_PARENT) {
+            if (func_node[s->node_func[v]] != HPA_NO_PARENT)
+                return h->fail(HPA_E_INVALID_TABLE, "function %u has two FUNC nodes", s->node_func[v]);
+            func_node[s->node_func[v]] = v;
+        }
+    }
+    uint32_t max_depth = 0;
+    {
+        std::vector<uint32_t> path;
+        for (uint32_t v = 0; v < M; ++v) {
+            path.clear();
+            uint32_t x = v;
+            while (depth[x] == 0xFFFFFFFFu && s->node_parent[x] != HPA_NO_PARENT) {
+                path.push_back(x);
+                if (path.size() > M) return h->fail(HPA_E_INVALID_TABLE, "structure tree has a cycle");
+                x = s->node_parent[x];
+            }
+            if (depth[x] == 0xFFFFFFFFu) depth[x] = 0;
+            uint32_t d = depth[x];
+            for (size_t i = path.size(); i-- > 0;) depth[path[i]] = ++d;
+            max_depth = std::max(max_depth, d);
+        }
+    }
+    // call sites
+    for (uint32_t e = 0; e < E; ++e) {
+        if (s->cs_caller[e] >= F || s->cs_callee[e] >= F)
+            return h->fail(HPA_E_INVALID_TABLE, "call site %u names a function >= n_funcs", e);
+        const uint32_t n = s->cs_node[e];
+        if (n >= M || s->node_kind[n] != HPA_NODE_CALL || s->node_func[n] != s->cs_caller[e])
+            return h->fail(HPA_E_INVALID_TABLE, "call site %u: cs_node must be a CALL node of the caller", e);
+    }
+    B->n_nodes = M; B->n_funcs = F; B->n_calls = E; B->n_ranges = R; B->max_depth = max_depth;
+    // attribution tables: ranges as offsets from the segment base, and a
+    // bucket directory with about one range per bucket
+    uint32_t dshift = 4;
+    while (dshift < 31 && (span >> dshift) > 2 * R) ++dshift;
+    const uint64_t n_dir = (span >> dshift) + 1;
+    std::vector<uint4> rng(R);
+    for (uint64_t i = 0; i < R; ++i)
+        rng[i] = make_uint4((uint32_t)(s->range_lo[i] - base), (uint32_t)(s->range_hi[i] - base), s->range_node[i], 0);
+    std::vector<uint32_t> dir(n_dir + 1);
+    {
+        uint64_t i = 0;
+        for (uint64_t b = 0; b <= n_dir; ++b) {
+            const uint64_t start = b << dshift;
+            while (i < R && rng[i].y <= start) ++i;
+            dir[b] = (uint32_t)i;
+        }
+    }
+    hpa_status st;
+    uint4* d_rng; uint32_t* d_dir;
+    if ((st = upload(h, B, rng, &d_rng)) || (st = upload(h, B, dir, &d_dir))) return st;
+    B->dev.pc_base = base;
+    B->dev.span = span;
+    B->dev.dshift = dshift;
+    B->dev.n_dir = (uint32_t)n_dir;
+    B->dev.n_ranges = (uint32_t)R;
+    B->dev.n_nodes = M;
+    B->dev.dir = d_dir;
+    B->dev.rng = d_rng;
+    // host copies kept for the other analyses
+    B->node_parent.assign(s->node_parent, s->node_parent + M);
+    B->node_kind.assign(s->node_kind, s->node_kind + M);
+    B->node_func.assign(s->node_func, s->node_func + M);
+    B->node_depth = depth;
+    if (E) {
+        B->cs_caller.assign(s->cs_caller, s->cs_caller + E);
+        B->cs_callee.assign(s->cs_callee, s->cs_callee + E);
+        B->cs_node.assign(s->cs_node, s->cs_node + E);
+    }
+    return build_callgraph(h, B);
+}
+
+extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary_info* info, uint32_t* cnode_of_func) {
+    if (!h) return HPA_E_INVALID_ARG;
+    Binary* B = h->binary(id);
+    if (!B) return h->fail(HPA_E_INVALID_ARG, "no binary %u", id);
+    if (info) {
+        info->n_nodes = B->n_nodes; info->n_funcs = B->n_funcs; info->n_calls = B->n_calls;
+        info->n_cnodes = B->n_cnodes; info->n_scc = B->n_scc; info->cdag_levels = B->cdag_levels;
+        info->n_ranges = B->n_ranges;
+    }
+    if (cnode_of_func) std::copy(B->cnode_of_func.begin(), B->cnode_of_func.end(), cnode_of_func);
+    return HPA_OK;
+}
+
+// ------------------------------------------------------------------ aggregation calls
+hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs) {
+    if (n == 0) return HPA_OK;
+    uint64_t N = 0, G = 0, tiles = 0;
+    uint32_t max_nodes = 0, max_stall = 1;
+    bool has_cnt = false;
+    for (uint32_t b = 0; b < n; ++b) {
+        const hpa_samples& s = in[b];
+        Binary* B = binary(binary_ids[b]);
+        if (!B) return fail(HPA_E_INVALID_ARG, "buffer %u: no binary %u", b, binary_ids[b]);
+        if (s.n_ctx == 0) return fail(HPA_E_INVALID_ARG, "buffer %u: n_ctx must be >= 1", b);
+        if (s.n_stall == 0 || s.n_stall > HPA_MAX_STALL)
+            return fail(HPA_E_INVALID_ARG, "buffer %u: n_stall must be in [1, %u]", b, HPA_MAX_STALL);
+        if (s.n && (!s.pc || !s.ctx || !s.stall)) return fail(HPA_E_INVALID_ARG, "buffer %u: null sample array", b);
+        hpa_profile& o = outs[b];
+        if (!o.n_keys || (o.capacity && (!o.key_ctx || !o.key_node || !o.key_stall || !o.val)))
+            return fail(HPA_E_INVALID_ARG, "buffer %u: output arrays missing", b);
+        N += s.n;
+        G += s.n_ctx;
+        tiles += (s.n + TILE - 1) / TILE;
+        max_nodes = std::max(max_nodes, B->n_nodes);
+        max_stall = std::max(max_stall, s.n_stall);
+        has_cnt |= s.count != nullptr;
+    }
+    if (N >= 0xFFFFFFF0ull) return fail(HPA_E_INVALID_ARG, "too many samples in one call (%llu)", (unsigned long long)N);
+    if (G >= 0xFFFFFFF0ull) return fail(HPA_E_INVALID_ARG, "too many contexts in one call");
+    const uint32_t sb = ceil_log2_u64(max_stall);
+    const uint32_t nb = ceil_log2_u64((uint64_t)max_nodes + 1);
+    if (nb + sb > 32) return fail(HPA_E_INVALID_ARG, "(n_nodes + 1) * 2^stall_bits exceeds 2^32");
+    const uint32_t sbits = nb + sb;
+    uint32_t cap = opt.leaf_capacity;
+    if (cap == 0) cap = (G && N / G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL;
+    if (cap != LEAF_CAP_SMALL && cap != LEAF_CAP_LARGE)
+        return fail(HPA_E_INVALID_ARG, "leaf_capacity must be 0, %u or %u", LEAF_CAP_SMALL, LEAF_CAP_LARGE);
+    const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
+
+    AggWork w{};
+    w.G = (uint32_t)G; w.n_buf = n; w.n_tiles = tiles; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
+    w.span_log = std::min<uint32_t>(10, 32 - sbits);
+    w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt;
+    // scratch layout
+    auto layout = [&](Carve& c) {
+        w.grp_hist = c.take<uint32_t>(G + 1);
+        w.grp_cursor = c.take<uint32_t>(G + 1);
+        w.item_id = c.take<uint32_t>(G + 1);
+        w.item_grp0 = c.take<uint32_t>(G + 1);
+        w.item_nleaf = c.take<uint32_t>(G + 1);
+        w.leaf_start = c.take<uint32_t>(L_max);
+        w.leaf_end = c.take<uint32_t>(L_max);
+        w.leaf_grp0 = c.take<uint32_t>(L_max);
+        w.leaf_info = c.take<uint32_t>(L_max);
+        w.leaf_d = c.take<uint32_t>(L_max + 1);
+        w.buf_first_leaf = c.take<uint32_t>(n + 1);
+        w.buf_bad = c.take<unsigned long long>(n);
+        w.rec_sub = c.take<uint32_t>(N + 1);
+        w.rec_cnt = has_cnt ? c.take<uint32_t>(N + 1) : nullptr;
+        w.rec2_sub = c.take<uint32_t>(N + 1);
+        w.rec2_cnt = has_cnt ? c.take<uint32_t>(N + 1) : nullptr;
+        w.tmp_key = c.take<uint32_t>(N + 1);
+        w.tmp_val = c.take<uint64_t>(N + 1);
+        w.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max<uint64_t>(G, L_max)));
+    };
+    Carve probe{nullptr};
+    layout(probe);
+    hpa_status st = ensure_scratch(probe.off + 256);
+    if (st) return st;
+    Carve real{(char*)scratch};
+    layout(real);
+    // descriptors
+    const size_t desc_bytes = n * sizeof(BufDev) + (n + 1) * 8 + (n + 1) * 4 + 512;
+    if ((st = ensure_staging(desc_bytes))) return st;
+    Carve hs{(char*)staging};
+    BufDev* hb = hs.take<BufDev>(n);
+    uint64_t* htile = hs.take<uint64_t>(n + 1);
+    uint32_t* hgrp = hs.take<uint32_t>(n + 1);
+    const size_t used = hs.off;
+    uint64_t tb = 0;
+    uint32_t gb = 0;
+    for (uint32_t b = 0; b < n; ++b) {
+        const hpa_samples& s = in[b];
+        hpa_profile& o = outs[b];
+        BufDev d{};
+        d.pc = s.pc; d.ctx = s.ctx; d.stall = s.stall; d.count = s.count; d.n = s.n;
+        d.tile_base = tb; d.n_ctx = s.n_ctx; d.n_stall = s.n_stall; d.grp_base = gb; d.bin = binary_ids[b];
+        d.total = o.total; d.unknown = o.unknown;
+        d.key_ctx = o.key_ctx; d.key_node = o.key_node; d.key_stall = o.key_stall; d.val = o.val;
+        d.n_keys = o.n_keys; d.capacity = o.capacity;
+        hb[b] = d;
+        htile[b] = tb;
+        hgrp[b] = gb;
+        tb += (s.n + TILE - 1) / TILE;
+        gb += s.n_ctx;
+        o.n_ctx = s.n_ctx;
+        o.n_stall = s.n_stall;
+    }
+    htile[n] = tb;
+    hgrp[n] = gb;
+    if ((st = upload_staging(used))) return st;
+    char* ds = (char*)d_staging;
+    w.bufs = (const BufDev*)(ds + ((char*)hb - (char*)staging));
+    w.buf_tile = (const uint64_t*)(ds + ((char*)htile - (char*)staging));
+    w.buf_grp = (const uint32_t*)(ds + ((char*)hgrp - (char*)staging));
+    w.bins = d_bins;
+    w.status = d_status;
+    for (uint32_t b = 0; b < n; ++b) {
+        if (outs[b].total) cudaMemsetAsync(outs[b].total, 0, 8 * in[b].n_stall, stream);
+        if (outs[b].unknown) cudaMemsetAsync(outs[b].unknown, 0, 8 * in[b].n_stall, stream);
+    }
+    run_aggregate(w, stream, sms, &launches);
+    return cuda(cudaGetLastError(), "aggregation launch");
+}
+
+extern "C" hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, const hpa_samples* in, hpa_profile* out) {
+    if (!h || !in || !out) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    return h->aggregate(1, &binary_id, in, out);
+}
+
+extern "C" hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t max_groups) {
+    if (!h) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    const uint64_t N = max_samples, G = max_groups;
+    const uint64_t L = G + 6 * (N / LEAF_CAP_SMALL + 1) + 300;
+    size_t bytes = (G + 1) * 4 * 5 + L * 4 * 5 + (N + 1) * (4 * 5 + 8) + 256 * 40 + scan_tmp_words(std::max(G, L)) * 4;
+    return h->ensure_scratch(bytes + (1 << 20));
+}
+
+extern "C" hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
+                                                 hpa_profile* out) {
+    if (!h || !in || !out) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    const uint64_t n = in->n;
+    const bool cnt = in->count != nullptr;
+    // device copies of the inputs and outputs, kept by the handle
+    const size_t out_cap = out->capacity;
+    auto layout = [&](Carve& c, hpa_samples& di, hpa_profile& d) {
+        di = *in;
+        di.pc = c.take<uint64_t>(n);
+        di.ctx = c.take<uint32_t>(n);
+        di.stall = c.take<uint8_t>(n);
+        di.count = cnt ? c.take<uint32_t>(n) : nullptr;
+        d = *out;
+        d.key_ctx = c.take<uint32_t>(out_cap);
+        d.key_node = c.take<uint32_t>(out_cap);
+        d.key_stall = c.take<uint8_t>(out_cap);
+        d.val = c.take<uint64_t>(out_cap);
+        d.n_keys = c.take<uint64_t>(1);
+        d.total = out->total ? c.take<uint64_t>(HPA_MAX_STALL) : nullptr;
+        d.unknown = out->unknown ? c.take<uint64_t>(HPA_MAX_STALL) : nullptr;
+    };
+    hpa_samples di;
+    hpa_profile d;
+    Carve probe{nullptr};
+    layout(probe, di, d);
+    const size_t need = probe.off + 256;
+    hpa_status st;
+    if (need > h->host_io_cap) {
+        if ((st = h->cuda(cudaStreamSynchronize(h->stream), "sync"))) return st;
+        if (h->host_io) cudaFree(h->host_io);
+        h->host_io = nullptr;
+        h->host_io_cap = 0;
+        if (cudaMalloc(&h->host_io, need) != cudaSuccess) {
+            cudaGetLastError();
+            return h->fail(HPA_E_OOM, "host-call buffers of %zu bytes", need);
+        }
+        h->host_io_cap = need;
+    }
+    Carve c{(char*)h->host_io};
+    layout(c, di, d);
+    uint64_t* pc = (uint64_t*)di.pc;
+    uint32_t* ctx = (uint32_t*)di.ctx;
+    uint8_t* stall = (uint8_t*)di.stall;
+    uint32_t* count = (uint32_t*)di.count;
+    cudaStream_t s = h->stream;
+    if ((st = h->cuda(cudaMemcpyAsync(pc, in->pc, n * 8, cudaMemcpyHostToDevice, s), "H2D pc")) ||
+        (st = h->cuda(cudaMemcpyAsync(ctx, in->ctx, n * 4, cudaMemcpyHostToDevice, s), "H2D ctx")) ||
+        (st = h->cuda(cudaMemcpyAsync(stall, in->stall, n, cudaMemcpyHostToDevice, s), "H2D stall")))
+        return st;
+    if (cnt && (st = h->cuda(cudaMemcpyAsync(count, in->count, n * 4, cudaMemcpyHostToDevice, s), "H2D count")))
+        return st;
+    if ((st = h->aggregate(1, &binary_id, &di, &d))) return st;
+    uint64_t K = 0;
+    if ((st = h->cuda(cudaMemcpyAsync(&K, d.n_keys, 8, cudaMemcpyDeviceToHost, s), "D2H n_keys")) ||
+        (st = h->cuda(cudaStreamSynchronize(s), "sync")))
+        return st;
+    const uint64_t k = std::min<uint64_t>(K, out_cap);
+    if (k) {
+        if ((st = h->cuda(cudaMemcpyAsync(out->key_ctx, d.key_ctx, k * 4, cudaMemcpyDeviceToHost, s), "D2H")) ||
+            (st = h->cuda(cudaMemcpyAsync(out->key_node, d.key_node, k * 4, cudaMemcpyDeviceToHost, s), "D2H")) ||
+            (st = h->cuda(cudaMemcpyAsync(out->key_stall, d.key_stall, k, cudaMemcpyDeviceToHost, s), "D2H")) ||
+            (st = h->cuda(cudaMemcpyAsync(out->val, d.val, k * 8, cudaMemcpyDeviceToHost, s), "D2H")))
+            return st;
+    }
+    if (out->total) cudaMemcpyAsync(out->total, d.total, 8 * in->n_stall, cudaMemcpyDeviceToHost, s);
+    if (out->unknown) cudaMemcpyAsync(out->unknown, d.unknown, 8 * in->n_stall, cudaMemcpyDeviceToHost, s);
+    *out->n_keys = K;
+    out->n_ctx = d.n_ctx;
+    out->n_stall = d.n_stall;
+    return hpa_sync(h, nullptr);
+}

@@ -1,0 +1,109 @@
+// Host-side state of libhpa: the handle and loaded binaries.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "hpa.h"
+#include "hpa_internal.h"
+
+namespace hpa {
+
+// Device tables of a binary's static call graph (Section 6.3 steps 1 and 3),
+// shared by every context.
+struct DevCallGraph {
+    uint32_t F, E, V, n_levels, M;
+    const uint32_t* node_func;   // [M]
+    const uint32_t* node_cs;     // [M] call site of a CALL node, else 0xFFFFFFFF
+    const uint32_t* cs_caller;   // [E]
+    const uint32_t* cs_callee;   // [E]
+    const uint32_t* cnode_of_func;  // [F]
+    const uint32_t* fin_off;     // [F+1] in-edges of each function (original graph)
+    const uint32_t* fin_edge;    // [E]
+    const uint32_t* cin_off;     // [V+1] external in-edges of each condensed node
+    const uint32_t* cin_edge;
+    const uint32_t* cout_off;    // [V+1] external out-edges of each condensed node
+    const uint32_t* cout_edge;
+    const uint32_t* level_off;   // [n_levels+1] condensed nodes by height (sinks first)
+    const uint32_t* level_node;
+    const uint8_t* edge_intra;   // [E] 1 if the edge lies inside one SCC
+    const uint8_t* cnode_live;   // [V] 0 for rows of functions inside a non-trivial SCC
+};
+
+struct Binary {
+    DevBinary dev{};
+    DevCallGraph cg{};
+    std::vector<void*> dev_allocs;
+    uint32_t n_nodes = 0, n_funcs = 0, n_calls = 0, max_depth = 0;
+    uint64_t n_ranges = 0;
+    std::vector<uint32_t> node_parent, node_func, node_depth;
+    std::vector<uint8_t> node_kind;
+    std::vector<uint32_t> cs_caller, cs_callee, cs_node;
+    uint32_t n_cnodes = 0, n_scc = 0, cdag_levels = 0;
+    std::vector<uint32_t> cnode_of_func;
+    const uint32_t* d_node_parent = nullptr;   // structure tree on the device
+    ~Binary();
+};
+
+struct CachedGraph {
+    uint64_t key = 0;
+    uint64_t epoch = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace hpa
+
+struct hpa_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    hpa_options opt{};
+    std::string err;
+    int sms = 0;
+    hpa::DevStatus* d_status = nullptr;
+    std::vector<hpa::Binary*> bins;
+    hpa::DevBinary* d_bins = nullptr;
+    size_t d_bins_cap = 0;
+    void* scratch = nullptr;
+    size_t scratch_cap = 0;
+    uint64_t scratch_epoch = 0;
+    void* staging = nullptr;      // pinned host descriptors
+    void* d_staging = nullptr;
+    size_t staging_cap = 0;
+    cudaEvent_t staging_event = nullptr;
+    bool staging_event_live = false;
+    uint64_t launches = 0;
+    std::vector<hpa::CachedGraph> graphs;
+    void* host_io = nullptr;
+    size_t host_io_cap = 0;
+    void* pinned_io = nullptr;
+
+    ~hpa_handle();
+    hpa_status fail(hpa_status st, const char* fmt, ...);
+    hpa_status cuda(cudaError_t e, const char* what);
+    bool capturing() const;
+    hpa_status ensure_scratch(size_t bytes);
+    hpa_status ensure_staging(size_t bytes);
+    hpa_status upload_staging(size_t bytes);
+    hpa::Binary* binary(uint32_t id);
+    hpa_status refresh_bin_table();
+    hpa_status aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs);
+};
+
+namespace hpa {
+hpa_status build_callgraph(hpa_handle* h, Binary* B);
+
+// copy a host vector into a device allocation owned by binary B
+template <typename T>
+inline hpa_status upload(hpa_handle* h, Binary* B, const std::vector<T>& v, T** out) {
+    *out = nullptr;
+    if (v.empty()) return HPA_OK;
+    void* p = nullptr;
+    if (cudaMalloc(&p, v.size() * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return h->fail(HPA_E_OOM, "structure table of %zu bytes", v.size() * sizeof(T));
+    }
+    B->dev_allocs.push_back(p);
+    *out = (T*)p;
+    return h->cuda(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "structure upload");
+}
+}

@@ -1,0 +1,91 @@
+// Internal declarations shared by the host orchestration (hpa_host.cu) and
+// the kernel translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hpa_dev.cuh"
+
+namespace hpa {
+
+// One sample buffer of an aggregation call, as the kernels read it.
+struct BufDev {
+    const uint64_t* pc;
+    const uint32_t* ctx;
+    const uint8_t* stall;
+    const uint32_t* count;      // may be null (every record counts 1)
+    uint64_t n;
+    uint64_t tile_base;         // first global tile of this buffer
+    uint32_t n_ctx;
+    uint32_t n_stall;
+    uint32_t grp_base;          // first global group (group = grp_base + ctx)
+    uint32_t bin;               // index into the DevBinary table
+    uint32_t first_leaf_item;   // (filled on device) unused by the host
+    uint32_t pad;
+    uint64_t* total;            // per-stall totals (may be null)
+    uint64_t* unknown;
+    // outputs
+    uint32_t* key_ctx;
+    uint32_t* key_node;
+    uint8_t* key_stall;
+    uint64_t* val;
+    uint64_t* n_keys;
+    uint64_t capacity;
+};
+
+// Scratch of one aggregation call (device pointers).
+struct AggWork {
+    uint32_t G;            // groups (sum of n_ctx)
+    uint32_t n_buf;
+    uint64_t n_tiles;
+    uint32_t cap;          // leaf capacity
+    uint32_t q;            // cap / 2
+    uint32_t sb;           // stall bits
+    uint32_t sbits;        // subkey bits (node bits + stall bits)
+    uint32_t span_log;     // at most 2^span_log groups per item (32 - sbits)
+    uint32_t L_max;        // leaf table capacity
+    uint32_t has_cnt;
+    uint32_t* grp_hist;    // [G+1] -> exclusive scan -> seg_off
+    uint32_t* grp_cursor;  // [G]
+    uint32_t* item_id;     // [G+1] flags -> exclusive scan
+    uint32_t* item_grp0;   // [G]
+    uint32_t* item_nleaf;  // [G+1] -> exclusive scan -> leaf_base
+    uint32_t* leaf_start;  // [L_max]
+    uint32_t* leaf_end;    // [L_max]
+    uint32_t* leaf_grp0;   // [L_max]
+    uint32_t* leaf_info;   // [L_max] bit0: records in rec2; bits 8..: buffer index
+    uint32_t* leaf_d;      // [L_max+1] -> exclusive scan -> leaf_out
+    uint32_t* buf_first_leaf;     // [n_buf + 1]
+    unsigned long long* buf_bad;  // [n_buf]
+    uint32_t* rec_sub;     // [N]
+    uint32_t* rec_cnt;     // [N] (if has_cnt)
+    uint32_t* rec2_sub;    // [N]
+    uint32_t* rec2_cnt;    // [N]
+    uint32_t* tmp_key;     // [N]
+    uint64_t* tmp_val;     // [N]
+    uint32_t* scan_tmp;    // device-wide scan partials
+    const BufDev* bufs;    // [n_buf]
+    const uint64_t* buf_tile;     // [n_buf + 1] tile prefix
+    const uint32_t* buf_grp;      // [n_buf + 1] group prefix
+    const DevBinary* bins;
+    DevStatus* status;
+};
+
+constexpr int TILE = 4096;            // samples per tile of the sample-reading kernels
+constexpr uint32_t HPA_MAX_STALL_DEV = 32;
+constexpr uint32_t LEAF_CAP_SMALL = 4096;   // 256 threads, two CTAs per SM
+constexpr uint32_t LEAF_CAP_LARGE = 11264;  // 512 threads, one CTA per SM
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_EPT = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_EPT;
+
+// device-wide exclusive scan of n uint32 values (in place allowed);
+// out[n] receives the total.  tmp needs scan_tmp_words(n) words.
+size_t scan_tmp_words(uint64_t n);
+void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cudaStream_t s, uint64_t* launches);
+
+// aggregation pipeline (A1 + A2) over a prepared AggWork
+void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
+
+}  // namespace hpa

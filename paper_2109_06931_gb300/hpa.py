@@ -1,0 +1,288 @@
+"""Python binding of libhpa.so (include/hpa.h): argument marshalling only.
+
+Every analysis step runs in the library's CUDA kernels; this module converts
+torch tensors and numpy arrays into the C structures and calls the C ABI.
+It raises if the library or a CUDA device is missing -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+HPA_OK, HPA_E_INVALID_ARG, HPA_E_INVALID_TABLE, HPA_E_INVALID_SAMPLE = 0, 1, 2, 3
+HPA_E_CAPACITY, HPA_E_OOM, HPA_E_CUDA, HPA_E_TIMEOUT, HPA_E_INTERNAL = 4, 5, 6, 7, 8
+HPA_UNKNOWN_NODE = 0xFFFFFFFF
+HPA_NO_PARENT = 0xFFFFFFFF
+HPA_MAX_STALL = 32
+HPA_EDGE_FIXUP, HPA_EDGE_FIXUP2, HPA_EDGE_INTRA_SCC = 1, 2, 4
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_TABLE", 3: "INVALID_SAMPLE", 4: "CAPACITY",
+                5: "OOM", 6: "CUDA", 7: "TIMEOUT", 8: "INTERNAL"}
+
+vp, u8p, u32p, u64p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)
+
+
+class hpa_options(C.Structure):
+    _fields_ = [("issued_mask", C.c_uint32), ("leaf_capacity", C.c_uint32), ("timeout_iters", C.c_uint32),
+                ("reserved", C.c_uint32 * 5)]
+
+
+class hpa_structure(C.Structure):
+    _fields_ = [("n_ranges", C.c_uint64), ("range_lo", vp), ("range_hi", vp), ("range_node", vp),
+                ("n_nodes", C.c_uint32), ("node_parent", vp), ("node_kind", vp), ("node_func", vp),
+                ("n_funcs", C.c_uint32), ("n_calls", C.c_uint32), ("cs_caller", vp), ("cs_callee", vp),
+                ("cs_node", vp)]
+
+
+class hpa_binary_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_uint32), ("n_funcs", C.c_uint32), ("n_calls", C.c_uint32),
+                ("n_cnodes", C.c_uint32), ("n_scc", C.c_uint32), ("cdag_levels", C.c_uint32),
+                ("n_ranges", C.c_uint64)]
+
+
+class hpa_samples(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("pc", vp), ("ctx", vp), ("stall", vp), ("count", vp),
+                ("n_ctx", C.c_uint32), ("n_stall", C.c_uint32)]
+
+
+class hpa_profile(C.Structure):
+    _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp), ("val", vp),
+                ("n_keys", vp), ("total", vp), ("unknown", vp), ("n_ctx", C.c_uint32), ("n_stall", C.c_uint32)]
+
+
+class hpa_gpucct(C.Structure):
+    _fields_ = [("n_req", C.c_uint32), ("req_ctx", vp), ("incl", vp), ("a", vp), ("flags", vp)]
+
+
+class hpa_cct(C.Structure):
+    _fields_ = [("n_nodes", C.c_uint32), ("parent", vp)]
+
+
+class hpa_derived(C.Structure):
+    _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp),
+                ("sum", vp), ("min", vp), ("max", vp), ("mean", vp), ("std", vp), ("cov", vp),
+                ("n_keys", vp), ("n_ctx", C.c_uint32), ("S", vp), ("S_issued", vp), ("W", vp), ("frac", vp)]
+
+
+EXPORTS = ["hpa_create", "hpa_destroy", "hpa_last_error", "hpa_sync", "hpa_reserve", "hpa_kernel_launches",
+           "hpa_load_structure", "hpa_unload_structure", "hpa_binary_info_get", "hpa_attribute_samples",
+           "hpa_attribute_samples_host", "hpa_attribute_batch", "hpa_apportion_callgraph",
+           "hpa_propagate_inclusive", "hpa_derive_metrics"]
+
+_lib = None
+
+
+def lib(build_if_needed: bool = True):
+    """Load libhpa.so (building it first if needed)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_needed:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libhpa.so not built at {path}")
+        L = C.CDLL(path)
+        H = vp
+        L.hpa_create.argtypes = [C.POINTER(H), C.c_int, vp, C.POINTER(hpa_options)]
+        L.hpa_destroy.argtypes = [H]
+        L.hpa_last_error.argtypes = [H]
+        L.hpa_last_error.restype = C.c_char_p
+        L.hpa_sync.argtypes = [H, u64p]
+        L.hpa_reserve.argtypes = [H, C.c_uint64, C.c_uint64]
+        L.hpa_kernel_launches.argtypes = [H]
+        L.hpa_kernel_launches.restype = C.c_uint64
+        L.hpa_load_structure.argtypes = [H, C.POINTER(hpa_structure), u32p]
+        L.hpa_unload_structure.argtypes = [H, C.c_uint32]
+        L.hpa_binary_info_get.argtypes = [H, C.c_uint32, C.POINTER(hpa_binary_info), vp]
+        L.hpa_attribute_samples.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
+        L.hpa_attribute_samples_host.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
+        L.hpa_attribute_batch.argtypes = [H, C.c_uint32, u32p, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
+        L.hpa_apportion_callgraph.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_gpucct)]
+        L.hpa_propagate_inclusive.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile),
+                                              C.POINTER(hpa_cct), vp]
+        L.hpa_derive_metrics.argtypes = [H, C.POINTER(C.POINTER(hpa_profile)), C.c_uint32, C.POINTER(hpa_derived)]
+        for f in EXPORTS:
+            if f not in ("hpa_last_error", "hpa_kernel_launches"):
+                getattr(L, f).restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+class HpaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return C.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(C.c_void_p)
+
+
+def _u32(t):
+    return t.view(torch.int32) if t.dtype in (torch.int32, torch.uint32) else t.to(torch.int32)
+
+
+@dataclass
+class Profile:
+    """Device-resident raw-metric profile (sorted unique keys)."""
+    key_ctx: torch.Tensor    # int32 view of uint32
+    key_node: torch.Tensor   # int32 view of uint32 (-1 = UNKNOWN)
+    key_stall: torch.Tensor  # uint8
+    val: torch.Tensor        # int64 view of uint64
+    n_keys: torch.Tensor     # int64[1]
+    total: torch.Tensor
+    unknown: torch.Tensor
+    n_ctx: int
+    n_stall: int
+    capacity: int
+
+    def c(self) -> hpa_profile:
+        return hpa_profile(self.capacity, _ptr(self.key_ctx), _ptr(self.key_node), _ptr(self.key_stall),
+                           _ptr(self.val), _ptr(self.n_keys), _ptr(self.total), _ptr(self.unknown),
+                           self.n_ctx, self.n_stall)
+
+    def count(self) -> int:
+        return int(self.n_keys.item())
+
+    def numpy(self):
+        k = min(self.count(), self.capacity)
+        return (self.key_ctx[:k].cpu().numpy().view(np.uint32), self.key_node[:k].cpu().numpy().view(np.uint32),
+                self.key_stall[:k].cpu().numpy(), self.val[:k].cpu().numpy().view(np.uint64))
+
+
+def new_profile(capacity: int, n_stall: int, device) -> Profile:
+    cap = max(1, int(capacity))
+    z = lambda n, dt: torch.empty(n, dtype=dt, device=device)
+    return Profile(z(cap, torch.int32), z(cap, torch.int32), z(cap, torch.uint8), z(cap, torch.int64),
+                   torch.zeros(1, dtype=torch.int64, device=device), torch.zeros(HPA_MAX_STALL, dtype=torch.int64, device=device),
+                   torch.zeros(HPA_MAX_STALL, dtype=torch.int64, device=device), 0, n_stall, cap)
+
+
+class Hpa:
+    """One library handle bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, issued_mask: int = 1,
+                 leaf_capacity: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("hpa needs a CUDA device; there is no CPU implementation")
+        self.L = lib()
+        self.device = torch.device("cuda", device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.h = C.c_void_p()
+        opt = hpa_options(issued_mask, leaf_capacity, 0)
+        st = self.L.hpa_create(C.byref(self.h), device, C.c_void_p(self.stream.cuda_stream), C.byref(opt))
+        if st:
+            raise HpaError(st, "hpa_create failed")
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            self.L.hpa_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st):
+        if st:
+            raise HpaError(st, self.L.hpa_last_error(self.h).decode())
+
+    def sync(self):
+        bad = C.c_uint64(0)
+        st = self.L.hpa_sync(self.h, C.byref(bad))
+        if st:
+            raise HpaError(st, self.L.hpa_last_error(self.h).decode())
+        return int(bad.value)
+
+    def sync_status(self):
+        """(status, bad) without raising."""
+        bad = C.c_uint64(0)
+        st = self.L.hpa_sync(self.h, C.byref(bad))
+        return int(st), int(bad.value)
+
+    def launches(self) -> int:
+        return int(self.L.hpa_kernel_launches(self.h))
+
+    def reserve(self, max_samples: int, max_groups: int):
+        self.check(self.L.hpa_reserve(self.h, max_samples, max_groups))
+
+    # ---- structure
+    def load_structure(self, b) -> int:
+        """b: an object with numpy arrays range_lo/hi/node, node_parent/kind/func, cs_* (see synth.Binary)."""
+        arrs = dict(
+            range_lo=np.ascontiguousarray(b.range_lo, np.uint64), range_hi=np.ascontiguousarray(b.range_hi, np.uint64),
+            range_node=np.ascontiguousarray(b.range_node, np.uint32),
+            node_parent=np.ascontiguousarray(b.node_parent, np.uint32),
+            node_kind=np.ascontiguousarray(b.node_kind, np.uint8), node_func=np.ascontiguousarray(b.node_func, np.uint32),
+            cs_caller=np.ascontiguousarray(b.cs_caller, np.uint32), cs_callee=np.ascontiguousarray(b.cs_callee, np.uint32),
+            cs_node=np.ascontiguousarray(b.cs_node, np.uint32))
+        s = hpa_structure(arrs["range_lo"].shape[0], _ptr(arrs["range_lo"]), _ptr(arrs["range_hi"]),
+                          _ptr(arrs["range_node"]), arrs["node_parent"].shape[0], _ptr(arrs["node_parent"]),
+                          _ptr(arrs["node_kind"]), _ptr(arrs["node_func"]), int(b.n_funcs), arrs["cs_caller"].shape[0],
+                          _ptr(arrs["cs_caller"]), _ptr(arrs["cs_callee"]), _ptr(arrs["cs_node"]))
+        bid = C.c_uint32(0)
+        self.check(self.L.hpa_load_structure(self.h, C.byref(s), C.byref(bid)))
+        return int(bid.value)
+
+    def unload_structure(self, bid: int):
+        self.check(self.L.hpa_unload_structure(self.h, bid))
+
+    def binary_info(self, bid: int):
+        info = hpa_binary_info()
+        F = C.c_uint32()
+        self.check(self.L.hpa_binary_info_get(self.h, bid, C.byref(info), None))
+        cof = np.zeros(info.n_funcs, np.uint32)
+        self.check(self.L.hpa_binary_info_get(self.h, bid, C.byref(info), _ptr(cof)))
+        return info, cof
+
+    # ---- samples
+    @staticmethod
+    def samples_c(pc, ctx, stall, count, n_ctx, n_stall) -> hpa_samples:
+        return hpa_samples(int(pc.shape[0]), _ptr(pc), _ptr(ctx), _ptr(stall), _ptr(count), int(n_ctx), int(n_stall))
+
+    def attribute_samples(self, bid: int, s, out: Profile | None = None, capacity: int | None = None) -> Profile:
+        """s: synth.Samples-like with device tensors pc (int64), ctx (int32), stall (uint8), count (int32|None)."""
+        if out is None:
+            out = new_profile(s.n if capacity is None else capacity, s.n_stall, self.device)
+        ci = self.samples_c(s.pc, s.ctx, s.stall, s.count, s.n_ctx, s.n_stall)
+        co = out.c()
+        self.check(self.L.hpa_attribute_samples(self.h, bid, C.byref(ci), C.byref(co)))
+        out.n_ctx, out.n_stall = s.n_ctx, s.n_stall
+        return out
+
+    def attribute_samples_host(self, bid: int, pc, ctx, stall, count, n_ctx, n_stall, capacity=None):
+        """Host arrays in, host arrays out (numpy or pinned CPU tensors)."""
+        n = int(pc.shape[0])
+        cap = n if capacity is None else capacity
+        out = dict(ctx=np.empty(cap, np.uint32), node=np.empty(cap, np.uint32), stall=np.empty(cap, np.uint8),
+                   val=np.empty(cap, np.uint64), n=np.zeros(1, np.uint64), total=np.zeros(HPA_MAX_STALL, np.uint64),
+                   unknown=np.zeros(HPA_MAX_STALL, np.uint64))
+        ci = self.samples_c(pc, ctx, stall, count, n_ctx, n_stall)
+        co = hpa_profile(cap, _ptr(out["ctx"]), _ptr(out["node"]), _ptr(out["stall"]), _ptr(out["val"]),
+                         _ptr(out["n"]), _ptr(out["total"]), _ptr(out["unknown"]), 0, 0)
+        self.check(self.L.hpa_attribute_samples_host(self.h, bid, C.byref(ci), C.byref(co)))
+        return out
+
+    def attribute_batch(self, bids, samples, outs=None):
+        n = len(samples)
+        if outs is None:
+            outs = [new_profile(s.n, s.n_stall, self.device) for s in samples]
+        ins = (hpa_samples * n)(*[self.samples_c(s.pc, s.ctx, s.stall, s.count, s.n_ctx, s.n_stall) for s in samples])
+        cos = (hpa_profile * n)(*[o.c() for o in outs])
+        ids = (C.c_uint32 * n)(*bids)
+        self.check(self.L.hpa_attribute_batch(self.h, n, ids, ins, cos))
+        for o, s in zip(outs, samples):
+            o.n_ctx, o.n_stall = s.n_ctx, s.n_stall
+        return outs

@@ -1,0 +1,187 @@
+"""GPU parity of attribution + aggregation (Sections 4.2, 4.5, 5) against the
+CPU oracle: every key, node id and count bit-exact."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import assert_same_keys, samples_from_numpy
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2109_06931_gb300 import hpa
+    h = hpa.Hpa(0)
+    yield h
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def plain(H):
+    B = synth.PLAIN.binary()
+    return B, H.load_structure(B)
+
+
+@pytest.fixture(scope="module")
+def large_bin(H):
+    B = synth.LARGE.binary()
+    return B, H.load_structure(B)
+
+
+def run(H, bid, S, **kw):
+    out = H.attribute_samples(bid, S, **kw)
+    H.sync()
+    return out
+
+
+def test_golden_fixture(H):
+    g = json.load(open(os.path.join(GOLD, "attribution_small.json")))
+    s = np.array(g["samples"], dtype=np.uint64)
+    M = 10
+    B = synth.Binary(np.array(g["range_lo"], np.uint64), np.array(g["range_hi"], np.uint64),
+                     np.array(g["range_node"], np.uint32), np.full(M, synth.NO_PARENT, np.uint32),
+                     np.zeros(M, np.uint8), np.arange(M, dtype=np.uint32), np.arange(M, dtype=np.uint32),
+                     np.zeros(M, np.uint64), np.zeros(M, np.uint64), np.zeros(0, np.uint64),
+                     np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.uint32), 0, 0)
+    bid = H.load_structure(B)
+    S = samples_from_numpy(s[:, 0], s[:, 1], s[:, 2], s[:, 3], g["n_ctx"], g["n_stall"])
+    out = run(H, bid, S)
+    got = list(zip(*[a.tolist() for a in out.numpy()]))
+    assert [list(r) for r in got] == g["expected_keys"]
+    assert out.total[:4].cpu().tolist() == g["expected_total"]
+    assert out.unknown[:4].cpu().tolist() == g["expected_unknown"]
+
+
+@pytest.mark.parametrize("frac,counts", [(0.01, False), (0.2, False), (1.0, False), (0.3, True)])
+def test_plain_workload(H, plain, frac, counts):
+    B, bid = plain
+    w = synth.scaled(synth.PLAIN, frac)
+    w.counts = counts
+    S = w.samples(B, device="cuda")
+    out = run(H, bid, S)
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 4095, 4096, 4097, 12289])
+def test_ragged_sizes(H, plain, n):
+    B, bid = plain
+    S = synth.make_samples(77, B, n, 13, 1.1, device="cuda")
+    out = run(H, bid, S)
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+
+
+@pytest.mark.parametrize("n_ctx", [1, 2, 7])
+def test_big_groups(H, plain, n_ctx):
+    """Few contexts: every group exceeds a leaf and is split into sub-bins."""
+    B, bid = plain
+    S = synth.make_samples(5, B, 300_000, n_ctx, 1.1, counts=True, device="cuda")
+    out = run(H, bid, S)
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+
+
+def test_heavy_sub_bin(H, plain):
+    """All samples in one function of one context: a sub-bin far larger than a
+    leaf, aggregated in dense shared-memory windows."""
+    B, bid = plain
+    f = 17
+    n = 400_000
+    idx = np.arange(n)
+    slots = int((B.func_hi[f] - B.func_lo[f]) // 16)
+    pc = B.func_lo[f] + (synth.np_below(3, 1, idx, slots) * 16).astype(np.uint64)
+    st = synth.np_below(3, 2, idx, 16).astype(np.uint8)
+    S = samples_from_numpy(pc, np.zeros(n, np.uint32), st, None, 1, 16)
+    out = run(H, bid, S)
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+
+
+def test_skewed_contexts(H, large_bin):
+    """A few hot contexts next to many cold ones, structure of the large binary."""
+    B, bid = large_bin
+    wts = np.ones(3000)
+    wts[[5, 900, 2999]] = 2000.0
+    S = synth.make_samples(9, B, 1_500_000, 3000, 0.9, counts=True, device="cuda", ctx_weights=wts)
+    out = run(H, bid, S)
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+
+
+@pytest.mark.parametrize("cap", [4096, 11264])
+def test_leaf_capacity_variants_agree(cap, plain):
+    from paper_2109_06931_gb300 import hpa
+    B, _ = plain
+    h = hpa.Hpa(0, leaf_capacity=cap)
+    bid = h.load_structure(B)
+    S = synth.make_samples(11, B, 500_000, 40, 1.1, counts=True, device="cuda")
+    out = h.attribute_samples(bid, S)
+    h.sync()
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+    h.close()
+
+
+def test_large_structure(H, large_bin):
+    B, bid = large_bin
+    S = synth.LARGE.samples(B, device="cuda", n=3_000_000)
+    out = run(H, bid, S)
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+
+
+def test_invalid_samples_fail_whole_call(H, plain):
+    from paper_2109_06931_gb300 import hpa
+    B, bid = plain
+    S = synth.make_samples(2, B, 10_000, 8, 1.1, device="cuda")
+    S.ctx[5] = 8
+    S.ctx[77] = 1000
+    S.stall[100] = 16
+    out = H.attribute_samples(bid, S)
+    st, bad = H.sync_status()
+    assert st == hpa.HPA_E_INVALID_SAMPLE and bad == 3
+    assert out.count() == 0
+    # the handle keeps working afterwards
+    S2 = synth.make_samples(2, B, 10_000, 8, 1.1, device="cuda")
+    assert_same_keys(run(H, bid, S2), oracle.attribute_samples(B, S2))
+
+
+def test_capacity_too_small(H, plain):
+    from paper_2109_06931_gb300 import hpa
+    B, bid = plain
+    S = synth.make_samples(4, B, 50_000, 30, 1.1, device="cuda")
+    ref = oracle.attribute_samples(B, S)
+    out = H.attribute_samples(bid, S, capacity=len(ref) - 1)
+    st, _ = H.sync_status()
+    assert st == hpa.HPA_E_CAPACITY and out.count() == len(ref)
+    out = H.attribute_samples(bid, S, capacity=len(ref))
+    H.sync()
+    assert_same_keys(out, ref)
+
+
+def test_batch_equals_plain_runs(H, plain, large_bin):
+    B1, b1 = plain
+    B2, b2 = large_bin
+    sizes = [0, 1, 5000, 70_000, 4096, 200_000, 33_333]
+    ss, bins, bs = [], [], []
+    for i, n in enumerate(sizes):
+        B, bid = (B1, b1) if i % 2 == 0 else (B2, b2)
+        ss.append(synth.make_samples(100 + i, B, n, 50 + 30 * i, 1.0, counts=(i % 3 == 0), device="cuda"))
+        bins.append(bid); bs.append(B)
+    outs = H.attribute_batch(bins, ss)
+    H.sync()
+    for o, S, B in zip(outs, ss, bs):
+        assert_same_keys(o, oracle.attribute_samples(B, S))
+
+
+def test_host_entry_point(H, plain):
+    B, bid = plain
+    S = synth.make_samples(21, B, 100_000, 64, 1.1, counts=True)
+    out = H.attribute_samples_host(bid, S.pc.numpy(), S.ctx.numpy(), S.stall.numpy(), S.count.numpy(), 64, 16)
+    ref = oracle.attribute_samples(B, S)
+    k = int(out["n"][0])
+    assert k == len(ref)
+    for a, b in zip((out["ctx"], out["node"], out["stall"], out["val"]), (ref.ctx, ref.node, ref.stall, ref.val)):
+        assert np.array_equal(a[:k], b)
+    assert np.array_equal(out["total"][:16], ref.total)
