@@ -482,7 +482,29 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
             uint32_t n_runs;
             const uint32_t rid0 = block_exclusive_scan<uint32_t, THREADS>(heads, sw, &n_runs);
             const unsigned long long carry = block_seg_carry<THREADS>(mine, sws);
+            // keys whose counts add up to 0 are omitted; zero counts are rare,
+            // so the compacting walk only runs when a leaf holds one
+            bool zero = false;
+            if constexpr (HAS_CNT)
+                for (int i = c0; i < c1; ++i) zero |= S.val[cur][i] == 0;
+            const bool any_zero = __syncthreads_or(zero);
+            uint32_t out_base = 0, n_out = n_runs;
+            if (any_zero) {
+                uint32_t nz = 0;
+                int run = (int)rid0 - 1;
+                unsigned long long a = carry;
+                for (int i = c0; i < c1; ++i) {
+                    const uint32_t k = S.key[cur][i];
+                    if (i == 0 || k != S.key[cur][i - 1]) { ++run; a = 0; }
+                    unsigned long long v = 1;
+                    if constexpr (HAS_CNT) v = S.val[cur][i];
+                    a += v;
+                    if ((i == (int)n - 1 || S.key[cur][i + 1] != k) && a) ++nz;
+                }
+                out_base = block_exclusive_scan<uint32_t, THREADS>(nz, sw, &n_out);
+            }
             int run = (int)rid0 - 1;
+            uint32_t o = out_base;
             unsigned long long a = carry;
             for (int i = c0; i < c1; ++i) {
                 const uint32_t k = S.key[cur][i];
@@ -491,10 +513,17 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 if constexpr (HAS_CNT) v = S.val[cur][i];
                 a += v;
                 if (i == (int)n - 1 || S.key[cur][i + 1] != k) {
-                    w.tmp_key[start + run] = k;
-                    w.tmp_val[start + run] = a;
+                    if (!any_zero) {
+                        w.tmp_key[start + run] = k;
+                        w.tmp_val[start + run] = a;
+                    } else if (a) {
+                        w.tmp_key[start + o] = k;
+                        w.tmp_val[start + o] = a;
+                        ++o;
+                    }
                 }
             }
+            n_runs = n_out;
             if (threadIdx.x == 0) w.leaf_d[l] = n_runs;
             __syncthreads();
         } else {
