@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: attributed PC samples per second on one GB300.
+
+One step = attribution of every sample of one synthetic buffer to the
+structure tree plus exact aggregation into sorted (ctx, node, stall) raw
+metrics (hpa_attribute_samples).  The default workload is the large plain
+profile: 40,000 functions / 512 MB code / 2,000,000 line ranges,
+2x10^8 samples with uint32 counts, 20,000 launch contexts.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+instead (single-threaded, on a bounded sample of the same workload).
+Under torchrun every rank runs an independent replica on its own GPU
+(the analysis of independent sample buffers needs no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "attributed PC samples/sec"
+UNIT = "samples/s"
+FALLBACK_HBM = 6800.0
+
+
+def workload(name: str):
+    return {"large": synth.LARGE, "plain": synth.PLAIN}[name]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" == r[5 + i].strip()})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(w, B, target_s: float, max_n: int):
+    """Samples/s of the oracle on the first n samples of the workload."""
+    import oracle
+    oracle.build()
+    n = 100_000
+    S = w.samples(B, device="cpu", n=n)
+    t = time.perf_counter()
+    oracle.attribute_samples(B, S)
+    est = max(time.perf_counter() - t, 1e-3) / n
+    n = int(min(max_n, max(n, target_s / est)))
+    S = w.samples(B, device="cpu", n=n)
+    t = time.perf_counter()
+    k = oracle.attribute_samples(B, S)
+    dt = time.perf_counter() - t
+    assert k.status == 0
+    return n / dt, n, dt
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    B = w.binary()
+    import oracle
+    oracle.build()
+    # one bounded sample per step, sized for about args.ref_step_s seconds
+    rate, _, _ = cpu_oracle_rate(w, B, 1.0, 2_000_000)
+    n = int(min(w.n_samples, max(10_000, rate * args.ref_step_s)))
+    S = w.samples(B, device="cpu", n=n)
+    for _ in range(args.warmup):
+        oracle.attribute_samples(B, S)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.attribute_samples(B, S)
+    dt = time.perf_counter() - t
+    v = n * args.steps / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "samples_per_step": n, "note": "CPU oracle, bounded sample"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {n} samples of {w.name}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "plain"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-s", type=float, default=4.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    from paper_2109_06931_gb300 import hpa as H
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    B = w.binary()
+    S = w.samples(B, device=dev)
+    N = S.n
+    stream = torch.cuda.Stream(dev)
+    h = H.Hpa(local, stream=stream)
+    bid = h.load_structure(B)
+    out = H.new_profile(N, S.n_stall, dev)
+    h.reserve(N, S.n_ctx)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        h.attribute_samples(bid, S, out=out)
+    h.sync()
+    K = out.count()
+
+    # ---- device-timed steps (inputs resident in HBM, larger than L2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = h.launches()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            h.attribute_samples(bid, S, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    h.sync()
+    launches = (h.launches() - l0) // args.steps
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world, dev)
+    barrier(world)
+    value = N * world / (ms / 1e3)
+
+    # ---- per-phase kernel times (CUDA events on the launching stream)
+    h.set_phase_timing(True)
+    for _ in range(args.steps):
+        h.attribute_samples(bid, S, out=out)
+    h.sync()
+    ph, calls = h.phase_times()
+    h.set_phase_timing(False)
+    ph = {k: v / max(calls, 1) for k, v in ph.items()}
+    has_cnt = S.count is not None
+    in_b = 17 if has_cnt else 13
+    rec_b = 8 if has_cnt else 4
+    # algorithmic bytes per launch of each phase (per-unit figures x units)
+    algo = {"hist+plan": 4 * N, "attribute+scatter": (in_b + rec_b) * N, "big-split": 0,
+            "leaf sort/reduce": rec_b * N + 12 * K, "emit": 12 * K + 17 * K}
+    dom = max(ph, key=ph.get)
+    peak, peak_kind = peaks()
+    ach = algo[dom] / (ph[dom] / 1e3) / 1e9 if ph[dom] > 0 else 0.0
+    path_bytes = in_b * N + 17 * K
+    path_ach = path_bytes / (ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda t: t.cpu().pin_memory()
+        hp = {"pc": pin(S.pc), "ctx": pin(S.ctx), "stall": pin(S.stall), "count": pin(S.count) if has_cnt else None}
+        del S
+        torch.cuda.empty_cache()
+        cap = K
+        ho = {"ctx": torch.empty(cap, dtype=torch.int32).pin_memory(), "node": torch.empty(cap, dtype=torch.int32).pin_memory(),
+              "stall": torch.empty(cap, dtype=torch.uint8).pin_memory(), "val": torch.empty(cap, dtype=torch.int64).pin_memory(),
+              "n": torch.zeros(1, dtype=torch.int64), "total": torch.zeros(32, dtype=torch.int64),
+              "unknown": torch.zeros(32, dtype=torch.int64)}
+        steps_e2e = max(1, min(args.steps, 5))
+        h.attribute_samples_host(bid, hp["pc"], hp["ctx"], hp["stall"], hp["count"], w.n_ctx, w.n_stall,
+                                 capacity=cap, out=ho)
+        barrier(world)
+        t = time.perf_counter()
+        for _ in range(steps_e2e):
+            h.attribute_samples_host(bid, hp["pc"], hp["ctx"], hp["stall"], hp["count"], w.n_ctx, w.n_stall,
+                                     capacity=cap, out=ho)
+        dt = (time.perf_counter() - t) / steps_e2e
+        dt = max_over_ranks(dt, world, dev)
+        assert int(ho["n"][0]) == K
+        e2e = {"value": N * world / dt, "unit": UNIT, "h2d_bytes_per_step": in_b * N,
+               "d2h_bytes_per_step": 17 * K + 8 + 16 * w.n_stall, "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, n_cpu, dt_cpu = cpu_oracle_rate(w, B, args.cpu_seconds, 20_000_000)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {n_cpu} samples of {w.name} ({dt_cpu:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": w.name, "samples": N, "keys": K, "functions": w.n_funcs,
+                       "line_ranges": w.n_line_ranges, "contexts": w.n_ctx, "counts": has_cnt,
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "peak_kind": peak_kind, "traffic": None,
+                         "algorithmic_bytes_per_launch": algo[dom], "ms_per_launch": ph[dom]},
+            "path_roofline": {"achieved": path_ach, "frac": path_ach / peak, "unit": "GB/s",
+                              "algorithmic_bytes_per_step": path_bytes},
+            "phases_ms": ph,
+            "clocks": clk.summary(),
+            "gpu_launches": int(launches * args.steps),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

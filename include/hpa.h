@@ -210,6 +210,14 @@ hpa_status hpa_sync(hpa_handle* h, uint64_t* bad);
 hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t max_groups);
 /* Number of kernels the handle has launched so far. */
 uint64_t hpa_kernel_launches(hpa_handle* h);
+/* Per-phase timing of the aggregation pipeline with CUDA events recorded on
+ * the handle's stream between its kernels (enable != 0 starts a fresh
+ * accumulation; 0 stops).  Phases: 0 group histogram and plan, 1 attribute +
+ * scatter, 2 big-group split, 3 leaf sort/reduce, 4 emit.                    */
+hpa_status hpa_set_phase_timing(hpa_handle* h, int enable);
+/* After hpa_sync: ms[i] = total milliseconds of phase i over `*calls` timed
+ * calls (i < n_max).  Returns HPA_OK; *n_phases receives the phase count.    */
+hpa_status hpa_phase_times(hpa_handle* h, uint32_t n_max, double* ms, uint64_t* calls, uint32_t* n_phases);
 
 /* ---- structure (Section 5, Section 6.3 steps 1 and 3) ------------------- */
 

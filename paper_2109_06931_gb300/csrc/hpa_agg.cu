@@ -648,7 +648,8 @@ static void launch_leaf(const AggWork& w, cudaStream_t s, int sms, int per_sm) {
     k_leaf<THREADS, CAP, HAS_CNT><<<sms * per_sm, THREADS, Cfg::SMEM, s>>>(w);
 }
 
-void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
+void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
+    if (ev) cudaEventRecord(ev[0], s);
     cudaMemsetAsync(w.grp_hist, 0, sizeof(uint32_t) * ((size_t)w.G + 1), s);
     cudaMemsetAsync(w.leaf_d, 0, sizeof(uint32_t) * ((size_t)w.L_max + 1), s);
     cudaMemsetAsync(w.buf_bad, 0, sizeof(unsigned long long) * w.n_buf, s);
@@ -663,6 +664,7 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
     scan_u32(w.item_nleaf, w.item_nleaf, w.G, w.scan_tmp, s, launches);
     k_leaves<<<std::max(gblocks, 1), 256, 0, s>>>(w);
     *launches += 5;
+    if (ev) cudaEventRecord(ev[1], s);
     const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;
     const size_t acc_bytes = (size_t)nsm * 256 * 8;
     const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
@@ -673,7 +675,11 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
         cudaFuncSetAttribute(k_attr_scatter<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
         k_attr_scatter<false, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
     }
+    *launches += 1;
+    if (ev) cudaEventRecord(ev[2], s);
     k_big_partition<<<sms * 4, 256, 0, s>>>(w);
+    *launches += 1;
+    if (ev) cudaEventRecord(ev[3], s);
     if (w.cap == LEAF_CAP_LARGE) {
         if (w.has_cnt) launch_leaf<512, LEAF_CAP_LARGE, true>(w, s, sms, 1);
         else launch_leaf<512, LEAF_CAP_LARGE, false>(w, s, sms, 1);
@@ -681,10 +687,13 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
         if (w.has_cnt) launch_leaf<256, LEAF_CAP_SMALL, true>(w, s, sms, 2);
         else launch_leaf<256, LEAF_CAP_SMALL, false>(w, s, sms, 2);
     }
+    *launches += 1;
+    if (ev) cudaEventRecord(ev[4], s);
     scan_u32(w.leaf_d, w.leaf_d, w.L_max, w.scan_tmp, s, launches);
     k_emit<<<sms * 8, 256, 0, s>>>(w);
     k_finalize<<<1, 256, 0, s>>>(w);
-    *launches += 5;
+    *launches += 2;
+    if (ev) cudaEventRecord(ev[5], s);
 }
 
 }  // namespace hpa

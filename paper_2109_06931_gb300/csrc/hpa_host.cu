@@ -146,6 +146,8 @@ hpa_handle::~hpa_handle() {
     if (d_bins) cudaFree(d_bins);
     if (staging_event) cudaEventDestroy(staging_event);
     for (auto& g : graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& v : ev_pool) for (cudaEvent_t e : v) cudaEventDestroy(e);
+    for (auto& v : ev_pending) for (cudaEvent_t e : v) cudaEventDestroy(e);
     if (host_io) cudaFree(host_io);
     if (pinned_io) cudaFreeHost(pinned_io);
 }
@@ -161,11 +163,62 @@ extern "C" const char* hpa_last_error(hpa_handle* h) { return h ? h->err.c_str()
 
 extern "C" uint64_t hpa_kernel_launches(hpa_handle* h) { return h ? h->launches : 0; }
 
+cudaEvent_t* hpa_handle::phase_events() {
+    std::vector<cudaEvent_t> v;
+    if (!ev_pool.empty()) {
+        v = std::move(ev_pool.back());
+        ev_pool.pop_back();
+    } else {
+        v.resize(N_PHASES + 1);
+        for (auto& e : v) cudaEventCreate(&e);
+    }
+    ev_pending.push_back(std::move(v));
+    return ev_pending.back().data();
+}
+
+void hpa_handle::collect_phase_times() {
+    for (auto& v : ev_pending) {
+        for (int i = 0; i < N_PHASES; ++i) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, v[i], v[i + 1]) == cudaSuccess) phase_ms[i] += ms;
+            else cudaGetLastError();
+        }
+        ++phase_calls;
+        ev_pool.push_back(std::move(v));
+    }
+    ev_pending.clear();
+}
+
+extern "C" hpa_status hpa_set_phase_timing(hpa_handle* h, int enable) {
+    if (!h) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    h->collect_phase_times();
+    h->timing = enable != 0;
+    if (enable) {
+        for (int i = 0; i < N_PHASES; ++i) h->phase_ms[i] = 0;
+        h->phase_calls = 0;
+    }
+    return HPA_OK;
+}
+
+extern "C" hpa_status hpa_phase_times(hpa_handle* h, uint32_t n_max, double* ms, uint64_t* calls, uint32_t* n_phases) {
+    if (!h) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    h->collect_phase_times();
+    for (uint32_t i = 0; i < n_max && i < (uint32_t)N_PHASES; ++i) if (ms) ms[i] = h->phase_ms[i];
+    if (calls) *calls = h->phase_calls;
+    if (n_phases) *n_phases = N_PHASES;
+    return HPA_OK;
+}
+
 extern "C" hpa_status hpa_sync(hpa_handle* h, uint64_t* bad) {
     if (!h) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     hpa_status st = h->cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (st) return st;
+    h->collect_phase_times();
     DevStatus ds;
     st = h->cuda(cudaMemcpy(&ds, h->d_status, sizeof ds, cudaMemcpyDeviceToHost), "read device status");
     if (st) return st;
@@ -468,7 +521,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         if (outs[b].total) cudaMemsetAsync(outs[b].total, 0, 8 * in[b].n_stall, stream);
         if (outs[b].unknown) cudaMemsetAsync(outs[b].unknown, 0, 8 * in[b].n_stall, stream);
     }
-    run_aggregate(w, stream, sms, &launches);
+    run_aggregate(w, stream, sms, &launches, timing ? phase_events() : nullptr);
     return cuda(cudaGetLastError(), "aggregation launch");
 }
 

@@ -76,6 +76,13 @@ struct hpa_handle {
     void* host_io = nullptr;
     size_t host_io_cap = 0;
     void* pinned_io = nullptr;
+    // phase timing
+    bool timing = false;
+    std::vector<std::vector<cudaEvent_t>> ev_pool, ev_pending;
+    double phase_ms[hpa::N_PHASES] = {0};
+    uint64_t phase_calls = 0;
+    cudaEvent_t* phase_events();
+    void collect_phase_times();
 
     ~hpa_handle();
     hpa_status fail(hpa_status st, const char* fmt, ...);

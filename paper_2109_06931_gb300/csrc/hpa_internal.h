@@ -86,6 +86,8 @@ size_t scan_tmp_words(uint64_t n);
 void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cudaStream_t s, uint64_t* launches);
 
 // aggregation pipeline (A1 + A2) over a prepared AggWork
-void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
+constexpr int N_PHASES = 5;
+// ev (may be null): N_PHASES + 1 events recorded at the phase boundaries
+void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev);
 
 }  // namespace hpa

@@ -72,7 +72,8 @@ class hpa_derived(C.Structure):
 EXPORTS = ["hpa_create", "hpa_destroy", "hpa_last_error", "hpa_sync", "hpa_reserve", "hpa_kernel_launches",
            "hpa_load_structure", "hpa_unload_structure", "hpa_binary_info_get", "hpa_attribute_samples",
            "hpa_attribute_samples_host", "hpa_attribute_batch", "hpa_apportion_callgraph",
-           "hpa_propagate_inclusive", "hpa_derive_metrics"]
+           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_set_phase_timing", "hpa_phase_times"]
+PHASES = ["hist+plan", "attribute+scatter", "big-split", "leaf sort/reduce", "emit"]
 
 _lib = None
 
@@ -106,6 +107,8 @@ def lib(build_if_needed: bool = True):
         L.hpa_propagate_inclusive.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile),
                                               C.POINTER(hpa_cct), vp]
         L.hpa_derive_metrics.argtypes = [H, C.POINTER(C.POINTER(hpa_profile)), C.c_uint32, C.POINTER(hpa_derived)]
+        L.hpa_set_phase_timing.argtypes = [H, C.c_int]
+        L.hpa_phase_times.argtypes = [H, C.c_uint32, vp, u64p, u32p]
         for f in EXPORTS:
             if f not in ("hpa_last_error", "hpa_kernel_launches"):
                 getattr(L, f).restype = C.c_int32
@@ -215,6 +218,17 @@ class Hpa:
     def launches(self) -> int:
         return int(self.L.hpa_kernel_launches(self.h))
 
+    def set_phase_timing(self, on: bool):
+        self.check(self.L.hpa_set_phase_timing(self.h, 1 if on else 0))
+
+    def phase_times(self):
+        """{phase name: total ms} and the number of timed calls."""
+        ms = np.zeros(8, np.float64)
+        calls = C.c_uint64()
+        n = C.c_uint32()
+        self.check(self.L.hpa_phase_times(self.h, 8, _ptr(ms), C.byref(calls), C.byref(n)))
+        return {PHASES[i]: float(ms[i]) for i in range(n.value)}, int(calls.value)
+
     def reserve(self, max_samples: int, max_groups: int):
         self.check(self.L.hpa_reserve(self.h, max_samples, max_groups))
 
@@ -262,13 +276,15 @@ class Hpa:
         out.n_ctx, out.n_stall = s.n_ctx, s.n_stall
         return out
 
-    def attribute_samples_host(self, bid: int, pc, ctx, stall, count, n_ctx, n_stall, capacity=None):
-        """Host arrays in, host arrays out (numpy or pinned CPU tensors)."""
+    def attribute_samples_host(self, bid: int, pc, ctx, stall, count, n_ctx, n_stall, capacity=None, out=None):
+        """Host arrays in, host arrays out (numpy arrays or CPU tensors, pinned for full speed).
+        out: optional dict of preallocated host arrays ctx, node, stall, val, n, total, unknown."""
         n = int(pc.shape[0])
         cap = n if capacity is None else capacity
-        out = dict(ctx=np.empty(cap, np.uint32), node=np.empty(cap, np.uint32), stall=np.empty(cap, np.uint8),
-                   val=np.empty(cap, np.uint64), n=np.zeros(1, np.uint64), total=np.zeros(HPA_MAX_STALL, np.uint64),
-                   unknown=np.zeros(HPA_MAX_STALL, np.uint64))
+        if out is None:
+            out = dict(ctx=np.empty(cap, np.uint32), node=np.empty(cap, np.uint32), stall=np.empty(cap, np.uint8),
+                       val=np.empty(cap, np.uint64), n=np.zeros(1, np.uint64), total=np.zeros(HPA_MAX_STALL, np.uint64),
+                       unknown=np.zeros(HPA_MAX_STALL, np.uint64))
         ci = self.samples_c(pc, ctx, stall, count, n_ctx, n_stall)
         co = hpa_profile(cap, _ptr(out["ctx"]), _ptr(out["node"]), _ptr(out["stall"]), _ptr(out["val"]),
                          _ptr(out["n"]), _ptr(out["total"]), _ptr(out["unknown"]), 0, 0)

@@ -383,7 +383,10 @@ def make_samples(seed: int, b: Binary, n: int, n_ctx: int, zipf_s: float,
         ccdf = torch.from_numpy(c).to(dev)
     flo = torch.from_numpy(b.func_lo.view(np.int64)).to(dev)
     nsl = torch.from_numpy(((b.func_hi - b.func_lo) // np.uint64(16)).astype(np.int64)).to(dev)
-    pcs, ctxs, stalls, cnts = [], [], [], []
+    pcs = [torch.zeros(0, dtype=torch.int64, device=dev)]
+    ctxs = [torch.zeros(0, dtype=torch.int32, device=dev)]
+    stalls = [torch.zeros(0, dtype=torch.uint8, device=dev)]
+    cnts = [torch.zeros(0, dtype=torch.int32, device=dev)]
     for a in range(start, start + n, chunk):
         e = min(start + n, a + chunk)
         idx = torch.arange(a, e, device=dev, dtype=torch.int64)
