@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "plain"])
+    ap.add_argument("--samples", type=int, default=0, help="override the sample count (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -181,6 +182,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload(args.workload)
+    if args.samples:
+        w = synth.scaled(w, args.samples / w.n_samples)
     B = w.binary()
     S = w.samples(B, device=dev)
     N = S.n
