@@ -354,16 +354,17 @@ __global__ void __launch_bounds__(256) k_big_partition(AggWork w) {
             const uint32_t sub = w.rec_sub[i];
             const uint32_t p = s0 + atomicAdd(&hist[sub >> shift], 1u);
             w.rec2_sub[p] = sub;
-            if (w.has_cnt) w.rec2_cnt[p] = w.rec_cnt[i];
+            if (w.val64) w.rec2_v64[p] = w.rec_v64[i];
+            else if (w.has_cnt) w.rec2_cnt[p] = w.rec_cnt[i];
         }
         __syncthreads();
     }
 }
 
 // ------------------------------------------------------------------ K11: leaves
-template <int THREADS, int CAP, bool HAS_CNT>
+template <int THREADS, int CAP, bool HAS_CNT, typename V>
 struct LeafCfg {
-    using Sort = BlockRadix<THREADS, CAP, 8, uint32_t, HAS_CNT>;
+    using Sort = BlockRadix<THREADS, CAP, 8, V, HAS_CNT>;
     static constexpr int EPT = (CAP + THREADS - 1) / THREADS;
     static constexpr size_t SORT_BYTES = sizeof(typename Sort::Smem);
     static constexpr int WD = 8192;                              // dense window (uint64 counters)
@@ -410,9 +411,9 @@ __device__ __forceinline__ unsigned long long block_seg_carry(SegPair x, SegPair
     return pre.s;
 }
 
-template <int THREADS, int CAP, bool HAS_CNT>
+template <int THREADS, int CAP, bool HAS_CNT, typename V>
 __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
-    using Cfg = LeafCfg<THREADS, CAP, HAS_CNT>;
+    using Cfg = LeafCfg<THREADS, CAP, HAS_CNT, V>;
     using Sort = typename Cfg::Sort;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename Sort::Smem& S = *reinterpret_cast<typename Sort::Smem*>(smem_raw);
@@ -428,7 +429,9 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
         const uint32_t info = w.leaf_info[l];
         const uint32_t n = end - start;
         const uint32_t* src_sub = (info & 1u) ? w.rec2_sub : w.rec_sub;
-        const uint32_t* src_cnt = (info & 1u) ? w.rec2_cnt : w.rec_cnt;
+        const V* src_cnt;
+        if constexpr (sizeof(V) == 8) src_cnt = (const V*)((info & 1u) ? w.rec2_v64 : w.rec_v64);
+        else src_cnt = (const V*)((info & 1u) ? w.rec2_cnt : w.rec_cnt);
         if (n == 0) {
             if (threadIdx.x == 0) w.leaf_d[l] = 0;
             continue;
@@ -636,51 +639,37 @@ __global__ void k_finalize(AggWork w) {
 }
 
 // ------------------------------------------------------------------ driver
-template <int THREADS, int CAP, bool HAS_CNT>
+template <int THREADS, int CAP, bool HAS_CNT, typename V = uint32_t>
 static void launch_leaf(const AggWork& w, cudaStream_t s, int sms, int per_sm) {
-    using Cfg = LeafCfg<THREADS, CAP, HAS_CNT>;
+    using Cfg = LeafCfg<THREADS, CAP, HAS_CNT, V>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_leaf<THREADS, CAP, HAS_CNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_leaf<THREADS, CAP, HAS_CNT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg::SMEM);
         attr_set = true;
     }
-    k_leaf<THREADS, CAP, HAS_CNT><<<sms * per_sm, THREADS, Cfg::SMEM, s>>>(w);
+    k_leaf<THREADS, CAP, HAS_CNT, V><<<sms * per_sm, THREADS, Cfg::SMEM, s>>>(w);
 }
 
-void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
-    if (ev) cudaEventRecord(ev[0], s);
-    cudaMemsetAsync(w.grp_hist, 0, sizeof(uint32_t) * ((size_t)w.G + 1), s);
-    cudaMemsetAsync(w.leaf_d, 0, sizeof(uint32_t) * ((size_t)w.L_max + 1), s);
-    cudaMemsetAsync(w.buf_bad, 0, sizeof(unsigned long long) * w.n_buf, s);
-    const int gblocks = (int)std::min<uint64_t>((w.G + 255) / 256, (uint64_t)sms * 16);
-    const int hist_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 8));
-    k_grp_hist<<<hist_blocks, 256, 0, s>>>(w);
+static void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
+    const int gblocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 255) / 256, (uint64_t)sms * 16));
     scan_u32(w.grp_hist, w.grp_hist, w.G, w.scan_tmp, s, launches);
-    k_item_flags<<<std::max(gblocks, 1), 256, 0, s>>>(w);
+    k_item_flags<<<gblocks, 256, 0, s>>>(w);
     scan_u32(w.item_id, w.item_id, w.G, w.scan_tmp, s, launches);
-    k_items<<<std::max(gblocks, 1), 256, 0, s>>>(w);
-    k_items_size<<<std::max(gblocks, 1), 256, 0, s>>>(w);
+    k_items<<<gblocks, 256, 0, s>>>(w);
+    k_items_size<<<gblocks, 256, 0, s>>>(w);
     scan_u32(w.item_nleaf, w.item_nleaf, w.G, w.scan_tmp, s, launches);
-    k_leaves<<<std::max(gblocks, 1), 256, 0, s>>>(w);
-    *launches += 5;
-    if (ev) cudaEventRecord(ev[1], s);
-    const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;
-    const size_t acc_bytes = (size_t)nsm * 256 * 8;
-    const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
-    if (w.has_cnt) {
-        cudaFuncSetAttribute(k_attr_scatter<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
-        k_attr_scatter<true, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
-    } else {
-        cudaFuncSetAttribute(k_attr_scatter<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
-        k_attr_scatter<false, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
-    }
-    *launches += 1;
-    if (ev) cudaEventRecord(ev[2], s);
+    k_leaves<<<gblocks, 256, 0, s>>>(w);
+    *launches += 4;
+}
+
+static void run_finish(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
     k_big_partition<<<sms * 4, 256, 0, s>>>(w);
     *launches += 1;
     if (ev) cudaEventRecord(ev[3], s);
-    if (w.cap == LEAF_CAP_LARGE) {
+    if (w.val64) {
+        launch_leaf<256, LEAF_CAP_SMALL, true, uint64_t>(w, s, sms, 1);
+    } else if (w.cap == LEAF_CAP_LARGE) {
         if (w.has_cnt) launch_leaf<512, LEAF_CAP_LARGE, true>(w, s, sms, 1);
         else launch_leaf<512, LEAF_CAP_LARGE, false>(w, s, sms, 1);
     } else {
@@ -694,6 +683,81 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
     k_finalize<<<1, 256, 0, s>>>(w);
     *launches += 2;
     if (ev) cudaEventRecord(ev[5], s);
+}
+
+static void clear_work(const AggWork& w, cudaStream_t s) {
+    cudaMemsetAsync(w.grp_hist, 0, sizeof(uint32_t) * ((size_t)w.G + 1), s);
+    cudaMemsetAsync(w.leaf_d, 0, sizeof(uint32_t) * ((size_t)w.L_max + 1), s);
+    cudaMemsetAsync(w.buf_bad, 0, sizeof(unsigned long long) * w.n_buf, s);
+}
+
+void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
+    if (ev) cudaEventRecord(ev[0], s);
+    clear_work(w, s);
+    const int hist_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 8));
+    k_grp_hist<<<hist_blocks, 256, 0, s>>>(w);
+    *launches += 1;
+    run_plan(w, s, sms, launches);
+    if (ev) cudaEventRecord(ev[1], s);
+    const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;
+    const size_t acc_bytes = (size_t)nsm * 256 * 8;
+    const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
+    if (w.has_cnt) {
+        cudaFuncSetAttribute(k_attr_scatter<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
+        k_attr_scatter<true, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
+    } else {
+        cudaFuncSetAttribute(k_attr_scatter<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
+        k_attr_scatter<false, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
+    }
+    *launches += 1;
+    if (ev) cudaEventRecord(ev[2], s);
+    run_finish(w, s, sms, launches, ev);
+}
+
+// ------------------------------------------------------------------ inclusive over the structure tree
+// (Section 6.1: values propagate up the tree).  Each key is expanded to its
+// node and every ancestor up to the function node, then the expanded records
+// are aggregated by the same plan / leaf / emit kernels with 64-bit values.
+__global__ void k_expand_hist(AggWork w, ExpandSrc x) {
+    const uint64_t K = min(*x.n_keys, x.cap);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = x.ctx[i], n = x.node[i];
+        if (c >= x.n_ctx || (n != UNKNOWN && n >= x.M)) { atomicAdd(&w.buf_bad[0], 1ull); continue; }
+        atomicAdd(&w.grp_hist[c], n == UNKNOWN ? 1u : x.depth[n] + 1u);
+    }
+}
+
+__global__ void k_expand_scatter(AggWork w, ExpandSrc x) {
+    const uint64_t K = min(*x.n_keys, x.cap);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = x.ctx[i], n0 = x.node[i];
+        if (c >= x.n_ctx || (n0 != UNKNOWN && n0 >= x.M)) continue;
+        const uint32_t r = x.stall[i];
+        const uint64_t v = x.val[i];
+        const uint32_t cnt = n0 == UNKNOWN ? 1u : x.depth[n0] + 1u;
+        uint32_t slot = atomicAdd(&w.grp_cursor[c], cnt);
+        if (n0 == UNKNOWN) {
+            w.rec_sub[slot] = (x.M << w.sb) | r;
+            w.rec_v64[slot] = v;
+            continue;
+        }
+        uint32_t n = n0;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            w.rec_sub[slot + k] = (n << w.sb) | r;
+            w.rec_v64[slot + k] = v;
+            n = x.parent[n];
+        }
+    }
+}
+
+void run_expand_aggregate(const AggWork& w, const ExpandSrc& x, cudaStream_t s, int sms, uint64_t* launches) {
+    clear_work(w, s);
+    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((x.cap + 255) / 256, (uint64_t)sms * 8));
+    k_expand_hist<<<blocks, 256, 0, s>>>(w, x);
+    run_plan(w, s, sms, launches);
+    k_expand_scatter<<<blocks, 256, 0, s>>>(w, x);
+    *launches += 2;
+    run_finish(w, s, sms, launches, nullptr);
 }
 
 }  // namespace hpa

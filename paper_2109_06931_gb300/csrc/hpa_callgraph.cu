@@ -163,6 +163,9 @@ hpa_status build_callgraph(hpa_handle* h, Binary* B) {
     uint32_t* par;
     if ((st = upload(h, B, B->node_parent, &par))) return st;
     B->d_node_parent = par;
+    uint32_t* dep;
+    if ((st = upload(h, B, B->node_depth, &dep))) return st;
+    B->d_node_depth = dep;
     return HPA_OK;
 }
 

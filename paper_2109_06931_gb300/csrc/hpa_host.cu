@@ -95,19 +95,6 @@ Binary* hpa_handle::binary(uint32_t id) {
     return bins[id];
 }
 
-// Arena carve-out helper
-struct Carve {
-    char* base;
-    size_t off = 0;
-    template <typename T>
-    T* take(size_t n) {
-        off = (off + 255) & ~size_t(255);
-        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
-        off += n * sizeof(T);
-        return p;
-    }
-};
-
 // ------------------------------------------------------------------ create / destroy
 extern "C" hpa_status hpa_create(hpa_handle** out, int device, void* cuda_stream, const hpa_options* opt) {
     if (!out) return HPA_E_INVALID_ARG;
@@ -150,6 +137,7 @@ hpa_handle::~hpa_handle() {
     for (auto& v : ev_pending) for (cudaEvent_t e : v) cudaEventDestroy(e);
     if (host_io) cudaFree(host_io);
     if (pinned_io) cudaFreeHost(pinned_io);
+    if (cct_scratch) cudaFree(cct_scratch);
 }
 
 extern "C" hpa_status hpa_destroy(hpa_handle* h) {
@@ -414,6 +402,47 @@ extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary
 }
 
 // ------------------------------------------------------------------ aggregation calls
+// Scratch layout of one aggregation over N records in G groups (n_buf buffers).
+hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n, uint32_t cap, uint32_t sb,
+                                  uint32_t sbits, bool has_cnt, bool val64) {
+    const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
+    w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
+    w.span_log = std::min<uint32_t>(10, 32 - sbits);
+    w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt || val64; w.val64 = val64;
+    auto layout = [&](Carve& c) {
+        w.grp_hist = c.take<uint32_t>(G + 1);
+        w.grp_cursor = c.take<uint32_t>(G + 1);
+        w.item_id = c.take<uint32_t>(G + 1);
+        w.item_grp0 = c.take<uint32_t>(G + 1);
+        w.item_nleaf = c.take<uint32_t>(G + 1);
+        w.leaf_start = c.take<uint32_t>(L_max);
+        w.leaf_end = c.take<uint32_t>(L_max);
+        w.leaf_grp0 = c.take<uint32_t>(L_max);
+        w.leaf_info = c.take<uint32_t>(L_max);
+        w.leaf_d = c.take<uint32_t>(L_max + 1);
+        w.buf_first_leaf = c.take<uint32_t>(n + 1);
+        w.buf_bad = c.take<unsigned long long>(n);
+        w.rec_sub = c.take<uint32_t>(N + 1);
+        w.rec_cnt = (has_cnt && !val64) ? c.take<uint32_t>(N + 1) : nullptr;
+        w.rec2_sub = c.take<uint32_t>(N + 1);
+        w.rec2_cnt = (has_cnt && !val64) ? c.take<uint32_t>(N + 1) : nullptr;
+        w.rec_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
+        w.rec2_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
+        w.tmp_key = c.take<uint32_t>(N + 1);
+        w.tmp_val = c.take<uint64_t>(N + 1);
+        w.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max<uint64_t>(G, L_max)));
+    };
+    Carve probe{nullptr};
+    layout(probe);
+    hpa_status st = ensure_scratch(probe.off + 256);
+    if (st) return st;
+    Carve real{(char*)scratch};
+    layout(real);
+    w.bins = d_bins;
+    w.status = d_status;
+    return HPA_OK;
+}
+
 hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs) {
     if (n == 0) return HPA_OK;
     uint64_t N = 0, G = 0, tiles = 0;
@@ -447,40 +476,10 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     if (cap == 0) cap = (G && N / G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL;
     if (cap != LEAF_CAP_SMALL && cap != LEAF_CAP_LARGE)
         return fail(HPA_E_INVALID_ARG, "leaf_capacity must be 0, %u or %u", LEAF_CAP_SMALL, LEAF_CAP_LARGE);
-    const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
-
     AggWork w{};
-    w.G = (uint32_t)G; w.n_buf = n; w.n_tiles = tiles; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
-    w.span_log = std::min<uint32_t>(10, 32 - sbits);
-    w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt;
-    // scratch layout
-    auto layout = [&](Carve& c) {
-        w.grp_hist = c.take<uint32_t>(G + 1);
-        w.grp_cursor = c.take<uint32_t>(G + 1);
-        w.item_id = c.take<uint32_t>(G + 1);
-        w.item_grp0 = c.take<uint32_t>(G + 1);
-        w.item_nleaf = c.take<uint32_t>(G + 1);
-        w.leaf_start = c.take<uint32_t>(L_max);
-        w.leaf_end = c.take<uint32_t>(L_max);
-        w.leaf_grp0 = c.take<uint32_t>(L_max);
-        w.leaf_info = c.take<uint32_t>(L_max);
-        w.leaf_d = c.take<uint32_t>(L_max + 1);
-        w.buf_first_leaf = c.take<uint32_t>(n + 1);
-        w.buf_bad = c.take<unsigned long long>(n);
-        w.rec_sub = c.take<uint32_t>(N + 1);
-        w.rec_cnt = has_cnt ? c.take<uint32_t>(N + 1) : nullptr;
-        w.rec2_sub = c.take<uint32_t>(N + 1);
-        w.rec2_cnt = has_cnt ? c.take<uint32_t>(N + 1) : nullptr;
-        w.tmp_key = c.take<uint32_t>(N + 1);
-        w.tmp_val = c.take<uint64_t>(N + 1);
-        w.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max<uint64_t>(G, L_max)));
-    };
-    Carve probe{nullptr};
-    layout(probe);
-    hpa_status st = ensure_scratch(probe.off + 256);
+    hpa_status st = carve_work(w, N, G, n, cap, sb, sbits, has_cnt, false);
     if (st) return st;
-    Carve real{(char*)scratch};
-    layout(real);
+    w.n_tiles = tiles;
     // descriptors
     const size_t desc_bytes = n * sizeof(BufDev) + (n + 1) * 8 + (n + 1) * 4 + 512;
     if ((st = ensure_staging(desc_bytes))) return st;
@@ -515,8 +514,6 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     w.bufs = (const BufDev*)(ds + ((char*)hb - (char*)staging));
     w.buf_tile = (const uint64_t*)(ds + ((char*)htile - (char*)staging));
     w.buf_grp = (const uint32_t*)(ds + ((char*)hgrp - (char*)staging));
-    w.bins = d_bins;
-    w.status = d_status;
     for (uint32_t b = 0; b < n; ++b) {
         if (outs[b].total) cudaMemsetAsync(outs[b].total, 0, 8 * in[b].n_stall, stream);
         if (outs[b].unknown) cudaMemsetAsync(outs[b].unknown, 0, 8 * in[b].n_stall, stream);

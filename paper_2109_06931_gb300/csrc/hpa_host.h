@@ -42,7 +42,21 @@ struct Binary {
     uint32_t n_cnodes = 0, n_scc = 0, cdag_levels = 0;
     std::vector<uint32_t> cnode_of_func;
     const uint32_t* d_node_parent = nullptr;   // structure tree on the device
+    const uint32_t* d_node_depth = nullptr;
     ~Binary();
+};
+
+// Bump allocator over a scratch arena (base null: only measures the size).
+struct Carve {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
 };
 
 struct CachedGraph {
@@ -76,6 +90,8 @@ struct hpa_handle {
     void* host_io = nullptr;
     size_t host_io_cap = 0;
     void* pinned_io = nullptr;
+    void* cct_scratch = nullptr;
+    size_t cct_cap = 0;
     // phase timing
     bool timing = false;
     std::vector<std::vector<cudaEvent_t>> ev_pool, ev_pending;
@@ -94,6 +110,10 @@ struct hpa_handle {
     hpa::Binary* binary(uint32_t id);
     hpa_status refresh_bin_table();
     hpa_status aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs);
+    hpa_status carve_work(hpa::AggWork& w, uint64_t N, uint64_t G, uint32_t n_buf, uint32_t cap, uint32_t sb,
+                          uint32_t sbits, bool has_cnt, bool val64);
+    // descriptors of single-output pipelines (expansion, union) in the staging area
+    hpa_status stage_single_output(hpa::AggWork& w, uint32_t bin, uint32_t n_ctx, const hpa_profile& out);
 };
 
 namespace hpa {

@@ -58,10 +58,13 @@ struct AggWork {
     uint32_t* leaf_d;      // [L_max+1] -> exclusive scan -> leaf_out
     uint32_t* buf_first_leaf;     // [n_buf + 1]
     unsigned long long* buf_bad;  // [n_buf]
+    uint32_t val64;        // record values are uint64 (rec_v64) instead of uint32 (rec_cnt)
     uint32_t* rec_sub;     // [N]
-    uint32_t* rec_cnt;     // [N] (if has_cnt)
+    uint32_t* rec_cnt;     // [N] (if has_cnt and !val64)
     uint32_t* rec2_sub;    // [N]
     uint32_t* rec2_cnt;    // [N]
+    uint64_t* rec_v64;     // [N] (if val64)
+    uint64_t* rec2_v64;    // [N]
     uint32_t* tmp_key;     // [N]
     uint64_t* tmp_val;     // [N]
     uint32_t* scan_tmp;    // device-wide scan partials
@@ -89,5 +92,22 @@ void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cuda
 constexpr int N_PHASES = 5;
 // ev (may be null): N_PHASES + 1 events recorded at the phase boundaries
 void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev);
+
+// Keys of a profile expanded to every structure ancestor (inclusive metrics
+// over the structure tree): each key (ctx, node, stall, val) yields one record
+// per node on the path node -> function node; UNKNOWN yields itself only.
+struct ExpandSrc {
+    const uint32_t* ctx;
+    const uint32_t* node;
+    const uint8_t* stall;
+    const uint64_t* val;
+    const uint64_t* n_keys;   // device count of keys
+    uint64_t cap;             // host bound on the key count
+    const uint32_t* parent;   // structure tree
+    const uint32_t* depth;    // depth of each node (FUNC = 0)
+    uint32_t M;               // n_nodes (UNKNOWN is coded as M)
+    uint32_t n_ctx;
+};
+void run_expand_aggregate(const AggWork& w, const ExpandSrc& x, cudaStream_t s, int sms, uint64_t* launches);
 
 }  // namespace hpa

@@ -1,11 +1,5 @@
 // Entry points whose kernels live in later translation units.
 #include "hpa_host.h"
-extern "C" hpa_status hpa_apportion_callgraph(hpa_handle* h, uint32_t, const hpa_profile*, hpa_gpucct*) {
-    return h ? h->fail(HPA_E_INVALID_ARG, "not built yet") : HPA_E_INVALID_ARG;
-}
-extern "C" hpa_status hpa_propagate_inclusive(hpa_handle* h, uint32_t, const hpa_profile*, hpa_profile*, const hpa_cct*, uint64_t*) {
-    return h ? h->fail(HPA_E_INVALID_ARG, "not built yet") : HPA_E_INVALID_ARG;
-}
 extern "C" hpa_status hpa_derive_metrics(hpa_handle* h, const hpa_profile* const*, uint32_t, hpa_derived*) {
     return h ? h->fail(HPA_E_INVALID_ARG, "not built yet") : HPA_E_INVALID_ARG;
 }

@@ -186,6 +186,7 @@ class Hpa:
         if st:
             raise HpaError(st, "hpa_create failed")
         self._keep = []
+        self._depth = {}
 
     def close(self):
         if self.h:
@@ -248,6 +249,16 @@ class Hpa:
                           _ptr(arrs["cs_caller"]), _ptr(arrs["cs_callee"]), _ptr(arrs["cs_node"]))
         bid = C.c_uint32(0)
         self.check(self.L.hpa_load_structure(self.h, C.byref(s), C.byref(bid)))
+        # structure-tree depth bounds the inclusive expansion
+        par = arrs["node_parent"]
+        depth = np.zeros(par.shape[0], np.int64)
+        cur = np.arange(par.shape[0])
+        alive = par[cur] != HPA_NO_PARENT
+        while alive.any():
+            depth[alive] += 1
+            cur = np.where(alive, par[np.minimum(cur, par.shape[0] - 1)], cur)
+            alive = alive & (par[np.minimum(cur, par.shape[0] - 1)] != HPA_NO_PARENT)
+        self._depth[int(bid.value)] = int(depth.max()) if depth.size else 0
         return int(bid.value)
 
     def unload_structure(self, bid: int):
@@ -290,6 +301,52 @@ class Hpa:
                          _ptr(out["n"]), _ptr(out["total"]), _ptr(out["unknown"]), 0, 0)
         self.check(self.L.hpa_attribute_samples_host(self.h, bid, C.byref(ci), C.byref(co)))
         return out
+
+    def propagate_inclusive(self, bid: int, p: Profile, tree: bool = True, cct_parent: torch.Tensor | None = None,
+                            tree_capacity: int | None = None):
+        """Inclusive metrics (Section 6.1).  Returns (tree Profile or None, cct tensor [n_cct, n_stall] or None).
+        The input profile's key count bounds the expansion, so it is read first."""
+        k = p.count()
+        pin = p.c()
+        pin.capacity = k
+        tree_out = None
+        tc = None
+        if tree:
+            info, _ = self.binary_info(bid)
+            cap = tree_capacity if tree_capacity is not None else max(1, k * (self.max_depth(bid) + 1))
+            tree_out = new_profile(cap, p.n_stall, self.device)
+            tc = tree_out.c()
+        cct_out = None
+        cc = None
+        if cct_parent is not None:
+            n = int(cct_parent.shape[0])
+            cct_out = torch.empty((n, p.n_stall), dtype=torch.int64, device=self.device)
+            cc = hpa_cct(n, _ptr(cct_parent))
+        self.check(self.L.hpa_propagate_inclusive(self.h, bid, C.byref(pin), C.byref(tc) if tc is not None else None,
+                                                  C.byref(cc) if cc is not None else None,
+                                                  _ptr(cct_out) if cct_out is not None else None))
+        if tree_out is not None:
+            tree_out.n_ctx, tree_out.n_stall = p.n_ctx, p.n_stall
+        return tree_out, cct_out
+
+    def apportion_callgraph(self, bid: int, p: Profile, req_ctx):
+        """GPU calling context trees (Section 6.3) of the requested contexts.
+        Returns (incl [n_req, V, S+1] f32, a [n_req, E, S+1] f32, flags [n_req, E] u8)."""
+        info, _ = self.binary_info(bid)
+        req = torch.as_tensor(np.asarray(req_ctx, np.uint32).view(np.int32), device=self.device)
+        n = int(req.shape[0])
+        M = p.n_stall + 1
+        incl = torch.empty((n, info.n_cnodes, M), dtype=torch.float32, device=self.device)
+        a = torch.empty((n, info.n_calls, M), dtype=torch.float32, device=self.device)
+        flags = torch.empty((n, info.n_calls), dtype=torch.uint8, device=self.device)
+        g = hpa_gpucct(n, _ptr(req), _ptr(incl), _ptr(a), _ptr(flags))
+        pc = p.c()
+        self.check(self.L.hpa_apportion_callgraph(self.h, bid, C.byref(pc), C.byref(g)))
+        self._keep = [req]
+        return incl, a, flags
+
+    def max_depth(self, bid: int) -> int:
+        return self._depth.get(bid, 16)
 
     def attribute_batch(self, bids, samples, outs=None):
         n = len(samples)

@@ -1,0 +1,98 @@
+"""GPU parity of the approximate GPU calling context tree (Section 6.3):
+FP32 results from the GPU against the FP64 oracle within 1e-5 relative
+(exact zeros where the oracle is zero); edge flags bit-exact."""
+import json
+import os
+import types
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import samples_from_numpy
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2109_06931_gb300 import hpa
+    h = hpa.Hpa(0)
+    yield h
+    h.close()
+
+
+def check(res_gpu, ref, q_idx=None):
+    incl, a, flags = (t.cpu().numpy() for t in res_gpu)
+    assert incl.shape == ref.incl.shape and a.shape == ref.a.shape
+    for got, exp in ((incl, ref.incl), (a, ref.a)):
+        zero = exp == 0
+        assert (got[zero] == 0).all(), "nonzero where the oracle is exactly zero"
+        err = np.abs(got[~zero] - exp[~zero]) / np.abs(exp[~zero])
+        assert err.size == 0 or err.max() <= RTOL, f"max rel err {err.max()}"
+    assert np.array_equal(flags, ref.flags)
+
+
+def _gold_binary(g):
+    F = len(g["functions"])
+    cs = g["call_sites"]
+    M = len(g["node_func"])
+    lo = np.arange(M, dtype=np.uint64) * 16 + 4096
+    return types.SimpleNamespace(
+        range_lo=lo, range_hi=lo + np.uint64(16), range_node=np.arange(M, dtype=np.uint32),
+        node_parent=np.array(g["node_parent"], np.uint32), node_kind=np.array(g["node_kind"], np.uint8),
+        node_func=np.array(g["node_func"], np.uint32), n_funcs=F,
+        cs_caller=np.array(cs["caller"], np.uint32), cs_callee=np.array(cs["callee"], np.uint32),
+        cs_node=np.array(cs["node"], np.uint32)), lo
+
+
+@pytest.mark.parametrize("name", ["gpucct_fig5.json", "gpucct_selfcall.json"])
+def test_golden(H, name):
+    g = json.load(open(os.path.join(GOLD, name)))
+    B, lo = _gold_binary(g)
+    bid = H.load_structure(B)
+    info, cof = H.binary_info(bid)
+    assert info.n_cnodes == g["expected_V"] and cof.tolist() == g["expected_cnode_of_func"]
+    # samples: one record per key, PC = the node's range, count = the key's value
+    ks = np.array(g["keys"], np.uint64)
+    S = samples_from_numpy(lo[ks[:, 1].astype(np.int64)], ks[:, 0], ks[:, 2], ks[:, 3],
+                           max(g["req_ctx"]) + 1, g["n_stall"])
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    res = H.apportion_callgraph(bid, p, g["req_ctx"])
+    H.sync()
+    ref = oracle.apportion(B, g["n_stall"], oracle.attribute_samples(B, S), np.array(g["req_ctx"], np.uint32))
+    check(res, ref)
+
+
+def test_plain_workload(H):
+    w = synth.PLAIN
+    B = w.binary()
+    bid = H.load_structure(B)
+    S = w.samples(B, device="cuda")
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    req = np.arange(0, 500, 7, dtype=np.uint32)
+    res = H.apportion_callgraph(bid, p, req)
+    H.sync()
+    check(res, oracle.apportion(B, 16, oracle.attribute_samples(B, S), req))
+
+
+def test_recursive_sccs_large_graph(H):
+    """Call graph of the large binary (120,000 call sites, 50 recursive SCCs)."""
+    w = synth.LARGE
+    B = w.binary()
+    bid = H.load_structure(B)
+    info, _ = H.binary_info(bid)
+    assert info.n_scc >= 40
+    S = w.samples(B, device="cuda", n=2_000_000)
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    req = np.array([0, 1, 777, 19_999, 12_345], np.uint32)
+    res = H.apportion_callgraph(bid, p, req)
+    H.sync()
+    check(res, oracle.apportion(B, 16, oracle.attribute_samples(B, S), req))
