@@ -91,7 +91,7 @@ def cpu_oracle_rate(w, B, target_s: float, max_n: int):
     """Samples/s of the oracle on the first n samples of the workload."""
     import oracle
     oracle.build()
-    n = 100_000
+    n = 1_000_000
     S = w.samples(B, device="cpu", n=n)
     t = time.perf_counter()
     oracle.attribute_samples(B, S)
@@ -167,6 +167,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "plain"])
     ap.add_argument("--samples", type=int, default=0, help="override the sample count (profiling runs)")
+    ap.add_argument("--cursor-shift", type=int, default=None, help="scatter cursor padding (log2 words)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -188,7 +189,7 @@ def main():
     S = w.samples(B, device=dev)
     N = S.n
     stream = torch.cuda.Stream(dev)
-    h = H.Hpa(local, stream=stream)
+    h = H.Hpa(local, stream=stream, cursor_shift=args.cursor_shift)
     bid = h.load_structure(B)
     out = H.new_profile(N, S.n_stall, dev)
     h.reserve(N, S.n_ctx)

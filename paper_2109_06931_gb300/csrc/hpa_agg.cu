@@ -111,33 +111,48 @@ __device__ __forceinline__ uint32_t big_bits(uint32_t n, uint32_t cap, uint32_t 
 }
 
 // ------------------------------------------------------------------ K1: records per group
+// Each CTA takes a contiguous run of tiles.  A buffer with at most
+// HIST_SMEM_MAX contexts is counted in shared memory and flushed when the
+// CTA leaves that buffer; larger context spaces count in global memory.
 __global__ void __launch_bounds__(256) k_grp_hist(AggWork w) {
-    __shared__ uint32_t sh[2048];
-    for (uint64_t t = blockIdx.x; t < w.n_tiles; t += gridDim.x) {
+    extern __shared__ uint32_t sh[];
+    const uint64_t per = (w.n_tiles + gridDim.x - 1) / gridDim.x;
+    const uint64_t t0 = blockIdx.x * per, t1 = min(w.n_tiles, t0 + per);
+    uint32_t cur_b = 0xFFFFFFFFu, cur_n = 0, cur_base = 0;
+    bool priv = false;
+    auto flush = [&]() {
+        if (priv) {
+            __syncthreads();
+            for (uint32_t c = threadIdx.x; c < cur_n; c += blockDim.x)
+                if (sh[c]) atomicAdd(&w.grp_hist[cur_base + c], sh[c]);
+            __syncthreads();
+        }
+    };
+    for (uint64_t t = t0; t < t1; ++t) {
         const uint32_t b = upper_index<uint64_t>(w.buf_tile, w.n_buf, t);
-        const BufDev B = w.bufs[b];
+        const BufDev& B = w.bufs[b];
+        if (b != cur_b) {
+            flush();
+            cur_b = b; cur_n = B.n_ctx; cur_base = B.grp_base;
+            priv = cur_n <= HIST_SMEM_MAX;
+            if (priv) {
+                for (uint32_t c = threadIdx.x; c < cur_n; c += blockDim.x) sh[c] = 0;
+                __syncthreads();
+            }
+        }
         const uint64_t i0 = (t - B.tile_base) * TILE;
         const uint64_t i1 = min(i0 + TILE, B.n);
-        const bool priv = B.n_ctx <= 2048;
-        if (priv) {
-            for (uint32_t c = threadIdx.x; c < B.n_ctx; c += blockDim.x) sh[c] = 0;
-            __syncthreads();
-        }
+        const uint32_t* ctx = B.ctx;
         uint32_t bad = 0;
         for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const uint32_t c = __ldg(&B.ctx[i]);
-            if (c >= B.n_ctx) { ++bad; continue; }
+            const uint32_t c = __ldg(&ctx[i]);
+            if (c >= cur_n) { ++bad; continue; }
             if (priv) atomicAdd(&sh[c], 1u);
-            else atomicAdd(&w.grp_hist[B.grp_base + c], 1u);
+            else atomicAdd(&w.grp_hist[cur_base + c], 1u);
         }
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
-        if (priv) {
-            __syncthreads();
-            for (uint32_t c = threadIdx.x; c < B.n_ctx; c += blockDim.x)
-                if (sh[c]) atomicAdd(&w.grp_hist[B.grp_base + c], sh[c]);
-            __syncthreads();
-        }
     }
+    flush();
 }
 
 // ------------------------------------------------------------------ K3..K8: items and leaves
@@ -161,7 +176,7 @@ __global__ void k_item_flags(AggWork w) {
             }
         }
         w.item_id[g] = f;
-        w.grp_cursor[g] = s0;
+        w.grp_cursor[(size_t)g << w.cur_shift] = s0;
     }
 }
 
@@ -303,7 +318,7 @@ __global__ void __launch_bounds__(256) k_attr_scatter(AggWork w) {
             for (int u = 0; u < U; ++u) {
                 if (!ok[u]) continue;
                 const bool bad_stall = st[u] >= B.n_stall;
-                const uint32_t slot = atomicAdd(&w.grp_cursor[B.grp_base + c[u]], 1u);
+                const uint32_t slot = atomicAdd(&w.grp_cursor[(size_t)(B.grp_base + c[u]) << w.cur_shift], 1u);
                 w.rec_sub[slot] = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
                 if (HAS_CNT) w.rec_cnt[slot] = bad_stall ? 0u : cnt[u];
                 if (bad_stall) {
@@ -694,8 +709,11 @@ static void clear_work(const AggWork& w, cudaStream_t s) {
 void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
     clear_work(w, s);
-    const int hist_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 8));
-    k_grp_hist<<<hist_blocks, 256, 0, s>>>(w);
+    const size_t hsm = (size_t)HIST_SMEM_MAX * 4;
+    const int per_sm = 2;
+    const int hist_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * per_sm));
+    cudaFuncSetAttribute(k_grp_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+    k_grp_hist<<<hist_blocks, 256, hsm, s>>>(w);
     *launches += 1;
     run_plan(w, s, sms, launches);
     if (ev) cudaEventRecord(ev[1], s);
@@ -735,7 +753,7 @@ __global__ void k_expand_scatter(AggWork w, ExpandSrc x) {
         const uint32_t r = x.stall[i];
         const uint64_t v = x.val[i];
         const uint32_t cnt = n0 == UNKNOWN ? 1u : x.depth[n0] + 1u;
-        uint32_t slot = atomicAdd(&w.grp_cursor[c], cnt);
+        uint32_t slot = atomicAdd(&w.grp_cursor[(size_t)c << w.cur_shift], cnt);
         if (n0 == UNKNOWN) {
             w.rec_sub[slot] = (x.M << w.sb) | r;
             w.rec_v64[slot] = v;

@@ -148,9 +148,32 @@ struct BlockRadix {
         uint32_t key[2][CAP];
         V val[HAS_V ? 2 : 1][HAS_V ? CAP : 1];
         uint16_t rank[CAP];
-        uint32_t cnt[W * BINS];       // digit-major: cnt[d * W + w]
+        uint32_t cnt[W * BINS];       // warp-major: cnt[w * BINS + d] (conflict-free per warp)
         uint32_t sw[33];
     };
+
+    // Exclusive scan of the per-warp counts in digit-major, warp-minor order
+    // (entry e = d * W + w lives at cnt[w * BINS + d]).
+    __device__ static void scan_digit_major(Smem& s) {
+        const int base = threadIdx.x * SCAN_EPT;
+        uint32_t loc[SCAN_EPT];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < SCAN_EPT; ++i) {
+            const int e = base + i;
+            loc[i] = s.cnt[(e % W) * BINS + e / W];
+            sum += loc[i];
+        }
+        uint32_t tot;
+        uint32_t pre = block_exclusive_scan<uint32_t, THREADS>(sum, s.sw, &tot);
+#pragma unroll
+        for (int i = 0; i < SCAN_EPT; ++i) {
+            const int e = base + i;
+            s.cnt[(e % W) * BINS + e / W] = pre;
+            pre += loc[i];
+        }
+        __syncthreads();
+    }
 
     // Sorts s.key[0][0..n) (and s.val[0]) by their low `bits` bits.
     // Returns the buffer index (0 or 1) that holds the result.
@@ -172,20 +195,20 @@ struct BlockRadix {
                 const uint32_t d = ok ? ((s.key[cur][i] >> shift) & dmask) : 0xFFFFFFFFu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, d);
                 if (ok) {
-                    const uint32_t before = s.cnt[d * W + warp];
+                    const uint32_t before = s.cnt[warp * BINS + d];
                     s.rank[i] = (uint16_t)(before + __popc(peers & lanemask_lt()));
                 }
                 __syncwarp();
-                if (ok && (peers & lanemask_lt()) == 0) s.cnt[d * W + warp] += __popc(peers);
+                if (ok && (peers & lanemask_lt()) == 0) s.cnt[warp * BINS + d] += __popc(peers);
                 __syncwarp();
             }
             __syncthreads();
-            block_scan_array<uint32_t, THREADS, SCAN_EPT>(s.cnt, W * BINS, s.sw);
+            scan_digit_major(s);
             // pass B
             for (int i = lo + lane; i < hi; i += 32) {
                 const uint32_t k = s.key[cur][i];
                 const uint32_t d = (k >> shift) & dmask;
-                const uint32_t pos = s.cnt[d * W + warp] + s.rank[i];
+                const uint32_t pos = s.cnt[warp * BINS + d] + s.rank[i];
                 s.key[cur ^ 1][pos] = k;
                 if constexpr (HAS_V) s.val[cur ^ 1][pos] = s.val[cur][i];
             }

@@ -408,10 +408,13 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
     const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
     w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
     w.span_log = std::min<uint32_t>(10, 32 - sbits);
+    // scatter cursors padded to 2^cur_shift words (option reserved[0] = shift + 1)
+    w.cur_shift = opt.reserved[0] ? std::min<uint32_t>(opt.reserved[0] - 1, 6) : 3;
+    if (((G + 1) << w.cur_shift) > (64ull << 20)) w.cur_shift = 0;
     w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt || val64; w.val64 = val64;
     auto layout = [&](Carve& c) {
         w.grp_hist = c.take<uint32_t>(G + 1);
-        w.grp_cursor = c.take<uint32_t>(G + 1);
+        w.grp_cursor = c.take<uint32_t>((G + 1) << w.cur_shift);
         w.item_id = c.take<uint32_t>(G + 1);
         w.item_grp0 = c.take<uint32_t>(G + 1);
         w.item_nleaf = c.take<uint32_t>(G + 1);

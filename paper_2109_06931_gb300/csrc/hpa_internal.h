@@ -47,7 +47,8 @@ struct AggWork {
     uint32_t L_max;        // leaf table capacity
     uint32_t has_cnt;
     uint32_t* grp_hist;    // [G+1] -> exclusive scan -> seg_off
-    uint32_t* grp_cursor;  // [G]
+    uint32_t* grp_cursor;  // [G << cur_shift] scatter cursors, one per 2^cur_shift words
+    uint32_t cur_shift;
     uint32_t* item_id;     // [G+1] flags -> exclusive scan
     uint32_t* item_grp0;   // [G]
     uint32_t* item_nleaf;  // [G+1] -> exclusive scan -> leaf_base
@@ -77,6 +78,7 @@ struct AggWork {
 
 constexpr int TILE = 4096;            // samples per tile of the sample-reading kernels
 constexpr uint32_t HPA_MAX_STALL_DEV = 32;
+constexpr uint32_t HIST_SMEM_MAX = 24576;    // contexts counted in shared memory (96 KB)
 constexpr uint32_t LEAF_CAP_SMALL = 4096;   // 256 threads, two CTAs per SM
 constexpr uint32_t LEAF_CAP_LARGE = 11264;  // 512 threads, one CTA per SM
 constexpr int SCAN_THREADS = 512;

@@ -174,7 +174,7 @@ class Hpa:
     """One library handle bound to a CUDA device and stream."""
 
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, issued_mask: int = 1,
-                 leaf_capacity: int = 0):
+                 leaf_capacity: int = 0, cursor_shift: int | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("hpa needs a CUDA device; there is no CPU implementation")
         self.L = lib()
@@ -182,6 +182,8 @@ class Hpa:
         self.stream = stream or torch.cuda.current_stream(self.device)
         self.h = C.c_void_p()
         opt = hpa_options(issued_mask, leaf_capacity, 0)
+        if cursor_shift is not None:
+            opt.reserved[0] = cursor_shift + 1
         st = self.L.hpa_create(C.byref(self.h), device, C.c_void_p(self.stream.cuda_stream), C.byref(opt))
         if st:
             raise HpaError(st, "hpa_create failed")
