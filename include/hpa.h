@@ -126,7 +126,7 @@ typedef struct {
  * the number of keys written, or -- with status HPA_E_CAPACITY from hpa_sync --
  * the number needed.  total / unknown (device uint64[n_stall], may be NULL)
  * receive the per-stall sum of all counts and of the UNKNOWN ones.
- * n_ctx / n_stall are filled in by the producing call.                        */
+ * n_ctx / n_stall / n_nodes are filled in by the producing call.              */
 typedef struct {
     uint64_t capacity;
     uint32_t* key_ctx;
@@ -138,6 +138,8 @@ typedef struct {
     uint64_t* unknown;
     uint32_t n_ctx;
     uint32_t n_stall;
+    uint32_t n_nodes;     /* nodes of the binary the keys refer to */
+    uint32_t reserved;
 } hpa_profile;
 
 /* Approximate GPU calling context trees of requested launch contexts

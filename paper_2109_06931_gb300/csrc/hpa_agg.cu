@@ -91,16 +91,6 @@ void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cuda
 
 // ------------------------------------------------------------------ helpers
 // largest b with pre[b] <= x (pre is non-decreasing, pre[0] = 0)
-template <typename T>
-__device__ __forceinline__ uint32_t upper_index(const T* pre, uint32_t n, T x) {
-    uint32_t lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const uint32_t m = (lo + hi) >> 1;
-        if (pre[m] <= x) lo = m; else hi = m;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ uint32_t big_bits(uint32_t n, uint32_t cap, uint32_t sbits) {
     // 2^h sub-bins of about cap / 2 records each
     const uint32_t want = (uint32_t)((2ull * n + cap - 1) / cap);
@@ -666,7 +656,7 @@ static void launch_leaf(const AggWork& w, cudaStream_t s, int sms, int per_sm) {
     k_leaf<THREADS, CAP, HAS_CNT, V><<<sms * per_sm, THREADS, Cfg::SMEM, s>>>(w);
 }
 
-static void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
+void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
     const int gblocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 255) / 256, (uint64_t)sms * 16));
     scan_u32(w.grp_hist, w.grp_hist, w.G, w.scan_tmp, s, launches);
     k_item_flags<<<gblocks, 256, 0, s>>>(w);
@@ -678,9 +668,18 @@ static void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launch
     *launches += 4;
 }
 
-static void run_finish(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
+void launch_finalize(const AggWork& w, cudaStream_t s, uint64_t* launches) {
+    k_finalize<<<1, 256, 0, s>>>(w);
+    *launches += 1;
+}
+
+void launch_big_partition(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
     k_big_partition<<<sms * 4, 256, 0, s>>>(w);
     *launches += 1;
+}
+
+static void run_finish(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
+    launch_big_partition(w, s, sms, launches);
     if (ev) cudaEventRecord(ev[3], s);
     if (w.val64) {
         launch_leaf<256, LEAF_CAP_SMALL, true, uint64_t>(w, s, sms, 1);
@@ -695,12 +694,12 @@ static void run_finish(const AggWork& w, cudaStream_t s, int sms, uint64_t* laun
     if (ev) cudaEventRecord(ev[4], s);
     scan_u32(w.leaf_d, w.leaf_d, w.L_max, w.scan_tmp, s, launches);
     k_emit<<<sms * 8, 256, 0, s>>>(w);
-    k_finalize<<<1, 256, 0, s>>>(w);
-    *launches += 2;
+    launch_finalize(w, s, launches);
+    *launches += 1;
     if (ev) cudaEventRecord(ev[5], s);
 }
 
-static void clear_work(const AggWork& w, cudaStream_t s) {
+void clear_work(const AggWork& w, cudaStream_t s) {
     cudaMemsetAsync(w.grp_hist, 0, sizeof(uint32_t) * ((size_t)w.G + 1), s);
     cudaMemsetAsync(w.leaf_d, 0, sizeof(uint32_t) * ((size_t)w.L_max + 1), s);
     cudaMemsetAsync(w.buf_bad, 0, sizeof(unsigned long long) * w.n_buf, s);

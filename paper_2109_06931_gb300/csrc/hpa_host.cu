@@ -441,6 +441,7 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
     if (st) return st;
     Carve real{(char*)scratch};
     layout(real);
+    last_carve = real.off;
     w.bins = d_bins;
     w.status = d_status;
     return HPA_OK;
@@ -509,6 +510,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         gb += s.n_ctx;
         o.n_ctx = s.n_ctx;
         o.n_stall = s.n_stall;
+        o.n_nodes = binary(binary_ids[b])->n_nodes;
     }
     htile[n] = tb;
     hgrp[n] = gb;
@@ -611,5 +613,6 @@ extern "C" hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_
     *out->n_keys = K;
     out->n_ctx = d.n_ctx;
     out->n_stall = d.n_stall;
+    out->n_nodes = d.n_nodes;
     return hpa_sync(h, nullptr);
 }

@@ -90,6 +90,7 @@ struct hpa_handle {
     void* host_io = nullptr;
     size_t host_io_cap = 0;
     void* pinned_io = nullptr;
+    size_t last_carve = 0;        // scratch bytes used by the last carve_work
     void* cct_scratch = nullptr;
     size_t cct_cap = 0;
     // phase timing

@@ -117,6 +117,7 @@ extern "C" hpa_status hpa_propagate_inclusive(hpa_handle* h, uint32_t binary_id,
         if ((st = h->carve_work(w, N, p->n_ctx, 1, LEAF_CAP_SMALL, sb, nb + sb, true, true))) return st;
         tree_out->n_ctx = p->n_ctx;
         tree_out->n_stall = p->n_stall;
+        tree_out->n_nodes = B->n_nodes;
         if ((st = h->stage_single_output(w, binary_id, p->n_ctx, *tree_out))) return st;
         ExpandSrc x{p->key_ctx, p->key_node, p->key_stall, p->val, p->n_keys, p->capacity,
                     B->d_node_parent, B->d_node_depth, B->n_nodes, p->n_ctx};

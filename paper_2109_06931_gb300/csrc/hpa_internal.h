@@ -112,4 +112,21 @@ struct ExpandSrc {
 };
 void run_expand_aggregate(const AggWork& w, const ExpandSrc& x, cudaStream_t s, int sms, uint64_t* launches);
 
+// shared stages for other producers
+void clear_work(const AggWork& w, cudaStream_t s);
+void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
+void launch_big_partition(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
+void launch_finalize(const AggWork& w, cudaStream_t s, uint64_t* launches);
+
+// largest b with pre[b] <= x (pre non-decreasing, pre[0] = 0)
+template <typename T>
+__device__ __forceinline__ uint32_t upper_index(const T* pre, uint32_t n, T x) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (pre[m] <= x) lo = m; else hi = m;
+    }
+    return lo;
+}
+
 }  // namespace hpa

@@ -52,7 +52,8 @@ class hpa_samples(C.Structure):
 
 class hpa_profile(C.Structure):
     _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp), ("val", vp),
-                ("n_keys", vp), ("total", vp), ("unknown", vp), ("n_ctx", C.c_uint32), ("n_stall", C.c_uint32)]
+                ("n_keys", vp), ("total", vp), ("unknown", vp), ("n_ctx", C.c_uint32), ("n_stall", C.c_uint32),
+                ("n_nodes", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class hpa_gpucct(C.Structure):
@@ -147,11 +148,12 @@ class Profile:
     n_ctx: int
     n_stall: int
     capacity: int
+    n_nodes: int = 0
 
     def c(self) -> hpa_profile:
         return hpa_profile(self.capacity, _ptr(self.key_ctx), _ptr(self.key_node), _ptr(self.key_stall),
                            _ptr(self.val), _ptr(self.n_keys), _ptr(self.total), _ptr(self.unknown),
-                           self.n_ctx, self.n_stall)
+                           self.n_ctx, self.n_stall, self.n_nodes, 0)
 
     def count(self) -> int:
         return int(self.n_keys.item())
@@ -286,7 +288,7 @@ class Hpa:
         ci = self.samples_c(s.pc, s.ctx, s.stall, s.count, s.n_ctx, s.n_stall)
         co = out.c()
         self.check(self.L.hpa_attribute_samples(self.h, bid, C.byref(ci), C.byref(co)))
-        out.n_ctx, out.n_stall = s.n_ctx, s.n_stall
+        out.n_ctx, out.n_stall, out.n_nodes = s.n_ctx, s.n_stall, co.n_nodes
         return out
 
     def attribute_samples_host(self, bid: int, pc, ctx, stall, count, n_ctx, n_stall, capacity=None, out=None):
@@ -328,7 +330,7 @@ class Hpa:
                                                   C.byref(cc) if cc is not None else None,
                                                   _ptr(cct_out) if cct_out is not None else None))
         if tree_out is not None:
-            tree_out.n_ctx, tree_out.n_stall = p.n_ctx, p.n_stall
+            tree_out.n_ctx, tree_out.n_stall, tree_out.n_nodes = p.n_ctx, p.n_stall, p.n_nodes
         return tree_out, cct_out
 
     def apportion_callgraph(self, bid: int, p: Profile, req_ctx):
@@ -347,6 +349,32 @@ class Hpa:
         self._keep = [req]
         return incl, a, flags
 
+    def derive_metrics(self, profiles, n_ctx: int | None = None, capacity: int | None = None):
+        """Cross-profile statistics (Section 4.5) and per-context warp issue rate (Section 7)."""
+        P = len(profiles)
+        n_ctx = n_ctx or max(p.n_ctx for p in profiles)
+        S = max(p.n_stall for p in profiles)
+        cap = capacity if capacity is not None else max(1, sum(p.count() for p in profiles))
+        d = self.device
+        out = dict(ctx=torch.empty(cap, dtype=torch.int32, device=d), node=torch.empty(cap, dtype=torch.int32, device=d),
+                   stall=torch.empty(cap, dtype=torch.uint8, device=d), sum=torch.empty(cap, dtype=torch.int64, device=d),
+                   min=torch.empty(cap, dtype=torch.int64, device=d), max=torch.empty(cap, dtype=torch.int64, device=d),
+                   mean=torch.empty(cap, dtype=torch.float32, device=d), std=torch.empty(cap, dtype=torch.float32, device=d),
+                   cov=torch.empty(cap, dtype=torch.float32, device=d), n=torch.zeros(1, dtype=torch.int64, device=d),
+                   S=torch.empty(n_ctx, dtype=torch.int64, device=d), S_issued=torch.empty(n_ctx, dtype=torch.int64, device=d),
+                   W=torch.empty(n_ctx, dtype=torch.float32, device=d),
+                   frac=torch.empty((n_ctx, S), dtype=torch.float32, device=d))
+        o = hpa_derived(cap, _ptr(out["ctx"]), _ptr(out["node"]), _ptr(out["stall"]), _ptr(out["sum"]),
+                        _ptr(out["min"]), _ptr(out["max"]), _ptr(out["mean"]), _ptr(out["std"]), _ptr(out["cov"]),
+                        _ptr(out["n"]), n_ctx, _ptr(out["S"]), _ptr(out["S_issued"]), _ptr(out["W"]), _ptr(out["frac"]))
+        cps = [p.c() for p in profiles]
+        for c, p in zip(cps, profiles):
+            c.capacity = p.count()
+        arr = (C.POINTER(hpa_profile) * P)(*[C.pointer(c) for c in cps])
+        self.check(self.L.hpa_derive_metrics(self.h, arr, P, C.byref(o)))
+        self._keep = [cps, arr]
+        return out
+
     def max_depth(self, bid: int) -> int:
         return self._depth.get(bid, 16)
 
@@ -358,6 +386,6 @@ class Hpa:
         cos = (hpa_profile * n)(*[o.c() for o in outs])
         ids = (C.c_uint32 * n)(*bids)
         self.check(self.L.hpa_attribute_batch(self.h, n, ids, ins, cos))
-        for o, s in zip(outs, samples):
-            o.n_ctx, o.n_stall = s.n_ctx, s.n_stall
+        for o, s, c in zip(outs, samples, cos):
+            o.n_ctx, o.n_stall, o.n_nodes = s.n_ctx, s.n_stall, c.n_nodes
         return outs
