@@ -213,7 +213,7 @@ __global__ void k_leaves(AggWork w) {
 
 // ------------------------------------------------------------------ K9: attribute + scatter
 template <bool HAS_CNT, int U>
-__global__ void __launch_bounds__(256) k_attr_scatter(AggWork w) {
+__global__ void __launch_bounds__(256, 4) k_attr_scatter(AggWork w) {
     extern __shared__ unsigned long long acc[];          // [n_stall_max][256] per-thread totals
     __shared__ unsigned long long unk[HPA_MAX_STALL_DEV];
     const uint32_t tid = threadIdx.x;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_attr_scatter(AggWork w) {
         uint32_t bad = 0;
         for (uint64_t base = i0 + tid; base < i1; base += 256 * U) {
             uint64_t pc[U];
-            uint32_t c[U], st[U], cnt[U], off[U], lo[U], hi[U], nd[U];
+            uint32_t c[U], st[U], cnt[U], off[U], nd[U];
             bool ok[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -266,42 +266,26 @@ __global__ void __launch_bounds__(256) k_attr_scatter(AggWork w) {
                     ok[u] = c[u] < B.n_ctx;
                 }
             }
-            // attribution, all U lookups in lockstep (Section 4.2: PC -> structure node)
+            // attribution (Section 4.2: PC -> structure node), the U lookups
+            // in lockstep: one directory load answers most of them
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 nd[u] = M;
-                lo[u] = hi[u] = 0;
                 if (ok[u]) {
                     const uint64_t o = pc[u] - bin.pc_base;
                     if (o < bin.span) {
                         off[u] = (uint32_t)o;
-                        const uint32_t bk = off[u] >> bin.dshift;
-                        lo[u] = __ldg(&bin.dir[bk]);
-                        hi[u] = __ldg(&bin.dir[bk + 1]);
-                        nd[u] = 0xFFFFFFFEu;    // search pending
+                        nd[u] = __ldg(&bin.dir[off[u] >> bin.dshift]);
                     }
                 }
-            }
-            for (int it = 0; it < 40; ++it) {
-                bool any = false;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (nd[u] == 0xFFFFFFFEu && lo[u] < hi[u]) {
-                        const uint32_t m = (lo[u] + hi[u]) >> 1;
-                        if (__ldg(&bin.rng[m].y) > off[u]) hi[u] = m; else lo[u] = m + 1;
-                        any = true;
-                    }
-                }
-                if (!any) break;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (nd[u] == 0xFFFFFFFEu) {
-                    nd[u] = M;
-                    if (lo[u] < bin.n_ranges) {
-                        const uint4 r = __ldg(&bin.rng[lo[u]]);
-                        if (r.x <= off[u]) nd[u] = r.z;
-                    }
+                if (nd[u] & DIR_SEARCH) {
+                    uint32_t i = nd[u] & ~DIR_SEARCH;
+                    uint4 r = __ldg(&bin.rng[i]);
+                    while (r.y <= off[u] && i + 1 < bin.n_ranges) r = __ldg(&bin.rng[++i]);
+                    nd[u] = (r.x <= off[u] && off[u] < r.y) ? r.z : M;
                 }
             }
 #pragma unroll
@@ -309,8 +293,9 @@ __global__ void __launch_bounds__(256) k_attr_scatter(AggWork w) {
                 if (!ok[u]) continue;
                 const bool bad_stall = st[u] >= B.n_stall;
                 const uint32_t slot = atomicAdd(&w.grp_cursor[(size_t)(B.grp_base + c[u]) << w.cur_shift], 1u);
-                w.rec_sub[slot] = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
-                if (HAS_CNT) w.rec_cnt[slot] = bad_stall ? 0u : cnt[u];
+                const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
+                if (HAS_CNT) w.rec_pair[slot] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
+                else w.rec_sub[slot] = sub;
                 if (bad_stall) {
                     ++bad;
                 } else {
@@ -342,8 +327,9 @@ __global__ void __launch_bounds__(256) k_big_partition(AggWork w) {
         const uint32_t shift = w.sbits - h;
         for (uint32_t j = threadIdx.x; j <= nb; j += blockDim.x) hist[j] = 0;
         __syncthreads();
+        const bool pair = w.rec_pair != nullptr;
         for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x)
-            atomicAdd(&hist[w.rec_sub[i] >> shift], 1u);
+            atomicAdd(&hist[(pair ? w.rec_pair[i].x : w.rec_sub[i]) >> shift], 1u);
         __syncthreads();
         block_scan_array<uint32_t, 256, 17>(hist, nb + 1, sw);
         const uint32_t l0 = leaf_base[it];
@@ -356,11 +342,15 @@ __global__ void __launch_bounds__(256) k_big_partition(AggWork w) {
         }
         __syncthreads();
         for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-            const uint32_t sub = w.rec_sub[i];
-            const uint32_t p = s0 + atomicAdd(&hist[sub >> shift], 1u);
-            w.rec2_sub[p] = sub;
-            if (w.val64) w.rec2_v64[p] = w.rec_v64[i];
-            else if (w.has_cnt) w.rec2_cnt[p] = w.rec_cnt[i];
+            if (pair) {
+                const uint2 r = w.rec_pair[i];
+                w.rec2_pair[s0 + atomicAdd(&hist[r.x >> shift], 1u)] = r;
+            } else {
+                const uint32_t sub = w.rec_sub[i];
+                const uint32_t p = s0 + atomicAdd(&hist[sub >> shift], 1u);
+                w.rec2_sub[p] = sub;
+                if (w.val64) w.rec2_v64[p] = w.rec_v64[i];
+            }
         }
         __syncthreads();
     }
@@ -377,66 +367,129 @@ struct LeafCfg {
     static constexpr size_t SMEM = SORT_BYTES > DENSE_BYTES ? SORT_BYTES : DENSE_BYTES;
 };
 
-struct SegPair { uint32_t f; unsigned long long s; };
+// Runs of equal keys in a sorted shared-memory array, reduced warp-striped:
+// warp w owns a contiguous chunk and walks it 32 elements per row (lane l
+// reads element row * 32 + l, so shared-memory reads are conflict-free).
+// Run sums come from a segmented inclusive scan per row plus a carry for the
+// run still open at the row's (and the previous warp's) end.
+struct RunCtx {
+    uint32_t heads;          // heads in this warp's chunk
+    unsigned long long tail; // sum of the run left open at the chunk's end
+    uint32_t has_head;
+};
 
-__device__ __forceinline__ SegPair seg_combine(SegPair a, SegPair b) {
-    return SegPair{a.f | b.f, b.f ? b.s : a.s + b.s};
+template <typename V, bool HAS_V>
+__device__ __forceinline__ unsigned long long val_at(const V* vals, int i) {
+    if constexpr (HAS_V) return (unsigned long long)vals[i];
+    else return 1ull;
 }
 
-// exclusive segmented scan across the block (one pair per thread)
-template <int THREADS>
-__device__ __forceinline__ unsigned long long block_seg_carry(SegPair x, SegPair* sw) {
-    constexpr int W = THREADS / 32;
-    const int warp = threadIdx.x >> 5, lane = lane_id();
-    SegPair inc = x;
+// mode 0: write every run at its run id; mode 1: count runs with a non-zero
+// sum; mode 2: write only runs with a non-zero sum, compacted from nz_base.
+template <typename V, bool HAS_V>
+__device__ __forceinline__ uint32_t warp_runs(const uint32_t* K, const V* vals, int n, int w0, int w1,
+                                              int run0, unsigned long long carry, int mode, uint32_t nz_base,
+                                              uint32_t* out_key, unsigned long long* out_val) {
+    const int lane = lane_id();
+    int run = run0;
+    uint32_t nz = nz_base, nz_count = 0;
+    for (int base = w0; base < w1; base += 32) {
+        const int i = base + lane;
+        const bool ok = i < w1;
+        const uint32_t k = ok ? K[i] : 0u;
+        const bool h = ok && (i == 0 || K[i - 1] != k);
+        unsigned long long v = ok ? val_at<V, HAS_V>(vals, i) : 0ull;
+        const uint32_t hb = __ballot_sync(0xffffffffu, h);
+        // inclusive segmented scan of (h, v) across the row
+        uint32_t f = h;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        SegPair y;
-        y.f = __shfl_up_sync(0xffffffffu, inc.f, o);
-        y.s = __shfl_up_sync(0xffffffffu, inc.s, o);
-        if (lane >= o) inc = seg_combine(y, inc);
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v2 = __shfl_up_sync(0xffffffffu, v, o);
+            const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, o);
+            if (lane >= o) {
+                if (!f) v += v2;
+                f |= f2;
+            }
+        }
+        if (!f) v += carry;
+        const int rid = run + __popc(hb & (lanemask_lt() | (1u << lane)));
+        const bool end = ok && (i == n - 1 || K[i + 1] != k);
+        if (mode == 0) {
+            if (end) { out_key[rid] = k; out_val[rid] = v; }
+        } else {
+            const uint32_t nzb = __ballot_sync(0xffffffffu, end && v != 0);
+            if (mode == 2 && end && v != 0) {
+                const uint32_t pos = nz + __popc(nzb & lanemask_lt());
+                out_key[pos] = k;
+                out_val[pos] = v;
+            }
+            nz += __popc(nzb);
+            nz_count += __popc(nzb);
+        }
+        run += __popc(hb);
+        carry = __shfl_sync(0xffffffffu, v, 31);
     }
-    SegPair exc;
-    exc.f = __shfl_up_sync(0xffffffffu, inc.f, 1);
-    exc.s = __shfl_up_sync(0xffffffffu, inc.s, 1);
-    if (lane == 0) exc = SegPair{0, 0};
-    if (lane == 31) sw[warp] = inc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        SegPair run{0, 0};
-        for (int i = 0; i < W; ++i) {
-            SegPair t = sw[i];
-            sw[i] = run;
-            run = seg_combine(run, t);
+    return nz_count;
+}
+
+// per-warp heads and open-run tail over the warp's chunk
+template <typename V, bool HAS_V>
+__device__ __forceinline__ RunCtx warp_run_summary(const uint32_t* K, const V* vals, int w0, int w1) {
+    const int lane = lane_id();
+    RunCtx r{0, 0ull, 0};
+    for (int base = w0; base < w1; base += 32) {
+        const int i = base + lane;
+        const bool ok = i < w1;
+        const uint32_t k = ok ? K[i] : 0u;
+        const bool h = ok && (i == 0 || K[i - 1] != k);
+        const unsigned long long v = ok ? val_at<V, HAS_V>(vals, i) : 0ull;
+        const uint32_t hb = __ballot_sync(0xffffffffu, h);
+        r.heads += __popc(hb);
+        if (hb) {
+            const int last = 31 - __clz(hb);
+            r.tail = warp_sum(lane >= last ? v : 0ull);
+            r.has_head = 1;
+        } else {
+            r.tail += warp_sum(v);
         }
     }
-    __syncthreads();
-    const SegPair pre = seg_combine(sw[warp], exc);
-    __syncthreads();
-    return pre.s;
+    return r;
 }
 
 template <int THREADS, int CAP, bool HAS_CNT, typename V>
 __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
     using Cfg = LeafCfg<THREADS, CAP, HAS_CNT, V>;
     using Sort = typename Cfg::Sort;
+    constexpr int W = THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename Sort::Smem& S = *reinterpret_cast<typename Sort::Smem*>(smem_raw);
     __shared__ uint32_t sw[33];
-    __shared__ SegPair sws[32];
     __shared__ uint32_t gb[1025];
     __shared__ unsigned long long red[2];
+    __shared__ uint32_t s_run0[W], s_nz[W];
+    __shared__ unsigned long long s_carry[W];
+    __shared__ uint32_t s_any_zero;
     const uint32_t n_leaves = w.item_nleaf[w.G];
     const uint32_t* seg = w.grp_hist;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
 
     for (uint32_t l = blockIdx.x; l < n_leaves; l += gridDim.x) {
         const uint32_t start = w.leaf_start[l], end = w.leaf_end[l];
         const uint32_t info = w.leaf_info[l];
         const uint32_t n = end - start;
-        const uint32_t* src_sub = (info & 1u) ? w.rec2_sub : w.rec_sub;
-        const V* src_cnt;
-        if constexpr (sizeof(V) == 8) src_cnt = (const V*)((info & 1u) ? w.rec2_v64 : w.rec_v64);
-        else src_cnt = (const V*)((info & 1u) ? w.rec2_cnt : w.rec_cnt);
+        const bool second = info & 1u;
+        const uint2* src_pair = second ? w.rec2_pair : w.rec_pair;
+        const uint32_t* src_sub = second ? w.rec2_sub : w.rec_sub;
+        const uint64_t* src_v64 = second ? w.rec2_v64 : w.rec_v64;
+        auto rec = [&](uint32_t i, uint32_t& k, unsigned long long& v) {
+            if constexpr (HAS_CNT && sizeof(V) == 4) {
+                const uint2 r = src_pair[i];
+                k = r.x; v = r.y;
+            } else {
+                k = src_sub[i];
+                if constexpr (HAS_CNT) v = src_v64[i]; else v = 1ull;
+            }
+        };
         if (n == 0) {
             if (threadIdx.x == 0) w.leaf_d[l] = 0;
             continue;
@@ -446,8 +499,7 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
             // groups whose records lie in [start, end)
             const uint32_t g0 = w.leaf_grp0[l];
             uint32_t ng = 1;
-            if (!(info & 1u)) {
-                // count groups: last group g with seg[g] < end
+            if (!second) {
                 uint32_t lo = g0, hi = min(w.G, g0 + 1024u);
                 while (hi - lo > 1) {
                     const uint32_t m = (lo + hi) >> 1;
@@ -460,79 +512,71 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 for (uint32_t j = threadIdx.x; j <= ng; j += THREADS) gb[j] = seg[g0 + j] - start;
                 __syncthreads();
             }
+            uint32_t zero = 0;
             for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
-                S.key[0][i] = src_sub[start + i];
-                if constexpr (HAS_CNT) S.val[0][i] = src_cnt[start + i];
+                uint32_t k;
+                unsigned long long v;
+                rec(start + i, k, v);
+                S.key[0][i] = k;
+                if constexpr (HAS_CNT) { S.val[0][i] = (V)v; zero |= v == 0; }
             }
+            if (threadIdx.x == 0) s_any_zero = 0;
             __syncthreads();
+            if (zero) s_any_zero = 1;
             if (ng > 1) {
                 // tag each record with its group inside the leaf
                 for (uint32_t j = threadIdx.x; j < ng; j += THREADS) {
                     const uint32_t a = gb[j], e = min(gb[j + 1], n);
                     for (uint32_t i = a; i < e; ++i) S.key[0][i] |= j << w.sbits;
                 }
-                __syncthreads();
             }
+            __syncthreads();
             const int cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
-            // runs of equal keys: heads, then a segmented carry across threads
-            const int c0 = threadIdx.x * Cfg::EPT;
-            const int c1 = min((int)n, c0 + Cfg::EPT);
-            uint32_t heads = 0;
-            SegPair mine{0, 0};
-            for (int i = c0; i < c1; ++i) {
-                const uint32_t k = S.key[cur][i];
-                const bool h = (i == 0) || (k != S.key[cur][i - 1]);
-                unsigned long long v = 1;
-                if constexpr (HAS_CNT) v = S.val[cur][i];
-                if (h) { ++heads; mine.f = 1; mine.s = 0; }
-                mine.s += v;
-            }
-            uint32_t n_runs;
-            const uint32_t rid0 = block_exclusive_scan<uint32_t, THREADS>(heads, sw, &n_runs);
-            const unsigned long long carry = block_seg_carry<THREADS>(mine, sws);
-            // keys whose counts add up to 0 are omitted; zero counts are rare,
-            // so the compacting walk only runs when a leaf holds one
-            bool zero = false;
-            if constexpr (HAS_CNT)
-                for (int i = c0; i < c1; ++i) zero |= S.val[cur][i] == 0;
-            const bool any_zero = __syncthreads_or(zero);
-            uint32_t out_base = 0, n_out = n_runs;
-            if (any_zero) {
-                uint32_t nz = 0;
-                int run = (int)rid0 - 1;
-                unsigned long long a = carry;
-                for (int i = c0; i < c1; ++i) {
-                    const uint32_t k = S.key[cur][i];
-                    if (i == 0 || k != S.key[cur][i - 1]) { ++run; a = 0; }
-                    unsigned long long v = 1;
-                    if constexpr (HAS_CNT) v = S.val[cur][i];
-                    a += v;
-                    if ((i == (int)n - 1 || S.key[cur][i + 1] != k) && a) ++nz;
+            const uint32_t* Kc = S.key[cur];
+            const V* Vc = HAS_CNT ? S.val[HAS_CNT ? cur : 0] : nullptr;
+            const int wch = ((((int)n + W - 1) / W) + 31) & ~31;
+            const int w0 = min((int)n, warp * wch), w1 = min((int)n, w0 + wch);
+            const RunCtx rc = warp_run_summary<V, HAS_CNT>(Kc, Vc, w0, w1);
+            if (lane == 0) { s_run0[warp] = rc.heads; s_carry[warp] = rc.tail; s_nz[warp] = rc.has_head; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                // exclusive scan of heads, segmented exclusive scan of open-run tails
+                uint32_t runs = 0;
+                unsigned long long open = 0;
+                for (int x = 0; x < W; ++x) {
+                    const uint32_t hcount = s_run0[x], hh = s_nz[x];
+                    const unsigned long long t = s_carry[x];
+                    s_run0[x] = runs;
+                    s_carry[x] = open;
+                    runs += hcount;
+                    open = hh ? t : open + t;
                 }
-                out_base = block_exclusive_scan<uint32_t, THREADS>(nz, sw, &n_out);
+                sw[32] = runs;
             }
-            int run = (int)rid0 - 1;
-            uint32_t o = out_base;
-            unsigned long long a = carry;
-            for (int i = c0; i < c1; ++i) {
-                const uint32_t k = S.key[cur][i];
-                if (i == 0 || k != S.key[cur][i - 1]) { ++run; a = 0; }
-                unsigned long long v = 1;
-                if constexpr (HAS_CNT) v = S.val[cur][i];
-                a += v;
-                if (i == (int)n - 1 || S.key[cur][i + 1] != k) {
-                    if (!any_zero) {
-                        w.tmp_key[start + run] = k;
-                        w.tmp_val[start + run] = a;
-                    } else if (a) {
-                        w.tmp_key[start + o] = k;
-                        w.tmp_val[start + o] = a;
-                        ++o;
-                    }
+            __syncthreads();
+            const uint32_t n_runs = sw[32];
+            const int run0 = (int)s_run0[warp] - 1;
+            const unsigned long long carry = s_carry[warp];
+            uint32_t n_out = n_runs;
+            if (!s_any_zero) {
+                warp_runs<V, HAS_CNT>(Kc, Vc, (int)n, w0, w1, run0, carry, 0, 0, w.tmp_key + start, (unsigned long long*)(w.tmp_val + start));
+            } else {
+                // keys whose counts add up to 0 are omitted (compacting walk)
+                const uint32_t nzc = warp_runs<V, HAS_CNT>(Kc, Vc, (int)n, w0, w1, run0, carry, 1, 0, nullptr, nullptr);
+                __syncthreads();
+                if (lane == 0) s_nz[warp] = nzc;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    uint32_t t = 0;
+                    for (int x = 0; x < W; ++x) { const uint32_t c = s_nz[x]; s_nz[x] = t; t += c; }
+                    sw[32] = t;
                 }
+                __syncthreads();
+                n_out = sw[32];
+                warp_runs<V, HAS_CNT>(Kc, Vc, (int)n, w0, w1, run0, carry, 2, s_nz[warp], w.tmp_key + start,
+                                      (unsigned long long*)(w.tmp_val + start));
             }
-            n_runs = n_out;
-            if (threadIdx.x == 0) w.leaf_d[l] = n_runs;
+            if (threadIdx.x == 0) w.leaf_d[l] = n_out;
             __syncthreads();
         } else {
             // oversized sub-bin (one group): dense shared-memory windows over
@@ -540,7 +584,9 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
             unsigned long long* dense = reinterpret_cast<unsigned long long*>(smem_raw);
             uint32_t mn = 0xFFFFFFFFu, mx = 0;
             for (uint32_t i = start + threadIdx.x; i < end; i += THREADS) {
-                const uint32_t k = src_sub[i];
+                uint32_t k;
+                unsigned long long v;
+                rec(i, k, v);
                 mn = min(mn, k); mx = max(mx, k);
             }
             for (int o = 16; o > 0; o >>= 1) {
@@ -549,7 +595,7 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
             }
             if (threadIdx.x == 0) { red[0] = 0xFFFFFFFFull; red[1] = 0; }
             __syncthreads();
-            if (lane_id() == 0) {
+            if (lane == 0) {
                 atomicMin(&red[0], (unsigned long long)mn);
                 atomicMax(&red[1], (unsigned long long)mx);
             }
@@ -563,27 +609,28 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 for (int j = threadIdx.x; j < WD; j += THREADS) dense[j] = 0;
                 __syncthreads();
                 for (uint32_t i = start + threadIdx.x; i < end; i += THREADS) {
-                    const uint32_t k = src_sub[i];
-                    if (k >= wlo && (uint64_t)k < wlo + WD) {
-                        unsigned long long v = 1;
-                        if constexpr (HAS_CNT) v = src_cnt[i];
-                        atomicAdd(&dense[k - wlo], v);
-                    }
+                    uint32_t k;
+                    unsigned long long v;
+                    rec(i, k, v);
+                    if (k >= wlo && (uint64_t)k < wlo + WD) atomicAdd(&dense[k - wlo], v);
                 }
                 __syncthreads();
-                const int b0 = threadIdx.x * DEPT;
                 uint32_t nz = 0;
-                for (int j = 0; j < DEPT; ++j) nz += dense[b0 + j] != 0;
-                uint32_t tot;
-                uint32_t pos = block_exclusive_scan<uint32_t, THREADS>(nz, sw, &tot);
+                for (int j = 0; j < DEPT; ++j) nz += dense[j * THREADS + threadIdx.x] != 0;
+                // order: the window is compacted in key order, row by row
+                uint32_t tot = 0;
                 for (int j = 0; j < DEPT; ++j) {
-                    const unsigned long long v = dense[b0 + j];
+                    const int q = j * THREADS + threadIdx.x;
+                    const unsigned long long v = dense[q];
+                    uint32_t rt;
+                    const uint32_t pos = block_exclusive_scan<uint32_t, THREADS>(v != 0, sw, &rt);
                     if (v) {
-                        w.tmp_key[start + out + pos] = (uint32_t)(wlo + b0 + j);
-                        w.tmp_val[start + out + pos] = v;
-                        ++pos;
+                        w.tmp_key[start + out + tot + pos] = (uint32_t)(wlo + q);
+                        w.tmp_val[start + out + tot + pos] = v;
                     }
+                    tot += rt;
                 }
+                (void)nz;
                 out += tot;
                 __syncthreads();
             }

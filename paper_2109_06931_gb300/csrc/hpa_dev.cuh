@@ -24,10 +24,15 @@ __device__ __forceinline__ void raise_status(DevStatus* st, int32_t code, int32_
 
 // Program structure of one binary as the attribution kernels read it.
 //   rng[i] = {lo - pc_base, hi - pc_base, node, 0}, sorted, disjoint.
-//   dir[b] = first range whose hi - pc_base > b << dshift  (b in [0, n_dir]).
+//   dir[b], for the bucket [b << dshift, (b + 1) << dshift) of offsets:
+//     the node of the one range that covers the whole bucket, or n_nodes
+//     when no range touches it (UNKNOWN), or DIR_SEARCH | i with i the first
+//     range whose hi lies beyond the bucket start.
 // A PC p belongs to range i iff lo_i <= p < hi_i (half-open); ranges are
-// disjoint, so the only candidate is the first range with hi > p, which lies
-// between dir[b] and dir[b + 1] for p's bucket b.
+// disjoint, so the only candidate is the first range with hi > p.
+constexpr uint32_t DIR_SEARCH = 0x80000000u;
+constexpr uint64_t DIR_MAX_ENTRIES = 16ull << 20;   // 64 MB directory at most
+
 struct DevBinary {
     uint64_t pc_base;
     uint64_t span;          // range_hi[R-1] - pc_base (< 2^32)
@@ -44,19 +49,12 @@ __device__ __forceinline__ uint32_t attribute_pc(const DevBinary& b, uint64_t pc
     const uint64_t off64 = pc - b.pc_base;    // wraps to a huge value below the segment
     if (off64 >= b.span) return b.n_nodes;
     const uint32_t off = (uint32_t)off64;
-    const uint32_t bk = off >> b.dshift;
-    uint32_t i = __ldg(&b.dir[bk]);
-    uint32_t j = __ldg(&b.dir[bk + 1]);
-    // first range in [i, j] with hi > off; j itself qualifies (or is R)
-    while (i < j) {
-        const uint32_t m = (i + j) >> 1;
-        if (__ldg(&b.rng[m].y) > off) j = m; else i = m + 1;
-    }
-    if (i < b.n_ranges) {
-        const uint4 r = __ldg(&b.rng[i]);
-        if (r.x <= off) return r.z;
-    }
-    return b.n_nodes;
+    const uint32_t e = __ldg(&b.dir[off >> b.dshift]);
+    if (!(e & DIR_SEARCH)) return e;
+    uint32_t i = e & ~DIR_SEARCH;
+    uint4 r = __ldg(&b.rng[i]);
+    while (r.y <= off && i + 1 < b.n_ranges) r = __ldg(&b.rng[++i]);
+    return (r.x <= off && off < r.y) ? r.z : b.n_nodes;
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }

@@ -348,9 +348,12 @@ static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B) 
     }
     B->n_nodes = M; B->n_funcs = F; B->n_calls = E; B->n_ranges = R; B->max_depth = max_depth;
     // attribution tables: ranges as offsets from the segment base, and a
-    // bucket directory with about one range per bucket
+    // bucket directory (at most DIR_MAX_ENTRIES buckets of 2^dshift bytes).
+    // An entry answers directly when its bucket lies inside one range (the
+    // range's node) or touches no range (n_nodes, i.e. UNKNOWN); otherwise it
+    // holds DIR_SEARCH | first range whose hi lies beyond the bucket start.
     uint32_t dshift = 4;
-    while (dshift < 31 && (span >> dshift) > 2 * R) ++dshift;
+    while (dshift < 31 && (span >> dshift) + 1 > DIR_MAX_ENTRIES) ++dshift;
     const uint64_t n_dir = (span >> dshift) + 1;
     std::vector<uint4> rng(R);
     for (uint64_t i = 0; i < R; ++i)
@@ -359,9 +362,11 @@ static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B) 
     {
         uint64_t i = 0;
         for (uint64_t b = 0; b <= n_dir; ++b) {
-            const uint64_t start = b << dshift;
+            const uint64_t start = b << dshift, end = start + (1ull << dshift);
             while (i < R && rng[i].y <= start) ++i;
-            dir[b] = (uint32_t)i;
+            if (i < R && rng[i].x <= start && rng[i].y >= end) dir[b] = rng[i].z;
+            else if (i == R || rng[i].x >= end) dir[b] = M;
+            else dir[b] = DIR_SEARCH | (uint32_t)i;
         }
     }
     hpa_status st;
@@ -425,10 +430,13 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
         w.leaf_d = c.take<uint32_t>(L_max + 1);
         w.buf_first_leaf = c.take<uint32_t>(n + 1);
         w.buf_bad = c.take<unsigned long long>(n);
-        w.rec_sub = c.take<uint32_t>(N + 1);
-        w.rec_cnt = (has_cnt && !val64) ? c.take<uint32_t>(N + 1) : nullptr;
-        w.rec2_sub = c.take<uint32_t>(N + 1);
-        w.rec2_cnt = (has_cnt && !val64) ? c.take<uint32_t>(N + 1) : nullptr;
+        const bool pair = has_cnt && !val64;
+        w.rec_sub = pair ? nullptr : c.take<uint32_t>(N + 1);
+        w.rec_cnt = nullptr;
+        w.rec2_sub = pair ? nullptr : c.take<uint32_t>(N + 1);
+        w.rec2_cnt = nullptr;
+        w.rec_pair = pair ? c.take<uint2>(N + 1) : nullptr;
+        w.rec2_pair = pair ? c.take<uint2>(N + 1) : nullptr;
         w.rec_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
         w.rec2_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
         w.tmp_key = c.take<uint32_t>(N + 1);

@@ -66,6 +66,8 @@ struct AggWork {
     uint32_t* rec2_cnt;    // [N]
     uint64_t* rec_v64;     // [N] (if val64)
     uint64_t* rec2_v64;    // [N]
+    uint2* rec_pair;       // [N] {subkey, count} (if has_cnt and !val64; rec_sub unused then)
+    uint2* rec2_pair;      // [N]
     uint32_t* tmp_key;     // [N]
     uint64_t* tmp_val;     // [N]
     uint32_t* scan_tmp;    // device-wide scan partials
