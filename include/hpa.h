@@ -255,6 +255,22 @@ hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, const hpa_sa
 hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
                                       hpa_profile* out);
 
+/* hpa_attribute_samples for callers that cannot allocate device memory
+ * while they analyse samples -- for example code running during CUDA stream
+ * capture (allocation is not allowed there) or inside a runtime that owns
+ * the GPU's memory pool.  The paper has no counterpart: this is a property
+ * of the library, not of the method.  Same arguments, same results; in and
+ * out are DEVICE arrays owned by the caller as for hpa_attribute_samples.
+ * The call takes its scratch from one fixed 48 MiB array that the library
+ * reserves on every GPU that loads it (about 1.5 million samples with counts
+ * per call); a call that needs more returns HPA_E_INVALID_ARG and does
+ * nothing.  It calls no cudaMalloc / cudaFree.  The first call on a device
+ * looks up the array's device address; make that first call before any
+ * stream capture.  All calls on a device share the array: calls that overlap
+ * on the GPU (different streams or handles without synchronisation) race.  */
+hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
+                                         hpa_profile* out);
+
 /* Many sample buffers of uneven sizes, each against its own binary, in one
  * captured CUDA graph (the analogue of streaming aggregation over profiles,
  * Section 6.1).  outs[i] receives exactly what hpa_attribute_samples would

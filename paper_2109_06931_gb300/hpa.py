@@ -73,7 +73,8 @@ class hpa_derived(C.Structure):
 EXPORTS = ["hpa_create", "hpa_destroy", "hpa_last_error", "hpa_sync", "hpa_reserve", "hpa_kernel_launches",
            "hpa_load_structure", "hpa_unload_structure", "hpa_binary_info_get", "hpa_attribute_samples",
            "hpa_attribute_samples_host", "hpa_attribute_batch", "hpa_apportion_callgraph",
-           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_set_phase_timing", "hpa_phase_times"]
+           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_set_phase_timing", "hpa_phase_times",
+           "hpa_attribute_samples_noalloc"]
 PHASES = ["hist+plan", "attribute+scatter", "big-split", "leaf sort/reduce", "emit"]
 
 _lib = None
@@ -108,6 +109,7 @@ def lib(build_if_needed: bool = True):
         L.hpa_propagate_inclusive.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile),
                                               C.POINTER(hpa_cct), vp]
         L.hpa_derive_metrics.argtypes = [H, C.POINTER(C.POINTER(hpa_profile)), C.c_uint32, C.POINTER(hpa_derived)]
+        L.hpa_attribute_samples_noalloc.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_set_phase_timing.argtypes = [H, C.c_int]
         L.hpa_phase_times.argtypes = [H, C.c_uint32, vp, u64p, u32p]
         for f in EXPORTS:
@@ -288,6 +290,14 @@ class Hpa:
         ci = self.samples_c(s.pc, s.ctx, s.stall, s.count, s.n_ctx, s.n_stall)
         co = out.c()
         self.check(self.L.hpa_attribute_samples(self.h, bid, C.byref(ci), C.byref(co)))
+        out.n_ctx, out.n_stall, out.n_nodes = s.n_ctx, s.n_stall, co.n_nodes
+        return out
+
+    def attribute_samples_noalloc(self, bid: int, s, out: Profile) -> Profile:
+        """hpa_attribute_samples_noalloc: no device allocation during the call (static scratch)."""
+        ci = self.samples_c(s.pc, s.ctx, s.stall, s.count, s.n_ctx, s.n_stall)
+        co = out.c()
+        self.check(self.L.hpa_attribute_samples_noalloc(self.h, bid, C.byref(ci), C.byref(co)))
         out.n_ctx, out.n_stall, out.n_nodes = s.n_ctx, s.n_stall, co.n_nodes
         return out
 
