@@ -8,9 +8,10 @@
 //   k_item_flags,    groups are packed into items of <= cap records (runs of
 //   k_items, ...     small groups, or one group); a group with more than cap
 //                    records becomes a "big" item split into 2^h sub-bins
-//   k_attr_scatter   reads every sample once, attributes its PC to a
+//   k_attribute      reads every sample once, attributes its PC to a
 //                    structure node, packs (node, stall) into a subkey and
-//                    scatters (subkey, count) into its group's segment
+//                    stores (subkey, count) in sample order
+//   k_scatter        moves each record into its group's segment
 //   k_big_partition  splits big groups by the subkey's top h bits
 //   k_leaf           per leaf: shared-memory radix sort + run reduction (or a
 //                    dense shared-memory window for oversized sub-bins)
@@ -211,9 +212,14 @@ __global__ void k_leaves(AggWork w) {
     if (blockIdx.x == 0 && threadIdx.x == 0) w.buf_first_leaf[w.n_buf] = leaf_base[w.G];
 }
 
-// ------------------------------------------------------------------ K9: attribute + scatter
+// ------------------------------------------------------------------ K9a: attribute
+// Streams every sample once: attributes its PC to a structure node (Section
+// 4.2), packs (node, stall) into a subkey and stores {subkey, count} in sample
+// order (coalesced) in the second record buffer; accumulates per-stall totals
+// and UNKNOWN totals.  Only the directory / range loads are dependent, so
+// many samples per thread stay in flight.
 template <bool HAS_CNT, int U>
-__global__ void __launch_bounds__(256, 4) k_attr_scatter(AggWork w) {
+__global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
     extern __shared__ unsigned long long acc[];          // [n_stall_max][256] per-thread totals
     __shared__ unsigned long long unk[HPA_MAX_STALL_DEV];
     const uint32_t tid = threadIdx.x;
@@ -248,26 +254,23 @@ __global__ void __launch_bounds__(256, 4) k_attr_scatter(AggWork w) {
         const DevBinary bin = w.bins[B.bin];
         const uint64_t i0 = (t - B.tile_base) * TILE;
         const uint64_t i1 = min(i0 + TILE, B.n);
+        const uint64_t stage0 = t * TILE - i0;               // staging index = stage0 + i
         const uint32_t M = bin.n_nodes;
         uint32_t bad = 0;
         for (uint64_t base = i0 + tid; base < i1; base += 256 * U) {
             uint64_t pc[U];
-            uint32_t c[U], st[U], cnt[U], off[U], nd[U];
+            uint32_t st[U], cnt[U], off[U], nd[U];
             bool ok[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const uint64_t i = base + (uint64_t)u * 256;
                 ok[u] = i < i1;
                 if (ok[u]) {
-                    c[u] = __ldg(&B.ctx[i]);
                     st[u] = __ldg(&B.stall[i]);
                     pc[u] = __ldg((const unsigned long long*)&B.pc[i]);
                     cnt[u] = (HAS_CNT && B.count) ? __ldg(&B.count[i]) : 1u;
-                    ok[u] = c[u] < B.n_ctx;
                 }
             }
-            // attribution (Section 4.2: PC -> structure node), the U lookups
-            // in lockstep: one directory load answers most of them
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 nd[u] = M;
@@ -291,11 +294,11 @@ __global__ void __launch_bounds__(256, 4) k_attr_scatter(AggWork w) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (!ok[u]) continue;
+                const uint64_t i = base + (uint64_t)u * 256;
                 const bool bad_stall = st[u] >= B.n_stall;
-                const uint32_t slot = atomicAdd(&w.grp_cursor[(size_t)(B.grp_base + c[u]) << w.cur_shift], 1u);
                 const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
-                if (HAS_CNT) w.rec_pair[slot] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
-                else w.rec_sub[slot] = sub;
+                if (HAS_CNT) w.rec2_pair[stage0 + i] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
+                else w.rec2_sub[stage0 + i] = sub;
                 if (bad_stall) {
                     ++bad;
                 } else {
@@ -307,6 +310,46 @@ __global__ void __launch_bounds__(256, 4) k_attr_scatter(AggWork w) {
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
     }
     flush(cur_b);
+}
+
+// ------------------------------------------------------------------ K9b: scatter by context
+// Reads (ctx, staged record) in sample order and moves each record to its
+// context's segment; the cursor atomic is the only dependent operation.
+template <bool HAS_CNT, int U>
+__global__ void __launch_bounds__(256) k_scatter(AggWork w) {
+    for (uint64_t t = blockIdx.x; t < w.n_tiles; t += gridDim.x) {
+        const uint32_t b = upper_index<uint64_t>(w.buf_tile, w.n_buf, t);
+        const BufDev& B = w.bufs[b];
+        const uint32_t n_ctx = B.n_ctx, gbase = B.grp_base;
+        const uint32_t* ctx = B.ctx;
+        const uint64_t i0 = (t - B.tile_base) * TILE;
+        const uint64_t i1 = min(i0 + TILE, B.n);
+        const uint64_t stage0 = t * TILE - i0;
+        for (uint64_t base = i0 + threadIdx.x; base < i1; base += 256 * U) {
+            uint32_t c[U];
+            uint2 r[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint64_t i = base + (uint64_t)u * 256;
+                c[u] = 0xFFFFFFFFu;
+                if (i < i1) {
+                    c[u] = __ldg(&ctx[i]);
+                    if (HAS_CNT) r[u] = w.rec2_pair[stage0 + i];
+                    else r[u].x = w.rec2_sub[stage0 + i];
+                }
+            }
+            uint32_t slot[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c[u] < n_ctx) slot[u] = atomicAdd(&w.grp_cursor[(size_t)(gbase + c[u]) << w.cur_shift], 1u);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (c[u] >= n_ctx) continue;
+                if (HAS_CNT) w.rec_pair[slot[u]] = r[u];
+                else w.rec_sub[slot[u]] = r[u].x;
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------ K10: split big groups
@@ -765,14 +808,18 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
     if (ev) cudaEventRecord(ev[1], s);
     const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;
     const size_t acc_bytes = (size_t)nsm * 256 * 8;
-    const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
+    const int at_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
+    const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 8));
     if (w.has_cnt) {
-        cudaFuncSetAttribute(k_attr_scatter<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
-        k_attr_scatter<true, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
+        cudaFuncSetAttribute(k_attribute<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
+        k_attribute<true, 4><<<at_blocks, 256, acc_bytes, s>>>(w);
+        k_scatter<true, 8><<<sc_blocks, 256, 0, s>>>(w);
     } else {
-        cudaFuncSetAttribute(k_attr_scatter<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
-        k_attr_scatter<false, 4><<<sc_blocks, 256, acc_bytes, s>>>(w);
+        cudaFuncSetAttribute(k_attribute<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
+        k_attribute<false, 4><<<at_blocks, 256, acc_bytes, s>>>(w);
+        k_scatter<false, 8><<<sc_blocks, 256, 0, s>>>(w);
     }
+    *launches += 1;
     *launches += 1;
     if (ev) cudaEventRecord(ev[2], s);
     run_finish(w, s, sms, launches, ev);

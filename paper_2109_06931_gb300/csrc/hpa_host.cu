@@ -409,7 +409,8 @@ extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary
 // ------------------------------------------------------------------ aggregation calls
 // Scratch layout of one aggregation over N records in G groups (n_buf buffers).
 hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n, uint32_t cap, uint32_t sb,
-                                  uint32_t sbits, bool has_cnt, bool val64) {
+                                  uint32_t sbits, bool has_cnt, bool val64, uint64_t staged) {
+    const uint64_t N2 = std::max(N, staged);   // the second record buffer also stages samples in tile order
     const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
     w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
     w.span_log = std::min<uint32_t>(10, 32 - sbits);
@@ -433,10 +434,10 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
         const bool pair = has_cnt && !val64;
         w.rec_sub = pair ? nullptr : c.take<uint32_t>(N + 1);
         w.rec_cnt = nullptr;
-        w.rec2_sub = pair ? nullptr : c.take<uint32_t>(N + 1);
+        w.rec2_sub = pair ? nullptr : c.take<uint32_t>(N2 + 1);
         w.rec2_cnt = nullptr;
         w.rec_pair = pair ? c.take<uint2>(N + 1) : nullptr;
-        w.rec2_pair = pair ? c.take<uint2>(N + 1) : nullptr;
+        w.rec2_pair = pair ? c.take<uint2>(N2 + 1) : nullptr;
         w.rec_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
         w.rec2_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
         w.tmp_key = c.take<uint32_t>(N + 1);
@@ -489,7 +490,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     if (cap != LEAF_CAP_SMALL && cap != LEAF_CAP_LARGE)
         return fail(HPA_E_INVALID_ARG, "leaf_capacity must be 0, %u or %u", LEAF_CAP_SMALL, LEAF_CAP_LARGE);
     AggWork w{};
-    hpa_status st = carve_work(w, N, G, n, cap, sb, sbits, has_cnt, false);
+    hpa_status st = carve_work(w, N, G, n, cap, sb, sbits, has_cnt, false, tiles * TILE);
     if (st) return st;
     w.n_tiles = tiles;
     // descriptors
@@ -546,7 +547,7 @@ extern "C" hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t 
     cudaSetDevice(h->device);
     const uint64_t N = max_samples, G = max_groups;
     const uint64_t L = G + 6 * (N / LEAF_CAP_SMALL + 1) + 300;
-    size_t bytes = (G + 1) * 4 * 5 + L * 4 * 5 + (N + 1) * (4 * 5 + 8) + 256 * 40 + scan_tmp_words(std::max(G, L)) * 4;
+    size_t bytes = (G + 1) * 4 * 12 + L * 4 * 5 + (N + TILE + 1) * (4 * 6 + 8) + 256 * 40 + scan_tmp_words(std::max(G, L)) * 4;
     return h->ensure_scratch(bytes + (1 << 20));
 }
 

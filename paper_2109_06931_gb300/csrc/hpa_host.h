@@ -112,7 +112,7 @@ struct hpa_handle {
     hpa_status refresh_bin_table();
     hpa_status aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs);
     hpa_status carve_work(hpa::AggWork& w, uint64_t N, uint64_t G, uint32_t n_buf, uint32_t cap, uint32_t sb,
-                          uint32_t sbits, bool has_cnt, bool val64);
+                          uint32_t sbits, bool has_cnt, bool val64, uint64_t staged = 0);
     // descriptors of single-output pipelines (expansion, union) in the staging area
     hpa_status stage_single_output(hpa::AggWork& w, uint32_t bin, uint32_t n_ctx, const hpa_profile& out);
 };

@@ -107,9 +107,9 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
         w.buf_first_leaf = c.take<uint32_t>(2);
         w.buf_bad = c.take<unsigned long long>(1);
         w.rec_sub = has_cnt ? nullptr : c.take<uint32_t>(N + 1);
-        w.rec2_sub = has_cnt ? nullptr : c.take<uint32_t>(N + 1);
+        w.rec2_sub = has_cnt ? nullptr : c.take<uint32_t>(w.n_tiles * TILE + 1);
         w.rec_pair = has_cnt ? c.take<uint2>(N + 1) : nullptr;
-        w.rec2_pair = has_cnt ? c.take<uint2>(N + 1) : nullptr;
+        w.rec2_pair = has_cnt ? c.take<uint2>(w.n_tiles * TILE + 1) : nullptr;
         w.tmp_key = c.take<uint32_t>(N + 1);
         w.tmp_val = c.take<uint64_t>(N + 1);
         w.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max<uint64_t>(G, L_max)));
