@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_grp_hist(AggWork w) {
         const uint32_t* ctx = B.ctx;
         uint32_t bad = 0;
         for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const uint32_t c = __ldg(&ctx[i]);
+            const uint32_t c = ld_stream(&ctx[i]);
             if (c >= cur_n) { ++bad; continue; }
             if (priv) atomicAdd(&sh[c], 1u);
             else atomicAdd(&w.grp_hist[cur_base + c], 1u);
@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
     __shared__ unsigned long long unk[HPA_MAX_STALL_DEV];
     const uint32_t tid = threadIdx.x;
     const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;       // stall slots per thread
+    const uint64_t keep = policy_evict_last();
     for (uint32_t r = 0; r < nsm; ++r) acc[r * 256 + tid] = 0;
     if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
     __syncthreads();
@@ -266,9 +267,9 @@ __global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
                 const uint64_t i = base + (uint64_t)u * 256;
                 ok[u] = i < i1;
                 if (ok[u]) {
-                    st[u] = __ldg(&B.stall[i]);
-                    pc[u] = __ldg((const unsigned long long*)&B.pc[i]);
-                    cnt[u] = (HAS_CNT && B.count) ? __ldg(&B.count[i]) : 1u;
+                    st[u] = ld_stream(&B.stall[i]);
+                    pc[u] = ld_stream((const unsigned long long*)&B.pc[i]);
+                    cnt[u] = (HAS_CNT && B.count) ? ld_stream(&B.count[i]) : 1u;
                 }
             }
 #pragma unroll
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
                     const uint64_t o = pc[u] - bin.pc_base;
                     if (o < bin.span) {
                         off[u] = (uint32_t)o;
-                        nd[u] = __ldg(&bin.dir[off[u] >> bin.dshift]);
+                        nd[u] = ld_keep(&bin.dir[off[u] >> bin.dshift], keep);
                     }
                 }
             }
@@ -286,8 +287,8 @@ __global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
             for (int u = 0; u < U; ++u) {
                 if (nd[u] & DIR_SEARCH) {
                     uint32_t i = nd[u] & ~DIR_SEARCH;
-                    uint4 r = __ldg(&bin.rng[i]);
-                    while (r.y <= off[u] && i + 1 < bin.n_ranges) r = __ldg(&bin.rng[++i]);
+                    uint4 r = ld_keep4(&bin.rng[i], keep);
+                    while (r.y <= off[u] && i + 1 < bin.n_ranges) r = ld_keep4(&bin.rng[++i], keep);
                     nd[u] = (r.x <= off[u] && off[u] < r.y) ? r.z : M;
                 }
             }
@@ -297,8 +298,8 @@ __global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
                 const uint64_t i = base + (uint64_t)u * 256;
                 const bool bad_stall = st[u] >= B.n_stall;
                 const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
-                if (HAS_CNT) w.rec2_pair[stage0 + i] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
-                else w.rec2_sub[stage0 + i] = sub;
+                if (HAS_CNT) st_stream(&w.rec2_pair[stage0 + i], make_uint2(sub, bad_stall ? 0u : cnt[u]));
+                else st_stream(&w.rec2_sub[stage0 + i], sub);
                 if (bad_stall) {
                     ++bad;
                 } else {
@@ -333,9 +334,9 @@ __global__ void __launch_bounds__(256) k_scatter(AggWork w) {
                 const uint64_t i = base + (uint64_t)u * 256;
                 c[u] = 0xFFFFFFFFu;
                 if (i < i1) {
-                    c[u] = __ldg(&ctx[i]);
-                    if (HAS_CNT) r[u] = w.rec2_pair[stage0 + i];
-                    else r[u].x = w.rec2_sub[stage0 + i];
+                    c[u] = ld_stream(&ctx[i]);
+                    if (HAS_CNT) r[u] = ld_stream(&w.rec2_pair[stage0 + i]);
+                    else r[u].x = ld_stream(&w.rec2_sub[stage0 + i]);
                 }
             }
             uint32_t slot[U];
@@ -758,6 +759,21 @@ void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
     *launches += 4;
 }
 
+__global__ void k_zero_totals(AggWork w) {
+    for (uint32_t b = blockIdx.x; b < w.n_buf; b += gridDim.x) {
+        const BufDev& B = w.bufs[b];
+        for (uint32_t r = threadIdx.x; r < B.n_stall; r += blockDim.x) {
+            if (B.total) B.total[r] = 0;
+            if (B.unknown) B.unknown[r] = 0;
+        }
+    }
+}
+
+void launch_zero_totals(const AggWork& w, cudaStream_t s, uint64_t* launches) {
+    k_zero_totals<<<std::min<uint32_t>(w.n_buf, 1024), 32, 0, s>>>(w);
+    *launches += 1;
+}
+
 void launch_finalize(const AggWork& w, cudaStream_t s, uint64_t* launches) {
     k_finalize<<<1, 256, 0, s>>>(w);
     *launches += 1;
@@ -774,8 +790,8 @@ static void run_finish(const AggWork& w, cudaStream_t s, int sms, uint64_t* laun
     if (w.val64) {
         launch_leaf<256, LEAF_CAP_SMALL, true, uint64_t>(w, s, sms, 1);
     } else if (w.cap == LEAF_CAP_LARGE) {
-        if (w.has_cnt) launch_leaf<512, LEAF_CAP_LARGE, true>(w, s, sms, 1);
-        else launch_leaf<512, LEAF_CAP_LARGE, false>(w, s, sms, 1);
+        if (w.has_cnt) launch_leaf<LEAF_THREADS_LARGE, LEAF_CAP_LARGE, true>(w, s, sms, 1);
+        else launch_leaf<LEAF_THREADS_LARGE, LEAF_CAP_LARGE, false>(w, s, sms, 1);
     } else {
         if (w.has_cnt) launch_leaf<256, LEAF_CAP_SMALL, true>(w, s, sms, 2);
         else launch_leaf<256, LEAF_CAP_SMALL, false>(w, s, sms, 2);

@@ -57,6 +57,34 @@ __device__ __forceinline__ uint32_t attribute_pc(const DevBinary& b, uint64_t pc
     return (r.x <= off && off < r.y) ? r.z : b.n_nodes;
 }
 
+// L2 cache policies: tables that every sample probes should stay in L2
+// (evict_last); data read or written once streams through (evict_first).
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t* a, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_keep4(const uint4* a, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(pol));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* a) { return __ldcs(a); }
+__device__ __forceinline__ void st_stream(uint2* a, uint2 v) { __stcs(a, v); }
+__device__ __forceinline__ void st_stream(uint32_t* a, uint32_t v) { __stcs(a, v); }
+
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;

@@ -133,6 +133,7 @@ hpa_handle::~hpa_handle() {
     if (d_bins) cudaFree(d_bins);
     if (staging_event) cudaEventDestroy(staging_event);
     for (auto& g : graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
     for (auto& v : ev_pool) for (cudaEvent_t e : v) cudaEventDestroy(e);
     for (auto& v : ev_pending) for (cudaEvent_t e : v) cudaEventDestroy(e);
     if (host_io) cudaFree(host_io);
@@ -456,7 +457,8 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
     return HPA_OK;
 }
 
-hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs) {
+hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs,
+                                 bool use_graph) {
     if (n == 0) return HPA_OK;
     uint64_t N = 0, G = 0, tiles = 0;
     uint32_t max_nodes = 0, max_stall = 1;
@@ -523,17 +525,69 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     }
     htile[n] = tb;
     hgrp[n] = gb;
-    if ((st = upload_staging(used))) return st;
     char* ds = (char*)d_staging;
     w.bufs = (const BufDev*)(ds + ((char*)hb - (char*)staging));
     w.buf_tile = (const uint64_t*)(ds + ((char*)htile - (char*)staging));
     w.buf_grp = (const uint32_t*)(ds + ((char*)hgrp - (char*)staging));
+    if (use_graph && !timing) return launch_graph(w, used, n, in);
+    if ((st = upload_staging(used))) return st;
     for (uint32_t b = 0; b < n; ++b) {
         if (outs[b].total) cudaMemsetAsync(outs[b].total, 0, 8 * in[b].n_stall, stream);
         if (outs[b].unknown) cudaMemsetAsync(outs[b].unknown, 0, 8 * in[b].n_stall, stream);
     }
     run_aggregate(w, stream, sms, &launches, timing ? phase_events() : nullptr);
     return cuda(cudaGetLastError(), "aggregation launch");
+}
+
+// One CUDA graph per batch shape: the descriptor upload (from the pinned
+// staging area, rewritten before every replay), the zeroing of totals and
+// every kernel of the pipeline.  User pointers reach the kernels only
+// through the uploaded descriptors, so a replay serves new buffers of the
+// same shape.
+static uint64_t mix64(uint64_t h, uint64_t v) {
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+hpa_status hpa_handle::launch_graph(const AggWork& w, size_t staged_bytes, uint32_t n, const hpa_samples* in) {
+    uint64_t key = 0;
+    key = mix64(key, w.G); key = mix64(key, w.n_buf); key = mix64(key, w.n_tiles); key = mix64(key, w.cap);
+    key = mix64(key, w.sb); key = mix64(key, w.sbits); key = mix64(key, w.L_max); key = mix64(key, w.has_cnt);
+    key = mix64(key, w.cur_shift); key = mix64(key, staged_bytes); key = mix64(key, (uint64_t)(uintptr_t)w.grp_hist);
+    for (uint32_t b = 0; b < n; ++b) key = mix64(mix64(key, in[b].n), in[b].n_ctx);
+    CachedGraph* g = nullptr;
+    for (auto& c : graphs)
+        if (c.key == key && c.epoch == scratch_epoch) g = &c;
+    hpa_status st;
+    if (!g) {
+        if (!capture_stream && cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda(cudaGetLastError(), "capture stream");
+        cudaGraph_t graph = nullptr;
+        uint64_t k0 = launches;
+        if ((st = cuda(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeRelaxed), "begin capture"))) return st;
+        cudaMemcpyAsync(d_staging, staging, staged_bytes, cudaMemcpyHostToDevice, capture_stream);
+        launch_zero_totals(w, capture_stream, &launches);
+        run_aggregate(w, capture_stream, sms, &launches, nullptr);
+        cudaError_t e = cudaStreamEndCapture(capture_stream, &graph);
+        if ((st = cuda(e, "end capture"))) return st;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if ((st = cuda(e, "graph instantiate"))) return st;
+        if (graphs.size() >= 16) {
+            cudaGraphExecDestroy(graphs.front().exec);
+            graphs.erase(graphs.begin());
+        }
+        graphs.push_back(CachedGraph{key, scratch_epoch, launches - k0, exec});
+        launches = k0;
+        g = &graphs.back();
+    }
+    if ((st = cuda(cudaGraphLaunch(g->exec, stream), "graph launch"))) return st;
+    launches += g->kernels;
+    ++graph_replays;
+    st = cuda(cudaEventRecord(staging_event, stream), "cudaEventRecord");
+    staging_event_live = true;
+    return st;
 }
 
 extern "C" hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, const hpa_samples* in, hpa_profile* out) {

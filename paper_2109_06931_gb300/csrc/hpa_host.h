@@ -62,6 +62,7 @@ struct Carve {
 struct CachedGraph {
     uint64_t key = 0;
     uint64_t epoch = 0;
+    uint64_t kernels = 0;       // kernels one replay launches
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -91,6 +92,8 @@ struct hpa_handle {
     size_t host_io_cap = 0;
     void* pinned_io = nullptr;
     size_t last_carve = 0;        // scratch bytes used by the last carve_work
+    cudaStream_t capture_stream = nullptr;
+    uint64_t graph_replays = 0;
     void* cct_scratch = nullptr;
     size_t cct_cap = 0;
     // phase timing
@@ -110,7 +113,9 @@ struct hpa_handle {
     hpa_status upload_staging(size_t bytes);
     hpa::Binary* binary(uint32_t id);
     hpa_status refresh_bin_table();
-    hpa_status aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs);
+    hpa_status aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs,
+                         bool use_graph = false);
+    hpa_status launch_graph(const hpa::AggWork& w, size_t staged_bytes, uint32_t n, const hpa_samples* in);
     hpa_status carve_work(hpa::AggWork& w, uint64_t N, uint64_t G, uint32_t n_buf, uint32_t cap, uint32_t sb,
                           uint32_t sbits, bool has_cnt, bool val64, uint64_t staged = 0);
     // descriptors of single-output pipelines (expansion, union) in the staging area

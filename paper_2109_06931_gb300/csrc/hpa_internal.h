@@ -82,7 +82,8 @@ constexpr int TILE = 4096;            // samples per tile of the sample-reading 
 constexpr uint32_t HPA_MAX_STALL_DEV = 32;
 constexpr uint32_t HIST_SMEM_MAX = 24576;    // contexts counted in shared memory (96 KB)
 constexpr uint32_t LEAF_CAP_SMALL = 4096;   // 256 threads, two CTAs per SM
-constexpr uint32_t LEAF_CAP_LARGE = 11264;  // 512 threads, one CTA per SM
+constexpr uint32_t LEAF_CAP_LARGE = 10240;  // 1024 threads, one CTA per SM
+constexpr int LEAF_THREADS_LARGE = 1024;
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_EPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_EPT;
@@ -113,6 +114,10 @@ struct ExpandSrc {
     uint32_t n_ctx;
 };
 void run_expand_aggregate(const AggWork& w, const ExpandSrc& x, cudaStream_t s, int sms, uint64_t* launches);
+
+// zero every buffer's per-stall totals (device-side, so a captured graph
+// reads the current descriptors)
+void launch_zero_totals(const AggWork& w, cudaStream_t s, uint64_t* launches);
 
 // shared stages for other producers
 void clear_work(const AggWork& w, cudaStream_t s);

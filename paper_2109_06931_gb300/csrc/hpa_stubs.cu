@@ -3,5 +3,5 @@
 extern "C" hpa_status hpa_attribute_batch(hpa_handle* h, uint32_t n, const uint32_t* ids, const hpa_samples* in, hpa_profile* outs) {
     if (!h || (n && (!ids || !in || !outs))) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
-    return h->aggregate(n, ids, in, outs);
+    return h->aggregate(n, ids, in, outs, true);
 }

@@ -21,6 +21,7 @@ HPA_UNKNOWN_NODE = 0xFFFFFFFF
 HPA_NO_PARENT = 0xFFFFFFFF
 HPA_MAX_STALL = 32
 HPA_EDGE_FIXUP, HPA_EDGE_FIXUP2, HPA_EDGE_INTRA_SCC = 1, 2, 4
+LEAF_CAPS = (4096, 10240)   # leaf capacities of the aggregation (small, large)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_TABLE", 3: "INVALID_SAMPLE", 4: "CAPACITY",
                 5: "OOM", 6: "CUDA", 7: "TIMEOUT", 8: "INTERNAL"}
 

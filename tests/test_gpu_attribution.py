@@ -111,7 +111,7 @@ def test_skewed_contexts(H, large_bin):
     assert_same_keys(out, oracle.attribute_samples(B, S))
 
 
-@pytest.mark.parametrize("cap", [4096, 11264])
+@pytest.mark.parametrize("cap", [4096, 10240])
 def test_leaf_capacity_variants_agree(cap, plain):
     from paper_2109_06931_gb300 import hpa
     B, _ = plain
@@ -185,3 +185,21 @@ def test_host_entry_point(H, plain):
     for a, b in zip((out["ctx"], out["node"], out["stall"], out["val"]), (ref.ctx, ref.node, ref.stall, ref.val)):
         assert np.array_equal(a[:k], b)
     assert np.array_equal(out["total"][:16], ref.total)
+
+
+def test_batch_graph_replay_with_new_buffers(H, plain, large_bin):
+    """Two batched calls with the same shape replay one captured graph; the
+    second call's buffers hold different samples and must give their own
+    results."""
+    B1, b1 = plain
+    B2, b2 = large_bin
+    sizes = [50_000, 3, 120_000, 9_000]
+    bins = [b1, b2, b1, b2]
+    Bs = [B1, B2, B1, B2]
+    for rep in range(3):
+        ss = [synth.make_samples(500 + 10 * rep + i, Bs[i], n, 40 + i, 1.0, counts=(i != 2), device="cuda")
+              for i, n in enumerate(sizes)]
+        outs = H.attribute_batch(bins, ss)
+        H.sync()
+        for o, S, B in zip(outs, ss, Bs):
+            assert_same_keys(o, oracle.attribute_samples(B, S))
