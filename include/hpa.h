@@ -42,6 +42,7 @@ typedef int32_t hpa_status;
 #define HPA_E_CUDA            6  /* a CUDA runtime call failed                      */
 #define HPA_E_TIMEOUT         7  /* a bounded device wait gave up                   */
 #define HPA_E_INTERNAL        8  /* internal invariant violated (a bug)             */
+#define HPA_PENDING           9  /* a served request has not completed yet           */
 
 #define HPA_UNKNOWN_NODE 0xFFFFFFFFu  /* node of a PC covered by no range          */
 #define HPA_NO_PARENT    0xFFFFFFFFu  /* parent of a root                          */
@@ -304,6 +305,44 @@ hpa_status hpa_propagate_inclusive(hpa_handle* h, uint32_t binary_id, const hpa_
  * issued_mask).  ps: HOST array of profile descriptors with DEVICE data.    */
 hpa_status hpa_derive_metrics(hpa_handle* h, const hpa_profile* const* ps, uint32_t n_profiles,
                               hpa_derived* out);
+
+/* ---- serving ---------------------------------------------------------- */
+
+/* A request loop over sample buffers that arrive over time (the serving
+ * analogue of streaming aggregation, Section 6.1).  Requests are admitted in
+ * arrival order while their device bytes fit in a reserved pool of
+ * mem_cap_bytes (admission by free device memory); admitted requests form
+ * batches that run as one batched aggregation while the next batch's samples
+ * are copied in and the previous batch's keys are copied out.  Structure
+ * tables stay resident in the handle; results are written to the host arrays
+ * given at submit.  The server owns the handle while it exists: make no other
+ * call on that handle until hpa_server_destroy.                               */
+typedef struct hpa_server hpa_server;
+typedef struct {
+    uint64_t mem_cap_bytes;  /* device pool for admitted requests; 0 = 60 GiB    */
+    uint32_t max_batch;      /* requests per batch; 0 = 64                      */
+    uint32_t reserved[5];
+} hpa_server_options;
+typedef struct {
+    uint64_t submitted, completed, rejected, samples, batches;
+    double p50_ms, p99_ms, max_ms, mean_ms;   /* latency: submit -> result in host arrays */
+    double busy_s;                            /* first admission -> last completion        */
+} hpa_server_stats;
+
+hpa_status hpa_server_create(hpa_handle* h, const hpa_server_options* opt, hpa_server** out);
+/* Queue one request: in holds HOST sample arrays (pinned for full speed), out
+ * HOST key arrays (out->n_keys a host uint64); both must stay valid until the
+ * request completes.  Results equal hpa_attribute_samples on the same
+ * samples.  *ticket names the request.                                       */
+hpa_status hpa_server_submit(hpa_server* s, uint32_t binary_id, const hpa_samples* in, hpa_profile* out,
+                             uint64_t* ticket);
+/* HPA_PENDING while the request runs (waiting up to wait_ms first), else its
+ * final status (HPA_OK, HPA_E_CAPACITY, HPA_E_OOM if it can never fit); a
+ * completed ticket is forgotten after it has been reported once.            */
+hpa_status hpa_server_poll(hpa_server* s, uint64_t ticket, int wait_ms);
+hpa_status hpa_server_stats_get(hpa_server* s, hpa_server_stats* st);
+/* Finish every queued request, then free the server (not the handle).      */
+hpa_status hpa_server_destroy(hpa_server* s);
 
 #ifdef __cplusplus
 }

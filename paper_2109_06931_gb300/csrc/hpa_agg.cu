@@ -135,11 +135,21 @@ __global__ void __launch_bounds__(256) k_grp_hist(AggWork w) {
         const uint64_t i1 = min(i0 + TILE, B.n);
         const uint32_t* ctx = B.ctx;
         uint32_t bad = 0;
-        for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const uint32_t c = ld_stream(&ctx[i]);
-            if (c >= cur_n) { ++bad; continue; }
+        auto count = [&](uint32_t c) {
+            if (c >= cur_n) { ++bad; return; }
             if (priv) atomicAdd(&sh[c], 1u);
             else atomicAdd(&w.grp_hist[cur_base + c], 1u);
+        };
+        if (i1 - i0 == TILE && (((uintptr_t)(ctx + i0)) & 15) == 0) {
+            // full aligned tile: 16 contexts per thread in four 16-byte loads
+            const uint4* v = reinterpret_cast<const uint4*>(ctx + i0);
+            uint4 q[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = ld_stream(&v[k * 256 + threadIdx.x]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { count(q[k].x); count(q[k].y); count(q[k].z); count(q[k].w); }
+        } else {
+            for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) count(ld_stream(&ctx[i]));
         }
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
     }

@@ -17,13 +17,14 @@ from . import build as _build
 
 HPA_OK, HPA_E_INVALID_ARG, HPA_E_INVALID_TABLE, HPA_E_INVALID_SAMPLE = 0, 1, 2, 3
 HPA_E_CAPACITY, HPA_E_OOM, HPA_E_CUDA, HPA_E_TIMEOUT, HPA_E_INTERNAL = 4, 5, 6, 7, 8
+HPA_PENDING = 9
 HPA_UNKNOWN_NODE = 0xFFFFFFFF
 HPA_NO_PARENT = 0xFFFFFFFF
 HPA_MAX_STALL = 32
 HPA_EDGE_FIXUP, HPA_EDGE_FIXUP2, HPA_EDGE_INTRA_SCC = 1, 2, 4
 LEAF_CAPS = (4096, 10240)   # leaf capacities of the aggregation (small, large)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_TABLE", 3: "INVALID_SAMPLE", 4: "CAPACITY",
-                5: "OOM", 6: "CUDA", 7: "TIMEOUT", 8: "INTERNAL"}
+                5: "OOM", 6: "CUDA", 7: "TIMEOUT", 8: "INTERNAL", 9: "PENDING"}
 
 vp, u8p, u32p, u64p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)
 
@@ -65,6 +66,16 @@ class hpa_cct(C.Structure):
     _fields_ = [("n_nodes", C.c_uint32), ("parent", vp)]
 
 
+class hpa_server_options(C.Structure):
+    _fields_ = [("mem_cap_bytes", C.c_uint64), ("max_batch", C.c_uint32), ("reserved", C.c_uint32 * 5)]
+
+
+class hpa_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("samples", C.c_uint64), ("batches", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("max_ms", C.c_double), ("mean_ms", C.c_double), ("busy_s", C.c_double)]
+
+
 class hpa_derived(C.Structure):
     _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp),
                 ("sum", vp), ("min", vp), ("max", vp), ("mean", vp), ("std", vp), ("cov", vp),
@@ -75,7 +86,8 @@ EXPORTS = ["hpa_create", "hpa_destroy", "hpa_last_error", "hpa_sync", "hpa_reser
            "hpa_load_structure", "hpa_unload_structure", "hpa_binary_info_get", "hpa_attribute_samples",
            "hpa_attribute_samples_host", "hpa_attribute_batch", "hpa_apportion_callgraph",
            "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_set_phase_timing", "hpa_phase_times",
-           "hpa_attribute_samples_noalloc"]
+           "hpa_attribute_samples_noalloc", "hpa_server_create", "hpa_server_submit", "hpa_server_poll",
+           "hpa_server_stats_get", "hpa_server_destroy"]
 PHASES = ["hist+plan", "attribute+scatter", "big-split", "leaf sort/reduce", "emit"]
 
 _lib = None
@@ -112,6 +124,11 @@ def lib(build_if_needed: bool = True):
         L.hpa_derive_metrics.argtypes = [H, C.POINTER(C.POINTER(hpa_profile)), C.c_uint32, C.POINTER(hpa_derived)]
         L.hpa_attribute_samples_noalloc.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_set_phase_timing.argtypes = [H, C.c_int]
+        L.hpa_server_create.argtypes = [H, C.POINTER(hpa_server_options), C.POINTER(vp)]
+        L.hpa_server_submit.argtypes = [vp, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile), u64p]
+        L.hpa_server_poll.argtypes = [vp, C.c_uint64, C.c_int]
+        L.hpa_server_stats_get.argtypes = [vp, C.POINTER(hpa_server_stats)]
+        L.hpa_server_destroy.argtypes = [vp]
         L.hpa_phase_times.argtypes = [H, C.c_uint32, vp, u64p, u32p]
         for f in EXPORTS:
             if f not in ("hpa_last_error", "hpa_kernel_launches"):
@@ -400,3 +417,48 @@ class Hpa:
         for o, s, c in zip(outs, samples, cos):
             o.n_ctx, o.n_stall, o.n_nodes = s.n_ctx, s.n_stall, c.n_nodes
         return outs
+
+
+class Server:
+    """Request loop over host sample buffers (hpa_server_*)."""
+
+    def __init__(self, h: Hpa, mem_cap_bytes: int = 0, max_batch: int = 0):
+        self.h = h
+        self.s = C.c_void_p()
+        opt = hpa_server_options(mem_cap_bytes, max_batch)
+        h.check(h.L.hpa_server_create(h.h, C.byref(opt), C.byref(self.s)))
+        self._live = {}
+
+    def submit(self, bid: int, pc, ctx, stall, count, n_ctx: int, n_stall: int, capacity: int | None = None):
+        """Host arrays (pinned CPU tensors for full speed).  Returns a ticket; the
+        result lands in self.result(ticket) once poll() reports completion."""
+        n = int(pc.shape[0])
+        cap = max(1, n if capacity is None else capacity)
+        out = dict(ctx=torch.empty(cap, dtype=torch.int32).pin_memory(), node=torch.empty(cap, dtype=torch.int32).pin_memory(),
+                   stall=torch.empty(cap, dtype=torch.uint8).pin_memory(), val=torch.empty(cap, dtype=torch.int64).pin_memory(),
+                   n=torch.zeros(1, dtype=torch.int64), total=torch.zeros(HPA_MAX_STALL, dtype=torch.int64).pin_memory(),
+                   unknown=torch.zeros(HPA_MAX_STALL, dtype=torch.int64).pin_memory())
+        ci = Hpa.samples_c(pc, ctx, stall, count, n_ctx, n_stall)
+        co = hpa_profile(cap, _ptr(out["ctx"]), _ptr(out["node"]), _ptr(out["stall"]), _ptr(out["val"]),
+                         _ptr(out["n"]), _ptr(out["total"]), _ptr(out["unknown"]), 0, 0, 0, 0)
+        t = C.c_uint64()
+        self.h.check(self.h.L.hpa_server_submit(self.s, bid, C.byref(ci), C.byref(co), C.byref(t)))
+        self._live[t.value] = (out, (pc, ctx, stall, count))
+        return int(t.value)
+
+    def poll(self, ticket: int, wait_ms: int = 0) -> int:
+        return int(self.h.L.hpa_server_poll(self.s, ticket, wait_ms))
+
+    def result(self, ticket: int):
+        out, _ = self._live.pop(ticket)
+        return out
+
+    def stats(self):
+        st = hpa_server_stats()
+        self.h.check(self.h.L.hpa_server_stats_get(self.s, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in hpa_server_stats._fields_}
+
+    def close(self):
+        if self.s:
+            self.h.L.hpa_server_destroy(self.s)
+            self.s = C.c_void_p()

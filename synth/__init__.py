@@ -489,3 +489,45 @@ def batch_sizes(seed: int, n_buf: int, lo: float, hi: float) -> np.ndarray:
     """Log-uniform buffer sizes in [lo, hi]."""
     u = np_unif(seed, 501, np.arange(n_buf))
     return np.floor(np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))).astype(np.int64)
+
+
+# batched: 256 per-rank buffers, sizes log-uniform in [1e4, 5e7], against 8
+# binaries of 2,000-40,000 functions (assigned round-robin)
+@dataclasses.dataclass
+class BatchWorkload:
+    name: str
+    seed: int
+    n_buffers: int
+    size_lo: float
+    size_hi: float
+    n_binaries: int
+    funcs_lo: int
+    funcs_hi: int
+    n_ctx: int
+    zipf_s: float
+    counts: bool
+    n_stall: int = 16
+
+    def sizes(self) -> np.ndarray:
+        return batch_sizes(self.seed, self.n_buffers, self.size_lo, self.size_hi)
+
+    def binary_params(self):
+        """(functions, code bytes, line ranges, call sites) per binary: the
+        large workload's densities scaled by the function count."""
+        u = np_unif(self.seed, 601, np.arange(self.n_binaries))
+        F = np.floor(np.exp(math.log(self.funcs_lo) + u * (math.log(self.funcs_hi) - math.log(self.funcs_lo))))
+        out = []
+        for f in F.astype(np.int64):
+            out.append((int(f), int(f) * 13_422, int(f) * 50, int(f) * 3))   # ~13 KB, 50 lines, 3 calls / function
+        return out
+
+    def binaries(self):
+        return [make_binary(self.seed * 31 + i, f, seg, lines, calls)
+                for i, (f, seg, lines, calls) in enumerate(self.binary_params())]
+
+    def buffer(self, b: int, binary: Binary, n: int, device="cpu") -> Samples:
+        return make_samples(self.seed * 1_000 + b, binary, n, self.n_ctx, self.zipf_s, self.n_stall,
+                            self.counts, device)
+
+
+BATCHED = BatchWorkload("batched-256x", SEED_BASE + 3, 256, 1e4, 5e7, 8, 2000, 40_000, 500, 1.0, True)
