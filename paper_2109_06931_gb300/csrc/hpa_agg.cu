@@ -22,6 +22,7 @@
 // (ctx, node, stall).
 
 #include <algorithm>
+#include <type_traits>
 
 #include "hpa_internal.h"
 
@@ -413,7 +414,11 @@ __global__ void __launch_bounds__(256) k_big_partition(AggWork w) {
 // ------------------------------------------------------------------ K11: leaves
 template <int THREADS, int CAP, bool HAS_CNT, typename V>
 struct LeafCfg {
-    using Sort = BlockRadix<THREADS, CAP, 8, V, HAS_CNT>;
+    // 32-bit counts (or none): packed elements, digits up to 9 bits;
+    // 64-bit values: key and value arrays, 8-bit digits
+    static constexpr bool PACKED = sizeof(V) == 4;
+    using E = std::conditional_t<HAS_CNT, uint64_t, uint32_t>;
+    using Sort = std::conditional_t<PACKED, PackedRadix<THREADS, CAP, E>, BlockRadix<THREADS, CAP, 8, V, HAS_CNT>>;
     static constexpr int EPT = (CAP + THREADS - 1) / THREADS;
     static constexpr size_t SORT_BYTES = sizeof(typename Sort::Smem);
     static constexpr int WD = 8192;                              // dense window (uint64 counters)
@@ -440,8 +445,9 @@ __device__ __forceinline__ unsigned long long val_at(const V* vals, int i) {
 
 // mode 0: write every run at its run id; mode 1: count runs with a non-zero
 // sum; mode 2: write only runs with a non-zero sum, compacted from nz_base.
-template <typename V, bool HAS_V>
-__device__ __forceinline__ uint32_t warp_runs(const uint32_t* K, const V* vals, int n, int w0, int w1,
+// KA(i) gives the key of element i, VA(i) its value.
+template <typename KA, typename VA>
+__device__ __forceinline__ uint32_t warp_runs(KA K, VA Vf, int n, int w0, int w1,
                                               int run0, unsigned long long carry, int mode, uint32_t nz_base,
                                               uint32_t* out_key, unsigned long long* out_val) {
     const int lane = lane_id();
@@ -450,9 +456,9 @@ __device__ __forceinline__ uint32_t warp_runs(const uint32_t* K, const V* vals, 
     for (int base = w0; base < w1; base += 32) {
         const int i = base + lane;
         const bool ok = i < w1;
-        const uint32_t k = ok ? K[i] : 0u;
-        const bool h = ok && (i == 0 || K[i - 1] != k);
-        unsigned long long v = ok ? val_at<V, HAS_V>(vals, i) : 0ull;
+        const uint32_t k = ok ? K(i) : 0u;
+        const bool h = ok && (i == 0 || K(i - 1) != k);
+        unsigned long long v = ok ? Vf(i) : 0ull;
         const uint32_t hb = __ballot_sync(0xffffffffu, h);
         // inclusive segmented scan of (h, v) across the row
         uint32_t f = h;
@@ -467,7 +473,7 @@ __device__ __forceinline__ uint32_t warp_runs(const uint32_t* K, const V* vals, 
         }
         if (!f) v += carry;
         const int rid = run + __popc(hb & (lanemask_lt() | (1u << lane)));
-        const bool end = ok && (i == n - 1 || K[i + 1] != k);
+        const bool end = ok && (i == n - 1 || K(i + 1) != k);
         if (mode == 0) {
             if (end) { out_key[rid] = k; out_val[rid] = v; }
         } else {
@@ -487,16 +493,16 @@ __device__ __forceinline__ uint32_t warp_runs(const uint32_t* K, const V* vals, 
 }
 
 // per-warp heads and open-run tail over the warp's chunk
-template <typename V, bool HAS_V>
-__device__ __forceinline__ RunCtx warp_run_summary(const uint32_t* K, const V* vals, int w0, int w1) {
+template <typename KA, typename VA>
+__device__ __forceinline__ RunCtx warp_run_summary(KA K, VA Vf, int w0, int w1) {
     const int lane = lane_id();
     RunCtx r{0, 0ull, 0};
     for (int base = w0; base < w1; base += 32) {
         const int i = base + lane;
         const bool ok = i < w1;
-        const uint32_t k = ok ? K[i] : 0u;
-        const bool h = ok && (i == 0 || K[i - 1] != k);
-        const unsigned long long v = ok ? val_at<V, HAS_V>(vals, i) : 0ull;
+        const uint32_t k = ok ? K(i) : 0u;
+        const bool h = ok && (i == 0 || K(i - 1) != k);
+        const unsigned long long v = ok ? Vf(i) : 0ull;
         const uint32_t hb = __ballot_sync(0xffffffffu, h);
         r.heads += __popc(hb);
         if (hb) {
@@ -571,8 +577,14 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 uint32_t k;
                 unsigned long long v;
                 rec(start + i, k, v);
-                S.key[0][i] = k;
-                if constexpr (HAS_CNT) { S.val[0][i] = (V)v; zero |= v == 0; }
+                if constexpr (Cfg::PACKED) {
+                    if constexpr (HAS_CNT) S.el[0][i] = ((uint64_t)k << 32) | (uint32_t)v;
+                    else S.el[0][i] = k;
+                } else {
+                    S.key[0][i] = k;
+                    if constexpr (HAS_CNT) S.val[0][i] = (V)v;
+                }
+                if constexpr (HAS_CNT) zero |= v == 0;
             }
             if (threadIdx.x == 0) s_any_zero = 0;
             __syncthreads();
@@ -581,16 +593,30 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 // tag each record with its group inside the leaf
                 for (uint32_t j = threadIdx.x; j < ng; j += THREADS) {
                     const uint32_t a = gb[j], e = min(gb[j + 1], n);
-                    for (uint32_t i = a; i < e; ++i) S.key[0][i] |= j << w.sbits;
+                    for (uint32_t i = a; i < e; ++i) {
+                        if constexpr (Cfg::PACKED) S.el[0][i] |= (typename Cfg::E)(j << w.sbits) << (HAS_CNT ? 32 : 0);
+                        else S.key[0][i] |= j << w.sbits;
+                    }
                 }
             }
             __syncthreads();
             const int cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
-            const uint32_t* Kc = S.key[cur];
-            const V* Vc = HAS_CNT ? S.val[HAS_CNT ? cur : 0] : nullptr;
+            auto Kc = [&S, cur](int i) -> uint32_t {
+                if constexpr (Cfg::PACKED) return Sort::key_of(S.el[cur][i]);
+                else return S.key[cur][i];
+            };
+            auto Vc = [&S, cur](int i) -> unsigned long long {
+                if constexpr (Cfg::PACKED) {
+                    if constexpr (HAS_CNT) return (uint32_t)S.el[cur][i];
+                    else return 1ull;
+                } else {
+                    if constexpr (HAS_CNT) return (unsigned long long)S.val[cur][i];
+                    else return 1ull;
+                }
+            };
             const int wch = ((((int)n + W - 1) / W) + 31) & ~31;
             const int w0 = min((int)n, warp * wch), w1 = min((int)n, w0 + wch);
-            const RunCtx rc = warp_run_summary<V, HAS_CNT>(Kc, Vc, w0, w1);
+            const RunCtx rc = warp_run_summary(Kc, Vc, w0, w1);
             if (lane == 0) { s_run0[warp] = rc.heads; s_carry[warp] = rc.tail; s_nz[warp] = rc.has_head; }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -613,10 +639,10 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
             const unsigned long long carry = s_carry[warp];
             uint32_t n_out = n_runs;
             if (!s_any_zero) {
-                warp_runs<V, HAS_CNT>(Kc, Vc, (int)n, w0, w1, run0, carry, 0, 0, w.tmp_key + start, (unsigned long long*)(w.tmp_val + start));
+                warp_runs(Kc, Vc, (int)n, w0, w1, run0, carry, 0, 0, w.tmp_key + start, (unsigned long long*)(w.tmp_val + start));
             } else {
                 // keys whose counts add up to 0 are omitted (compacting walk)
-                const uint32_t nzc = warp_runs<V, HAS_CNT>(Kc, Vc, (int)n, w0, w1, run0, carry, 1, 0, nullptr, nullptr);
+                const uint32_t nzc = warp_runs(Kc, Vc, (int)n, w0, w1, run0, carry, 1, 0, nullptr, nullptr);
                 __syncthreads();
                 if (lane == 0) s_nz[warp] = nzc;
                 __syncthreads();
@@ -627,7 +653,7 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 }
                 __syncthreads();
                 n_out = sw[32];
-                warp_runs<V, HAS_CNT>(Kc, Vc, (int)n, w0, w1, run0, carry, 2, s_nz[warp], w.tmp_key + start,
+                warp_runs(Kc, Vc, (int)n, w0, w1, run0, carry, 2, s_nz[warp], w.tmp_key + start,
                                       (unsigned long long*)(w.tmp_val + start));
             }
             if (threadIdx.x == 0) w.leaf_d[l] = n_out;

@@ -245,6 +245,96 @@ struct BlockRadix {
     }
 };
 
+// Block-wide stable LSD radix sort of packed elements: E = uint64_t holds
+// (key << 32 | value), E = uint32_t a key alone.  Digits are at most 9 bits
+// (a 26-bit key takes 3 passes); passes and digit width follow the key width.
+// Counter rows are padded by one word so the digit-major scan is free of bank
+// conflicts.  Same stable ranking as BlockRadix (warp-contiguous chunks,
+// __match_any_sync within a 32-element row).
+template <int THREADS, int CAP, typename E>
+struct PackedRadix {
+    static constexpr int W = THREADS / 32;
+    static constexpr int MAXB = 9, MAXBINS = 1 << MAXB, ROW = MAXBINS + 1;
+    static constexpr int MAX_EPT = MAXBINS * W / THREADS;
+
+    struct Smem {
+        E el[2][CAP];
+        uint16_t rank[CAP];
+        uint32_t cnt[W * ROW];
+        uint32_t sw[33];
+    };
+
+    __device__ static __forceinline__ uint32_t key_of(E e) {
+        if constexpr (sizeof(E) == 8) return (uint32_t)(e >> 32);
+        else return (uint32_t)e;
+    }
+
+    __device__ static int sort(Smem& s, int n, int bits) {
+        if (bits <= 0) return 0;
+        const int warp = threadIdx.x >> 5;
+        const int lane = lane_id();
+        const int passes = (bits + MAXB - 1) / MAXB;
+        const int rb = (bits + passes - 1) / passes;
+        const int bins = 1 << rb;
+        const int ept = bins * W / THREADS;
+        const int chunk = ((n + W - 1) / W + 31) & ~31;
+        const int lo = warp * chunk;
+        const int hi = min(n, lo + chunk);
+        int cur = 0;
+        for (int shift = 0; shift < bits; shift += rb) {
+            const uint32_t dmask = (1u << min(rb, bits - shift)) - 1;
+            for (int i = threadIdx.x; i < W * ROW; i += THREADS) s.cnt[i] = 0;
+            __syncthreads();
+            uint32_t* row = s.cnt + warp * ROW;
+            for (int base = lo; base < lo + chunk; base += 32) {
+                const int i = base + lane;
+                const bool ok = i < hi;
+                const uint32_t d = ok ? ((key_of(s.el[cur][i]) >> shift) & dmask) : 0xFFFFFFFFu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t below = __popc(peers & lanemask_lt());
+                if (ok) s.rank[i] = (uint16_t)(row[d] + below);
+                __syncwarp();
+                if (ok && below == 0) row[d] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            {
+                // exclusive scan in digit-major, warp-minor order
+                const int b0 = threadIdx.x * ept;
+                uint32_t loc[MAX_EPT];
+                uint32_t sum = 0;
+#pragma unroll
+                for (int k = 0; k < MAX_EPT; ++k) {
+                    if (k < ept) {
+                        const int e = b0 + k;
+                        loc[k] = s.cnt[(e % W) * ROW + e / W];
+                        sum += loc[k];
+                    }
+                }
+                uint32_t tot;
+                uint32_t pre = block_exclusive_scan<uint32_t, THREADS>(sum, s.sw, &tot);
+#pragma unroll
+                for (int k = 0; k < MAX_EPT; ++k) {
+                    if (k < ept) {
+                        const int e = b0 + k;
+                        s.cnt[(e % W) * ROW + e / W] = pre;
+                        pre += loc[k];
+                    }
+                }
+                __syncthreads();
+            }
+            for (int i = lo + lane; i < hi; i += 32) {
+                const E x = s.el[cur][i];
+                const uint32_t d = (key_of(x) >> shift) & dmask;
+                s.el[cur ^ 1][row[d] + s.rank[i]] = x;
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        return cur;
+    }
+};
+
 __host__ __device__ inline uint32_t ceil_log2_u64(uint64_t x) {
     uint32_t b = 0;
     while ((1ull << b) < x) ++b;

@@ -82,8 +82,8 @@ constexpr int TILE = 4096;            // samples per tile of the sample-reading 
 constexpr uint32_t HPA_MAX_STALL_DEV = 32;
 constexpr uint32_t HIST_SMEM_MAX = 24576;    // contexts counted in shared memory (96 KB)
 constexpr uint32_t LEAF_CAP_SMALL = 4096;   // 256 threads, two CTAs per SM
-constexpr uint32_t LEAF_CAP_LARGE = 10240;  // 1024 threads, one CTA per SM
-constexpr int LEAF_THREADS_LARGE = 1024;
+constexpr uint32_t LEAF_CAP_LARGE = 10240;  // 512 threads, one CTA per SM
+constexpr int LEAF_THREADS_LARGE = 512;
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_EPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_EPT;
