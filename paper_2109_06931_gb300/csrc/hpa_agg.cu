@@ -573,18 +573,23 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 __syncthreads();
             }
             uint32_t zero = 0;
-            for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
-                uint32_t k;
-                unsigned long long v;
-                rec(start + i, k, v);
-                if constexpr (Cfg::PACKED) {
-                    if constexpr (HAS_CNT) S.el[0][i] = ((uint64_t)k << 32) | (uint32_t)v;
-                    else S.el[0][i] = k;
-                } else {
-                    S.key[0][i] = k;
-                    if constexpr (HAS_CNT) S.val[0][i] = (V)v;
+            if constexpr (Cfg::PACKED) {
+                // records land in shared memory verbatim, without a register round trip
+                for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
+                    if constexpr (HAS_CNT) cp_async8(&S.el[0][i], &src_pair[start + i]);
+                    else cp_async4(&S.el[0][i], &src_sub[start + i]);
                 }
-                if constexpr (HAS_CNT) zero |= v == 0;
+                cp_async_wait_all();
+                if constexpr (HAS_CNT)
+                    for (uint32_t i = threadIdx.x; i < n; i += THREADS) zero |= Sort::val_of(S.el[0][i]) == 0;
+            } else {
+                for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
+                    uint32_t k;
+                    unsigned long long v;
+                    rec(start + i, k, v);
+                    S.key[0][i] = k;
+                    if constexpr (HAS_CNT) { S.val[0][i] = (V)v; zero |= v == 0; }
+                }
             }
             if (threadIdx.x == 0) s_any_zero = 0;
             __syncthreads();
@@ -594,7 +599,7 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 for (uint32_t j = threadIdx.x; j < ng; j += THREADS) {
                     const uint32_t a = gb[j], e = min(gb[j + 1], n);
                     for (uint32_t i = a; i < e; ++i) {
-                        if constexpr (Cfg::PACKED) S.el[0][i] |= (typename Cfg::E)(j << w.sbits) << (HAS_CNT ? 32 : 0);
+                        if constexpr (Cfg::PACKED) S.el[0][i] |= (typename Cfg::E)(j << w.sbits);
                         else S.key[0][i] |= j << w.sbits;
                     }
                 }
@@ -607,8 +612,7 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
             };
             auto Vc = [&S, cur](int i) -> unsigned long long {
                 if constexpr (Cfg::PACKED) {
-                    if constexpr (HAS_CNT) return (uint32_t)S.el[cur][i];
-                    else return 1ull;
+                    return (unsigned long long)Sort::val_of(S.el[cur][i]);
                 } else {
                     if constexpr (HAS_CNT) return (unsigned long long)S.val[cur][i];
                     else return 1ull;

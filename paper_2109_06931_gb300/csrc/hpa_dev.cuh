@@ -57,6 +57,19 @@ __device__ __forceinline__ uint32_t attribute_pc(const DevBinary& b, uint64_t pc
     return (r.x <= off && off < r.y) ? r.z : b.n_nodes;
 }
 
+// asynchronous global -> shared copies (cp.async, sm_80+)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
+
 // L2 cache policies: tables that every sample probes should stay in L2
 // (evict_last); data read or written once streams through (evict_first).
 __device__ __forceinline__ uint64_t policy_evict_last() {
@@ -246,7 +259,8 @@ struct BlockRadix {
 };
 
 // Block-wide stable LSD radix sort of packed elements: E = uint64_t holds
-// (key << 32 | value), E = uint32_t a key alone.  Digits are at most 9 bits
+// (value << 32 | key) -- the memory image of a {key, value} record, so records
+// are copied into shared memory verbatim -- and E = uint32_t a key alone.  Digits are at most 9 bits
 // (a 26-bit key takes 3 passes); passes and digit width follow the key width.
 // Counter rows are padded by one word so the digit-major scan is free of bank
 // conflicts.  Same stable ranking as BlockRadix (warp-contiguous chunks,
@@ -255,7 +269,7 @@ template <int THREADS, int CAP, typename E>
 struct PackedRadix {
     static constexpr int W = THREADS / 32;
     static constexpr int MAXB = 9, MAXBINS = 1 << MAXB, ROW = MAXBINS + 1;
-    static constexpr int MAX_EPT = MAXBINS * W / THREADS;
+    static constexpr int MAX_EPT = (MAXBINS * W + THREADS - 1) / THREADS;
 
     struct Smem {
         E el[2][CAP];
@@ -264,9 +278,10 @@ struct PackedRadix {
         uint32_t sw[33];
     };
 
-    __device__ static __forceinline__ uint32_t key_of(E e) {
+    __device__ static __forceinline__ uint32_t key_of(E e) { return (uint32_t)e; }
+    __device__ static __forceinline__ uint32_t val_of(E e) {
         if constexpr (sizeof(E) == 8) return (uint32_t)(e >> 32);
-        else return (uint32_t)e;
+        else return 1u;
     }
 
     __device__ static int sort(Smem& s, int n, int bits) {
@@ -276,7 +291,8 @@ struct PackedRadix {
         const int passes = (bits + MAXB - 1) / MAXB;
         const int rb = (bits + passes - 1) / passes;
         const int bins = 1 << rb;
-        const int ept = bins * W / THREADS;
+        const int total = bins * W;
+        const int ept = (total + THREADS - 1) / THREADS;
         const int chunk = ((n + W - 1) / W + 31) & ~31;
         const int lo = warp * chunk;
         const int hi = min(n, lo + chunk);
@@ -305,8 +321,9 @@ struct PackedRadix {
                 uint32_t sum = 0;
 #pragma unroll
                 for (int k = 0; k < MAX_EPT; ++k) {
-                    if (k < ept) {
-                        const int e = b0 + k;
+                    loc[k] = 0;
+                    const int e = b0 + k;
+                    if (k < ept && e < total) {
                         loc[k] = s.cnt[(e % W) * ROW + e / W];
                         sum += loc[k];
                     }
@@ -315,8 +332,8 @@ struct PackedRadix {
                 uint32_t pre = block_exclusive_scan<uint32_t, THREADS>(sum, s.sw, &tot);
 #pragma unroll
                 for (int k = 0; k < MAX_EPT; ++k) {
-                    if (k < ept) {
-                        const int e = b0 + k;
+                    const int e = b0 + k;
+                    if (k < ept && e < total) {
                         s.cnt[(e % W) * ROW + e / W] = pre;
                         pre += loc[k];
                     }
