@@ -431,11 +431,6 @@ struct LeafCfg {
 // reads element row * 32 + l, so shared-memory reads are conflict-free).
 // Run sums come from a segmented inclusive scan per row plus a carry for the
 // run still open at the row's (and the previous warp's) end.
-struct RunCtx {
-    uint32_t heads;          // heads in this warp's chunk
-    unsigned long long tail; // sum of the run left open at the chunk's end
-    uint32_t has_head;
-};
 
 template <typename V, bool HAS_V>
 __device__ __forceinline__ unsigned long long val_at(const V* vals, int i) {
@@ -445,10 +440,13 @@ __device__ __forceinline__ unsigned long long val_at(const V* vals, int i) {
 
 // mode 0: write every run at its run id; mode 1: count runs with a non-zero
 // sum; mode 2: write only runs with a non-zero sum, compacted from nz_base.
-// KA(i) gives the key of element i, VA(i) its value.
-template <typename KA, typename VA>
+// KA(i) gives the key of element i, VA(i) its value; T is the accumulation
+// type (32-bit when the leaf's values cannot overflow it).  A run's partial
+// sum in a row is the row's inclusive prefix minus the prefix just before the
+// run's head (found with a ballot), so one plain scan serves every run.
+template <typename T, typename KA, typename VA>
 __device__ __forceinline__ uint32_t warp_runs(KA K, VA Vf, int n, int w0, int w1,
-                                              int run0, unsigned long long carry, int mode, uint32_t nz_base,
+                                              int run0, T carry, int mode, uint32_t nz_base,
                                               uint32_t* out_key, unsigned long long* out_val) {
     const int lane = lane_id();
     int run = run0;
@@ -458,62 +456,115 @@ __device__ __forceinline__ uint32_t warp_runs(KA K, VA Vf, int n, int w0, int w1
         const bool ok = i < w1;
         const uint32_t k = ok ? K(i) : 0u;
         const bool h = ok && (i == 0 || K(i - 1) != k);
-        unsigned long long v = ok ? Vf(i) : 0ull;
+        const T v = ok ? (T)Vf(i) : T(0);
         const uint32_t hb = __ballot_sync(0xffffffffu, h);
-        // inclusive segmented scan of (h, v) across the row
-        uint32_t f = h;
+        T p = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long v2 = __shfl_up_sync(0xffffffffu, v, o);
-            const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, o);
-            if (lane >= o) {
-                if (!f) v += v2;
-                f |= f2;
-            }
+            const T t = __shfl_up_sync(0xffffffffu, p, o);
+            if (lane >= o) p += t;
         }
-        if (!f) v += carry;
-        const int rid = run + __popc(hb & (lanemask_lt() | (1u << lane)));
+        const uint32_t le = hb & (lanemask_lt() | (1u << lane));
+        const int hpos = le ? 31 - __clz(le) : 0;
+        const T ph = __shfl_sync(0xffffffffu, p, hpos > 0 ? hpos - 1 : 0);
+        const T sum = le ? (hpos > 0 ? p - ph : p) : p + carry;
+        const int rid = run + __popc(le);
         const bool end = ok && (i == n - 1 || K(i + 1) != k);
         if (mode == 0) {
-            if (end) { out_key[rid] = k; out_val[rid] = v; }
+            if (end) { out_key[rid] = k; out_val[rid] = (unsigned long long)sum; }
         } else {
-            const uint32_t nzb = __ballot_sync(0xffffffffu, end && v != 0);
-            if (mode == 2 && end && v != 0) {
+            const uint32_t nzb = __ballot_sync(0xffffffffu, end && sum != 0);
+            if (mode == 2 && end && sum != 0) {
                 const uint32_t pos = nz + __popc(nzb & lanemask_lt());
                 out_key[pos] = k;
-                out_val[pos] = v;
+                out_val[pos] = (unsigned long long)sum;
             }
             nz += __popc(nzb);
             nz_count += __popc(nzb);
         }
         run += __popc(hb);
-        carry = __shfl_sync(0xffffffffu, v, 31);
+        carry = __shfl_sync(0xffffffffu, sum, 31);
     }
     return nz_count;
 }
 
-// per-warp heads and open-run tail over the warp's chunk
-template <typename KA, typename VA>
-__device__ __forceinline__ RunCtx warp_run_summary(KA K, VA Vf, int w0, int w1) {
+// per-warp heads and the partial sum of the run left open at the chunk's end
+template <typename T>
+struct RunSum {
+    uint32_t heads;
+    T tail;
+    uint32_t has_head;
+};
+
+template <typename T, typename KA, typename VA>
+__device__ __forceinline__ RunSum<T> warp_run_summary(KA K, VA Vf, int w0, int w1) {
     const int lane = lane_id();
-    RunCtx r{0, 0ull, 0};
+    RunSum<T> r{0, T(0), 0};
     for (int base = w0; base < w1; base += 32) {
         const int i = base + lane;
         const bool ok = i < w1;
         const uint32_t k = ok ? K(i) : 0u;
         const bool h = ok && (i == 0 || K(i - 1) != k);
-        const unsigned long long v = ok ? Vf(i) : 0ull;
+        const T v = ok ? (T)Vf(i) : T(0);
         const uint32_t hb = __ballot_sync(0xffffffffu, h);
         r.heads += __popc(hb);
-        if (hb) {
-            const int last = 31 - __clz(hb);
-            r.tail = warp_sum(lane >= last ? v : 0ull);
-            r.has_head = 1;
-        } else {
-            r.tail += warp_sum(v);
-        }
+        const int last = hb ? 31 - __clz(hb) : 0;
+        T x = lane >= last ? v : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (hb) { r.tail = x; r.has_head = 1; }
+        else r.tail += x;
     }
     return r;
+}
+
+// Runs of one leaf: per-warp summaries, a block-level (segmented) scan over
+// the warps, then every warp writes its runs; keys with a zero sum are
+// dropped by a compacting second walk (only when a zero value exists).
+// Returns the number of keys written at out_key / out_val.
+template <typename T, int W, typename KA, typename VA>
+__device__ uint32_t leaf_runs(KA Kc, VA Vc, int n, int w0, int w1, bool any_zero, uint32_t* out_key,
+                              unsigned long long* out_val, uint32_t* s_run0, uint32_t* s_nz, T* s_carry,
+                              uint32_t* s_tot) {
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const RunSum<T> rc = warp_run_summary<T>(Kc, Vc, w0, w1);
+    if (lane == 0) { s_run0[warp] = rc.heads; s_carry[warp] = rc.tail; s_nz[warp] = rc.has_head; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t runs = 0;
+        T open = 0;
+        for (int x = 0; x < W; ++x) {
+            const uint32_t hcount = s_run0[x], hh = s_nz[x];
+            const T t = s_carry[x];
+            s_run0[x] = runs;
+            s_carry[x] = open;
+            runs += hcount;
+            open = hh ? t : open + t;
+        }
+        *s_tot = runs;
+    }
+    __syncthreads();
+    uint32_t n_out = *s_tot;
+    const int run0 = (int)s_run0[warp] - 1;
+    const T carry = s_carry[warp];
+    if (!any_zero) {
+        warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 0, 0, out_key, out_val);
+    } else {
+        const uint32_t nzc = warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 1, 0, nullptr, nullptr);
+        __syncthreads();
+        if (lane == 0) s_nz[warp] = nzc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int x = 0; x < W; ++x) { const uint32_t c = s_nz[x]; s_nz[x] = t; t += c; }
+            *s_tot = t;
+        }
+        __syncthreads();
+        n_out = *s_tot;
+        warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 2, s_nz[warp], out_key, out_val);
+    }
+    __syncthreads();
+    return n_out;
 }
 
 template <int THREADS, int CAP, bool HAS_CNT, typename V>
@@ -528,7 +579,7 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
     __shared__ unsigned long long red[2];
     __shared__ uint32_t s_run0[W], s_nz[W];
     __shared__ unsigned long long s_carry[W];
-    __shared__ uint32_t s_any_zero;
+    __shared__ uint32_t s_any_zero, s_tot;
     const uint32_t n_leaves = w.item_nleaf[w.G];
     const uint32_t* seg = w.grp_hist;
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -573,6 +624,7 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 __syncthreads();
             }
             uint32_t zero = 0;
+            unsigned long long vmax = 1;
             if constexpr (Cfg::PACKED) {
                 // records land in shared memory verbatim, without a register round trip
                 for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
@@ -581,14 +633,18 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 }
                 cp_async_wait_all();
                 if constexpr (HAS_CNT)
-                    for (uint32_t i = threadIdx.x; i < n; i += THREADS) zero |= Sort::val_of(S.el[0][i]) == 0;
+                    for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
+                        const uint32_t v = Sort::val_of(S.el[0][i]);
+                        zero |= v == 0;
+                        vmax = max(vmax, (unsigned long long)v);
+                    }
             } else {
                 for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
                     uint32_t k;
                     unsigned long long v;
                     rec(start + i, k, v);
                     S.key[0][i] = k;
-                    if constexpr (HAS_CNT) { S.val[0][i] = (V)v; zero |= v == 0; }
+                    if constexpr (HAS_CNT) { S.val[0][i] = (V)v; zero |= v == 0; vmax = max(vmax, v); }
                 }
             }
             if (threadIdx.x == 0) s_any_zero = 0;
@@ -620,46 +676,17 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
             };
             const int wch = ((((int)n + W - 1) / W) + 31) & ~31;
             const int w0 = min((int)n, warp * wch), w1 = min((int)n, w0 + wch);
-            const RunCtx rc = warp_run_summary(Kc, Vc, w0, w1);
-            if (lane == 0) { s_run0[warp] = rc.heads; s_carry[warp] = rc.tail; s_nz[warp] = rc.has_head; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                // exclusive scan of heads, segmented exclusive scan of open-run tails
-                uint32_t runs = 0;
-                unsigned long long open = 0;
-                for (int x = 0; x < W; ++x) {
-                    const uint32_t hcount = s_run0[x], hh = s_nz[x];
-                    const unsigned long long t = s_carry[x];
-                    s_run0[x] = runs;
-                    s_carry[x] = open;
-                    runs += hcount;
-                    open = hh ? t : open + t;
-                }
-                sw[32] = runs;
-            }
-            __syncthreads();
-            const uint32_t n_runs = sw[32];
-            const int run0 = (int)s_run0[warp] - 1;
-            const unsigned long long carry = s_carry[warp];
-            uint32_t n_out = n_runs;
-            if (!s_any_zero) {
-                warp_runs(Kc, Vc, (int)n, w0, w1, run0, carry, 0, 0, w.tmp_key + start, (unsigned long long*)(w.tmp_val + start));
-            } else {
-                // keys whose counts add up to 0 are omitted (compacting walk)
-                const uint32_t nzc = warp_runs(Kc, Vc, (int)n, w0, w1, run0, carry, 1, 0, nullptr, nullptr);
-                __syncthreads();
-                if (lane == 0) s_nz[warp] = nzc;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    uint32_t t = 0;
-                    for (int x = 0; x < W; ++x) { const uint32_t c = s_nz[x]; s_nz[x] = t; t += c; }
-                    sw[32] = t;
-                }
-                __syncthreads();
-                n_out = sw[32];
-                warp_runs(Kc, Vc, (int)n, w0, w1, run0, carry, 2, s_nz[warp], w.tmp_key + start,
-                                      (unsigned long long*)(w.tmp_val + start));
-            }
+            // 32-bit sums suffice when no run can reach 2^32
+            const bool wide = __syncthreads_or(vmax > (0xFFFFFFFFull / (unsigned long long)n));
+            uint32_t* ok_ = w.tmp_key + start;
+            unsigned long long* ov = (unsigned long long*)(w.tmp_val + start);
+            uint32_t n_out;
+            if (!wide)
+                n_out = leaf_runs<uint32_t, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, ok_, ov, s_run0, s_nz,
+                                               reinterpret_cast<uint32_t*>(s_carry), &s_tot);
+            else
+                n_out = leaf_runs<unsigned long long, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, ok_, ov, s_run0,
+                                                         s_nz, s_carry, &s_tot);
             if (threadIdx.x == 0) w.leaf_d[l] = n_out;
             __syncthreads();
         } else {

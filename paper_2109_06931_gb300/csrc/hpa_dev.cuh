@@ -308,9 +308,11 @@ struct PackedRadix {
                 const uint32_t d = ok ? ((key_of(s.el[cur][i]) >> shift) & dmask) : 0xFFFFFFFFu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, d);
                 const uint32_t below = __popc(peers & lanemask_lt());
-                if (ok) s.rank[i] = (uint16_t)(row[d] + below);
-                __syncwarp();
-                if (ok && below == 0) row[d] += __popc(peers);
+                // the warp is converged here (no branch since the last
+                // __syncwarp), so every lane reads before its group's leader writes
+                const uint32_t before = row[ok ? d : 0];
+                if (ok) s.rank[i] = (uint16_t)(before + below);
+                if (ok && below == 0) row[d] = before + __popc(peers);
                 __syncwarp();
             }
             __syncthreads();
