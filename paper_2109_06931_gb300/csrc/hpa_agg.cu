@@ -364,202 +364,6 @@ __global__ void __launch_bounds__(256) k_scatter(AggWork w) {
     }
 }
 
-// ------------------------------------------------------------------ K9c/K9d: two-level scatter
-// Attribution as in k_attribute, but each tile's records go straight to
-// coarse buckets of consecutive groups (<= BKT_PER_BUF per buffer): a
-// shared-memory count per bucket, one global reservation per (tile, bucket),
-// then every record lands in its bucket's reserved run.  k_scatter2 then
-// splits every bucket into its groups' segments with shared-memory counts and
-// one global reservation per (chunk, group).  No per-record global atomics.
-template <bool HAS_CNT, int U>
-__global__ void __launch_bounds__(256, 3) k_attribute2(AggWork w) {
-    constexpr int PER = TILE / 256;                      // samples per thread and tile
-    static_assert(PER % U == 0, "tile rounds");
-    __shared__ unsigned long long acc[8][HPA_MAX_STALL_DEV];   // per-warp stall totals
-    __shared__ unsigned long long unk[HPA_MAX_STALL_DEV];
-    __shared__ uint32_t hist[BKT_PER_BUF + 1], base_[BKT_PER_BUF + 1];
-    __shared__ uint2 a_pair[HAS_CNT ? TILE : 1];
-    __shared__ uint32_t a_sub[HAS_CNT ? 1 : TILE];
-    __shared__ uint16_t a_gl[TILE], a_lb[TILE];
-    const uint32_t tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;
-    const uint64_t keep = policy_evict_last();
-    for (uint32_t r = tid; r < 8 * HPA_MAX_STALL_DEV; r += 256) (&acc[0][0])[r] = 0;
-    if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
-    __syncthreads();
-    uint32_t cur_b = 0xFFFFFFFFu;
-    auto flush = [&](uint32_t b) {
-        __syncthreads();
-        if (b != 0xFFFFFFFFu && tid < nsm) {
-            const BufDev& B = w.bufs[b];
-            unsigned long long v = 0;
-            for (int x = 0; x < 8; ++x) v += acc[x][tid];
-            if (v && B.total) atomicAdd((unsigned long long*)&B.total[tid], v);
-            if (unk[tid] && B.unknown) atomicAdd((unsigned long long*)&B.unknown[tid], unk[tid]);
-        }
-        __syncthreads();
-        for (uint32_t r = tid; r < 8 * HPA_MAX_STALL_DEV; r += 256) (&acc[0][0])[r] = 0;
-        if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
-        __syncthreads();
-    };
-    for (uint64_t t = blockIdx.x; t < w.n_tiles; t += gridDim.x) {
-        const uint32_t b = upper_index<uint64_t>(w.buf_tile, w.n_buf, t);
-        if (b != cur_b) { flush(cur_b); cur_b = b; }
-        const BufDev B = w.bufs[b];
-        const DevBinary bin = w.bins[B.bin];
-        const uint64_t i0 = (t - B.tile_base) * TILE;
-        const uint64_t i1 = min(i0 + TILE, B.n);
-        const uint32_t M = bin.n_nodes, gpb = B.gpb;
-        const uint32_t nb = (B.n_ctx + gpb - 1) / gpb;
-        for (uint32_t j = tid; j < nb; j += 256) hist[j] = 0;
-        __syncthreads();
-        uint32_t bad = 0;
-#pragma unroll 1
-        for (int round = 0; round < PER / U; ++round) {
-            uint64_t pc[U];
-            uint32_t c[U], st[U], cnt[U], off[U], nd[U];
-            bool ok[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint64_t i = i0 + (uint64_t)(round * U + u) * 256 + tid;
-                ok[u] = i < i1;
-                c[u] = 0xFFFFFFFFu;
-                if (ok[u]) {
-                    c[u] = ld_stream(&B.ctx[i]);
-                    st[u] = ld_stream(&B.stall[i]);
-                    pc[u] = ld_stream((const unsigned long long*)&B.pc[i]);
-                    cnt[u] = (HAS_CNT && B.count) ? ld_stream(&B.count[i]) : 1u;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                nd[u] = M;
-                if (ok[u]) {
-                    const uint64_t o = pc[u] - bin.pc_base;
-                    if (o < bin.span) {
-                        off[u] = (uint32_t)o;
-                        nd[u] = ld_keep(&bin.dir[off[u] >> bin.dshift], keep);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (nd[u] & DIR_SEARCH) {
-                    uint32_t i = nd[u] & ~DIR_SEARCH;
-                    uint4 r = ld_keep4(&bin.rng[i], keep);
-                    while (r.y <= off[u] && i + 1 < bin.n_ranges) r = ld_keep4(&bin.rng[++i], keep);
-                    nd[u] = (r.x <= off[u] && off[u] < r.y) ? r.z : M;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t li = (uint32_t)(round * U + u) * 256 + tid;
-                a_lb[li] = 0xFFFFu;
-                if (!ok[u] || c[u] >= B.n_ctx) continue;       // invalid contexts were counted in k_grp_hist
-                const bool bad_stall = st[u] >= B.n_stall;
-                const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
-                const uint32_t lb = c[u] / gpb;
-                if (HAS_CNT) a_pair[li] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
-                else a_sub[li] = sub;
-                a_gl[li] = (uint16_t)(c[u] - lb * gpb);
-                a_lb[li] = (uint16_t)lb;
-                atomicAdd(&hist[lb], 1u);
-                if (bad_stall) {
-                    ++bad;
-                } else {
-                    atomicAdd(&acc[warp][st[u]], (unsigned long long)cnt[u]);
-                    if (nd[u] == M) atomicAdd(&unk[st[u]], (unsigned long long)cnt[u]);
-                }
-            }
-        }
-        if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
-        __syncthreads();
-        for (uint32_t j = tid; j < nb; j += 256) {
-            const uint32_t h = hist[j];
-            if (h) base_[j] = atomicAdd(&w.bkt_cursor[B.bkt_base + j], h);
-            hist[j] = 0;
-        }
-        __syncthreads();
-        for (uint32_t li = tid; li < TILE; li += 256) {
-            const uint32_t lb = a_lb[li];
-            if (lb == 0xFFFFu) continue;
-            const uint32_t slot = base_[lb] + atomicAdd(&hist[lb], 1u);
-            if (HAS_CNT) w.rec2_pair[slot] = a_pair[li];
-            else w.rec2_sub[slot] = a_sub[li];
-            w.rec2_gl[slot] = a_gl[li];
-        }
-        __syncthreads();
-    }
-    flush(cur_b);
-}
-
-__global__ void k_bkt_init(AggWork w) {
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < w.n_bkt; j += gridDim.x * blockDim.x)
-        w.bkt_cursor[j] = w.grp_hist[w.bkt_grp0[j]];
-}
-
-constexpr int SC2_CHUNK = 8192;
-constexpr int SC2_GROUPS = 4096;     // groups of a chunk counted in shared memory
-
-template <bool HAS_CNT>
-__global__ void __launch_bounds__(256) k_scatter2(AggWork w) {
-    __shared__ uint32_t cnt[SC2_GROUPS], base_[SC2_GROUPS];
-    __shared__ uint32_t s_b[2];
-    const uint32_t* seg = w.grp_hist;
-    const uint32_t total = seg[w.G];
-    const uint32_t n_chunks = (total + SC2_CHUNK - 1) / SC2_CHUNK;
-    // bucket of record p: the last bucket whose first record is <= p
-    auto bucket_of = [&](uint32_t p, uint32_t lo, uint32_t hi) {
-        while (hi - lo > 1) {
-            const uint32_t m = (lo + hi) >> 1;
-            if (seg[w.bkt_grp0[m]] <= p) lo = m; else hi = m;
-        }
-        return lo;
-    };
-    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
-        const uint32_t c0 = ch * SC2_CHUNK, c1 = min(total, c0 + SC2_CHUNK);
-        if (threadIdx.x == 0) {
-            s_b[0] = bucket_of(c0, 0, w.n_bkt);
-            s_b[1] = bucket_of(c1 - 1, s_b[0], w.n_bkt);
-        }
-        __syncthreads();
-        const uint32_t b0 = s_b[0], b1 = s_b[1];
-        const uint32_t g_lo = w.bkt_grp0[b0], g_hi = w.bkt_grp0[b1 + 1];
-        const bool local = g_hi - g_lo <= (uint32_t)SC2_GROUPS;
-        if (local) {
-            for (uint32_t j = threadIdx.x; j < g_hi - g_lo; j += 256) cnt[j] = 0;
-            __syncthreads();
-            for (uint32_t p = c0 + threadIdx.x; p < c1; p += 256) {
-                const uint32_t bk = b0 == b1 ? b0 : bucket_of(p, b0, b1 + 1);
-                atomicAdd(&cnt[w.bkt_grp0[bk] + w.rec2_gl[p] - g_lo], 1u);
-            }
-            __syncthreads();
-            for (uint32_t j = threadIdx.x; j < g_hi - g_lo; j += 256) {
-                const uint32_t c = cnt[j];
-                if (c) base_[j] = atomicAdd(&w.grp_cursor[(size_t)(g_lo + j) << w.cur_shift], c);
-                cnt[j] = 0;
-            }
-            __syncthreads();
-            for (uint32_t p = c0 + threadIdx.x; p < c1; p += 256) {
-                const uint32_t bk = b0 == b1 ? b0 : bucket_of(p, b0, b1 + 1);
-                const uint32_t lg = w.bkt_grp0[bk] + w.rec2_gl[p] - g_lo;
-                const uint32_t slot = base_[lg] + atomicAdd(&cnt[lg], 1u);
-                if (HAS_CNT) w.rec_pair[slot] = w.rec2_pair[p];
-                else w.rec_sub[slot] = w.rec2_sub[p];
-            }
-        } else {
-            for (uint32_t p = c0 + threadIdx.x; p < c1; p += 256) {
-                const uint32_t bk = bucket_of(p, b0, b1 + 1);
-                const uint32_t g = w.bkt_grp0[bk] + w.rec2_gl[p];
-                const uint32_t slot = atomicAdd(&w.grp_cursor[(size_t)g << w.cur_shift], 1u);
-                if (HAS_CNT) w.rec_pair[slot] = w.rec2_pair[p];
-                else w.rec_sub[slot] = w.rec2_sub[p];
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------------------ K10: split big groups
 __global__ void __launch_bounds__(256) k_big_partition(AggWork w) {
     __shared__ uint32_t hist[4096 + 1];
@@ -1089,18 +893,7 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
     const size_t acc_bytes = (size_t)nsm * 256 * 8;
     const int at_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
     const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 8));
-    if (w.two_level) {
-        k_bkt_init<<<(w.n_bkt + 255) / 256, 256, 0, s>>>(w);
-        const int a2 = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 3));
-        if (w.has_cnt) {
-            k_attribute2<true, 4><<<a2, 256, 0, s>>>(w);
-            k_scatter2<true><<<sms * 4, 256, 0, s>>>(w);
-        } else {
-            k_attribute2<false, 4><<<a2, 256, 0, s>>>(w);
-            k_scatter2<false><<<sms * 4, 256, 0, s>>>(w);
-        }
-        *launches += 2;
-    } else if (w.has_cnt) {
+    if (w.has_cnt) {
         cudaFuncSetAttribute(k_attribute<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
         k_attribute<true, 4><<<at_blocks, 256, acc_bytes, s>>>(w);
         k_scatter<true, 8><<<sc_blocks, 256, 0, s>>>(w);
@@ -1109,6 +902,7 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
         k_attribute<false, 4><<<at_blocks, 256, acc_bytes, s>>>(w);
         k_scatter<false, 8><<<sc_blocks, 256, 0, s>>>(w);
     }
+    *launches += 1;
     *launches += 1;
     if (ev) cudaEventRecord(ev[2], s);
     run_finish(w, s, sms, launches, ev);

@@ -410,7 +410,7 @@ extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary
 // ------------------------------------------------------------------ aggregation calls
 // Scratch layout of one aggregation over N records in G groups (n_buf buffers).
 hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n, uint32_t cap, uint32_t sb,
-                                  uint32_t sbits, bool has_cnt, bool val64, uint64_t staged, uint32_t n_bkt) {
+                                  uint32_t sbits, bool has_cnt, bool val64, uint64_t staged) {
     const uint64_t N2 = std::max(N, staged);   // the second record buffer also stages samples in tile order
     const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
     w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
@@ -444,10 +444,6 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
         w.tmp_key = c.take<uint32_t>(N + 1);
         w.tmp_val = c.take<uint64_t>(N + 1);
         w.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max<uint64_t>(G, L_max)));
-        w.two_level = n_bkt != 0;
-        w.n_bkt = n_bkt;
-        w.bkt_cursor = n_bkt ? c.take<uint32_t>(n_bkt + 1) : nullptr;
-        w.rec2_gl = n_bkt ? c.take<uint16_t>(N + 1) : nullptr;
     };
     Carve probe{nullptr};
     layout(probe);
@@ -495,28 +491,17 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     if (cap == 0) cap = (G && N / G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL;
     if (cap != LEAF_CAP_SMALL && cap != LEAF_CAP_LARGE)
         return fail(HPA_E_INVALID_ARG, "leaf_capacity must be 0, %u or %u", LEAF_CAP_SMALL, LEAF_CAP_LARGE);
-    // two-level scatter: <= BKT_PER_BUF coarse buckets of consecutive contexts per buffer
-    uint64_t n_bkt = 0;
-    bool two_level = true;
-    for (uint32_t b = 0; b < n; ++b) {
-        const uint64_t gpb = (in[b].n_ctx + BKT_PER_BUF - 1) / BKT_PER_BUF;
-        if (gpb > 65536) two_level = false;
-        n_bkt += (in[b].n_ctx + gpb - 1) / gpb;
-    }
-    if (!two_level || opt.reserved[1] == 1) n_bkt = 0;
     AggWork w{};
-    hpa_status st = carve_work(w, N, G, n, cap, sb, sbits, has_cnt, false, tiles * TILE, (uint32_t)n_bkt);
+    hpa_status st = carve_work(w, N, G, n, cap, sb, sbits, has_cnt, false, tiles * TILE);
     if (st) return st;
     w.n_tiles = tiles;
     // descriptors
-    const size_t desc_bytes = n * sizeof(BufDev) + (n + 1) * 8 + (n + 1) * 4 + (n_bkt + 1) * 4 + 1024;
+    const size_t desc_bytes = n * sizeof(BufDev) + (n + 1) * 8 + (n + 1) * 4 + 512;
     if ((st = ensure_staging(desc_bytes))) return st;
     Carve hs{(char*)staging};
     BufDev* hb = hs.take<BufDev>(n);
     uint64_t* htile = hs.take<uint64_t>(n + 1);
     uint32_t* hgrp = hs.take<uint32_t>(n + 1);
-    uint32_t* hbkt = hs.take<uint32_t>(n_bkt + 1);
-    uint32_t nbk = 0;
     const size_t used = hs.off;
     uint64_t tb = 0;
     uint32_t gb = 0;
@@ -529,11 +514,6 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         d.total = o.total; d.unknown = o.unknown;
         d.key_ctx = o.key_ctx; d.key_node = o.key_node; d.key_stall = o.key_stall; d.val = o.val;
         d.n_keys = o.n_keys; d.capacity = o.capacity;
-        if (n_bkt) {
-            d.gpb = (s.n_ctx + BKT_PER_BUF - 1) / BKT_PER_BUF;
-            d.bkt_base = nbk;
-            for (uint32_t j = 0; j * d.gpb < s.n_ctx; ++j) hbkt[nbk++] = gb + j * d.gpb;
-        }
         hb[b] = d;
         htile[b] = tb;
         hgrp[b] = gb;
@@ -549,7 +529,6 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     w.bufs = (const BufDev*)(ds + ((char*)hb - (char*)staging));
     w.buf_tile = (const uint64_t*)(ds + ((char*)htile - (char*)staging));
     w.buf_grp = (const uint32_t*)(ds + ((char*)hgrp - (char*)staging));
-    w.bkt_grp0 = (const uint32_t*)(ds + ((char*)hbkt - (char*)staging));
     if (use_graph && !timing) return launch_graph(w, used, n, in);
     if ((st = upload_staging(used))) return st;
     for (uint32_t b = 0; b < n; ++b) {

@@ -21,8 +21,8 @@ struct BufDev {
     uint32_t n_stall;
     uint32_t grp_base;          // first global group (group = grp_base + ctx)
     uint32_t bin;               // index into the DevBinary table
-    uint32_t gpb;               // groups per coarse bucket (two-level scatter)
-    uint32_t bkt_base;          // first coarse bucket of this buffer
+    uint32_t first_leaf_item;   // (filled on device) unused by the host
+    uint32_t pad;
     uint64_t* total;            // per-stall totals (may be null)
     uint64_t* unknown;
     // outputs
@@ -68,13 +68,6 @@ struct AggWork {
     uint64_t* rec2_v64;    // [N]
     uint2* rec_pair;       // [N] {subkey, count} (if has_cnt and !val64; rec_sub unused then)
     uint2* rec2_pair;      // [N]
-    // two-level scatter: samples reach their group segments through coarse
-    // buckets of consecutive groups (at most BKT_PER_BUF per buffer)
-    uint32_t two_level;
-    uint32_t n_bkt;
-    uint32_t* bkt_cursor;         // [n_bkt] next free record slot of each bucket
-    const uint32_t* bkt_grp0;     // [n_bkt + 1] first group of each bucket
-    uint16_t* rec2_gl;            // [N] group index inside its bucket, bucket-ordered records
     uint32_t* tmp_key;     // [N]
     uint64_t* tmp_val;     // [N]
     uint32_t* scan_tmp;    // device-wide scan partials
@@ -86,7 +79,6 @@ struct AggWork {
 };
 
 constexpr int TILE = 4096;            // samples per tile of the sample-reading kernels
-constexpr uint32_t BKT_PER_BUF = 256;  // coarse buckets per buffer (two-level scatter)
 constexpr uint32_t HPA_MAX_STALL_DEV = 32;
 constexpr uint32_t HIST_SMEM_MAX = 24576;    // contexts counted in shared memory (96 KB)
 constexpr uint32_t LEAF_CAP_SMALL = 4096;   // 256 threads, two CTAs per SM
