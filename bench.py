@@ -105,6 +105,55 @@ def cpu_oracle_rate(w, B, target_s: float, max_n: int):
     return n / dt, n, dt
 
 
+def timed(stream, fn, reps=3):
+    """Mean CUDA-event time (ms) of fn() on `stream` after one warm-up call."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_rows(h, bid, B, w, prof, stream, dev):
+    """Timings of the other rows of the path on the benchmark's profile:
+    GPU calling-context trees (64 contexts), inclusive propagation over the
+    host CCT (all contexts) and over the structure tree (a 10 % sample of the
+    profile, to bound scratch), derived metrics over 4 profiles."""
+    from paper_2109_06931_gb300 import hpa as H
+    out = {}
+    K = prof.count()
+    req = np.linspace(0, w.n_ctx - 1, 64).astype(np.uint32)
+    ms = timed(stream, lambda: (h.apportion_callgraph(bid, prof, req), h.sync()))
+    info, _ = h.binary_info(bid)
+    out["apportion"] = {"ms": ms, "contexts": len(req), "cnodes": info.n_cnodes, "calls": info.n_calls,
+                        "contexts_per_s": len(req) / (ms / 1e3)}
+    par = torch.from_numpy(w.cct().view(np.int32)).to(dev)
+    torch.cuda.synchronize()  # inputs are made on torch's stream, the handle runs on its own
+    ms = timed(stream, lambda: (h.propagate_inclusive(bid, prof, tree=False, cct_parent=par), h.sync()))
+    out["inclusive_cct"] = {"ms": ms, "cct_nodes": int(par.shape[0]), "keys": K, "keys_per_s": K / (ms / 1e3)}
+    S2 = w.samples(B, device=dev, n=w.n_samples // 10)
+    torch.cuda.synchronize()
+    p2 = h.attribute_samples(bid, S2)
+    h.sync()
+    k2 = p2.count()
+    ms = timed(stream, lambda: (h.propagate_inclusive(bid, p2), h.sync()), reps=2)
+    out["inclusive_tree"] = {"ms": ms, "keys": k2, "keys_per_s": k2 / (ms / 1e3)}
+    profs = [p2]
+    for i in range(3):
+        Si = w.samples(B, device=dev, n=w.n_samples // 10, start=(i + 1) * w.n_samples)
+        torch.cuda.synchronize()
+        profs.append(h.attribute_samples(bid, Si))
+        h.sync()
+    kk = sum(p.count() for p in profs)
+    ms = timed(stream, lambda: (h.derive_metrics(profs), h.sync()), reps=2)
+    out["derive"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
+    return out
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -178,6 +227,7 @@ def run_batched(args, world, rank, local):
     outs = [H.new_profile(b.n, b.n_stall, dev) for b in bufs]
     N = int(sum(b.n for b in bufs))
     h.reserve(N + 4096 * len(bufs), sum(b.n_ctx for b in bufs))
+    torch.cuda.synchronize()  # inputs are made on torch's stream, the handle runs on its own
     for _ in range(args.warmup):
         h.attribute_batch(bids, bufs, outs)
     h.sync()
@@ -208,6 +258,14 @@ def run_batched(args, world, rank, local):
     torch.cuda.synchronize()
     h.sync()
     ms_plain = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    # per-phase kernel times of the batched call (timing replaces graph replay)
+    h.set_phase_timing(True)
+    for _ in range(args.steps):
+        h.attribute_batch(bids, bufs, outs)
+    h.sync()
+    ph, calls = h.phase_times()
+    h.set_phase_timing(False)
+    ph = {k: v / max(calls, 1) for k, v in ph.items()}
     peak, peak_kind = peaks()
     path_bytes = 17 * N + 17 * K
     ach = path_bytes / (ms / 1e3) / 1e9
@@ -223,7 +281,7 @@ def run_batched(args, world, rank, local):
                       "form": "one hpa_attribute_samples per buffer"},
             "path_roofline": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                               "peak_kind": peak_kind, "algorithmic_bytes_per_step": path_bytes},
-            "clocks": clk.summary(), "gpu_launches": int(launches)}), flush=True)
+            "phases_ms": ph, "clocks": clk.summary(), "gpu_launches": int(launches)}), flush=True)
     h.close()
 
 
@@ -239,6 +297,7 @@ def main():
     ap.add_argument("--cursor-shift", type=int, default=None, help="scatter cursor padding (log2 words)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the apportion / inclusive / derive rows")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     args = ap.parse_args()
@@ -338,6 +397,8 @@ def main():
         e2e = {"value": N * world / dt, "unit": UNIT, "h2d_bytes_per_step": in_b * N,
                "d2h_bytes_per_step": 17 * K + 8 + 16 * w.n_stall, "ms_per_step": dt * 1e3}
 
+    rows = None if args.no_rows else measure_rows(h, bid, B, w, out, stream, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         rate, n_cpu, dt_cpu = cpu_oracle_rate(w, B, args.cpu_seconds, 20_000_000)
@@ -362,6 +423,7 @@ def main():
             "gpu_launches": int(launches * args.steps),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "rows": rows,
         }
         print(json.dumps(line), flush=True)
     h.close()

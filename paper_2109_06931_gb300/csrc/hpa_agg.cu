@@ -12,7 +12,8 @@
 //                    structure node, packs (node, stall) into a subkey and
 //                    stores (subkey, count) in sample order
 //   k_scatter        moves each record into its group's segment
-//   k_big_partition  splits big groups by the subkey's top h bits
+//   k_big_partition  splits big groups into fine bins (top subkey bits) and
+//                    cuts the bins into leaves of at most cap records
 //   k_leaf           per leaf: shared-memory radix sort + run reduction (or a
 //                    dense shared-memory window for oversized sub-bins)
 //   scan + k_emit    leaves are in key order; their run counts give every
@@ -93,13 +94,24 @@ void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cuda
 
 // ------------------------------------------------------------------ helpers
 // largest b with pre[b] <= x (pre is non-decreasing, pre[0] = 0)
-__device__ __forceinline__ uint32_t big_bits(uint32_t n, uint32_t cap, uint32_t sbits) {
-    // 2^h sub-bins of about cap / 2 records each
-    const uint32_t want = (uint32_t)((2ull * n + cap - 1) / cap);
-    uint32_t h = ceil_log2_u64(want);
-    h = max(h, 1u);
-    h = min(h, min(12u, sbits));
-    return h;
+// A big group (more than cap records) is split by fine bins: the top h bits
+// of its subkey.  A bin spans 2^(sbits - h) subkeys; h is chosen so that this
+// is at most one dense window of the leaf (2^13 subkeys) whenever 2^14 bins
+// allow it, so a bin that alone exceeds cap is reduced in one dense pass.
+__device__ __forceinline__ uint32_t fine_bits(uint32_t sbits) {
+    const uint32_t h = sbits > 13 ? sbits - 13 : 0;
+    return min(sbits, min((uint32_t)BIG_FINE_MAX_LOG, max(12u, h)));
+}
+
+// Leaves of a big group of n records are runs of consecutive fine bins: a
+// leaf starts at the first bin, at every bin whose offset enters a new window
+// of q records, and at every bin of more than q records.  That is at most
+// 1 + floor(n / q) + floor(n / (q + 1)) <= 2 ceil(n / q) starts, and a leaf of
+// bins of at most q records each holds fewer than 2q = cap records.
+__device__ __forceinline__ uint32_t big_leaf_slots(uint32_t n, uint32_t q) { return 2 * ((n + q - 1) / q); }
+
+__device__ __forceinline__ bool big_leaf_head(const uint32_t* off, uint32_t j, uint32_t q) {
+    return j == 0 || off[j] / q != off[j - 1] / q || off[j + 1] - off[j] > q;
 }
 
 // ------------------------------------------------------------------ K1: records per group
@@ -196,7 +208,7 @@ __global__ void k_items_size(AggWork w) {
             const uint32_t g0 = w.item_grp0[it];
             const uint32_t g1 = (it + 1 < n_items) ? w.item_grp0[it + 1] : w.G;
             const uint32_t n = seg[g1] - seg[g0];
-            nl = (n > w.cap) ? (1u << big_bits(n, w.cap, w.sbits)) : 1u;
+            nl = (n > w.cap) ? big_leaf_slots(n, w.q) : 1u;
         }
         w.item_nleaf[it] = nl;
     }
@@ -365,44 +377,65 @@ __global__ void __launch_bounds__(256) k_scatter(AggWork w) {
 }
 
 // ------------------------------------------------------------------ K10: split big groups
-__global__ void __launch_bounds__(256) k_big_partition(AggWork w) {
-    __shared__ uint32_t hist[4096 + 1];
+// One CTA per big group: fine-bin histogram, offsets, leaf boundaries (runs
+// of bins, see big_leaf_head) and a stable-per-bin scatter into rec2.
+__global__ void __launch_bounds__(BIG_THREADS) k_big_partition(AggWork w) {
+    extern __shared__ uint32_t off[];            // 2^h + 1 bin counts, then offsets, then cursors
     __shared__ uint32_t sw[33];
     const uint32_t n_items = w.item_id[w.G];
     const uint32_t* seg = w.grp_hist;
     const uint32_t* leaf_base = w.item_nleaf;
+    const uint32_t q = w.q;
+    const uint32_t h = fine_bits(w.sbits), nb = 1u << h, shift = w.sbits - h;
+    const bool pair = w.rec_pair != nullptr;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         const uint32_t g0 = w.item_grp0[it];
         const uint32_t g1 = (it + 1 < n_items) ? w.item_grp0[it + 1] : w.G;
         const uint32_t s0 = seg[g0], s1 = seg[g1];
         const uint32_t n = s1 - s0;
         if (n <= w.cap) continue;                 // uniform across the block
-        const uint32_t h = big_bits(n, w.cap, w.sbits);
-        const uint32_t nb = 1u << h;
-        const uint32_t shift = w.sbits - h;
-        for (uint32_t j = threadIdx.x; j <= nb; j += blockDim.x) hist[j] = 0;
+        for (uint32_t j = threadIdx.x; j <= nb; j += BIG_THREADS) off[j] = 0;
         __syncthreads();
-        const bool pair = w.rec_pair != nullptr;
-        for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x)
-            atomicAdd(&hist[(pair ? w.rec_pair[i].x : w.rec_sub[i]) >> shift], 1u);
+        for (uint32_t i = s0 + threadIdx.x; i < s1; i += BIG_THREADS)
+            atomicAdd(&off[(pair ? w.rec_pair[i].x : w.rec_sub[i]) >> shift], 1u);
         __syncthreads();
-        block_scan_array<uint32_t, 256, 17>(hist, nb + 1, sw);
+        block_scan_array<uint32_t, BIG_THREADS, BIG_EPT>(off, nb + 1, sw);   // off[nb] = n
+        // leaf boundaries
+        const uint32_t slots = big_leaf_slots(n, q);
         const uint32_t l0 = leaf_base[it];
         const uint32_t b = upper_index<uint32_t>(w.buf_grp, w.n_buf, g0);
-        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
-            w.leaf_start[l0 + j] = s0 + hist[j];
-            w.leaf_end[l0 + j] = s0 + (j + 1 < nb ? hist[j + 1] : n);
-            w.leaf_grp0[l0 + j] = g0;
-            w.leaf_info[l0 + j] = (b << 8) | 1u;
+        const uint32_t j0 = threadIdx.x * BIG_EPT;
+        uint32_t c = 0;
+#pragma unroll 4
+        for (uint32_t k = 0; k < BIG_EPT; ++k)
+            if (j0 + k < nb) c += big_leaf_head(off, j0 + k, q);
+        uint32_t n_lv;
+        uint32_t at = block_exclusive_scan<uint32_t, BIG_THREADS>(c, sw, &n_lv);
+        for (uint32_t k = 0; k < BIG_EPT && c; ++k) {
+            const uint32_t j = j0 + k;
+            if (j < nb && big_leaf_head(off, j, q)) {
+                if (at < slots) w.leaf_start[l0 + at] = s0 + off[j];
+                ++at;
+                --c;
+            }
+        }
+        if (n_lv > slots && threadIdx.x == 0) raise_status(w.status, 8 /* HPA_E_INTERNAL */, 10);
+        __syncthreads();
+        const uint32_t nl = min(n_lv, slots);
+        for (uint32_t k = threadIdx.x; k < slots; k += BIG_THREADS) {
+            if (k >= nl) w.leaf_start[l0 + k] = s1;   // unused slot: empty leaf
+            w.leaf_end[l0 + k] = (k + 1 < nl) ? w.leaf_start[l0 + k + 1] : s1;
+            w.leaf_grp0[l0 + k] = g0;
+            w.leaf_info[l0 + k] = (b << 8) | 1u;
         }
         __syncthreads();
-        for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        for (uint32_t i = s0 + threadIdx.x; i < s1; i += BIG_THREADS) {
             if (pair) {
                 const uint2 r = w.rec_pair[i];
-                w.rec2_pair[s0 + atomicAdd(&hist[r.x >> shift], 1u)] = r;
+                w.rec2_pair[s0 + atomicAdd(&off[r.x >> shift], 1u)] = r;
             } else {
                 const uint32_t sub = w.rec_sub[i];
-                const uint32_t p = s0 + atomicAdd(&hist[sub >> shift], 1u);
+                const uint32_t p = s0 + atomicAdd(&off[sub >> shift], 1u);
                 w.rec2_sub[p] = sub;
                 if (w.val64) w.rec2_v64[p] = w.rec_v64[i];
             }
@@ -847,7 +880,13 @@ void launch_finalize(const AggWork& w, cudaStream_t s, uint64_t* launches) {
 }
 
 void launch_big_partition(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
-    k_big_partition<<<sms * 4, 256, 0, s>>>(w);
+    constexpr size_t smem = ((1u << BIG_FINE_MAX_LOG) + 1) * 4;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_big_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_big_partition<<<sms * 3, BIG_THREADS, smem, s>>>(w);
     *launches += 1;
 }
 

@@ -84,6 +84,9 @@ constexpr uint32_t HIST_SMEM_MAX = 24576;    // contexts counted in shared memor
 constexpr uint32_t LEAF_CAP_SMALL = 4096;   // 256 threads, two CTAs per SM
 constexpr uint32_t LEAF_CAP_LARGE = 10240;  // 512 threads, one CTA per SM
 constexpr int LEAF_THREADS_LARGE = 512;
+constexpr uint32_t BIG_FINE_MAX_LOG = 14;   // at most 2^14 fine bins per big group (64 KB counters)
+constexpr int BIG_THREADS = 512;
+constexpr int BIG_EPT = ((1 << BIG_FINE_MAX_LOG) + 1 + BIG_THREADS - 1) / BIG_THREADS;
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_EPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_EPT;
