@@ -15,6 +15,7 @@ Under torchrun every rank runs an independent replica on its own GPU
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -38,6 +39,34 @@ FALLBACK_HBM = 6800.0
 
 def workload(name: str):
     return {"large": synth.LARGE, "plain": synth.PLAIN}[name]
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per sample of
+# the kernel that dominates each phase, from one ncu capture of the 2e7-sample
+# case (profiles/k_leaf_k_scatter_k_attribute_plain-large-20M.md), keyed by a
+# hash of the kernel sources it was taken on: a changed kernel reports null.
+KERNEL_SOURCES = ("hpa_agg.cu", "hpa_dev.cuh", "hpa_internal.h")
+TRAFFIC = {
+    "leaf sort/reduce": {"kernel": "k_leaf", "bytes_per_sample": 15.468, "sources": "e2938a2628997b4e"},
+    "attribute+scatter": {"kernel": "k_attribute + k_scatter", "bytes_per_sample": 47.83, "sources": "e2938a2628997b4e"},
+}
+
+
+def sources_hash() -> str:
+    import hashlib
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2109_06931_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(phase: str, n_samples: int):
+    t = TRAFFIC.get(phase)
+    if t is None or t["sources"] != sources_hash():
+        return None
+    return t["bytes_per_sample"] * n_samples
 
 
 def peaks():
@@ -154,6 +183,117 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     return out
 
 
+def run_serving(args, world, rank, local):
+    """Open-loop serving (hpa_server_*): Poisson arrivals at --rate requests/s
+    for --duration s, sizes log-uniform over [10^3, 10^7] samples, 16 resident
+    binaries.  Request payloads are slices of pinned per-binary sample pools
+    (host arrays, so every request is copied in and its keys copied out);
+    results land in a pinned output ring.  Reports samples/s over the run and
+    the server's submit -> result latency percentiles."""
+    from paper_2109_06931_gb300 import hpa as H
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = synth.SEED_BASE + 5
+    n_bin, pool_n, n_ctx, n_stall = 16, 10_000_000, 500, 16
+    lo_n, hi_n = 1e3, 1e7
+    # arrivals and sizes (seeded)
+    n_req = int(args.rate * args.duration * 1.2) + 16
+    gaps = -np.log1p(-synth.np_unif(seed, 1, np.arange(n_req))) / args.rate
+    arrive = np.cumsum(gaps)
+    n_req = int(np.searchsorted(arrive, args.duration))
+    arrive = arrive[:n_req]
+    u = synth.np_unif(seed, 2, np.arange(n_req))
+    sizes = np.floor(np.exp(np.log(lo_n) + u * (np.log(hi_n) - np.log(lo_n)))).astype(np.int64)
+    offs = np.floor(synth.np_unif(seed, 3, np.arange(n_req)) * (pool_n - sizes + 1)).astype(np.int64)
+    # binaries and pinned sample pools
+    fu = synth.np_unif(seed, 4, np.arange(n_bin))
+    funcs = np.floor(np.exp(np.log(2000) + fu * (np.log(8000) - np.log(2000)))).astype(np.int64)
+    bins = [synth.make_binary(seed * 31 + i, int(f), int(f) * 13_422, int(f) * 50, int(f) * 3)
+            for i, f in enumerate(funcs)]
+    pools = []
+    for i, b in enumerate(bins):
+        S = synth.make_samples(seed * 1_000 + i, b, pool_n, n_ctx, 1.0, n_stall, True, dev)
+        pools.append(tuple(t.cpu().pin_memory() for t in (S.pc, S.ctx, S.stall, S.count)))
+        del S
+    torch.cuda.synchronize()
+    ring_n = 1 << 28
+    ring = dict(ctx=torch.empty(ring_n, dtype=torch.int32).pin_memory(),
+                node=torch.empty(ring_n, dtype=torch.int32).pin_memory(),
+                stall=torch.empty(ring_n, dtype=torch.uint8).pin_memory(),
+                val=torch.empty(ring_n, dtype=torch.int64).pin_memory())
+    small = torch.zeros((n_req, 1 + 2 * H.HPA_MAX_STALL), dtype=torch.int64).pin_memory()
+    h = H.Hpa(local)
+    ids = [h.load_structure(b) for b in bins]
+    srv = H.Server(h, mem_cap_bytes=args.serve_mem_gb << 30)
+    live = collections.deque()          # (ticket, ring start, ring end) in submission order
+    head = 0
+    lag = np.zeros(n_req)
+
+    def retire(block: bool) -> bool:
+        if not live:
+            return False
+        t, _, _ = live[0]
+        st = srv.poll(t, 1000 if block else 0)
+        if st == H.HPA_PENDING:
+            return False
+        if st != 0:
+            raise RuntimeError(f"request failed with status {st}")
+        srv.result(t)
+        live.popleft()
+        return True
+
+    def room(a, b):
+        # ring entries [a, b) are free of every live request's slice
+        return all(e <= a or s >= b for _, s, e in live)
+
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= arrive[i]:
+                break
+            if not retire(False):
+                time.sleep(min(2e-4, arrive[i] - now))
+        n = int(sizes[i])
+        a = head if head + n <= ring_n else 0
+        while not room(a, a + n):
+            retire(True)
+        head = a + n
+        b = i % n_bin
+        pc, cx, st, ct = pools[b]
+        o = offs[i]
+        row = small[i]
+        out = dict(ctx=ring["ctx"][a:a + n], node=ring["node"][a:a + n], stall=ring["stall"][a:a + n],
+                   val=ring["val"][a:a + n], n=row[0:1], total=row[1:1 + H.HPA_MAX_STALL],
+                   unknown=row[1 + H.HPA_MAX_STALL:])
+        lag[i] = time.perf_counter() - t0 - arrive[i]
+        tk = srv.submit(ids[b], pc[o:o + n], cx[o:o + n], st[o:o + n], ct[o:o + n], n_ctx, n_stall, out=out)
+        live.append((tk, a, a + n))
+    while live:
+        retire(True)
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    h.close()
+    total = int(sizes.sum())
+    keys = int(small[:, 0].sum())
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": total * world / wall, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "serving", "rate_per_s": args.rate, "duration_s": args.duration,
+                       "requests": n_req, "binaries": n_bin, "samples": total, "sizes": "log-uniform [1e3, 1e7]",
+                       "admission_cap_gib": args.serve_mem_gb, "offered_samples_per_s": total / args.duration},
+            "latency_ms": {"p50": stats["p50_ms"], "p99": stats["p99_ms"], "max": stats["max_ms"],
+                           "mean": stats["mean_ms"], "measured": "submit -> keys in host arrays"},
+            "submit_lag_ms": {"p50": float(np.percentile(lag, 50) * 1e3), "p99": float(np.percentile(lag, 99) * 1e3)},
+            "server": {k: stats[k] for k in ("completed", "rejected", "batches", "busy_s")},
+            "e2e": {"value": total * world / wall, "unit": UNIT,
+                    "h2d_bytes_per_step": 17 * total, "d2h_bytes_per_step": 17 * keys + 8 * (1 + 2 * 16) * n_req}}),
+              flush=True)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -214,20 +354,37 @@ def run_batched(args, world, rank, local):
     from paper_2109_06931_gb300 import hpa as H
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = synth.BATCHED
-    sizes = w.sizes()
-    if args.samples:
-        sizes = np.maximum(1, (sizes * (args.samples / sizes.sum())).astype(np.int64))
-    bins = w.binaries()
     stream = torch.cuda.Stream(dev)
-    h = H.Hpa(local, stream=stream)
-    ids = [h.load_structure(b) for b in bins]
-    bufs = [w.buffer(i, bins[i % len(bins)], int(n), device=dev) for i, n in enumerate(sizes)]
-    bids = [ids[i % len(ids)] for i in range(len(bufs))]
-    outs = [H.new_profile(b.n, b.n_stall, dev) for b in bufs]
+    h = H.Hpa(local, stream=stream, sort_mode=args.sort_mode, partition=not args.no_part)
+    extra = {}
+    if args.workload == "many-ctx":
+        # 64 buffers of tuple samples over a 2x10^6-node merged CCT, one binary
+        w = synth.MANY_CTX
+        n_each = max(1, args.samples // w.n_buffers) if args.samples else w.n_samples
+        bins = [w.binary()]
+        ids = [h.load_structure(bins[0])]
+        bufs = [w.buffer(i, bins[0], n_each, device=dev) for i in range(w.n_buffers)]
+        bids = [ids[0]] * len(bufs)
+        outs = [H.new_profile(min(b.n, w.n_tuples), b.n_stall, dev) for b in bufs]
+        extra = {"cct_nodes": w.cct_nodes, "tuples_per_buffer": w.n_tuples}
+    else:
+        w = synth.BATCHED
+        sizes = w.sizes()
+        if args.samples:
+            sizes = np.maximum(1, (sizes * (args.samples / sizes.sum())).astype(np.int64))
+        bins = w.binaries()
+        ids = [h.load_structure(b) for b in bins]
+        bufs = [w.buffer(i, bins[i % len(bins)], int(n), device=dev) for i, n in enumerate(sizes)]
+        bids = [ids[i % len(ids)] for i in range(len(bufs))]
+        outs = [H.new_profile(b.n, b.n_stall, dev) for b in bufs]
     N = int(sum(b.n for b in bufs))
     h.reserve(N + 4096 * len(bufs), sum(b.n_ctx for b in bufs))
     torch.cuda.synchronize()  # inputs are made on torch's stream, the handle runs on its own
+    tuned = None
+    if not args.no_tune and args.sort_mode is None and not args.no_part:
+        big = int(np.argmax([b.n for b in bufs]))
+        chosen, cand_ms = h.tune(bids[big], bufs[big], out=outs[big])
+        tuned = dict(chosen, on_buffer=big, candidates_ms=[round(t, 3) for t in cand_ms])
     for _ in range(args.warmup):
         h.attribute_batch(bids, bufs, outs)
     h.sync()
@@ -276,7 +433,7 @@ def run_batched(args, world, rank, local):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": w.name, "buffers": len(bufs), "binaries": len(bins), "samples": N, "keys": K,
                        "form": "batched, one CUDA graph launch per step",
-                       "l2": "inputs larger than L2 (no flush)"},
+                       "l2": "inputs larger than L2 (no flush)", "tuned": tuned, **extra},
             "plain": {"value": N * world / (ms_plain / 1e3), "ms_per_step": ms_plain,
                       "form": "one hpa_attribute_samples per buffer"},
             "path_roofline": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
@@ -291,14 +448,20 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "plain", "batched"])
+    ap.add_argument("--workload", default="large", choices=["large", "plain", "batched", "many-ctx", "serving"])
     ap.add_argument("--samples", type=int, default=0, help="override the sample count (profiling runs)")
     ap.add_argument("--contexts", type=int, default=0, help="override the context count (profiling runs)")
     ap.add_argument("--cursor-shift", type=int, default=None, help="scatter cursor padding (log2 words)")
+    ap.add_argument("--sort-mode", type=int, default=None, help="leaf radix ranking: 0 by digit width, 1 match_any, 2 ballots")
+    ap.add_argument("--no-part", action="store_true", help="per-context cursor scatter instead of the partition path")
+    ap.add_argument("--no-tune", action="store_true", help="skip hpa_tune (use the per-call default configuration)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the apportion / inclusive / derive rows")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
+    ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
+    ap.add_argument("--serve-mem-gb", type=int, default=60, help="serving: admission pool (GiB)")
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -308,8 +471,11 @@ def main():
         return
     from paper_2109_06931_gb300 import hpa as H
 
-    if args.workload == "batched":
+    if args.workload in ("batched", "many-ctx"):
         run_batched(args, world, rank, local)
+        return
+    if args.workload == "serving":
+        run_serving(args, world, rank, local)
         return
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -323,11 +489,16 @@ def main():
     S = w.samples(B, device=dev)
     N = S.n
     stream = torch.cuda.Stream(dev)
-    h = H.Hpa(local, stream=stream, cursor_shift=args.cursor_shift)
+    h = H.Hpa(local, stream=stream, cursor_shift=args.cursor_shift, sort_mode=args.sort_mode,
+              partition=not args.no_part)
     bid = h.load_structure(B)
     out = H.new_profile(N, S.n_stall, dev)
     h.reserve(N, S.n_ctx)
     torch.cuda.synchronize()
+    tuned = None
+    if not args.no_tune and args.sort_mode is None and not args.no_part:
+        chosen, cand_ms = h.tune(bid, S, out=out)
+        tuned = dict(chosen, candidates_ms=[round(t, 3) for t in cand_ms])
     for _ in range(args.warmup):
         h.attribute_samples(bid, S, out=out)
     h.sync()
@@ -412,9 +583,10 @@ def main():
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": w.name, "samples": N, "keys": K, "functions": w.n_funcs,
                        "line_ranges": w.n_line_ranges, "contexts": w.n_ctx, "counts": has_cnt,
-                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                       "tuned": tuned},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak, "peak_kind": peak_kind, "traffic": None,
+                         "frac": ach / peak, "peak_kind": peak_kind, "traffic": traffic_per_launch(dom, N),
                          "algorithmic_bytes_per_launch": algo[dom], "ms_per_launch": ph[dom]},
             "path_roofline": {"achieved": path_ach, "frac": path_ach / peak, "unit": "GB/s",
                               "algorithmic_bytes_per_step": path_bytes},

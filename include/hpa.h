@@ -62,10 +62,18 @@ typedef struct hpa_handle hpa_handle;
 typedef struct {
     uint32_t issued_mask;   /* stall reasons that count as "issued" (not stalled) in the warp
                                issue rate W; default 0x1 (reason 0)                        */
-    uint32_t leaf_capacity; /* records per shared-memory leaf of the aggregation; 0 = chosen
-                               per call by the tuner (hpa_tune)                             */
+    uint32_t leaf_capacity; /* records per shared-memory leaf of the aggregation (4096 or
+                               10240); 0 = chosen per call from samples per context, or by
+                               hpa_tune                                                     */
     uint32_t timeout_iters; /* iteration limit of every bounded device wait; 0 = 1<<22     */
-    uint32_t reserved[5];
+    uint32_t cursor_pad;    /* spacing of the per-context scatter cursors: 0 = 8 words,
+                               n > 0 = 2^(n-1) words                                        */
+    uint32_t leaf_ranking;  /* equal-digit search of the leaf radix sort: 0 = by digit width,
+                               1 = __match_any_sync, 2 = ballots                            */
+    uint32_t grouping;      /* grouping of records by context: 0 = automatic (per-part
+                               counters when every buffer has <= 4096 contexts, else
+                               per-context cursors), 1 = per-context cursors always         */
+    uint32_t reserved[2];   /* must be zero                                                 */
 } hpa_options;
 
 /* Program structure of one GPU binary (Section 5).  HOST arrays, copied into
@@ -280,6 +288,21 @@ hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t binary_id, cons
  * the first failure.                                                          */
 hpa_status hpa_attribute_batch(hpa_handle* h, uint32_t n, const uint32_t* binary_ids,
                                const hpa_samples* in, hpa_profile* outs);
+
+/* Autotuner of the aggregation (no counterpart in the paper: a property of
+ * the library).  Runs hpa_attribute_samples on `in` under each candidate
+ * configuration -- leaf_capacity 4096 / 10240, grouping 0 / 1, leaf_ranking
+ * 1 / 2: HPA_TUNE_CANDIDATES in all, in that nesting order -- timing each
+ * with CUDA events on the handle's stream (one untimed run, then `reps`
+ * timed runs, 0 = 2), and keeps the fastest in the handle's options for the
+ * calls that follow.  in/out as for hpa_attribute_samples; out holds the
+ * last candidate's result.  best (may be null) receives the chosen options;
+ * ms (may be null, HPA_TUNE_CANDIDATES floats) the mean time of each
+ * candidate.  Synchronous: returns after the last run has finished.  Every
+ * candidate computes the same keys; only their speed differs.               */
+#define HPA_TUNE_CANDIDATES 8
+hpa_status hpa_tune(hpa_handle* h, uint32_t binary_id, const hpa_samples* in, hpa_profile* out, uint32_t reps,
+                    hpa_options* best, float* ms);
 
 /* Approximate GPU calling context tree per requested context (Section 6.3,
  * steps 1-4): call-site weights from the samples of call instructions, the

@@ -93,7 +93,6 @@ void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cuda
 }
 
 // ------------------------------------------------------------------ helpers
-// largest b with pre[b] <= x (pre is non-decreasing, pre[0] = 0)
 // A big group (more than cap records) is split by fine bins: the top h bits
 // of its subkey.  A bin spans 2^(sbits - h) subkeys; h is chosen so that this
 // is at most one dense window of the leaf (2^13 subkeys) whenever 2^14 bins
@@ -236,85 +235,69 @@ __global__ void k_leaves(AggWork w) {
 }
 
 // ------------------------------------------------------------------ K9a: attribute
-// Streams every sample once: attributes its PC to a structure node (Section
-// 4.2), packs (node, stall) into a subkey and stores {subkey, count} in sample
-// order (coalesced) in the second record buffer; accumulates per-stall totals
-// and UNKNOWN totals.  Only the directory / range loads are dependent, so
-// many samples per thread stay in flight.
-template <bool HAS_CNT, int U>
-__global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
-    extern __shared__ unsigned long long acc[];          // [n_stall_max][256] per-thread totals
-    __shared__ unsigned long long unk[HPA_MAX_STALL_DEV];
-    const uint32_t tid = threadIdx.x;
-    const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;       // stall slots per thread
-    const uint64_t keep = policy_evict_last();
-    for (uint32_t r = 0; r < nsm; ++r) acc[r * 256 + tid] = 0;
-    if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
-    __syncthreads();
-    uint32_t cur_b = 0xFFFFFFFFu;
-
-    auto flush = [&](uint32_t b) {
-        __syncthreads();
-        if (b != 0xFFFFFFFFu) {
-            const BufDev& B = w.bufs[b];
-            for (uint32_t r = tid >> 5; r < nsm; r += 8) {
-                unsigned long long v = 0;
-                for (uint32_t t = lane_id(); t < 256; t += 32) v += acc[r * 256 + t];
-                v = warp_sum(v);
-                if (lane_id() == 0 && v && B.total) atomicAdd((unsigned long long*)&B.total[r], v);
-                if (lane_id() == 0 && unk[r] && B.unknown) atomicAdd((unsigned long long*)&B.unknown[r], unk[r]);
+// U samples per thread: the structure node of each PC (Section 4.2) through
+// the direct-answer directory, with a short forward walk over the sorted
+// ranges where a directory bucket straddles several ranges.  Only these
+// loads are dependent, so U lookups per thread stay in flight.
+template <int U>
+__device__ __forceinline__ void lookup_nodes(const DevBinary& bin, const uint64_t (&pc)[U], const bool (&ok)[U],
+                                             uint32_t (&nd)[U], uint64_t keep) {
+    uint32_t off[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        nd[u] = bin.n_nodes;
+        off[u] = 0;
+        if (ok[u]) {
+            const uint64_t o = pc[u] - bin.pc_base;
+            if (o < bin.span) {
+                off[u] = (uint32_t)o;
+                nd[u] = ld_keep(&bin.dir[off[u] >> bin.dshift], keep);
             }
         }
-        __syncthreads();
-        for (uint32_t r = 0; r < nsm; ++r) acc[r * 256 + tid] = 0;
-        if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
-        __syncthreads();
-    };
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (nd[u] & DIR_SEARCH) {
+            uint32_t i = nd[u] & ~DIR_SEARCH;
+            uint4 r = ld_keep4(&bin.rng[i], keep);
+            while (r.y <= off[u] && i + 1 < bin.n_ranges) r = ld_keep4(&bin.rng[++i], keep);
+            nd[u] = (r.x <= off[u] && off[u] < r.y) ? r.z : bin.n_nodes;
+        }
+    }
+}
 
+// Streams every sample once: attributes its PC, packs (node, stall) into a
+// subkey and stores {subkey, count} in sample order (coalesced) in the
+// second record buffer, for k_scatter.  Used when a buffer has more contexts
+// than the partition path keeps in shared memory.
+template <bool HAS_CNT, int U>
+__global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
+    const uint32_t tid = threadIdx.x;
+    const uint64_t keep = policy_evict_last();
     for (uint64_t t = blockIdx.x; t < w.n_tiles; t += gridDim.x) {
         const uint32_t b = upper_index<uint64_t>(w.buf_tile, w.n_buf, t);
-        if (b != cur_b) { flush(cur_b); cur_b = b; }
         const BufDev B = w.bufs[b];
         const DevBinary bin = w.bins[B.bin];
         const uint64_t i0 = (t - B.tile_base) * TILE;
         const uint64_t i1 = min(i0 + TILE, B.n);
         const uint64_t stage0 = t * TILE - i0;               // staging index = stage0 + i
-        const uint32_t M = bin.n_nodes;
         uint32_t bad = 0;
         for (uint64_t base = i0 + tid; base < i1; base += 256 * U) {
             uint64_t pc[U];
-            uint32_t st[U], cnt[U], off[U], nd[U];
+            uint32_t st[U], cnt[U], nd[U];
             bool ok[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const uint64_t i = base + (uint64_t)u * 256;
                 ok[u] = i < i1;
+                pc[u] = 0; st[u] = 0; cnt[u] = 1u;
                 if (ok[u]) {
                     st[u] = ld_stream(&B.stall[i]);
                     pc[u] = ld_stream((const unsigned long long*)&B.pc[i]);
-                    cnt[u] = (HAS_CNT && B.count) ? ld_stream(&B.count[i]) : 1u;
+                    if (HAS_CNT && B.count) cnt[u] = ld_stream(&B.count[i]);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                nd[u] = M;
-                if (ok[u]) {
-                    const uint64_t o = pc[u] - bin.pc_base;
-                    if (o < bin.span) {
-                        off[u] = (uint32_t)o;
-                        nd[u] = ld_keep(&bin.dir[off[u] >> bin.dshift], keep);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (nd[u] & DIR_SEARCH) {
-                    uint32_t i = nd[u] & ~DIR_SEARCH;
-                    uint4 r = ld_keep4(&bin.rng[i], keep);
-                    while (r.y <= off[u] && i + 1 < bin.n_ranges) r = ld_keep4(&bin.rng[++i], keep);
-                    nd[u] = (r.x <= off[u] && off[u] < r.y) ? r.z : M;
-                }
-            }
+            lookup_nodes<U>(bin, pc, ok, nd, keep);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (!ok[u]) continue;
@@ -323,17 +306,11 @@ __global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
                 const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
                 if (HAS_CNT) st_stream(&w.rec2_pair[stage0 + i], make_uint2(sub, bad_stall ? 0u : cnt[u]));
                 else st_stream(&w.rec2_sub[stage0 + i], sub);
-                if (bad_stall) {
-                    ++bad;
-                } else {
-                    acc[st[u] * 256 + tid] += cnt[u];
-                    if (nd[u] == M) atomicAdd(&unk[st[u]], (unsigned long long)cnt[u]);
-                }
+                bad += bad_stall;
             }
         }
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
     }
-    flush(cur_b);
 }
 
 // ------------------------------------------------------------------ K9b: scatter by context
@@ -373,6 +350,113 @@ __global__ void __launch_bounds__(256) k_scatter(AggWork w) {
                 else w.rec_sub[slot[u]] = r[u].x;
             }
         }
+    }
+}
+
+// ------------------------------------------------------------------ partition path
+// For buffers whose contexts fit in shared memory, records are grouped by
+// context without global atomics.  Each buffer is cut into parts of
+// part_len samples; k_part_hist counts the valid records of every (context,
+// part) into part_cnt[cnt_base + ctx * parts + part] (context-major), one
+// exclusive scan of part_cnt then gives the position of each (context,
+// part)'s first record in the context-grouped record array, and
+// k_part_scatter attributes every sample and places its record with a
+// shared-memory cursor per context.  Group offsets are read off the scan.
+__global__ void __launch_bounds__(PART_THREADS) k_part_hist(AggWork w) {
+    extern __shared__ uint32_t sh[];
+    for (uint64_t p = blockIdx.x; p < w.n_parts; p += gridDim.x) {
+        const uint32_t b = upper_index<uint64_t>(w.buf_part, w.n_buf, p);
+        const BufDev& B = w.bufs[b];
+        const uint32_t n_ctx = B.n_ctx;
+        const uint64_t pl = p - B.part_base;
+        const uint64_t parts = w.buf_part[b + 1] - w.buf_part[b];
+        const uint64_t i0 = pl * w.part_len, i1 = min(i0 + w.part_len, B.n);
+        const uint32_t* ctx = B.ctx;
+        __syncthreads();
+        for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) sh[c] = 0;
+        __syncthreads();
+        uint32_t bad = 0;
+        auto count = [&](uint32_t c) {
+            if (c < n_ctx) atomicAdd(&sh[c], 1u);
+            else ++bad;
+        };
+        uint64_t i = i0;
+        if ((((uintptr_t)(ctx + i0)) & 15) == 0) {
+            // 16-byte loads over the aligned body (part_len is a multiple of 4)
+            const uint4* v = reinterpret_cast<const uint4*>(ctx + i0);
+            const uint64_t nv = (i1 - i0) / 4;
+            for (uint64_t k = threadIdx.x; k < nv; k += PART_THREADS) {
+                const uint4 q = ld_stream(&v[k]);
+                count(q.x); count(q.y); count(q.z); count(q.w);
+            }
+            i = i0 + nv * 4;
+        }
+        for (uint64_t j = i + threadIdx.x; j < i1; j += PART_THREADS) count(ld_stream(&ctx[j]));
+        if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
+        __syncthreads();
+        uint32_t* out = w.part_cnt + B.cnt_base + pl;
+        for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) out[(uint64_t)c * parts] = sh[c];
+    }
+}
+
+// group offsets (exclusive) from the scanned part counts
+__global__ void k_part_seg(AggWork w) {
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= w.G; g += gridDim.x * blockDim.x) {
+        if (g == w.G) { w.grp_hist[g] = w.part_cnt[w.n_cnt]; continue; }
+        const uint32_t b = upper_index<uint32_t>(w.buf_grp, w.n_buf, g);
+        const BufDev& B = w.bufs[b];
+        const uint64_t parts = w.buf_part[b + 1] - w.buf_part[b];
+        w.grp_hist[g] = w.part_cnt[B.cnt_base + (uint64_t)(g - B.grp_base) * parts];
+    }
+}
+
+template <bool HAS_CNT, int U>
+__global__ void __launch_bounds__(PART_THREADS, 2) k_part_scatter(AggWork w) {
+    extern __shared__ uint32_t cur[];                   // per-context record cursors of this part
+    const uint64_t keep = policy_evict_last();
+    for (uint64_t p = blockIdx.x; p < w.n_parts; p += gridDim.x) {
+        const uint32_t b = upper_index<uint64_t>(w.buf_part, w.n_buf, p);
+        const BufDev B = w.bufs[b];
+        const DevBinary bin = w.bins[B.bin];
+        const uint32_t n_ctx = B.n_ctx;
+        const uint64_t pl = p - B.part_base;
+        const uint64_t parts = w.buf_part[b + 1] - w.buf_part[b];
+        const uint64_t i0 = pl * w.part_len, i1 = min(i0 + w.part_len, B.n);
+        __syncthreads();                                // the previous part's cursors are done
+        const uint32_t* first = w.part_cnt + B.cnt_base + pl;
+        for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) cur[c] = first[(uint64_t)c * parts];
+        __syncthreads();
+        uint32_t bad = 0;
+        for (uint64_t base = i0 + threadIdx.x; base < i1; base += (uint64_t)PART_THREADS * U) {
+            uint64_t pc[U];
+            uint32_t st[U], cnt[U], cx[U], nd[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint64_t i = base + (uint64_t)u * PART_THREADS;
+                ok[u] = i < i1;
+                pc[u] = 0; st[u] = 0; cnt[u] = 1u; cx[u] = 0xFFFFFFFFu;
+                if (ok[u]) {
+                    cx[u] = ld_stream(&B.ctx[i]);
+                    st[u] = ld_stream(&B.stall[i]);
+                    pc[u] = ld_stream((const unsigned long long*)&B.pc[i]);
+                    if (HAS_CNT && B.count) cnt[u] = ld_stream(&B.count[i]);
+                    ok[u] = cx[u] < n_ctx;                  // counted as invalid by k_part_hist
+                }
+            }
+            lookup_nodes<U>(bin, pc, ok, nd, keep);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!ok[u]) continue;
+                const bool bad_stall = st[u] >= B.n_stall;
+                const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
+                const uint32_t pos = atomicAdd(&cur[cx[u]], 1u);
+                if (HAS_CNT) w.rec_pair[pos] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
+                else w.rec_sub[pos] = sub;
+                bad += bad_stall;
+            }
+        }
+        if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
     }
 }
 
@@ -694,7 +778,9 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
                 }
             }
             __syncthreads();
-            const int cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
+            int cur;
+            if constexpr (Cfg::PACKED) cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits), (int)w.sort_mode);
+            else cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
             auto Kc = [&S, cur](int i) -> uint32_t {
                 if constexpr (Cfg::PACKED) return Sort::key_of(S.el[cur][i]);
                 else return S.key[cur][i];
@@ -785,36 +871,77 @@ __global__ void __launch_bounds__(THREADS) k_leaf(AggWork w) {
 }
 
 // ------------------------------------------------------------------ K13: emit
+// Leaves are in key order, so leaf_out (the scanned run counts) places every
+// key.  With emit_totals, the per-stall totals and UNKNOWN totals of each
+// buffer are summed here over its keys (every valid record lies in exactly
+// one key): per-thread slots in shared memory, flushed when the CTA moves to
+// another buffer.
 __global__ void __launch_bounds__(256) k_emit(AggWork w) {
+    extern __shared__ unsigned long long acc[];          // [2^sb][256] per-thread totals (emit_totals)
+    __shared__ unsigned long long unk[HPA_MAX_STALL_DEV];
+    const uint32_t tid = threadIdx.x;
     const uint32_t n_leaves = w.item_nleaf[w.G];
     const uint32_t* leaf_out = w.leaf_d;
     const uint32_t smask = (w.sbits >= 32) ? 0xFFFFFFFFu : ((1u << w.sbits) - 1);
     const uint32_t stmask = (1u << w.sb) - 1;
+    const uint32_t nsm = 1u << w.sb;
+    const bool tot = w.emit_totals != 0;
+    if (tot) {
+        for (uint32_t r = 0; r < nsm; ++r) acc[r * 256 + tid] = 0;
+        if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
+    }
+    __syncthreads();
+    uint32_t cur_b = 0xFFFFFFFFu;
+    auto flush = [&]() {
+        __syncthreads();
+        if (cur_b != 0xFFFFFFFFu) {
+            const BufDev& B = w.bufs[cur_b];
+            for (uint32_t r = tid >> 5; r < nsm; r += 8) {
+                unsigned long long v = 0;
+                for (uint32_t t = lane_id(); t < 256; t += 32) { v += acc[r * 256 + t]; acc[r * 256 + t] = 0; }
+                v = warp_sum(v);
+                if (lane_id() == 0 && v && B.total) atomicAdd((unsigned long long*)&B.total[r], v);
+                if (lane_id() == 0 && unk[r] && B.unknown) atomicAdd((unsigned long long*)&B.unknown[r], unk[r]);
+            }
+        }
+        __syncthreads();
+        if (tid < HPA_MAX_STALL_DEV) unk[tid] = 0;
+        __syncthreads();
+    };
     for (uint32_t l = blockIdx.x; l < n_leaves; l += gridDim.x) {
         const uint32_t d = leaf_out[l + 1] - leaf_out[l];
-        if (d == 0) continue;
+        if (d == 0) continue;                             // uniform across the block
         const uint32_t info = w.leaf_info[l];
         const uint32_t b = info >> 8;
         const BufDev& B = w.bufs[b];
         if (w.buf_bad[b]) continue;
+        if (tot && b != cur_b) { flush(); cur_b = b; }
         const uint32_t M = w.bins[B.bin].n_nodes;
         const uint32_t start = w.leaf_start[l];
         const uint32_t g0 = w.leaf_grp0[l];
         const uint64_t o0 = (uint64_t)leaf_out[l] - leaf_out[w.buf_first_leaf[b]];
         const uint32_t gctx0 = g0 - B.grp_base;
-        for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+        for (uint32_t i = tid; i < d; i += blockDim.x) {
             const uint64_t pos = o0 + i;
-            if (pos >= B.capacity) break;
             const uint32_t k = w.tmp_key[start + i];
+            const unsigned long long v = w.tmp_val[start + i];
             const uint32_t sub = k & smask;
-            const uint32_t gl = (w.sbits >= 32) ? 0u : (k >> w.sbits);
             const uint32_t node = sub >> w.sb;
-            B.key_ctx[pos] = gctx0 + gl;
-            B.key_node[pos] = (node == M) ? UNKNOWN : node;
-            B.key_stall[pos] = (uint8_t)(sub & stmask);
-            B.val[pos] = w.tmp_val[start + i];
+            const uint32_t stall = sub & stmask;
+            if (tot) {
+                acc[stall * 256 + tid] += v;
+                if (node == M) atomicAdd(&unk[stall], v);
+            }
+            if (pos < B.capacity) {
+                const uint32_t gl = (w.sbits >= 32) ? 0u : (k >> w.sbits);
+                B.key_ctx[pos] = gctx0 + gl;
+                B.key_node[pos] = (node == M) ? UNKNOWN : node;
+                B.key_stall[pos] = (uint8_t)stall;
+                B.val[pos] = v;
+            }
         }
     }
+    if (tot) flush();
 }
 
 __global__ void k_finalize(AggWork w) {
@@ -847,9 +974,9 @@ static void launch_leaf(const AggWork& w, cudaStream_t s, int sms, int per_sm) {
     k_leaf<THREADS, CAP, HAS_CNT, V><<<sms * per_sm, THREADS, Cfg::SMEM, s>>>(w);
 }
 
-void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
+void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, bool seg_ready) {
     const int gblocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 255) / 256, (uint64_t)sms * 16));
-    scan_u32(w.grp_hist, w.grp_hist, w.G, w.scan_tmp, s, launches);
+    if (!seg_ready) scan_u32(w.grp_hist, w.grp_hist, w.G, w.scan_tmp, s, launches);
     k_item_flags<<<gblocks, 256, 0, s>>>(w);
     scan_u32(w.item_id, w.item_id, w.G, w.scan_tmp, s, launches);
     k_items<<<gblocks, 256, 0, s>>>(w);
@@ -905,7 +1032,13 @@ static void run_finish(const AggWork& w, cudaStream_t s, int sms, uint64_t* laun
     *launches += 1;
     if (ev) cudaEventRecord(ev[4], s);
     scan_u32(w.leaf_d, w.leaf_d, w.L_max, w.scan_tmp, s, launches);
-    k_emit<<<sms * 8, 256, 0, s>>>(w);
+    const size_t emit_smem = w.emit_totals ? ((size_t)256 << w.sb) * 8 : 0;
+    static bool emit_attr = false;
+    if (!emit_attr) {
+        cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * HPA_MAX_STALL_DEV * 8);
+        emit_attr = true;
+    }
+    k_emit<<<sms * 8, 256, emit_smem, s>>>(w);
     launch_finalize(w, s, launches);
     *launches += 1;
     if (ev) cudaEventRecord(ev[5], s);
@@ -920,29 +1053,47 @@ void clear_work(const AggWork& w, cudaStream_t s) {
 void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
     clear_work(w, s);
-    const size_t hsm = (size_t)HIST_SMEM_MAX * 4;
-    const int per_sm = 2;
-    const int hist_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * per_sm));
-    cudaFuncSetAttribute(k_grp_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
-    k_grp_hist<<<hist_blocks, 256, hsm, s>>>(w);
-    *launches += 1;
-    run_plan(w, s, sms, launches);
-    if (ev) cudaEventRecord(ev[1], s);
-    const uint32_t nsm = w.sb ? (1u << w.sb) : 1u;
-    const size_t acc_bytes = (size_t)nsm * 256 * 8;
-    const int at_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
-    const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 8));
-    if (w.has_cnt) {
-        cudaFuncSetAttribute(k_attribute<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
-        k_attribute<true, 4><<<at_blocks, 256, acc_bytes, s>>>(w);
-        k_scatter<true, 8><<<sc_blocks, 256, 0, s>>>(w);
+    if (w.part_mode) {
+        const size_t csm = (size_t)w.part_ctx_max * 4;
+        static bool attr = false;
+        if (!attr) {
+            const int mx = (int)PART_CTX_MAX * 4;
+            cudaFuncSetAttribute(k_part_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            cudaFuncSetAttribute(k_part_scatter<true, PART_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            cudaFuncSetAttribute(k_part_scatter<false, PART_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            attr = true;
+        }
+        const int pb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * 2));
+        k_part_hist<<<pb, PART_THREADS, csm, s>>>(w);
+        scan_u32(w.part_cnt, w.part_cnt, w.n_cnt, w.scan_tmp, s, launches);
+        const int gb = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 256) / 256, (uint64_t)sms * 16));
+        k_part_seg<<<gb, 256, 0, s>>>(w);
+        *launches += 2;
+        run_plan(w, s, sms, launches, true);
+        if (ev) cudaEventRecord(ev[1], s);
+        if (w.has_cnt) k_part_scatter<true, PART_U><<<pb, PART_THREADS, csm, s>>>(w);
+        else k_part_scatter<false, PART_U><<<pb, PART_THREADS, csm, s>>>(w);
+        *launches += 1;
     } else {
-        cudaFuncSetAttribute(k_attribute<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes);
-        k_attribute<false, 4><<<at_blocks, 256, acc_bytes, s>>>(w);
-        k_scatter<false, 8><<<sc_blocks, 256, 0, s>>>(w);
+        const size_t hsm = (size_t)HIST_SMEM_MAX * 4;
+        const int per_sm = 2;
+        const int hist_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * per_sm));
+        cudaFuncSetAttribute(k_grp_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        k_grp_hist<<<hist_blocks, 256, hsm, s>>>(w);
+        *launches += 1;
+        run_plan(w, s, sms, launches, false);
+        if (ev) cudaEventRecord(ev[1], s);
+        const int at_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 4));
+        const int sc_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * 8));
+        if (w.has_cnt) {
+            k_attribute<true, 4><<<at_blocks, 256, 0, s>>>(w);
+            k_scatter<true, 8><<<sc_blocks, 256, 0, s>>>(w);
+        } else {
+            k_attribute<false, 4><<<at_blocks, 256, 0, s>>>(w);
+            k_scatter<false, 8><<<sc_blocks, 256, 0, s>>>(w);
+        }
+        *launches += 2;
     }
-    *launches += 1;
-    *launches += 1;
     if (ev) cudaEventRecord(ev[2], s);
     run_finish(w, s, sms, launches, ev);
 }
@@ -987,7 +1138,7 @@ void run_expand_aggregate(const AggWork& w, const ExpandSrc& x, cudaStream_t s, 
     clear_work(w, s);
     const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((x.cap + 255) / 256, (uint64_t)sms * 8));
     k_expand_hist<<<blocks, 256, 0, s>>>(w, x);
-    run_plan(w, s, sms, launches);
+    run_plan(w, s, sms, launches, false);
     k_expand_scatter<<<blocks, 256, 0, s>>>(w, x);
     *launches += 2;
     run_finish(w, s, sms, launches, nullptr);

@@ -406,7 +406,7 @@ extern "C" hpa_status hpa_derive_metrics(hpa_handle* h, const hpa_profile* const
     cudaMemsetAsync(pcs, 0, (size_t)out->n_ctx * S * 8, s);
     const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, (uint64_t)sms * 8));
     k_union_hist<<<blocks, 256, 0, s>>>(w, A);
-    run_plan(w, s, sms, &h->launches);
+    run_plan(w, s, sms, &h->launches, false);
     k_union_scatter<<<blocks, 256, 0, s>>>(w, A);
     launch_big_partition(w, s, sms, &h->launches);
     using Sort = BlockRadix<DS_THREADS, DS_CAP, 8, uint64_t, true>;

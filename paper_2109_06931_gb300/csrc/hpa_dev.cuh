@@ -263,17 +263,17 @@ struct BlockRadix {
 // are copied into shared memory verbatim -- and E = uint32_t a key alone.  Digits are at most 9 bits
 // (a 26-bit key takes 3 passes); passes and digit width follow the key width.
 // Counter rows are padded by one word so the digit-major scan is free of bank
-// conflicts.  Same stable ranking as BlockRadix (warp-contiguous chunks,
-// __match_any_sync within a 32-element row).
+// conflicts.  Stable ranking as in BlockRadix (warp-contiguous chunks, equal
+// digits of a 32-element row found by __match_any_sync or by ballots).
 template <int THREADS, int CAP, typename E>
 struct PackedRadix {
     static constexpr int W = THREADS / 32;
     static constexpr int MAXB = 9, MAXBINS = 1 << MAXB, ROW = MAXBINS + 1;
     static constexpr int MAX_EPT = (MAXBINS * W + THREADS - 1) / THREADS;
+    static constexpr int RPT = (CAP + THREADS - 1) / THREADS;   // 32-element rows per warp at most
 
     struct Smem {
         E el[2][CAP];
-        uint16_t rank[CAP];
         uint32_t cnt[W * ROW];
         uint32_t sw[33];
     };
@@ -284,7 +284,25 @@ struct PackedRadix {
         else return 1u;
     }
 
-    __device__ static int sort(Smem& s, int n, int bits) {
+    // lanes of the warp whose digit equals this lane's (ok lanes only):
+    // one ballot per digit bit, plus one for the ok flag
+    __device__ static __forceinline__ uint32_t peers_ballot(uint32_t d, bool ok, int rb) {
+        uint32_t m = __ballot_sync(0xffffffffu, ok);
+        m = ok ? m : ~m;
+        for (int b = 0; b < rb; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t v = __ballot_sync(0xffffffffu, bit);
+            m &= bit ? v : ~v;
+        }
+        return m;
+    }
+
+    // Ranking within a 32-element row: lanes with equal digits are found
+    // with __match_any_sync (executed on the ADU), or with one ballot per
+    // digit bit.  Measured on GB300: ballots are faster for 9-bit digits,
+    // __match_any_sync for narrower ones.  match: 0 = by digit width,
+    // 1 = __match_any_sync, 2 = ballots.
+    __device__ static int sort(Smem& s, int n, int bits, int match = 0) {
         if (bits <= 0) return 0;
         const int warp = threadIdx.x >> 5;
         const int lane = lane_id();
@@ -296,24 +314,35 @@ struct PackedRadix {
         const int chunk = ((n + W - 1) / W + 31) & ~31;
         const int lo = warp * chunk;
         const int hi = min(n, lo + chunk);
+        const bool ballots = match == 2 || (match == 0 && rb >= MAXB);
         int cur = 0;
         for (int shift = 0; shift < bits; shift += rb) {
             const uint32_t dmask = (1u << min(rb, bits - shift)) - 1;
             for (int i = threadIdx.x; i < W * ROW; i += THREADS) s.cnt[i] = 0;
             __syncthreads();
             uint32_t* row = s.cnt + warp * ROW;
-            for (int base = lo; base < lo + chunk; base += 32) {
-                const int i = base + lane;
-                const bool ok = i < hi;
-                const uint32_t d = ok ? ((key_of(s.el[cur][i]) >> shift) & dmask) : 0xFFFFFFFFu;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
-                const uint32_t below = __popc(peers & lanemask_lt());
-                // the warp is converged here (no branch since the last
-                // __syncwarp), so every lane reads before its group's leader writes
-                const uint32_t before = row[ok ? d : 0];
-                if (ok) s.rank[i] = (uint16_t)(before + below);
-                if (ok && below == 0) row[d] = before + __popc(peers);
-                __syncwarp();
+            // pass A: each element's rank among the equal digits before it in
+            // the warp's chunk; elements stay in registers until pass B
+            E x[RPT];
+            uint32_t rk[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int base = lo + r * 32;
+                if (base < hi) {                           // warp-uniform
+                    const int i = base + lane;
+                    const bool ok = i < hi;
+                    x[r] = ok ? s.el[cur][i] : E(0);
+                    const uint32_t d = (key_of(x[r]) >> shift) & dmask;
+                    const uint32_t peers = ballots ? peers_ballot(d, ok, rb)
+                                                   : __match_any_sync(0xffffffffu, ok ? d : 0xFFFFFFFFu);
+                    const uint32_t below = __popc(peers & lanemask_lt());
+                    // the warp is converged here (no branch since the last
+                    // __syncwarp), so every lane reads before its group's leader writes
+                    const uint32_t before = row[ok ? d : 0];
+                    rk[r] = before + below;
+                    if (ok && below == 0) row[d] = before + __popc(peers);
+                    __syncwarp();
+                }
             }
             __syncthreads();
             {
@@ -342,10 +371,14 @@ struct PackedRadix {
                 }
                 __syncthreads();
             }
-            for (int i = lo + lane; i < hi; i += 32) {
-                const E x = s.el[cur][i];
-                const uint32_t d = (key_of(x) >> shift) & dmask;
-                s.el[cur ^ 1][row[d] + s.rank[i]] = x;
+            // pass B: scatter to digit offset + rank
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int i = lo + r * 32 + lane;
+                if (i < hi) {
+                    const uint32_t d = (key_of(x[r]) >> shift) & dmask;
+                    s.el[cur ^ 1][row[d] + rk[r]] = x[r];
+                }
             }
             __syncthreads();
             cur ^= 1;

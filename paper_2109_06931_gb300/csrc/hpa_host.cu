@@ -99,6 +99,10 @@ Binary* hpa_handle::binary(uint32_t id) {
 extern "C" hpa_status hpa_create(hpa_handle** out, int device, void* cuda_stream, const hpa_options* opt) {
     if (!out) return HPA_E_INVALID_ARG;
     *out = nullptr;
+    if (opt && (opt->reserved[0] || opt->reserved[1] || opt->leaf_ranking > 2 || opt->grouping > 1 ||
+                opt->cursor_pad > 7 ||
+                (opt->leaf_capacity && opt->leaf_capacity != LEAF_CAP_SMALL && opt->leaf_capacity != LEAF_CAP_LARGE)))
+        return HPA_E_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -410,14 +414,15 @@ extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary
 // ------------------------------------------------------------------ aggregation calls
 // Scratch layout of one aggregation over N records in G groups (n_buf buffers).
 hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n, uint32_t cap, uint32_t sb,
-                                  uint32_t sbits, bool has_cnt, bool val64, uint64_t staged) {
+                                  uint32_t sbits, bool has_cnt, bool val64, uint64_t staged, uint64_t cnt_words) {
     const uint64_t N2 = std::max(N, staged);   // the second record buffer also stages samples in tile order
     const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
     w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
     w.span_log = std::min<uint32_t>(10, 32 - sbits);
-    // scatter cursors padded to 2^cur_shift words (option reserved[0] = shift + 1)
-    w.cur_shift = opt.reserved[0] ? std::min<uint32_t>(opt.reserved[0] - 1, 6) : 3;
+    // scatter cursors padded to 2^cur_shift words
+    w.cur_shift = opt.cursor_pad ? std::min<uint32_t>(opt.cursor_pad - 1, 6) : 3;
     if (((G + 1) << w.cur_shift) > (64ull << 20)) w.cur_shift = 0;
+    w.sort_mode = std::min<uint32_t>(opt.leaf_ranking, 2);
     w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt || val64; w.val64 = val64;
     auto layout = [&](Carve& c) {
         w.grp_hist = c.take<uint32_t>(G + 1);
@@ -443,7 +448,8 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
         w.rec2_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
         w.tmp_key = c.take<uint32_t>(N + 1);
         w.tmp_val = c.take<uint64_t>(N + 1);
-        w.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max<uint64_t>(G, L_max)));
+        w.part_cnt = cnt_words ? c.take<uint32_t>(cnt_words) : nullptr;
+        w.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max<uint64_t>(std::max<uint64_t>(G, L_max), cnt_words)));
     };
     Carve probe{nullptr};
     layout(probe);
@@ -491,19 +497,42 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     if (cap == 0) cap = (G && N / G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL;
     if (cap != LEAF_CAP_SMALL && cap != LEAF_CAP_LARGE)
         return fail(HPA_E_INVALID_ARG, "leaf_capacity must be 0, %u or %u", LEAF_CAP_SMALL, LEAF_CAP_LARGE);
+    // partition path: every buffer's contexts fit in shared memory and the
+    // (context, part) counters stay within PART_CNT_MAX; parts of part_len
+    // samples, about 8 per SM over the whole call
+    uint32_t ctx_max = 0;
+    for (uint32_t b = 0; b < n; ++b) ctx_max = std::max(ctx_max, in[b].n_ctx);
+    const uint64_t target_parts = (uint64_t)sms * 8;
+    const uint64_t part_len = std::max<uint64_t>(TILE, (N + target_parts - 1) / target_parts + TILE - 1) / TILE * TILE;
+    uint64_t n_parts = 0, n_cnt = 0;
+    for (uint32_t b = 0; b < n; ++b) {
+        const uint64_t pb = (in[b].n + part_len - 1) / part_len;
+        n_parts += pb;
+        n_cnt += pb * in[b].n_ctx;
+    }
+    const bool part = opt.grouping != 1 && ctx_max <= PART_CTX_MAX && n_cnt <= PART_CNT_MAX;
     AggWork w{};
-    hpa_status st = carve_work(w, N, G, n, cap, sb, sbits, has_cnt, false, tiles * TILE);
+    hpa_status st = carve_work(w, N, G, n, cap, sb, sbits, has_cnt, false, part ? 0 : tiles * TILE, part ? n_cnt + 1 : 0);
     if (st) return st;
     w.n_tiles = tiles;
+    w.emit_totals = 1;
+    if (part) {
+        w.part_mode = 1;
+        w.part_ctx_max = ctx_max;
+        w.part_len = part_len;
+        w.n_parts = n_parts;
+        w.n_cnt = n_cnt;
+    }
     // descriptors
-    const size_t desc_bytes = n * sizeof(BufDev) + (n + 1) * 8 + (n + 1) * 4 + 512;
+    const size_t desc_bytes = n * sizeof(BufDev) + (n + 1) * 16 + (n + 1) * 4 + 512;
     if ((st = ensure_staging(desc_bytes))) return st;
     Carve hs{(char*)staging};
     BufDev* hb = hs.take<BufDev>(n);
     uint64_t* htile = hs.take<uint64_t>(n + 1);
     uint32_t* hgrp = hs.take<uint32_t>(n + 1);
+    uint64_t* hpart = hs.take<uint64_t>(n + 1);
     const size_t used = hs.off;
-    uint64_t tb = 0;
+    uint64_t tb = 0, pbase = 0, cbase = 0;
     uint32_t gb = 0;
     for (uint32_t b = 0; b < n; ++b) {
         const hpa_samples& s = in[b];
@@ -511,6 +540,11 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         BufDev d{};
         d.pc = s.pc; d.ctx = s.ctx; d.stall = s.stall; d.count = s.count; d.n = s.n;
         d.tile_base = tb; d.n_ctx = s.n_ctx; d.n_stall = s.n_stall; d.grp_base = gb; d.bin = binary_ids[b];
+        d.part_base = pbase; d.cnt_base = cbase;
+        hpart[b] = pbase;
+        const uint64_t pb = (s.n + part_len - 1) / part_len;
+        pbase += pb;
+        cbase += pb * s.n_ctx;
         d.total = o.total; d.unknown = o.unknown;
         d.key_ctx = o.key_ctx; d.key_node = o.key_node; d.key_stall = o.key_stall; d.val = o.val;
         d.n_keys = o.n_keys; d.capacity = o.capacity;
@@ -525,7 +559,9 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     }
     htile[n] = tb;
     hgrp[n] = gb;
+    hpart[n] = pbase;
     char* ds = (char*)d_staging;
+    w.buf_part = (const uint64_t*)(ds + ((char*)hpart - (char*)staging));
     w.bufs = (const BufDev*)(ds + ((char*)hb - (char*)staging));
     w.buf_tile = (const uint64_t*)(ds + ((char*)htile - (char*)staging));
     w.buf_grp = (const uint32_t*)(ds + ((char*)hgrp - (char*)staging));
@@ -554,6 +590,7 @@ hpa_status hpa_handle::launch_graph(const AggWork& w, size_t staged_bytes, uint3
     key = mix64(key, w.G); key = mix64(key, w.n_buf); key = mix64(key, w.n_tiles); key = mix64(key, w.cap);
     key = mix64(key, w.sb); key = mix64(key, w.sbits); key = mix64(key, w.L_max); key = mix64(key, w.has_cnt);
     key = mix64(key, w.cur_shift); key = mix64(key, staged_bytes); key = mix64(key, (uint64_t)(uintptr_t)w.grp_hist);
+    key = mix64(key, w.part_mode); key = mix64(key, w.part_len); key = mix64(key, w.n_parts); key = mix64(key, w.sort_mode);
     for (uint32_t b = 0; b < n; ++b) key = mix64(mix64(key, in[b].n), in[b].n_ctx);
     CachedGraph* g = nullptr;
     for (auto& c : graphs)
@@ -601,7 +638,9 @@ extern "C" hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t 
     cudaSetDevice(h->device);
     const uint64_t N = max_samples, G = max_groups;
     const uint64_t L = G + 6 * (N / LEAF_CAP_SMALL + 1) + 300;
-    size_t bytes = (G + 1) * 4 * 12 + L * 4 * 5 + (N + TILE + 1) * (4 * 6 + 8) + 256 * 40 + scan_tmp_words(std::max(G, L)) * 4;
+    const uint64_t C = std::min<uint64_t>(PART_CNT_MAX, G * ((uint64_t)h->sms * 8 + 2));   // part counters
+    size_t bytes = (G + 1) * 4 * 12 + L * 4 * 5 + (N + TILE + 1) * (4 * 6 + 8) + 256 * 40 + (C + 1) * 4 +
+                   scan_tmp_words(std::max(std::max(G, L), C)) * 4;
     return h->ensure_scratch(bytes + (1 << 20));
 }
 

@@ -117,7 +117,8 @@ struct hpa_handle {
                          bool use_graph = false);
     hpa_status launch_graph(const hpa::AggWork& w, size_t staged_bytes, uint32_t n, const hpa_samples* in);
     hpa_status carve_work(hpa::AggWork& w, uint64_t N, uint64_t G, uint32_t n_buf, uint32_t cap, uint32_t sb,
-                          uint32_t sbits, bool has_cnt, bool val64, uint64_t staged = 0);
+                          uint32_t sbits, bool has_cnt, bool val64, uint64_t staged = 0,
+                          uint64_t cnt_words = 0);   // part counters incl. the scan total (0: none)
     // descriptors of single-output pipelines (expansion, union) in the staging area
     hpa_status stage_single_output(hpa::AggWork& w, uint32_t bin, uint32_t n_ctx, const hpa_profile& out);
 };

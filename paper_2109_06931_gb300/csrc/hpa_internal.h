@@ -23,6 +23,8 @@ struct BufDev {
     uint32_t bin;               // index into the DevBinary table
     uint32_t first_leaf_item;   // (filled on device) unused by the host
     uint32_t pad;
+    uint64_t part_base;         // first global part of this buffer (partition path)
+    uint64_t cnt_base;          // first part counter of this buffer: sum of n_ctx * parts before it
     uint64_t* total;            // per-stall totals (may be null)
     uint64_t* unknown;
     // outputs
@@ -49,6 +51,7 @@ struct AggWork {
     uint32_t* grp_hist;    // [G+1] -> exclusive scan -> seg_off
     uint32_t* grp_cursor;  // [G << cur_shift] scatter cursors, one per 2^cur_shift words
     uint32_t cur_shift;
+    uint32_t sort_mode;    // leaf radix ranking: 0 by digit width, 1 match_any, 2 ballots
     uint32_t* item_id;     // [G+1] flags -> exclusive scan
     uint32_t* item_grp0;   // [G]
     uint32_t* item_nleaf;  // [G+1] -> exclusive scan -> leaf_base
@@ -76,6 +79,15 @@ struct AggWork {
     const uint32_t* buf_grp;      // [n_buf + 1] group prefix
     const DevBinary* bins;
     DevStatus* status;
+    // partition path (every buffer's contexts fit in shared memory)
+    uint32_t part_mode;
+    uint32_t part_ctx_max;        // largest n_ctx of the call
+    uint64_t part_len;            // samples per part
+    uint64_t n_parts;
+    uint64_t n_cnt;               // part counters: sum over buffers of n_ctx * parts
+    const uint64_t* buf_part;     // [n_buf + 1] part prefix
+    uint32_t* part_cnt;           // [n_cnt + 1] counts -> exclusive scan -> first record positions
+    uint32_t emit_totals;         // k_emit sums the per-stall and UNKNOWN totals
 };
 
 constexpr int TILE = 4096;            // samples per tile of the sample-reading kernels
@@ -87,6 +99,12 @@ constexpr int LEAF_THREADS_LARGE = 512;
 constexpr uint32_t BIG_FINE_MAX_LOG = 14;   // at most 2^14 fine bins per big group (64 KB counters)
 constexpr int BIG_THREADS = 512;
 constexpr int BIG_EPT = ((1 << BIG_FINE_MAX_LOG) + 1 + BIG_THREADS - 1) / BIG_THREADS;
+constexpr int PART_THREADS = 512;
+constexpr int PART_U = 4;                    // samples in flight per thread in k_part_scatter
+constexpr uint32_t PART_CTX_MAX = 4096;      // contexts per buffer on the partition path; with more, the
+                                             // (context, part) regions written at once overflow L2 and the
+                                             // per-context cursor path is faster
+constexpr uint64_t PART_CNT_MAX = 1ull << 26; // part counters per call on the partition path
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_EPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_EPT;
@@ -124,7 +142,7 @@ void launch_zero_totals(const AggWork& w, cudaStream_t s, uint64_t* launches);
 
 // shared stages for other producers
 void clear_work(const AggWork& w, cudaStream_t s);
-void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
+void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, bool seg_ready);
 void launch_big_partition(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
 void launch_finalize(const AggWork& w, cudaStream_t s, uint64_t* launches);
 

@@ -21,6 +21,7 @@ HPA_PENDING = 9
 HPA_UNKNOWN_NODE = 0xFFFFFFFF
 HPA_NO_PARENT = 0xFFFFFFFF
 HPA_MAX_STALL = 32
+HPA_TUNE_CANDIDATES = 8
 HPA_EDGE_FIXUP, HPA_EDGE_FIXUP2, HPA_EDGE_INTRA_SCC = 1, 2, 4
 LEAF_CAPS = (4096, 10240)   # leaf capacities of the aggregation (small, large)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_TABLE", 3: "INVALID_SAMPLE", 4: "CAPACITY",
@@ -31,7 +32,8 @@ vp, u8p, u32p, u64p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_uint32), C
 
 class hpa_options(C.Structure):
     _fields_ = [("issued_mask", C.c_uint32), ("leaf_capacity", C.c_uint32), ("timeout_iters", C.c_uint32),
-                ("reserved", C.c_uint32 * 5)]
+                ("cursor_pad", C.c_uint32), ("leaf_ranking", C.c_uint32), ("grouping", C.c_uint32),
+                ("reserved", C.c_uint32 * 2)]
 
 
 class hpa_structure(C.Structure):
@@ -118,6 +120,8 @@ def lib(build_if_needed: bool = True):
         L.hpa_attribute_samples.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_attribute_samples_host.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_attribute_batch.argtypes = [H, C.c_uint32, u32p, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
+        L.hpa_tune.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile), C.c_uint32,
+                               C.POINTER(hpa_options), vp]
         L.hpa_apportion_callgraph.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_gpucct)]
         L.hpa_propagate_inclusive.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile),
                                               C.POINTER(hpa_cct), vp]
@@ -196,7 +200,8 @@ class Hpa:
     """One library handle bound to a CUDA device and stream."""
 
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, issued_mask: int = 1,
-                 leaf_capacity: int = 0, cursor_shift: int | None = None):
+                 leaf_capacity: int = 0, cursor_shift: int | None = None,
+                 sort_mode: int | None = None, partition: bool = True):
         if not torch.cuda.is_available():
             raise RuntimeError("hpa needs a CUDA device; there is no CPU implementation")
         self.L = lib()
@@ -205,7 +210,11 @@ class Hpa:
         self.h = C.c_void_p()
         opt = hpa_options(issued_mask, leaf_capacity, 0)
         if cursor_shift is not None:
-            opt.reserved[0] = cursor_shift + 1
+            opt.cursor_pad = cursor_shift + 1
+        if sort_mode is not None:
+            opt.leaf_ranking = sort_mode
+        if not partition:
+            opt.grouping = 1
         st = self.L.hpa_create(C.byref(self.h), device, C.c_void_p(self.stream.cuda_stream), C.byref(opt))
         if st:
             raise HpaError(st, "hpa_create failed")
@@ -406,6 +415,20 @@ class Hpa:
     def max_depth(self, bid: int) -> int:
         return self._depth.get(bid, 16)
 
+    def tune(self, bid: int, s, out: Profile | None = None, reps: int = 2):
+        """hpa_tune: time every candidate configuration on this buffer and keep
+        the fastest for the calls that follow.  Returns (chosen options as a
+        dict, per-candidate ms)."""
+        if out is None:
+            out = new_profile(s.n, s.n_stall, self.device)
+        ci = self.samples_c(s.pc, s.ctx, s.stall, s.count, s.n_ctx, s.n_stall)
+        co = out.c()
+        best = hpa_options()
+        ms = np.zeros(HPA_TUNE_CANDIDATES, np.float32)
+        self.check(self.L.hpa_tune(self.h, bid, C.byref(ci), C.byref(co), reps, C.byref(best), _ptr(ms)))
+        chosen = {"leaf_capacity": best.leaf_capacity, "grouping": best.grouping, "leaf_ranking": best.leaf_ranking}
+        return chosen, ms.tolist()
+
     def attribute_batch(self, bids, samples, outs=None):
         n = len(samples)
         if outs is None:
@@ -429,15 +452,23 @@ class Server:
         h.check(h.L.hpa_server_create(h.h, C.byref(opt), C.byref(self.s)))
         self._live = {}
 
-    def submit(self, bid: int, pc, ctx, stall, count, n_ctx: int, n_stall: int, capacity: int | None = None):
+    def submit(self, bid: int, pc, ctx, stall, count, n_ctx: int, n_stall: int, capacity: int | None = None,
+               out: dict | None = None):
         """Host arrays (pinned CPU tensors for full speed).  Returns a ticket; the
-        result lands in self.result(ticket) once poll() reports completion."""
+        result lands in self.result(ticket) once poll() reports completion.
+        out: optional preallocated host arrays ctx, node, stall, val (capacity
+        entries each), n (1), total and unknown (HPA_MAX_STALL each)."""
         n = int(pc.shape[0])
-        cap = max(1, n if capacity is None else capacity)
-        out = dict(ctx=torch.empty(cap, dtype=torch.int32).pin_memory(), node=torch.empty(cap, dtype=torch.int32).pin_memory(),
-                   stall=torch.empty(cap, dtype=torch.uint8).pin_memory(), val=torch.empty(cap, dtype=torch.int64).pin_memory(),
-                   n=torch.zeros(1, dtype=torch.int64), total=torch.zeros(HPA_MAX_STALL, dtype=torch.int64).pin_memory(),
-                   unknown=torch.zeros(HPA_MAX_STALL, dtype=torch.int64).pin_memory())
+        if out is None:
+            cap = max(1, n if capacity is None else capacity)
+            out = dict(ctx=torch.empty(cap, dtype=torch.int32).pin_memory(),
+                       node=torch.empty(cap, dtype=torch.int32).pin_memory(),
+                       stall=torch.empty(cap, dtype=torch.uint8).pin_memory(),
+                       val=torch.empty(cap, dtype=torch.int64).pin_memory(),
+                       n=torch.zeros(1, dtype=torch.int64), total=torch.zeros(HPA_MAX_STALL, dtype=torch.int64).pin_memory(),
+                       unknown=torch.zeros(HPA_MAX_STALL, dtype=torch.int64).pin_memory())
+        else:
+            cap = int(out["ctx"].shape[0])
         ci = Hpa.samples_c(pc, ctx, stall, count, n_ctx, n_stall)
         co = hpa_profile(cap, _ptr(out["ctx"]), _ptr(out["node"]), _ptr(out["stall"]), _ptr(out["val"]),
                          _ptr(out["n"]), _ptr(out["total"]), _ptr(out["unknown"]), 0, 0, 0, 0)

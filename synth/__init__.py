@@ -324,6 +324,44 @@ def make_cct(seed: int, n_nodes: int, max_depth: int, max_fanout: int) -> np.nda
     return parent
 
 
+def make_cct_levels(seed: int, n_nodes: int, max_depth: int, max_fanout: int) -> np.ndarray:
+    """Large host calling-context tree built level by level (vectorised):
+    every node of a level draws 0..max_fanout children so that about n_nodes
+    nodes fit in max_depth levels; node ids follow the levels, so
+    parent[v] < v, parent[0] = NO_PARENT, depth <= max_depth."""
+    m = max(1.05, min(float(max_fanout), n_nodes ** (1.0 / max(2, (3 * max_depth) // 4))))
+    parent = [np.array([NO_PARENT], dtype=np.uint32)]
+    level = np.array([0], dtype=np.int64)
+    total = 1
+    d = 0
+    while total < n_nodes and d < max_depth:
+        u = np_unif(seed, 211 + d, np.arange(level.shape[0]))
+        kids = np.minimum(np.floor(-np.log1p(-u) * (m + 0.5)).astype(np.int64), max_fanout)   # ~ geometric
+        if kids.sum() == 0:
+            kids[0] = 1
+        kids = kids[: np.searchsorted(np.cumsum(kids), n_nodes - total, side="left") + 1]
+        par = np.repeat(level[: kids.shape[0]], kids)[: n_nodes - total]
+        nxt = np.arange(total, total + par.shape[0], dtype=np.int64)
+        parent.append(par.astype(np.uint32))
+        total += par.shape[0]
+        level = nxt
+        d += 1
+    out = np.concatenate(parent)
+    if out.shape[0] < n_nodes:
+        # depth limit reached first: the remaining nodes go to nodes above the
+        # last level that still have room for children, in id order
+        depth = np.concatenate([np.full(p.shape[0], k, np.int64) for k, p in enumerate(parent)])
+        while out.shape[0] < n_nodes:
+            fan = np.bincount(out[1:].astype(np.int64), minlength=out.shape[0])
+            room = np.where(depth < max_depth, max_fanout - fan, 0)
+            slots = np.repeat(np.arange(out.shape[0]), room)[: n_nodes - out.shape[0]]
+            if slots.shape[0] == 0:
+                raise ValueError("n_nodes does not fit in max_depth levels of max_fanout children")
+            out = np.concatenate([out, slots.astype(np.uint32)])
+            depth = np.concatenate([depth, depth[slots] + 1])
+    return out
+
+
 # ---------------------------------------------------------------- samples
 @dataclasses.dataclass
 class Samples:
@@ -530,4 +568,34 @@ class BatchWorkload:
                             self.counts, device)
 
 
+@dataclasses.dataclass
+class ManyCtxWorkload:
+    """Batched buffers over a large merged calling-context tree: per buffer,
+    n_tuples distinct (ctx, range, stall) tuples are drawn first and the
+    samples are uniform over the tuples (no counts); one binary."""
+    name: str
+    seed: int
+    n_buffers: int
+    n_samples: int
+    n_tuples: int
+    cct_nodes: int
+    cct_depth: int
+    base: "Workload"
+    n_stall: int = 16
+
+    def binary(self) -> Binary:
+        return self.base.binary()
+
+    def cct(self) -> np.ndarray:
+        return make_cct_levels(self.seed, self.cct_nodes, self.cct_depth, 8)
+
+    def buffer(self, b: int, binary: Binary, n: int | None = None, device="cpu") -> Samples:
+        return make_tuple_samples(self.seed * 1_000 + b, binary, self.n_samples if n is None else n,
+                                  self.cct_nodes, self.n_tuples, self.n_stall, device)
+
+
 BATCHED = BatchWorkload("batched-256x", SEED_BASE + 3, 256, 1e4, 5e7, 8, 2000, 40_000, 500, 1.0, True)
+# batched, many contexts: 64 buffers x 3x10^7 samples, 10^6 (ctx, range, stall)
+# tuples per buffer over a merged CCT of 2x10^6 nodes (depth <= 64); the large
+# workload's binary
+MANY_CTX = ManyCtxWorkload("batched-many-ctx-64x", SEED_BASE + 4, 64, 30_000_000, 1_000_000, 2_000_000, 64, LARGE)

@@ -203,3 +203,61 @@ def test_batch_graph_replay_with_new_buffers(H, plain, large_bin):
         H.sync()
         for o, S, B in zip(outs, ss, Bs):
             assert_same_keys(o, oracle.attribute_samples(B, S))
+
+
+@pytest.mark.parametrize("partition", [True, False])
+@pytest.mark.parametrize("counts", [False, True])
+def test_grouping_paths_agree(plain, large_bin, partition, counts):
+    """Both ways of grouping records by context (per-part counters with
+    shared-memory cursors, or per-context cursor atomics) give the oracle's
+    keys and totals, on the small and the large structure."""
+    from paper_2109_06931_gb300 import hpa
+    h = hpa.Hpa(0, partition=partition)
+    for B, seed, n, n_ctx, z in ((plain[0], 21, 700_001, 300, 1.1), (large_bin[0], 22, 1_200_000, 2000, 0.9)):
+        bid = h.load_structure(B)
+        S = synth.make_samples(seed, B, n, n_ctx, z, counts=counts, device="cuda")
+        out = h.attribute_samples(bid, S)
+        h.sync()
+        assert_same_keys(out, oracle.attribute_samples(B, S))
+    h.close()
+
+
+def test_many_contexts(H, plain):
+    """More contexts than the partition path keeps in shared memory: the
+    per-context cursor path runs and agrees with the oracle."""
+    B, bid = plain
+    S = synth.make_samples(31, B, 900_000, 40_000, 1.1, counts=True, device="cuda")
+    out = run(H, bid, S)
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_leaf_ranking_modes_agree(plain, mode):
+    from paper_2109_06931_gb300 import hpa
+    B, _ = plain
+    h = hpa.Hpa(0, sort_mode=mode)
+    bid = h.load_structure(B)
+    S = synth.make_samples(41, B, 600_000, 50, 1.1, counts=True, device="cuda")
+    out = h.attribute_samples(bid, S)
+    h.sync()
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+    h.close()
+
+
+def test_tuner_keeps_results_and_picks_a_candidate(plain):
+    """hpa_tune times every candidate configuration; each computes the same
+    keys, and the handle keeps the fastest for later calls."""
+    from paper_2109_06931_gb300 import hpa
+    B, _ = plain
+    h = hpa.Hpa(0)
+    bid = h.load_structure(B)
+    S = synth.make_samples(51, B, 400_000, 60, 1.1, counts=True, device="cuda")
+    chosen, ms = h.tune(bid, S)
+    assert len(ms) == hpa.HPA_TUNE_CANDIDATES and all(t > 0 for t in ms)
+    assert chosen["leaf_capacity"] in (4096, 10240) and chosen["grouping"] in (0, 1)
+    assert chosen["leaf_ranking"] in (1, 2)
+    ref = oracle.attribute_samples(B, S)
+    out = h.attribute_samples(bid, S)
+    h.sync()
+    assert_same_keys(out, ref)
+    h.close()
