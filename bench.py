@@ -355,7 +355,8 @@ def run_batched(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    h = H.Hpa(local, stream=stream, sort_mode=args.sort_mode, partition=not args.no_part)
+    h = H.Hpa(local, stream=stream, sort_mode=args.sort_mode, partition=not args.no_part,
+              small_leaves=args.small_leaves, leaf_hash=args.leaf_hash)
     extra = {}
     if args.workload == "many-ctx":
         # 64 buffers of tuple samples over a 2x10^6-node merged CCT, one binary
@@ -415,6 +416,15 @@ def run_batched(args, world, rank, local):
     torch.cuda.synchronize()
     h.sync()
     ms_plain = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    rows = None
+    if args.workload == "many-ctx" and not args.no_rows:
+        # inclusive propagation of one buffer's keys over the 2x10^6-node CCT
+        par = torch.from_numpy(w.cct().view(np.int32)).to(dev)
+        torch.cuda.synchronize()
+        k0 = outs[0].count()
+        t = timed(stream, lambda: (h.propagate_inclusive(bids[0], outs[0], tree=False, cct_parent=par), h.sync()))
+        rows = {"inclusive_cct": {"ms": t, "cct_nodes": int(par.shape[0]), "keys": k0,
+                                  "bytes_per_launch": 2 * int(par.shape[0]) * 8 * outs[0].n_stall}}
     # per-phase kernel times of the batched call (timing replaces graph replay)
     h.set_phase_timing(True)
     for _ in range(args.steps):
@@ -438,7 +448,7 @@ def run_batched(args, world, rank, local):
                       "form": "one hpa_attribute_samples per buffer"},
             "path_roofline": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                               "peak_kind": peak_kind, "algorithmic_bytes_per_step": path_bytes},
-            "phases_ms": ph, "clocks": clk.summary(), "gpu_launches": int(launches)}), flush=True)
+            "phases_ms": ph, "clocks": clk.summary(), "gpu_launches": int(launches), "rows": rows}), flush=True)
     h.close()
 
 
@@ -455,6 +465,8 @@ def main():
     ap.add_argument("--sort-mode", type=int, default=None, help="leaf radix ranking: 0 by digit width, 1 match_any, 2 ballots")
     ap.add_argument("--no-part", action="store_true", help="per-context cursor scatter instead of the partition path")
     ap.add_argument("--no-tune", action="store_true", help="skip hpa_tune (use the per-call default configuration)")
+    ap.add_argument("--small-leaves", type=int, default=0, help="0 automatic, 1 never, 2 always")
+    ap.add_argument("--leaf-hash", type=int, default=0, help="0 sort, 1 hash (with --no-tune)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the apportion / inclusive / derive rows")
@@ -490,7 +502,7 @@ def main():
     N = S.n
     stream = torch.cuda.Stream(dev)
     h = H.Hpa(local, stream=stream, cursor_shift=args.cursor_shift, sort_mode=args.sort_mode,
-              partition=not args.no_part)
+              partition=not args.no_part, small_leaves=args.small_leaves, leaf_hash=args.leaf_hash)
     bid = h.load_structure(B)
     out = H.new_profile(N, S.n_stall, dev)
     h.reserve(N, S.n_ctx)

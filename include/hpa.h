@@ -73,7 +73,13 @@ typedef struct {
     uint32_t grouping;      /* grouping of records by context: 0 = automatic (per-part
                                counters when every buffer has <= 4096 contexts, else
                                per-context cursors), 1 = per-context cursors always         */
-    uint32_t reserved[2];   /* must be zero                                                 */
+    uint32_t small_leaves;  /* leaves of <= 1024 records in a separate kernel of 128-thread
+                               CTAs: 0 = automatic (when a call averages fewer than 64
+                               samples per context), 1 = never, 2 = always                  */
+    uint32_t leaf_hash;     /* aggregation inside a leaf: 0 = radix sort of the records,
+                               1 = shared-memory hash table first, then a sort of the
+                               distinct keys (falls back to the sort for a leaf with too
+                               many distinct keys); pays off when samples repeat keys     */
 } hpa_options;
 
 /* Program structure of one GPU binary (Section 5).  HOST arrays, copied into
@@ -291,8 +297,9 @@ hpa_status hpa_attribute_batch(hpa_handle* h, uint32_t n, const uint32_t* binary
 
 /* Autotuner of the aggregation (no counterpart in the paper: a property of
  * the library).  Runs hpa_attribute_samples on `in` under each candidate
- * configuration -- leaf_capacity 4096 / 10240, grouping 0 / 1, leaf_ranking
- * 1 / 2: HPA_TUNE_CANDIDATES in all, in that nesting order -- timing each
+ * configuration -- leaf_capacity 4096 / 10240, grouping 0 / 1, leaf_hash
+ * 0 / 1 (sort or hash aggregation), leaf_ranking 1 / 2: HPA_TUNE_CANDIDATES
+ * in all, in that nesting order -- timing each
  * with CUDA events on the handle's stream (one untimed run, then `reps`
  * timed runs, 0 = 2), and keeps the fastest in the handle's options for the
  * calls that follow.  in/out as for hpa_attribute_samples; out holds the
@@ -300,7 +307,7 @@ hpa_status hpa_attribute_batch(hpa_handle* h, uint32_t n, const uint32_t* binary
  * ms (may be null, HPA_TUNE_CANDIDATES floats) the mean time of each
  * candidate.  Synchronous: returns after the last run has finished.  Every
  * candidate computes the same keys; only their speed differs.               */
-#define HPA_TUNE_CANDIDATES 8
+#define HPA_TUNE_CANDIDATES 16
 hpa_status hpa_tune(hpa_handle* h, uint32_t binary_id, const hpa_samples* in, hpa_profile* out, uint32_t reps,
                     hpa_options* best, float* ms);
 

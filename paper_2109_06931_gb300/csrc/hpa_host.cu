@@ -99,7 +99,7 @@ Binary* hpa_handle::binary(uint32_t id) {
 extern "C" hpa_status hpa_create(hpa_handle** out, int device, void* cuda_stream, const hpa_options* opt) {
     if (!out) return HPA_E_INVALID_ARG;
     *out = nullptr;
-    if (opt && (opt->reserved[0] || opt->reserved[1] || opt->leaf_ranking > 2 || opt->grouping > 1 ||
+    if (opt && (opt->leaf_hash > 1 || opt->small_leaves > 2 || opt->leaf_ranking > 2 || opt->grouping > 1 ||
                 opt->cursor_pad > 7 ||
                 (opt->leaf_capacity && opt->leaf_capacity != LEAF_CAP_SMALL && opt->leaf_capacity != LEAF_CAP_LARGE)))
         return HPA_E_INVALID_ARG;
@@ -156,7 +156,7 @@ extern "C" const char* hpa_last_error(hpa_handle* h) { return h ? h->err.c_str()
 
 extern "C" uint64_t hpa_kernel_launches(hpa_handle* h) { return h ? h->launches : 0; }
 
-cudaEvent_t* hpa_handle::phase_events() {
+cudaEvent_t* hpa_handle::phase_events(bool new_call) {
     std::vector<cudaEvent_t> v;
     if (!ev_pool.empty()) {
         v = std::move(ev_pool.back());
@@ -166,20 +166,23 @@ cudaEvent_t* hpa_handle::phase_events() {
         for (auto& e : v) cudaEventCreate(&e);
     }
     ev_pending.push_back(std::move(v));
+    ev_counts.push_back(new_call);
     return ev_pending.back().data();
 }
 
 void hpa_handle::collect_phase_times() {
-    for (auto& v : ev_pending) {
+    for (size_t k = 0; k < ev_pending.size(); ++k) {
+        auto& v = ev_pending[k];
         for (int i = 0; i < N_PHASES; ++i) {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, v[i], v[i + 1]) == cudaSuccess) phase_ms[i] += ms;
             else cudaGetLastError();
         }
-        ++phase_calls;
+        if (ev_counts[k]) ++phase_calls;
         ev_pool.push_back(std::move(v));
     }
     ev_pending.clear();
+    ev_counts.clear();
 }
 
 extern "C" hpa_status hpa_set_phase_timing(hpa_handle* h, int enable) {
@@ -463,11 +466,16 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
     return HPA_OK;
 }
 
+// Calls whose groups (contexts summed over the buffers) exceed SUB_GROUPS run
+// as consecutive sub-batches of whole buffers, one pipeline after another on
+// the same scratch, so that the per-group arrays of a sub-batch stay in L2.
+constexpr uint64_t SUB_GROUPS = 1ull << 20;
+
 hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs,
                                  bool use_graph) {
     if (n == 0) return HPA_OK;
-    uint64_t N = 0, G = 0, tiles = 0;
-    uint32_t max_nodes = 0, max_stall = 1;
+    uint64_t N = 0, G = 0;
+    uint32_t max_stall = 1;
     bool has_cnt = false;
     for (uint32_t b = 0; b < n; ++b) {
         const hpa_samples& s = in[b];
@@ -482,96 +490,143 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
             return fail(HPA_E_INVALID_ARG, "buffer %u: output arrays missing", b);
         N += s.n;
         G += s.n_ctx;
-        tiles += (s.n + TILE - 1) / TILE;
-        max_nodes = std::max(max_nodes, B->n_nodes);
         max_stall = std::max(max_stall, s.n_stall);
         has_cnt |= s.count != nullptr;
     }
     if (N >= 0xFFFFFFF0ull) return fail(HPA_E_INVALID_ARG, "too many samples in one call (%llu)", (unsigned long long)N);
     if (G >= 0xFFFFFFF0ull) return fail(HPA_E_INVALID_ARG, "too many contexts in one call");
     const uint32_t sb = ceil_log2_u64(max_stall);
-    const uint32_t nb = ceil_log2_u64((uint64_t)max_nodes + 1);
-    if (nb + sb > 32) return fail(HPA_E_INVALID_ARG, "(n_nodes + 1) * 2^stall_bits exceeds 2^32");
-    const uint32_t sbits = nb + sb;
-    uint32_t cap = opt.leaf_capacity;
-    if (cap == 0) cap = (G && N / G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL;
-    if (cap != LEAF_CAP_SMALL && cap != LEAF_CAP_LARGE)
+    if (opt.leaf_capacity && opt.leaf_capacity != LEAF_CAP_SMALL && opt.leaf_capacity != LEAF_CAP_LARGE)
         return fail(HPA_E_INVALID_ARG, "leaf_capacity must be 0, %u or %u", LEAF_CAP_SMALL, LEAF_CAP_LARGE);
-    // partition path: every buffer's contexts fit in shared memory and the
-    // (context, part) counters stay within PART_CNT_MAX; parts of part_len
-    // samples, about 8 per SM over the whole call
-    uint32_t ctx_max = 0;
-    for (uint32_t b = 0; b < n; ++b) ctx_max = std::max(ctx_max, in[b].n_ctx);
-    const uint64_t target_parts = (uint64_t)sms * 8;
-    const uint64_t part_len = std::max<uint64_t>(TILE, (N + target_parts - 1) / target_parts + TILE - 1) / TILE * TILE;
-    uint64_t n_parts = 0, n_cnt = 0;
+
+    // sub-batches and their configurations
+    struct Sub {
+        uint32_t b0 = 0, b1 = 0, sbits = 0, cap = 0, ctx_max = 0;
+        uint64_t N = 0, G = 0, tiles = 0, part_len = 0, n_parts = 0, n_cnt = 0;
+        uint32_t max_nodes = 0;
+        bool part = false;
+    };
+    std::vector<Sub> subs;
     for (uint32_t b = 0; b < n; ++b) {
-        const uint64_t pb = (in[b].n + part_len - 1) / part_len;
-        n_parts += pb;
-        n_cnt += pb * in[b].n_ctx;
+        if (subs.empty() || (subs.back().G + in[b].n_ctx > SUB_GROUPS && subs.back().b1 > subs.back().b0)) {
+            subs.emplace_back();
+            subs.back().b0 = subs.back().b1 = b;
+        }
+        Sub& u = subs.back();
+        u.b1 = b + 1;
+        u.N += in[b].n;
+        u.G += in[b].n_ctx;
+        u.tiles += (in[b].n + TILE - 1) / TILE;
+        u.max_nodes = std::max(u.max_nodes, binary(binary_ids[b])->n_nodes);
+        u.ctx_max = std::max(u.ctx_max, in[b].n_ctx);
     }
-    const bool part = opt.grouping != 1 && ctx_max <= PART_CTX_MAX && n_cnt <= PART_CNT_MAX;
-    AggWork w{};
-    hpa_status st = carve_work(w, N, G, n, cap, sb, sbits, has_cnt, false, part ? 0 : tiles * TILE, part ? n_cnt + 1 : 0);
+    uint64_t N_max = 0, G_max = 0, staged_max = 0, cnt_words_max = 0;
+    uint32_t n_max = 0, sbits_max = 0, cap_min = LEAF_CAP_LARGE;
+    const uint64_t target_parts = (uint64_t)sms * 8;
+    for (Sub& u : subs) {
+        const uint32_t nb = ceil_log2_u64((uint64_t)u.max_nodes + 1);
+        if (nb + sb > 32) return fail(HPA_E_INVALID_ARG, "(n_nodes + 1) * 2^stall_bits exceeds 2^32");
+        u.sbits = nb + sb;
+        u.cap = opt.leaf_capacity ? opt.leaf_capacity
+                                  : ((u.G && u.N / u.G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL);
+        // partition path: every buffer's contexts fit in shared memory and the
+        // (context, part) counters stay within PART_CNT_MAX; parts of part_len
+        // samples, about 8 per SM over the sub-batch
+        u.part_len = std::max<uint64_t>(TILE, (u.N + target_parts - 1) / target_parts + TILE - 1) / TILE * TILE;
+        for (uint32_t b = u.b0; b < u.b1; ++b) {
+            const uint64_t pb = (in[b].n + u.part_len - 1) / u.part_len;
+            u.n_parts += pb;
+            u.n_cnt += pb * in[b].n_ctx;
+        }
+        u.part = opt.grouping != 1 && u.ctx_max <= PART_CTX_MAX && u.n_cnt <= PART_CNT_MAX;
+        N_max = std::max(N_max, u.N);
+        G_max = std::max(G_max, u.G);
+        n_max = std::max(n_max, u.b1 - u.b0);
+        sbits_max = std::max(sbits_max, u.sbits);
+        cap_min = std::min(cap_min, u.cap);
+        staged_max = std::max(staged_max, u.part ? 0 : u.tiles * TILE);
+        cnt_words_max = std::max(cnt_words_max, u.part ? u.n_cnt + 1 : 0);
+    }
+    AggWork w0{};
+    hpa_status st = carve_work(w0, N_max, G_max, n_max, cap_min, sb, sbits_max, has_cnt, false, staged_max,
+                               cnt_words_max);
     if (st) return st;
-    w.n_tiles = tiles;
-    w.emit_totals = 1;
-    if (part) {
-        w.part_mode = 1;
-        w.part_ctx_max = ctx_max;
-        w.part_len = part_len;
-        w.n_parts = n_parts;
-        w.n_cnt = n_cnt;
-    }
-    // descriptors
-    const size_t desc_bytes = n * sizeof(BufDev) + (n + 1) * 16 + (n + 1) * 4 + 512;
+
+    // descriptors: every buffer's BufDev, then per sub-batch its prefix arrays
+    const size_t desc_bytes = n * sizeof(BufDev) + (n + subs.size()) * 24 + 64 * subs.size() + 512;
     if ((st = ensure_staging(desc_bytes))) return st;
     Carve hs{(char*)staging};
     BufDev* hb = hs.take<BufDev>(n);
-    uint64_t* htile = hs.take<uint64_t>(n + 1);
-    uint32_t* hgrp = hs.take<uint32_t>(n + 1);
-    uint64_t* hpart = hs.take<uint64_t>(n + 1);
-    const size_t used = hs.off;
-    uint64_t tb = 0, pbase = 0, cbase = 0;
-    uint32_t gb = 0;
-    for (uint32_t b = 0; b < n; ++b) {
-        const hpa_samples& s = in[b];
-        hpa_profile& o = outs[b];
-        BufDev d{};
-        d.pc = s.pc; d.ctx = s.ctx; d.stall = s.stall; d.count = s.count; d.n = s.n;
-        d.tile_base = tb; d.n_ctx = s.n_ctx; d.n_stall = s.n_stall; d.grp_base = gb; d.bin = binary_ids[b];
-        d.part_base = pbase; d.cnt_base = cbase;
-        hpart[b] = pbase;
-        const uint64_t pb = (s.n + part_len - 1) / part_len;
-        pbase += pb;
-        cbase += pb * s.n_ctx;
-        d.total = o.total; d.unknown = o.unknown;
-        d.key_ctx = o.key_ctx; d.key_node = o.key_node; d.key_stall = o.key_stall; d.val = o.val;
-        d.n_keys = o.n_keys; d.capacity = o.capacity;
-        hb[b] = d;
-        htile[b] = tb;
-        hgrp[b] = gb;
-        tb += (s.n + TILE - 1) / TILE;
-        gb += s.n_ctx;
-        o.n_ctx = s.n_ctx;
-        o.n_stall = s.n_stall;
-        o.n_nodes = binary(binary_ids[b])->n_nodes;
-    }
-    htile[n] = tb;
-    hgrp[n] = gb;
-    hpart[n] = pbase;
     char* ds = (char*)d_staging;
-    w.buf_part = (const uint64_t*)(ds + ((char*)hpart - (char*)staging));
-    w.bufs = (const BufDev*)(ds + ((char*)hb - (char*)staging));
-    w.buf_tile = (const uint64_t*)(ds + ((char*)htile - (char*)staging));
-    w.buf_grp = (const uint32_t*)(ds + ((char*)hgrp - (char*)staging));
-    if (use_graph && !timing) return launch_graph(w, used, n, in);
+    auto dev_of = [&](const void* p) { return ds + ((const char*)p - (const char*)staging); };
+    std::vector<AggWork> ws;
+    for (const Sub& u : subs) {
+        const uint32_t nk = u.b1 - u.b0;
+        uint64_t* htile = hs.take<uint64_t>(nk + 1);
+        uint32_t* hgrp = hs.take<uint32_t>(nk + 1);
+        uint64_t* hpart = hs.take<uint64_t>(nk + 1);
+        uint64_t tb = 0, pbase = 0, cbase = 0;
+        uint32_t gb = 0;
+        for (uint32_t b = u.b0; b < u.b1; ++b) {
+            const uint32_t k = b - u.b0;
+            const hpa_samples& s = in[b];
+            hpa_profile& o = outs[b];
+            BufDev d{};
+            d.pc = s.pc; d.ctx = s.ctx; d.stall = s.stall; d.count = s.count; d.n = s.n;
+            d.tile_base = tb; d.n_ctx = s.n_ctx; d.n_stall = s.n_stall; d.grp_base = gb; d.bin = binary_ids[b];
+            d.part_base = pbase; d.cnt_base = cbase;
+            d.total = o.total; d.unknown = o.unknown;
+            d.key_ctx = o.key_ctx; d.key_node = o.key_node; d.key_stall = o.key_stall; d.val = o.val;
+            d.n_keys = o.n_keys; d.capacity = o.capacity;
+            hb[b] = d;
+            htile[k] = tb;
+            hgrp[k] = gb;
+            hpart[k] = pbase;
+            const uint64_t pb = (s.n + u.part_len - 1) / u.part_len;
+            pbase += pb;
+            cbase += pb * s.n_ctx;
+            tb += (s.n + TILE - 1) / TILE;
+            gb += s.n_ctx;
+            o.n_ctx = s.n_ctx;
+            o.n_stall = s.n_stall;
+            o.n_nodes = binary(binary_ids[b])->n_nodes;
+        }
+        htile[nk] = tb;
+        hgrp[nk] = gb;
+        hpart[nk] = pbase;
+        AggWork w = w0;
+        w.G = (uint32_t)u.G;
+        w.n_buf = nk;
+        w.cap = u.cap;
+        w.q = u.cap / 2;
+        w.sbits = u.sbits;
+        w.span_log = std::min<uint32_t>(10, 32 - u.sbits);
+        w.n_tiles = u.tiles;
+        w.emit_totals = 1;
+        w.small_leaves = opt.small_leaves == 2 || (opt.small_leaves == 0 && u.N < 64 * u.G);
+        w.leaf_hash = opt.leaf_hash;
+        if (u.part) {
+            w.part_mode = 1;
+            w.part_ctx_max = u.ctx_max;
+            w.part_len = u.part_len;
+            w.n_parts = u.n_parts;
+            w.n_cnt = u.n_cnt;
+        }
+        w.bufs = (const BufDev*)dev_of(hb + u.b0);
+        w.buf_tile = (const uint64_t*)dev_of(htile);
+        w.buf_grp = (const uint32_t*)dev_of(hgrp);
+        w.buf_part = (const uint64_t*)dev_of(hpart);
+        ws.push_back(w);
+    }
+    const size_t used = hs.off;
+    if (use_graph && !timing) return launch_graph(ws, used, n, in);
     if ((st = upload_staging(used))) return st;
     for (uint32_t b = 0; b < n; ++b) {
         if (outs[b].total) cudaMemsetAsync(outs[b].total, 0, 8 * in[b].n_stall, stream);
         if (outs[b].unknown) cudaMemsetAsync(outs[b].unknown, 0, 8 * in[b].n_stall, stream);
     }
-    run_aggregate(w, stream, sms, &launches, timing ? phase_events() : nullptr);
+    for (size_t k = 0; k < ws.size(); ++k)
+        run_aggregate(ws[k], stream, sms, &launches, timing ? phase_events(k == 0) : nullptr);
     return cuda(cudaGetLastError(), "aggregation launch");
 }
 
@@ -585,12 +640,17 @@ static uint64_t mix64(uint64_t h, uint64_t v) {
     return h;
 }
 
-hpa_status hpa_handle::launch_graph(const AggWork& w, size_t staged_bytes, uint32_t n, const hpa_samples* in) {
-    uint64_t key = 0;
-    key = mix64(key, w.G); key = mix64(key, w.n_buf); key = mix64(key, w.n_tiles); key = mix64(key, w.cap);
-    key = mix64(key, w.sb); key = mix64(key, w.sbits); key = mix64(key, w.L_max); key = mix64(key, w.has_cnt);
-    key = mix64(key, w.cur_shift); key = mix64(key, staged_bytes); key = mix64(key, (uint64_t)(uintptr_t)w.grp_hist);
-    key = mix64(key, w.part_mode); key = mix64(key, w.part_len); key = mix64(key, w.n_parts); key = mix64(key, w.sort_mode);
+hpa_status hpa_handle::launch_graph(const std::vector<AggWork>& ws, size_t staged_bytes, uint32_t n,
+                                    const hpa_samples* in) {
+    uint64_t key = mix64(0, ws.size());
+    for (const AggWork& w : ws) {
+        key = mix64(key, w.G); key = mix64(key, w.n_buf); key = mix64(key, w.n_tiles); key = mix64(key, w.cap);
+        key = mix64(key, w.sb); key = mix64(key, w.sbits); key = mix64(key, w.L_max); key = mix64(key, w.has_cnt);
+        key = mix64(key, w.cur_shift); key = mix64(key, (uint64_t)(uintptr_t)w.grp_hist);
+        key = mix64(key, w.part_mode); key = mix64(key, w.part_len); key = mix64(key, w.n_parts);
+        key = mix64(key, w.sort_mode); key = mix64(key, w.small_leaves); key = mix64(key, w.leaf_hash);
+    }
+    key = mix64(key, staged_bytes);
     for (uint32_t b = 0; b < n; ++b) key = mix64(mix64(key, in[b].n), in[b].n_ctx);
     CachedGraph* g = nullptr;
     for (auto& c : graphs)
@@ -603,8 +663,8 @@ hpa_status hpa_handle::launch_graph(const AggWork& w, size_t staged_bytes, uint3
         uint64_t k0 = launches;
         if ((st = cuda(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeRelaxed), "begin capture"))) return st;
         cudaMemcpyAsync(d_staging, staging, staged_bytes, cudaMemcpyHostToDevice, capture_stream);
-        launch_zero_totals(w, capture_stream, &launches);
-        run_aggregate(w, capture_stream, sms, &launches, nullptr);
+        for (const AggWork& w : ws) launch_zero_totals(w, capture_stream, &launches);
+        for (const AggWork& w : ws) run_aggregate(w, capture_stream, sms, &launches, nullptr);
         cudaError_t e = cudaStreamEndCapture(capture_stream, &graph);
         if ((st = cuda(e, "end capture"))) return st;
         cudaGraphExec_t exec = nullptr;

@@ -99,9 +99,10 @@ struct hpa_handle {
     // phase timing
     bool timing = false;
     std::vector<std::vector<cudaEvent_t>> ev_pool, ev_pending;
+    std::vector<bool> ev_counts;   // per pending event set: starts a new call
     double phase_ms[hpa::N_PHASES] = {0};
     uint64_t phase_calls = 0;
-    cudaEvent_t* phase_events();
+    cudaEvent_t* phase_events(bool new_call = true);
     void collect_phase_times();
 
     ~hpa_handle();
@@ -115,7 +116,8 @@ struct hpa_handle {
     hpa_status refresh_bin_table();
     hpa_status aggregate(uint32_t n, const uint32_t* binary_ids, const hpa_samples* in, hpa_profile* outs,
                          bool use_graph = false);
-    hpa_status launch_graph(const hpa::AggWork& w, size_t staged_bytes, uint32_t n, const hpa_samples* in);
+    hpa_status launch_graph(const std::vector<hpa::AggWork>& ws, size_t staged_bytes, uint32_t n,
+                            const hpa_samples* in);
     hpa_status carve_work(hpa::AggWork& w, uint64_t N, uint64_t G, uint32_t n_buf, uint32_t cap, uint32_t sb,
                           uint32_t sbits, bool has_cnt, bool val64, uint64_t staged = 0,
                           uint64_t cnt_words = 0);   // part counters incl. the scan total (0: none)

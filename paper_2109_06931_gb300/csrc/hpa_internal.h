@@ -88,6 +88,8 @@ struct AggWork {
     const uint64_t* buf_part;     // [n_buf + 1] part prefix
     uint32_t* part_cnt;           // [n_cnt + 1] counts -> exclusive scan -> first record positions
     uint32_t emit_totals;         // k_emit sums the per-stall and UNKNOWN totals
+    uint32_t small_leaves;        // leaves of <= SMALL_LEAF_CAP records go to the small-leaf kernel
+    uint32_t leaf_hash;           // leaves aggregate in a shared-memory hash table before sorting
 };
 
 constexpr int TILE = 4096;            // samples per tile of the sample-reading kernels
@@ -96,6 +98,8 @@ constexpr uint32_t HIST_SMEM_MAX = 24576;    // contexts counted in shared memor
 constexpr uint32_t LEAF_CAP_SMALL = 4096;   // 256 threads, two CTAs per SM
 constexpr uint32_t LEAF_CAP_LARGE = 10240;  // 512 threads, one CTA per SM
 constexpr int LEAF_THREADS_LARGE = 512;
+constexpr uint32_t SMALL_LEAF_CAP = 1024;    // leaves up to this size run in 128-thread CTAs, 8 per SM
+constexpr int SMALL_LEAF_THREADS = 128;
 constexpr uint32_t BIG_FINE_MAX_LOG = 14;   // at most 2^14 fine bins per big group (64 KB counters)
 constexpr int BIG_THREADS = 512;
 constexpr int BIG_EPT = ((1 << BIG_FINE_MAX_LOG) + 1 + BIG_THREADS - 1) / BIG_THREADS;
@@ -144,6 +148,8 @@ void launch_zero_totals(const AggWork& w, cudaStream_t s, uint64_t* launches);
 void clear_work(const AggWork& w, cudaStream_t s);
 void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, bool seg_ready);
 void launch_big_partition(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
+// every leaf kernel of one aggregation (hpa_leaf.cu)
+void launch_leaves(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
 void launch_finalize(const AggWork& w, cudaStream_t s, uint64_t* launches);
 
 // largest b with pre[b] <= x (pre non-decreasing, pre[0] = 0)

@@ -2,8 +2,10 @@
 // the caller's own buffer.  The configurations differ only in speed: leaf
 // capacity (shared-memory leaves of 4096 records, two CTAs per SM, or 10240
 // records, one CTA per SM), grouping of records by context (per-part counters
-// with shared-memory cursors, or per-context cursor atomics) and the
-// equal-digit search of the leaf radix sort (__match_any_sync or ballots).
+// with shared-memory cursors, or per-context cursor atomics) and aggregation
+// inside a leaf (radix sort of the records, or a shared-memory hash table
+// and a sort of the distinct keys) and the equal-digit search of the leaf
+// radix sort (__match_any_sync or ballots).
 
 #include "hpa_host.h"
 
@@ -27,10 +29,12 @@ extern "C" hpa_status hpa_tune(hpa_handle* h, uint32_t binary_id, const hpa_samp
     int k = 0;
     for (int c = 0; c < 2 && !st; ++c)
         for (uint32_t g = 0; g < 2 && !st; ++g)
-            for (uint32_t r = 1; r <= 2 && !st; ++r, ++k) {
+            for (uint32_t hsh = 0; hsh <= 1 && !st; ++hsh)
+                for (uint32_t r = 1; r <= 2 && !st; ++r, ++k) {
                 hpa_options o = base;
                 o.leaf_capacity = caps[c];
                 o.grouping = g;
+                o.leaf_hash = hsh;
                 o.leaf_ranking = r;
                 h->opt = o;
                 if ((st = h->aggregate(1, &binary_id, in, out))) break;          // untimed

@@ -21,7 +21,7 @@ HPA_PENDING = 9
 HPA_UNKNOWN_NODE = 0xFFFFFFFF
 HPA_NO_PARENT = 0xFFFFFFFF
 HPA_MAX_STALL = 32
-HPA_TUNE_CANDIDATES = 8
+HPA_TUNE_CANDIDATES = 16
 HPA_EDGE_FIXUP, HPA_EDGE_FIXUP2, HPA_EDGE_INTRA_SCC = 1, 2, 4
 LEAF_CAPS = (4096, 10240)   # leaf capacities of the aggregation (small, large)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_TABLE", 3: "INVALID_SAMPLE", 4: "CAPACITY",
@@ -33,7 +33,7 @@ vp, u8p, u32p, u64p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_uint32), C
 class hpa_options(C.Structure):
     _fields_ = [("issued_mask", C.c_uint32), ("leaf_capacity", C.c_uint32), ("timeout_iters", C.c_uint32),
                 ("cursor_pad", C.c_uint32), ("leaf_ranking", C.c_uint32), ("grouping", C.c_uint32),
-                ("reserved", C.c_uint32 * 2)]
+                ("small_leaves", C.c_uint32), ("leaf_hash", C.c_uint32)]
 
 
 class hpa_structure(C.Structure):
@@ -201,7 +201,8 @@ class Hpa:
 
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, issued_mask: int = 1,
                  leaf_capacity: int = 0, cursor_shift: int | None = None,
-                 sort_mode: int | None = None, partition: bool = True):
+                 sort_mode: int | None = None, partition: bool = True, small_leaves: int = 0,
+                 leaf_hash: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("hpa needs a CUDA device; there is no CPU implementation")
         self.L = lib()
@@ -215,6 +216,8 @@ class Hpa:
             opt.leaf_ranking = sort_mode
         if not partition:
             opt.grouping = 1
+        opt.small_leaves = small_leaves
+        opt.leaf_hash = leaf_hash
         st = self.L.hpa_create(C.byref(self.h), device, C.c_void_p(self.stream.cuda_stream), C.byref(opt))
         if st:
             raise HpaError(st, "hpa_create failed")
@@ -426,7 +429,8 @@ class Hpa:
         best = hpa_options()
         ms = np.zeros(HPA_TUNE_CANDIDATES, np.float32)
         self.check(self.L.hpa_tune(self.h, bid, C.byref(ci), C.byref(co), reps, C.byref(best), _ptr(ms)))
-        chosen = {"leaf_capacity": best.leaf_capacity, "grouping": best.grouping, "leaf_ranking": best.leaf_ranking}
+        chosen = {"leaf_capacity": best.leaf_capacity, "grouping": best.grouping, "leaf_hash": best.leaf_hash,
+                  "leaf_ranking": best.leaf_ranking}
         return chosen, ms.tolist()
 
     def attribute_batch(self, bids, samples, outs=None):

@@ -47,17 +47,14 @@ def test_library_loads_and_binding_types():
 
 
 @pytest.mark.parametrize("field,value", [("leaf_capacity", 5000), ("leaf_ranking", 3), ("grouping", 2),
-                                         ("cursor_pad", 8), ("reserved", 1)])
+                                         ("cursor_pad", 8), ("small_leaves", 3), ("leaf_hash", 2)])
 def test_create_rejects_invalid_options(field, value):
     """Option checks come before any device call, so they hold without a GPU."""
     import ctypes
     from paper_2109_06931_gb300 import hpa as H
     L = H.lib()
     opt = H.hpa_options()
-    if field == "reserved":
-        opt.reserved[1] = value
-    else:
-        setattr(opt, field, value)
+    setattr(opt, field, value)
     h = ctypes.c_void_p()
     assert L.hpa_create(ctypes.byref(h), 0, None, ctypes.byref(opt)) == H.HPA_E_INVALID_ARG
     assert not h.value

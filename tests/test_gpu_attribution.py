@@ -255,9 +255,76 @@ def test_tuner_keeps_results_and_picks_a_candidate(plain):
     chosen, ms = h.tune(bid, S)
     assert len(ms) == hpa.HPA_TUNE_CANDIDATES and all(t > 0 for t in ms)
     assert chosen["leaf_capacity"] in (4096, 10240) and chosen["grouping"] in (0, 1)
-    assert chosen["leaf_ranking"] in (1, 2)
+    assert chosen["leaf_hash"] in (0, 1)
     ref = oracle.attribute_samples(B, S)
     out = h.attribute_samples(bid, S)
     h.sync()
     assert_same_keys(out, ref)
+    h.close()
+
+
+def test_batch_split_into_sub_batches(H, plain, large_bin):
+    """A batch whose contexts add up to more than one sub-batch takes (1M
+    groups) runs as consecutive pipelines, in the graph and outside it; each
+    buffer still gets exactly its own keys."""
+    B1, b1 = plain
+    B2, b2 = large_bin
+    n_ctx = [1_500_000, 2_000_000, 3, 2_500_000, 900_000]
+    ss, bins, bs = [], [], []
+    for i, c in enumerate(n_ctx):
+        B, bid = (B1, b1) if i % 2 == 0 else (B2, b2)
+        ss.append(synth.make_tuple_samples(700 + i, B, 150_000 + 10_000 * i, c, 20_000, device="cuda"))
+        bins.append(bid); bs.append(B)
+    refs = [oracle.attribute_samples(B, S) for B, S in zip(bs, ss)]
+    for rep in range(2):                                   # capture, then replay
+        outs = H.attribute_batch(bins, ss)
+        H.sync()
+        for o, r in zip(outs, refs):
+            assert_same_keys(o, r)
+    H.set_phase_timing(True)                               # phase timing runs the pipelines eagerly
+    outs = H.attribute_batch(bins, ss)
+    H.sync()
+    ph, calls = H.phase_times()
+    H.set_phase_timing(False)
+    assert calls == 1
+    for o, r in zip(outs, refs):
+        assert_same_keys(o, r)
+
+
+@pytest.mark.parametrize("small", [1, 2])
+def test_small_leaf_kernel_on_and_off(plain, small):
+    """Leaves of up to 1024 records in the small-CTA kernel (2) or in the leaf
+    capacity's kernel (1): same keys, for few and for many samples per context."""
+    from paper_2109_06931_gb300 import hpa
+    B, _ = plain
+    h = hpa.Hpa(0, small_leaves=small)
+    bid = h.load_structure(B)
+    for S in (synth.make_tuple_samples(61, B, 500_000, 40_000, 30_000, device="cuda"),
+              synth.make_samples(62, B, 400_000, 100, 1.1, counts=True, device="cuda")):
+        out = h.attribute_samples(bid, S)
+        h.sync()
+        assert_same_keys(out, oracle.attribute_samples(B, S))
+    h.close()
+
+
+@pytest.mark.parametrize("small", [1, 2])
+def test_hash_leaves_agree(plain, large_bin, small):
+    """Hash aggregation inside leaves: many repeats (tuple samples), few
+    repeats with counts (the large structure, where most leaves fall back to
+    sorting), zero counts, and split groups."""
+    from paper_2109_06931_gb300 import hpa
+    B1, _ = plain
+    B2, _ = large_bin
+    h = hpa.Hpa(0, leaf_hash=1, small_leaves=small)
+    b1, b2 = h.load_structure(B1), h.load_structure(B2)
+    cases = [(B1, b1, synth.make_tuple_samples(71, B1, 600_000, 30_000, 20_000, device="cuda")),
+             (B2, b2, synth.make_samples(72, B2, 800_000, 300, 0.9, counts=True, device="cuda")),
+             (B1, b1, synth.make_samples(73, B1, 300_000, 2, 1.1, counts=True, device="cuda"))]
+    S = synth.make_samples(74, B1, 200_000, 50, 1.1, counts=True, device="cuda")
+    S.count[::3] = 0                                        # zero counts: keys that only sum to 0 vanish
+    cases.append((B1, b1, S))
+    for B, bid, S in cases:
+        out = h.attribute_samples(bid, S)
+        h.sync()
+        assert_same_keys(out, oracle.attribute_samples(B, S))
     h.close()
