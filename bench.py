@@ -274,7 +274,32 @@ def run_serving(args, world, rank, local):
     wall = time.perf_counter() - t0
     stats = srv.stats()
     srv.close()
+    # the same arrivals (the first --plain-seconds of them), one synchronous
+    # hpa_attribute_samples_host call per request in arrival order: a request
+    # starts when it has arrived and the previous one is done
+    m = int(np.searchsorted(arrive, args.plain_seconds))
+    lat = np.zeros(m)
+    t0 = time.perf_counter()
+    for i in range(m):
+        now = time.perf_counter() - t0
+        if now < arrive[i]:
+            time.sleep(arrive[i] - now)
+        n = int(sizes[i])
+        b = i % n_bin
+        pc, cx, st, ct = pools[b]
+        o = offs[i]
+        row = small[i]
+        out = dict(ctx=ring["ctx"][:n], node=ring["node"][:n], stall=ring["stall"][:n], val=ring["val"][:n],
+                   n=row[0:1], total=row[1:1 + H.HPA_MAX_STALL], unknown=row[1 + H.HPA_MAX_STALL:])
+        h.attribute_samples_host(ids[b], pc[o:o + n], cx[o:o + n], st[o:o + n], ct[o:o + n], n_ctx, n_stall,
+                                 out=out)
+        lat[i] = time.perf_counter() - t0 - arrive[i]
+    plain_wall = time.perf_counter() - t0
     h.close()
+    plain = {"requests": m, "samples_per_s": float(sizes[:m].sum() / plain_wall),
+             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                            "max": float(lat.max() * 1e3)},
+             "form": "one hpa_attribute_samples_host call per request, arrival order"}
     total = int(sizes.sum())
     keys = int(small[:, 0].sum())
     if rank == 0:
@@ -289,6 +314,7 @@ def run_serving(args, world, rank, local):
                            "mean": stats["mean_ms"], "measured": "submit -> keys in host arrays"},
             "submit_lag_ms": {"p50": float(np.percentile(lag, 50) * 1e3), "p99": float(np.percentile(lag, 99) * 1e3)},
             "server": {k: stats[k] for k in ("completed", "rejected", "batches", "busy_s")},
+            "plain": plain,
             "e2e": {"value": total * world / wall, "unit": UNIT,
                     "h2d_bytes_per_step": 17 * total, "d2h_bytes_per_step": 17 * keys + 8 * (1 + 2 * 16) * n_req}}),
               flush=True)
@@ -473,6 +499,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
+    ap.add_argument("--plain-seconds", type=float, default=5.0,
+                    help="serving: seconds of the same arrivals replayed as one call per request")
     ap.add_argument("--serve-mem-gb", type=int, default=60, help="serving: admission pool (GiB)")
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     args = ap.parse_args()
