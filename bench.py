@@ -43,12 +43,11 @@ def workload(name: str):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per sample of
 # the kernel that dominates each phase, from one ncu capture of the 2e7-sample
-# case (profiles/k_leaf_k_scatter_k_attribute_plain-large-20M.md), keyed by a
+# case (profiles/k_leaf_plain-large-20M.md), keyed by a
 # hash of the kernel sources it was taken on: a changed kernel reports null.
-KERNEL_SOURCES = ("hpa_agg.cu", "hpa_dev.cuh", "hpa_internal.h")
+KERNEL_SOURCES = ("hpa_agg.cu", "hpa_leaf.cu", "hpa_dev.cuh", "hpa_internal.h")
 TRAFFIC = {
-    "leaf sort/reduce": {"kernel": "k_leaf", "bytes_per_sample": 15.468, "sources": "e2938a2628997b4e"},
-    "attribute+scatter": {"kernel": "k_attribute + k_scatter", "bytes_per_sample": 47.83, "sources": "e2938a2628997b4e"},
+    "leaf sort/reduce": {"kernel": "k_leaf", "bytes_per_sample": 15.439, "sources": "84d93f0f21a02f86"},
 }
 
 
