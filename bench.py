@@ -319,6 +319,32 @@ def run_serving(args, world, rank, local):
               flush=True)
 
 
+def bind_near_gpu(dev_index: int):
+    """Run on the CPU cores next to the GPU (its PCI device's local_cpulist in
+    sysfs), so that pinned host buffers, allocated first-touch after this, sit
+    in the memory nearest the GPU.  Reads only; silently does nothing where
+    the information is missing."""
+    try:
+        props = torch.cuda.get_device_properties(dev_index)
+        bus = "%04x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return sorted(cpus)
+    except Exception:
+        pass
+    return None
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -487,7 +513,7 @@ def main():
     ap.add_argument("--samples", type=int, default=0, help="override the sample count (profiling runs)")
     ap.add_argument("--contexts", type=int, default=0, help="override the context count (profiling runs)")
     ap.add_argument("--cursor-shift", type=int, default=None, help="scatter cursor padding (log2 words)")
-    ap.add_argument("--sort-mode", type=int, default=None, help="leaf radix ranking: 0 by digit width, 1 match_any, 2 ballots")
+    ap.add_argument("--sort-mode", type=int, default=None, help="leaf radix ranking: 0 by digit width, 1 match_any, 2 ballots, 3 alternate")
     ap.add_argument("--no-part", action="store_true", help="per-context cursor scatter instead of the partition path")
     ap.add_argument("--no-tune", action="store_true", help="skip hpa_tune (use the per-call default configuration)")
     ap.add_argument("--small-leaves", type=int, default=0, help="0 automatic, 1 never, 2 always")
@@ -505,6 +531,8 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
+    if args.impl != "reference" and torch.cuda.is_available():
+        args.cpu_binding = bind_near_gpu(local)
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
@@ -605,7 +633,8 @@ def main():
         dt = max_over_ranks(dt, world, dev)
         assert int(ho["n"][0]) == K
         e2e = {"value": N * world / dt, "unit": UNIT, "h2d_bytes_per_step": in_b * N,
-               "d2h_bytes_per_step": 17 * K + 8 + 16 * w.n_stall, "ms_per_step": dt * 1e3}
+               "d2h_bytes_per_step": 17 * K + 8 + 16 * w.n_stall, "ms_per_step": dt * 1e3,
+               "host_cpus_near_gpu": len(args.cpu_binding) if getattr(args, "cpu_binding", None) else None}
 
     rows = None if args.no_rows else measure_rows(h, bid, B, w, out, stream, dev)
 

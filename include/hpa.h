@@ -66,10 +66,11 @@ typedef struct {
                                10240); 0 = chosen per call from samples per context, or by
                                hpa_tune                                                     */
     uint32_t timeout_iters; /* iteration limit of every bounded device wait; 0 = 1<<22     */
-    uint32_t cursor_pad;    /* spacing of the per-context scatter cursors: 0 = 8 words,
-                               n > 0 = 2^(n-1) words                                        */
-    uint32_t leaf_ranking;  /* equal-digit search of the leaf radix sort: 0 = by digit width,
-                               1 = __match_any_sync, 2 = ballots                            */
+    uint32_t cursor_pad;    /* spacing of the per-context scatter cursors: 0 = 8 words for
+                               up to 65,536 groups, else 1; n > 0 = 2^(n-1) words          */
+    uint32_t leaf_ranking;  /* equal-digit search of the leaf radix sort: 0 = by digit width
+                               (3 for 9-bit digits, else 1), 1 = __match_any_sync,
+                               2 = ballots, 3 = the two alternately, row by row             */
     uint32_t grouping;      /* grouping of records by context: 0 = automatic (per-part
                                counters when every buffer has <= 4096 contexts, else
                                per-context cursors), 1 = per-context cursors always         */
@@ -298,7 +299,7 @@ hpa_status hpa_attribute_batch(hpa_handle* h, uint32_t n, const uint32_t* binary
 /* Autotuner of the aggregation (no counterpart in the paper: a property of
  * the library).  Runs hpa_attribute_samples on `in` under each candidate
  * configuration -- leaf_capacity 4096 / 10240, grouping 0 / 1, leaf_hash
- * 0 / 1 (sort or hash aggregation), leaf_ranking 1 / 2: HPA_TUNE_CANDIDATES
+ * 0 / 1 (sort or hash aggregation), leaf_ranking 1 / 3: HPA_TUNE_CANDIDATES
  * in all, in that nesting order -- timing each
  * with CUDA events on the handle's stream (one untimed run, then `reps`
  * timed runs, 0 = 2), and keeps the fastest in the handle's options for the

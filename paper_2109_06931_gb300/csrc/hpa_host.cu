@@ -99,7 +99,7 @@ Binary* hpa_handle::binary(uint32_t id) {
 extern "C" hpa_status hpa_create(hpa_handle** out, int device, void* cuda_stream, const hpa_options* opt) {
     if (!out) return HPA_E_INVALID_ARG;
     *out = nullptr;
-    if (opt && (opt->leaf_hash > 1 || opt->small_leaves > 2 || opt->leaf_ranking > 2 || opt->grouping > 1 ||
+    if (opt && (opt->leaf_hash > 1 || opt->small_leaves > 2 || opt->leaf_ranking > 3 || opt->grouping > 1 ||
                 opt->cursor_pad > 7 ||
                 (opt->leaf_capacity && opt->leaf_capacity != LEAF_CAP_SMALL && opt->leaf_capacity != LEAF_CAP_LARGE)))
         return HPA_E_INVALID_ARG;
@@ -138,6 +138,11 @@ hpa_handle::~hpa_handle() {
     if (staging_event) cudaEventDestroy(staging_event);
     for (auto& g : graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
     if (capture_stream) cudaStreamDestroy(capture_stream);
+    for (int i = 0; i < N_COPY_STREAMS; ++i) {
+        if (copy_streams[i]) cudaStreamDestroy(copy_streams[i]);
+        if (copy_join[i]) cudaEventDestroy(copy_join[i]);
+    }
+    if (copy_fork) cudaEventDestroy(copy_fork);
     for (auto& v : ev_pool) for (cudaEvent_t e : v) cudaEventDestroy(e);
     for (auto& v : ev_pending) for (cudaEvent_t e : v) cudaEventDestroy(e);
     if (host_io) cudaFree(host_io);
@@ -422,10 +427,11 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
     const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
     w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
     w.span_log = std::min<uint32_t>(10, 32 - sbits);
-    // scatter cursors padded to 2^cur_shift words
-    w.cur_shift = opt.cursor_pad ? std::min<uint32_t>(opt.cursor_pad - 1, 6) : 3;
+    // scatter cursors padded to 2^cur_shift words; by default only while the
+    // padded cursors take at most 2 MB (beyond that they crowd L2 instead)
+    w.cur_shift = opt.cursor_pad ? std::min<uint32_t>(opt.cursor_pad - 1, 6) : (G <= 65536 ? 3 : 0);
     if (((G + 1) << w.cur_shift) > (64ull << 20)) w.cur_shift = 0;
-    w.sort_mode = std::min<uint32_t>(opt.leaf_ranking, 2);
+    w.sort_mode = std::min<uint32_t>(opt.leaf_ranking, 3);
     w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt || val64; w.val64 = val64;
     auto layout = [&](Carve& c) {
         w.grp_hist = c.take<uint32_t>(G + 1);
@@ -704,6 +710,38 @@ extern "C" hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t 
     return h->ensure_scratch(bytes + (1 << 20));
 }
 
+// Host <-> device copies in chunks of 64 MB, round-robin over the copy
+// streams, ordered after the work already on the handle's stream and joined
+// back into it: several copy engines move one call's arrays at once.
+hpa_status hpa_handle::copies(const Copy* c, int n, cudaMemcpyKind kind) {
+    if (!copy_fork) {
+        if (cudaEventCreateWithFlags(&copy_fork, cudaEventDisableTiming) != cudaSuccess)
+            return cuda(cudaGetLastError(), "copy event");
+        for (int i = 0; i < N_COPY_STREAMS; ++i)
+            if (cudaStreamCreateWithFlags(&copy_streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&copy_join[i], cudaEventDisableTiming) != cudaSuccess)
+                return cuda(cudaGetLastError(), "copy streams");
+    }
+    hpa_status st;
+    if ((st = cuda(cudaEventRecord(copy_fork, stream), "cudaEventRecord"))) return st;
+    for (int i = 0; i < N_COPY_STREAMS; ++i)
+        if ((st = cuda(cudaStreamWaitEvent(copy_streams[i], copy_fork, 0), "cudaStreamWaitEvent"))) return st;
+    constexpr size_t CHUNK = 64ull << 20;
+    int k = 0;
+    for (int j = 0; j < n; ++j)
+        for (size_t off = 0; off < c[j].bytes; off += CHUNK, ++k) {
+            const size_t b = std::min(CHUNK, c[j].bytes - off);
+            if ((st = cuda(cudaMemcpyAsync((char*)c[j].dst + off, (const char*)c[j].src + off, b, kind,
+                                           copy_streams[k % N_COPY_STREAMS]), "cudaMemcpyAsync")))
+                return st;
+        }
+    for (int i = 0; i < N_COPY_STREAMS; ++i) {
+        if ((st = cuda(cudaEventRecord(copy_join[i], copy_streams[i]), "cudaEventRecord"))) return st;
+        if ((st = cuda(cudaStreamWaitEvent(stream, copy_join[i], 0), "cudaStreamWaitEvent"))) return st;
+    }
+    return HPA_OK;
+}
+
 extern "C" hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
                                                  hpa_profile* out) {
     if (!h || !in || !out) return HPA_E_INVALID_ARG;
@@ -751,12 +789,9 @@ extern "C" hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_
     uint8_t* stall = (uint8_t*)di.stall;
     uint32_t* count = (uint32_t*)di.count;
     cudaStream_t s = h->stream;
-    if ((st = h->cuda(cudaMemcpyAsync(pc, in->pc, n * 8, cudaMemcpyHostToDevice, s), "H2D pc")) ||
-        (st = h->cuda(cudaMemcpyAsync(ctx, in->ctx, n * 4, cudaMemcpyHostToDevice, s), "H2D ctx")) ||
-        (st = h->cuda(cudaMemcpyAsync(stall, in->stall, n, cudaMemcpyHostToDevice, s), "H2D stall")))
-        return st;
-    if (cnt && (st = h->cuda(cudaMemcpyAsync(count, in->count, n * 4, cudaMemcpyHostToDevice, s), "H2D count")))
-        return st;
+    const hpa_handle::Copy cin[4] = {{pc, in->pc, n * 8}, {ctx, in->ctx, n * 4}, {stall, in->stall, n},
+                                     {count, in->count, cnt ? n * 4 : 0}};
+    if ((st = h->copies(cin, 4, cudaMemcpyHostToDevice))) return st;
     if ((st = h->aggregate(1, &binary_id, &di, &d))) return st;
     uint64_t K = 0;
     if ((st = h->cuda(cudaMemcpyAsync(&K, d.n_keys, 8, cudaMemcpyDeviceToHost, s), "D2H n_keys")) ||
@@ -764,11 +799,9 @@ extern "C" hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_
         return st;
     const uint64_t k = std::min<uint64_t>(K, out_cap);
     if (k) {
-        if ((st = h->cuda(cudaMemcpyAsync(out->key_ctx, d.key_ctx, k * 4, cudaMemcpyDeviceToHost, s), "D2H")) ||
-            (st = h->cuda(cudaMemcpyAsync(out->key_node, d.key_node, k * 4, cudaMemcpyDeviceToHost, s), "D2H")) ||
-            (st = h->cuda(cudaMemcpyAsync(out->key_stall, d.key_stall, k, cudaMemcpyDeviceToHost, s), "D2H")) ||
-            (st = h->cuda(cudaMemcpyAsync(out->val, d.val, k * 8, cudaMemcpyDeviceToHost, s), "D2H")))
-            return st;
+        const hpa_handle::Copy cout[4] = {{out->key_ctx, d.key_ctx, k * 4}, {out->key_node, d.key_node, k * 4},
+                                          {out->key_stall, d.key_stall, k}, {out->val, d.val, k * 8}};
+        if ((st = h->copies(cout, 4, cudaMemcpyDeviceToHost))) return st;
     }
     if (out->total) cudaMemcpyAsync(out->total, d.total, 8 * in->n_stall, cudaMemcpyDeviceToHost, s);
     if (out->unknown) cudaMemcpyAsync(out->unknown, d.unknown, 8 * in->n_stall, cudaMemcpyDeviceToHost, s);

@@ -93,6 +93,12 @@ struct hpa_handle {
     void* pinned_io = nullptr;
     size_t last_carve = 0;        // scratch bytes used by the last carve_work
     cudaStream_t capture_stream = nullptr;
+    // copies between host and device spread over several streams (copy engines)
+    static constexpr int N_COPY_STREAMS = 4;
+    cudaStream_t copy_streams[N_COPY_STREAMS] = {};
+    cudaEvent_t copy_fork = nullptr, copy_join[N_COPY_STREAMS] = {};
+    struct Copy { void* dst; const void* src; size_t bytes; };
+    hpa_status copies(const Copy* c, int n, cudaMemcpyKind kind);
     uint64_t graph_replays = 0;
     void* cct_scratch = nullptr;
     size_t cct_cap = 0;

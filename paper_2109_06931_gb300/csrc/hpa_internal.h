@@ -51,7 +51,7 @@ struct AggWork {
     uint32_t* grp_hist;    // [G+1] -> exclusive scan -> seg_off
     uint32_t* grp_cursor;  // [G << cur_shift] scatter cursors, one per 2^cur_shift words
     uint32_t cur_shift;
-    uint32_t sort_mode;    // leaf radix ranking: 0 by digit width, 1 match_any, 2 ballots
+    uint32_t sort_mode;    // leaf radix ranking: 0 by digit width, 1 match_any, 2 ballots, 3 alternate
     uint32_t* item_id;     // [G+1] flags -> exclusive scan
     uint32_t* item_grp0;   // [G]
     uint32_t* item_nleaf;  // [G+1] -> exclusive scan -> leaf_base

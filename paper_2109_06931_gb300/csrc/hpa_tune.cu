@@ -5,7 +5,7 @@
 // with shared-memory cursors, or per-context cursor atomics) and aggregation
 // inside a leaf (radix sort of the records, or a shared-memory hash table
 // and a sort of the distinct keys) and the equal-digit search of the leaf
-// radix sort (__match_any_sync or ballots).
+// radix sort (__match_any_sync, or alternating with ballots).
 
 #include "hpa_host.h"
 
@@ -30,7 +30,7 @@ extern "C" hpa_status hpa_tune(hpa_handle* h, uint32_t binary_id, const hpa_samp
     for (int c = 0; c < 2 && !st; ++c)
         for (uint32_t g = 0; g < 2 && !st; ++g)
             for (uint32_t hsh = 0; hsh <= 1 && !st; ++hsh)
-                for (uint32_t r = 1; r <= 2 && !st; ++r, ++k) {
+                for (uint32_t r = 1; r <= 3 && !st; r += 2, ++k) {     // __match_any_sync, alternating
                 hpa_options o = base;
                 o.leaf_capacity = caps[c];
                 o.grouping = g;

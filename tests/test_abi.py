@@ -46,7 +46,7 @@ def test_library_loads_and_binding_types():
             H.Hpa(0)
 
 
-@pytest.mark.parametrize("field,value", [("leaf_capacity", 5000), ("leaf_ranking", 3), ("grouping", 2),
+@pytest.mark.parametrize("field,value", [("leaf_capacity", 5000), ("leaf_ranking", 4), ("grouping", 2),
                                          ("cursor_pad", 8), ("small_leaves", 3), ("leaf_hash", 2)])
 def test_create_rejects_invalid_options(field, value):
     """Option checks come before any device call, so they hold without a GPU."""

@@ -231,7 +231,7 @@ def test_many_contexts(H, plain):
     assert_same_keys(out, oracle.attribute_samples(B, S))
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_leaf_ranking_modes_agree(plain, mode):
     from paper_2109_06931_gb300 import hpa
     B, _ = plain
@@ -255,7 +255,7 @@ def test_tuner_keeps_results_and_picks_a_candidate(plain):
     chosen, ms = h.tune(bid, S)
     assert len(ms) == hpa.HPA_TUNE_CANDIDATES and all(t > 0 for t in ms)
     assert chosen["leaf_capacity"] in (4096, 10240) and chosen["grouping"] in (0, 1)
-    assert chosen["leaf_hash"] in (0, 1)
+    assert chosen["leaf_hash"] in (0, 1) and chosen["leaf_ranking"] in (1, 3)
     ref = oracle.attribute_samples(B, S)
     out = h.attribute_samples(bid, S)
     h.sync()
