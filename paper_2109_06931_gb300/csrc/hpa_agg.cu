@@ -411,9 +411,28 @@ __global__ void k_part_seg(AggWork w) {
     }
 }
 
+// Shared memory of k_part_scatter for up to nb bins: per-bin cursors of the
+// part, the tile's per-bin counts / offsets, and the tile's records staged in
+// bin order (record + bin).
+__host__ __device__ inline size_t part_scatter_smem(uint32_t nb) {
+    return (size_t)nb * 4 + ((size_t)nb + 1) * 4 + 8 + (size_t)PART_TILE * (8 + 2);
+}
+
+// Each part is processed in tiles of PART_TILE samples: the tile's records
+// are ranked by bin with shared-memory atomics, staged in bin order, and
+// then written so that consecutive threads store consecutive records of a
+// bin (coalesced runs instead of lone 8-byte stores, which the L2 would have
+// to merge with DRAM data when it evicts partly written sectors).
 template <bool HAS_CNT, int U>
 __global__ void __launch_bounds__(PART_THREADS, 2) k_part_scatter(AggWork w) {
-    extern __shared__ uint32_t cur[];                   // per-context record cursors of this part
+    static_assert(PART_TILE == PART_THREADS * U, "one tile = U samples per thread");
+    extern __shared__ __align__(16) unsigned char psm[];
+    __shared__ uint32_t sw[33];
+    const uint32_t nbmax = w.part_ctx_max;
+    uint32_t* cur = reinterpret_cast<uint32_t*>(psm);                 // [nbmax] cursors of the part
+    uint32_t* th = cur + nbmax;                                         // [nbmax + 1] tile counts -> offsets
+    uint2* srec = reinterpret_cast<uint2*>(psm + (((size_t)nbmax * 4 + ((size_t)nbmax + 1) * 4 + 7) & ~(size_t)7));
+    uint16_t* sbin = reinterpret_cast<uint16_t*>(srec + PART_TILE);
     const uint64_t keep = policy_evict_last();
     for (uint64_t p = blockIdx.x; p < w.n_parts; p += gridDim.x) {
         const uint32_t b = upper_index<uint64_t>(w.buf_part, w.n_buf, p);
@@ -426,15 +445,16 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part_scatter(AggWork w) {
         __syncthreads();                                // the previous part's cursors are done
         const uint32_t* first = w.part_cnt + B.cnt_base + pl;
         for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) cur[c] = first[(uint64_t)c * parts];
-        __syncthreads();
         uint32_t bad = 0;
-        for (uint64_t base = i0 + threadIdx.x; base < i1; base += (uint64_t)PART_THREADS * U) {
+        for (uint64_t t0 = i0; t0 < i1; t0 += PART_TILE) {
+            for (uint32_t c = threadIdx.x; c <= n_ctx; c += PART_THREADS) th[c] = 0;
+            __syncthreads();
             uint64_t pc[U];
-            uint32_t st[U], cnt[U], cx[U], nd[U];
+            uint32_t st[U], cnt[U], cx[U], nd[U], rk[U];
             bool ok[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint64_t i = base + (uint64_t)u * PART_THREADS;
+                const uint64_t i = t0 + (uint64_t)u * PART_THREADS + threadIdx.x;
                 ok[u] = i < i1;
                 pc[u] = 0; st[u] = 0; cnt[u] = 1u; cx[u] = 0xFFFFFFFFu;
                 if (ok[u]) {
@@ -447,15 +467,31 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part_scatter(AggWork w) {
             }
             lookup_nodes<U>(bin, pc, ok, nd, keep);
 #pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u]) rk[u] = atomicAdd(&th[cx[u]], 1u);
+            __syncthreads();
+            const uint32_t tot = block_scan_array<uint32_t, PART_THREADS, PART_SCAN_EPT>(th, (int)n_ctx, sw);
+            if (threadIdx.x == 0) th[n_ctx] = tot;
+#pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (!ok[u]) continue;
                 const bool bad_stall = st[u] >= B.n_stall;
                 const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
-                const uint32_t pos = atomicAdd(&cur[cx[u]], 1u);
-                if (HAS_CNT) w.rec_pair[pos] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
-                else w.rec_sub[pos] = sub;
+                const uint32_t q = th[cx[u]] + rk[u];
+                srec[q] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
+                sbin[q] = (uint16_t)cx[u];
                 bad += bad_stall;
             }
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < tot; j += PART_THREADS) {
+                const uint32_t c = sbin[j];
+                const uint32_t dst = cur[c] + (j - th[c]);
+                if (HAS_CNT) w.rec_pair[dst] = srec[j];
+                else w.rec_sub[dst] = srec[j].x;
+            }
+            __syncthreads();
+            for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) cur[c] += th[c + 1] - th[c];
+            __syncthreads();
         }
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
     }
@@ -693,12 +729,13 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
     clear_work(w, s);
     if (w.part_mode) {
         const size_t csm = (size_t)w.part_ctx_max * 4;
+        const size_t ssm = part_scatter_smem(w.part_ctx_max);
         static bool attr = false;
         if (!attr) {
-            const int mx = (int)PART_CTX_MAX * 4;
+            const int mx = (int)PART_CTX_MAX * 4, mxs = (int)part_scatter_smem(PART_CTX_MAX);
             cudaFuncSetAttribute(k_part_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-            cudaFuncSetAttribute(k_part_scatter<true, PART_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-            cudaFuncSetAttribute(k_part_scatter<false, PART_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            cudaFuncSetAttribute(k_part_scatter<true, PART_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs);
+            cudaFuncSetAttribute(k_part_scatter<false, PART_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs);
             attr = true;
         }
         const int pb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * 2));
@@ -709,8 +746,8 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
         *launches += 2;
         run_plan(w, s, sms, launches, true);
         if (ev) cudaEventRecord(ev[1], s);
-        if (w.has_cnt) k_part_scatter<true, PART_U><<<pb, PART_THREADS, csm, s>>>(w);
-        else k_part_scatter<false, PART_U><<<pb, PART_THREADS, csm, s>>>(w);
+        if (w.has_cnt) k_part_scatter<true, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
+        else k_part_scatter<false, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
         *launches += 1;
     } else {
         const size_t hsm = (size_t)HIST_SMEM_MAX * 4;
