@@ -357,12 +357,16 @@ __global__ void __launch_bounds__(256) k_scatter(AggWork w) {
 // ------------------------------------------------------------------ partition path
 // For buffers whose contexts fit in shared memory, records are grouped by
 // context without global atomics.  Each buffer is cut into parts of
-// part_len samples; k_part_hist counts the valid records of every (context,
-// part) into part_cnt[cnt_base + ctx * parts + part] (context-major), one
-// exclusive scan of part_cnt then gives the position of each (context,
-// part)'s first record in the context-grouped record array, and
-// k_part_scatter attributes every sample and places its record with a
-// shared-memory cursor per context.  Group offsets are read off the scan.
+// part_len samples; k_part_hist counts the valid records of every (bin,
+// part) into part_cnt[cnt_base + bin * parts + part] (bin-major), one
+// exclusive scan of part_cnt then gives the position of each (bin, part)'s
+// first record in the bin-grouped record array, and k_part_scatter
+// attributes every sample and places its record with a shared-memory cursor
+// per bin.  With part_mode 1 a bin is a context and the group offsets are
+// read off the scan.  With part_mode 2 (more contexts) a bin is a bucket of
+// 2^part_shift consecutive contexts, the records land bucket-grouped in the
+// second record buffer with their context's low bits in rec2_dig, and a
+// second pass of the same shape groups each bucket by those bits.
 __global__ void __launch_bounds__(PART_THREADS) k_part_hist(AggWork w) {
     extern __shared__ uint32_t sh[];
     for (uint64_t p = blockIdx.x; p < w.n_parts; p += gridDim.x) {
@@ -373,12 +377,14 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_hist(AggWork w) {
         const uint64_t parts = w.buf_part[b + 1] - w.buf_part[b];
         const uint64_t i0 = pl * w.part_len, i1 = min(i0 + w.part_len, B.n);
         const uint32_t* ctx = B.ctx;
+        const uint32_t shift = w.part_shift;
+        const uint32_t nbin = (n_ctx + (1u << shift) - 1) >> shift;
         __syncthreads();
-        for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) sh[c] = 0;
+        for (uint32_t c = threadIdx.x; c < nbin; c += PART_THREADS) sh[c] = 0;
         __syncthreads();
         uint32_t bad = 0;
         auto count = [&](uint32_t c) {
-            if (c < n_ctx) atomicAdd(&sh[c], 1u);
+            if (c < n_ctx) atomicAdd(&sh[c >> shift], 1u);
             else ++bad;
         };
         uint64_t i = i0;
@@ -396,7 +402,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_hist(AggWork w) {
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
         __syncthreads();
         uint32_t* out = w.part_cnt + B.cnt_base + pl;
-        for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) out[(uint64_t)c * parts] = sh[c];
+        for (uint32_t c = threadIdx.x; c < nbin; c += PART_THREADS) out[(uint64_t)c * parts] = sh[c];
     }
 }
 
@@ -443,11 +449,14 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part_scatter(AggWork w) {
         const uint64_t parts = w.buf_part[b + 1] - w.buf_part[b];
         const uint64_t i0 = pl * w.part_len, i1 = min(i0 + w.part_len, B.n);
         __syncthreads();                                // the previous part's cursors are done
+        const uint32_t shift = w.part_shift, dmask = (1u << shift) - 1;
+        const uint32_t nbin = (n_ctx + dmask) >> shift;
+        const bool two = w.part_mode == 2;
         const uint32_t* first = w.part_cnt + B.cnt_base + pl;
-        for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) cur[c] = first[(uint64_t)c * parts];
+        for (uint32_t c = threadIdx.x; c < nbin; c += PART_THREADS) cur[c] = first[(uint64_t)c * parts];
         uint32_t bad = 0;
         for (uint64_t t0 = i0; t0 < i1; t0 += PART_TILE) {
-            for (uint32_t c = threadIdx.x; c <= n_ctx; c += PART_THREADS) th[c] = 0;
+            for (uint32_t c = threadIdx.x; c <= nbin; c += PART_THREADS) th[c] = 0;
             __syncthreads();
             uint64_t pc[U];
             uint32_t st[U], cnt[U], cx[U], nd[U], rk[U];
@@ -468,32 +477,166 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part_scatter(AggWork w) {
             lookup_nodes<U>(bin, pc, ok, nd, keep);
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (ok[u]) rk[u] = atomicAdd(&th[cx[u]], 1u);
+                if (ok[u]) rk[u] = atomicAdd(&th[cx[u] >> shift], 1u);
             __syncthreads();
-            const uint32_t tot = block_scan_array<uint32_t, PART_THREADS, PART_SCAN_EPT>(th, (int)n_ctx, sw);
-            if (threadIdx.x == 0) th[n_ctx] = tot;
+            const uint32_t tot = block_scan_array<uint32_t, PART_THREADS, PART_SCAN_EPT>(th, (int)nbin, sw);
+            if (threadIdx.x == 0) th[nbin] = tot;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (!ok[u]) continue;
                 const bool bad_stall = st[u] >= B.n_stall;
                 const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
-                const uint32_t q = th[cx[u]] + rk[u];
+                const uint32_t q = th[cx[u] >> shift] + rk[u];
                 srec[q] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
-                sbin[q] = (uint16_t)cx[u];
+                sbin[q] = (uint16_t)(two ? ((cx[u] >> shift) << 8 | (cx[u] & dmask)) : cx[u]);
                 bad += bad_stall;
             }
             __syncthreads();
             for (uint32_t j = threadIdx.x; j < tot; j += PART_THREADS) {
-                const uint32_t c = sbin[j];
+                const uint32_t sb = sbin[j];
+                const uint32_t c = two ? sb >> 8 : sb;
                 const uint32_t dst = cur[c] + (j - th[c]);
-                if (HAS_CNT) w.rec_pair[dst] = srec[j];
-                else w.rec_sub[dst] = srec[j].x;
+                if (two) {
+                    if (HAS_CNT) w.rec2_pair[dst] = srec[j];
+                    else w.rec2_sub[dst] = srec[j].x;
+                    w.rec2_dig[dst] = (uint8_t)sb;
+                } else {
+                    if (HAS_CNT) w.rec_pair[dst] = srec[j];
+                    else w.rec_sub[dst] = srec[j].x;
+                }
             }
             __syncthreads();
-            for (uint32_t c = threadIdx.x; c < n_ctx; c += PART_THREADS) cur[c] += th[c + 1] - th[c];
+            for (uint32_t c = threadIdx.x; c < nbin; c += PART_THREADS) cur[c] += th[c + 1] - th[c];
             __syncthreads();
         }
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
+    }
+}
+
+// ------------------------------------------------------------------ second pass (part_mode 2)
+// Segment s = (buffer b, bucket k): the records of contexts [k << shift,
+// (k + 1) << shift) of b, contiguous in the second record buffer after the
+// first pass.  Each segment is cut into chunks of PART2_LEN records; the
+// counters of chunk j of segment s for digit d (a context's low bits) sit at
+// cnt2[(seg_chunk[s] << shift) + d * chunks(s) + j], digit-major within the
+// segment, so one exclusive scan places every (context, chunk).
+__device__ __forceinline__ void seg_bounds(const AggWork& w, uint32_t s, uint64_t& start, uint64_t& end) {
+    const uint32_t b = upper_index<uint32_t>(w.buf_seg, w.n_buf, s);
+    const BufDev& B = w.bufs[b];
+    const uint64_t parts = w.buf_part[b + 1] - w.buf_part[b];
+    const uint64_t k = s - B.seg_base;
+    start = w.part_cnt[B.cnt_base + k * parts];
+    end = w.part_cnt[B.cnt_base + (k + 1) * parts];     // the next bucket's start, or the next buffer's
+}
+
+__global__ void k_seg_chunks(AggWork w) {
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < w.n_seg; s += gridDim.x * blockDim.x) {
+        uint64_t a, e;
+        seg_bounds(w, s, a, e);
+        w.seg_chunk[s] = (uint32_t)((e - a + PART2_LEN - 1) / PART2_LEN);
+    }
+}
+
+// chunk k -> segment s, chunk j within it, its record range and chunk count
+__device__ __forceinline__ void chunk_of(const AggWork& w, uint32_t k, uint32_t& s, uint32_t& j, uint32_t& chs,
+                                         uint64_t& a, uint64_t& e) {
+    s = upper_index<uint32_t>(w.seg_chunk, w.n_seg, k);
+    j = k - w.seg_chunk[s];
+    chs = w.seg_chunk[s + 1] - w.seg_chunk[s];
+    uint64_t sa, se;
+    seg_bounds(w, s, sa, se);
+    a = sa + (uint64_t)j * PART2_LEN;
+    e = min(a + PART2_LEN, se);
+}
+
+__global__ void __launch_bounds__(PART_THREADS) k_part2_hist(AggWork w) {
+    __shared__ uint32_t h[256];
+    const uint32_t n_chunks = w.seg_chunk[w.n_seg];
+    const uint32_t nd = 1u << w.part_shift;
+    for (uint32_t k = blockIdx.x; k < n_chunks; k += gridDim.x) {
+        uint32_t s, j, chs;
+        uint64_t a, e;
+        chunk_of(w, k, s, j, chs, a, e);
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d < nd; d += PART_THREADS) h[d] = 0;
+        __syncthreads();
+        for (uint64_t i = a + threadIdx.x; i < e; i += PART_THREADS) atomicAdd(&h[w.rec2_dig[i]], 1u);
+        __syncthreads();
+        uint32_t* out = w.cnt2 + ((uint64_t)w.seg_chunk[s] << w.part_shift) + j;
+        for (uint32_t d = threadIdx.x; d < nd; d += PART_THREADS) out[(uint64_t)d * chs] = h[d];
+    }
+}
+
+// group offsets (exclusive) from the scanned second-pass counters
+__global__ void k_part2_seg(AggWork w) {
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= w.G; g += gridDim.x * blockDim.x) {
+        if (g == w.G) { w.grp_hist[g] = w.cnt2[w.n_cnt2]; continue; }
+        const uint32_t b = upper_index<uint32_t>(w.buf_grp, w.n_buf, g);
+        const BufDev& B = w.bufs[b];
+        const uint32_t c = g - B.grp_base;
+        const uint32_t s = B.seg_base + (c >> w.part_shift);
+        const uint32_t d = c & ((1u << w.part_shift) - 1);
+        const uint32_t chs = w.seg_chunk[s + 1] - w.seg_chunk[s];
+        w.grp_hist[g] = w.cnt2[((uint64_t)w.seg_chunk[s] << w.part_shift) + (uint64_t)d * chs];
+    }
+}
+
+// second pass: each chunk's records staged by digit, tile by tile, and
+// written as coalesced runs to their contexts' segments
+template <bool HAS_CNT>
+__global__ void __launch_bounds__(PART_THREADS, 2) k_part2_scatter(AggWork w) {
+    constexpr int U = PART_U;
+    __shared__ uint32_t cur[256], th[257], sw[33];
+    __shared__ uint2 srec[PART_TILE];
+    __shared__ uint8_t sdig[PART_TILE];
+    const uint32_t n_chunks = w.seg_chunk[w.n_seg];
+    const uint32_t nd = 1u << w.part_shift;
+    for (uint32_t k = blockIdx.x; k < n_chunks; k += gridDim.x) {
+        uint32_t s, j, chs;
+        uint64_t a, e;
+        chunk_of(w, k, s, j, chs, a, e);
+        __syncthreads();
+        const uint32_t* first = w.cnt2 + ((uint64_t)w.seg_chunk[s] << w.part_shift) + j;
+        for (uint32_t d = threadIdx.x; d < nd; d += PART_THREADS) cur[d] = first[(uint64_t)d * chs];
+        for (uint64_t t0 = a; t0 < e; t0 += PART_TILE) {
+            for (uint32_t d = threadIdx.x; d <= nd; d += PART_THREADS) th[d] = 0;
+            __syncthreads();
+            uint2 r[U];
+            uint32_t dg[U], rk[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint64_t i = t0 + (uint64_t)u * PART_THREADS + threadIdx.x;
+                dg[u] = 0xFFFFFFFFu;
+                if (i < e) {
+                    if (HAS_CNT) r[u] = ld_stream(&w.rec2_pair[i]);
+                    else r[u].x = ld_stream(&w.rec2_sub[i]);
+                    dg[u] = w.rec2_dig[i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (dg[u] != 0xFFFFFFFFu) rk[u] = atomicAdd(&th[dg[u]], 1u);
+            __syncthreads();
+            const uint32_t tot = block_scan_array<uint32_t, PART_THREADS, 1>(th, (int)nd, sw);
+            if (threadIdx.x == 0) th[nd] = tot;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (dg[u] == 0xFFFFFFFFu) continue;
+                const uint32_t q = th[dg[u]] + rk[u];
+                srec[q] = r[u];
+                sdig[q] = (uint8_t)dg[u];
+            }
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < tot; i += PART_THREADS) {
+                const uint32_t d = sdig[i];
+                const uint32_t dst = cur[d] + (i - th[d]);
+                if (HAS_CNT) w.rec_pair[dst] = srec[i];
+                else w.rec_sub[dst] = srec[i].x;
+            }
+            __syncthreads();
+            for (uint32_t d = threadIdx.x; d < nd; d += PART_THREADS) cur[d] += th[d + 1] - th[d];
+            __syncthreads();
+        }
     }
 }
 
@@ -741,14 +884,33 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
         const int pb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * 2));
         k_part_hist<<<pb, PART_THREADS, csm, s>>>(w);
         scan_u32(w.part_cnt, w.part_cnt, w.n_cnt, w.scan_tmp, s, launches);
-        const int gb = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 256) / 256, (uint64_t)sms * 16));
-        k_part_seg<<<gb, 256, 0, s>>>(w);
-        *launches += 2;
-        run_plan(w, s, sms, launches, true);
-        if (ev) cudaEventRecord(ev[1], s);
-        if (w.has_cnt) k_part_scatter<true, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
-        else k_part_scatter<false, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
         *launches += 1;
+        const int gb = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 256) / 256, (uint64_t)sms * 16));
+        if (w.part_mode == 1) {
+            k_part_seg<<<gb, 256, 0, s>>>(w);
+            *launches += 1;
+            run_plan(w, s, sms, launches, true);
+            if (ev) cudaEventRecord(ev[1], s);
+            if (w.has_cnt) k_part_scatter<true, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
+            else k_part_scatter<false, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
+            *launches += 1;
+        } else {
+            // first pass into buckets, then each bucket by context
+            if (ev) cudaEventRecord(ev[1], s);
+            if (w.has_cnt) k_part_scatter<true, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
+            else k_part_scatter<false, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
+            const int sg = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.n_seg + 255) / 256, (uint64_t)sms * 4));
+            k_seg_chunks<<<sg, 256, 0, s>>>(w);
+            scan_u32(w.seg_chunk, w.seg_chunk, w.n_seg, w.scan_tmp, s, launches);
+            cudaMemsetAsync(w.cnt2, 0, sizeof(uint32_t) * ((size_t)w.n_cnt2 + 1), s);
+            k_part2_hist<<<sms * 4, PART_THREADS, 0, s>>>(w);
+            scan_u32(w.cnt2, w.cnt2, w.n_cnt2, w.scan_tmp, s, launches);
+            k_part2_seg<<<gb, 256, 0, s>>>(w);
+            run_plan(w, s, sms, launches, true);
+            if (w.has_cnt) k_part2_scatter<true><<<sms * 2, PART_THREADS, 0, s>>>(w);
+            else k_part2_scatter<false><<<sms * 2, PART_THREADS, 0, s>>>(w);
+            *launches += 5;
+        }
     } else {
         const size_t hsm = (size_t)HIST_SMEM_MAX * 4;
         const int per_sm = 2;

@@ -422,7 +422,8 @@ extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary
 // ------------------------------------------------------------------ aggregation calls
 // Scratch layout of one aggregation over N records in G groups (n_buf buffers).
 hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n, uint32_t cap, uint32_t sb,
-                                  uint32_t sbits, bool has_cnt, bool val64, uint64_t staged, uint64_t cnt_words) {
+                                  uint32_t sbits, bool has_cnt, bool val64, uint64_t staged, uint64_t cnt_words,
+                                  uint64_t seg_words, uint64_t cnt2_words) {
     const uint64_t N2 = std::max(N, staged);   // the second record buffer also stages samples in tile order
     const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
     w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
@@ -458,7 +459,11 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
         w.tmp_key = c.take<uint32_t>(N + 1);
         w.tmp_val = c.take<uint64_t>(N + 1);
         w.part_cnt = cnt_words ? c.take<uint32_t>(cnt_words) : nullptr;
-        w.scan_tmp = c.take<uint32_t>(scan_tmp_words(std::max<uint64_t>(std::max<uint64_t>(G, L_max), cnt_words)));
+        w.seg_chunk = seg_words ? c.take<uint32_t>(seg_words) : nullptr;
+        w.cnt2 = cnt2_words ? c.take<uint32_t>(cnt2_words) : nullptr;
+        w.rec2_dig = seg_words ? c.take<uint8_t>(N + 16) : nullptr;
+        w.scan_tmp = c.take<uint32_t>(scan_tmp_words(
+            std::max<uint64_t>(std::max<uint64_t>(G, L_max), std::max(std::max(cnt_words, seg_words), cnt2_words))));
     };
     Carve probe{nullptr};
     layout(probe);
@@ -508,9 +513,8 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     // sub-batches and their configurations
     struct Sub {
         uint32_t b0 = 0, b1 = 0, sbits = 0, cap = 0, ctx_max = 0;
-        uint64_t N = 0, G = 0, tiles = 0, part_len = 0, n_parts = 0, n_cnt = 0;
-        uint32_t max_nodes = 0;
-        bool part = false;
+        uint64_t N = 0, G = 0, tiles = 0, part_len = 0, n_parts = 0, n_cnt = 0, n_seg = 0, n_cnt2 = 0;
+        uint32_t max_nodes = 0, mode = 0, shift = 0, nbin_max = 0;
     };
     std::vector<Sub> subs;
     for (uint32_t b = 0; b < n; ++b) {
@@ -526,7 +530,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         u.max_nodes = std::max(u.max_nodes, binary(binary_ids[b])->n_nodes);
         u.ctx_max = std::max(u.ctx_max, in[b].n_ctx);
     }
-    uint64_t N_max = 0, G_max = 0, staged_max = 0, cnt_words_max = 0;
+    uint64_t N_max = 0, G_max = 0, staged_max = 0, cnt_words_max = 0, seg_words_max = 0, cnt2_words_max = 0;
     uint32_t n_max = 0, sbits_max = 0, cap_min = LEAF_CAP_LARGE;
     const uint64_t target_parts = (uint64_t)sms * 8;
     for (Sub& u : subs) {
@@ -535,31 +539,41 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         u.sbits = nb + sb;
         u.cap = opt.leaf_capacity ? opt.leaf_capacity
                                   : ((u.G && u.N / u.G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL);
-        // partition path: every buffer's contexts fit in shared memory and the
-        // (context, part) counters stay within PART_CNT_MAX; parts of part_len
-        // samples, about 8 per SM over the sub-batch
+        // partition paths (no global atomics): bins = contexts when every
+        // buffer has at most PART_CTX_MAX of them (mode 1), buckets of
+        // 2^shift contexts and a second pass up to PART2_CTX_MAX (mode 2),
+        // else per-context cursors (mode 0); parts of part_len samples,
+        // about 8 per SM over the sub-batch
         u.part_len = std::max<uint64_t>(TILE, (u.N + target_parts - 1) / target_parts + TILE - 1) / TILE * TILE;
+        if (opt.grouping != 1) u.mode = u.ctx_max <= PART_CTX_MAX ? 1 : (u.ctx_max <= PART2_CTX_MAX ? 2 : 0);
+        u.shift = u.mode == 2 ? ceil_log2_u64(u.ctx_max) - 8 : 0;
         for (uint32_t b = u.b0; b < u.b1; ++b) {
             const uint64_t pb = (in[b].n + u.part_len - 1) / u.part_len;
+            const uint32_t nbin = (in[b].n_ctx + (1u << u.shift) - 1) >> u.shift;
             u.n_parts += pb;
-            u.n_cnt += pb * in[b].n_ctx;
+            u.n_cnt += pb * nbin;
+            u.n_seg += nbin;
+            u.nbin_max = std::max(u.nbin_max, nbin);
         }
-        u.part = opt.grouping != 1 && u.ctx_max <= PART_CTX_MAX && u.n_cnt <= PART_CNT_MAX;
+        if (u.n_cnt > PART_CNT_MAX) u.mode = 0;
+        if (u.mode == 2) u.n_cnt2 = (u.N / PART2_LEN + u.n_seg + 1) << u.shift;
         N_max = std::max(N_max, u.N);
         G_max = std::max(G_max, u.G);
         n_max = std::max(n_max, u.b1 - u.b0);
         sbits_max = std::max(sbits_max, u.sbits);
         cap_min = std::min(cap_min, u.cap);
-        staged_max = std::max(staged_max, u.part ? 0 : u.tiles * TILE);
-        cnt_words_max = std::max(cnt_words_max, u.part ? u.n_cnt + 1 : 0);
+        staged_max = std::max(staged_max, u.mode ? 0 : u.tiles * TILE);
+        cnt_words_max = std::max(cnt_words_max, u.mode ? u.n_cnt + 1 : 0);
+        seg_words_max = std::max(seg_words_max, u.mode == 2 ? u.n_seg + 2 : 0);
+        cnt2_words_max = std::max(cnt2_words_max, u.mode == 2 ? u.n_cnt2 + 1 : 0);
     }
     AggWork w0{};
     hpa_status st = carve_work(w0, N_max, G_max, n_max, cap_min, sb, sbits_max, has_cnt, false, staged_max,
-                               cnt_words_max);
+                               cnt_words_max, seg_words_max, cnt2_words_max);
     if (st) return st;
 
     // descriptors: every buffer's BufDev, then per sub-batch its prefix arrays
-    const size_t desc_bytes = n * sizeof(BufDev) + (n + subs.size()) * 24 + 64 * subs.size() + 512;
+    const size_t desc_bytes = n * sizeof(BufDev) + (n + subs.size()) * 28 + 64 * subs.size() + 512;
     if ((st = ensure_staging(desc_bytes))) return st;
     Carve hs{(char*)staging};
     BufDev* hb = hs.take<BufDev>(n);
@@ -571,8 +585,9 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         uint64_t* htile = hs.take<uint64_t>(nk + 1);
         uint32_t* hgrp = hs.take<uint32_t>(nk + 1);
         uint64_t* hpart = hs.take<uint64_t>(nk + 1);
+        uint32_t* hseg = hs.take<uint32_t>(nk + 1);
         uint64_t tb = 0, pbase = 0, cbase = 0;
-        uint32_t gb = 0;
+        uint32_t gb = 0, sgb = 0;
         for (uint32_t b = u.b0; b < u.b1; ++b) {
             const uint32_t k = b - u.b0;
             const hpa_samples& s = in[b];
@@ -580,7 +595,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
             BufDev d{};
             d.pc = s.pc; d.ctx = s.ctx; d.stall = s.stall; d.count = s.count; d.n = s.n;
             d.tile_base = tb; d.n_ctx = s.n_ctx; d.n_stall = s.n_stall; d.grp_base = gb; d.bin = binary_ids[b];
-            d.part_base = pbase; d.cnt_base = cbase;
+            d.part_base = pbase; d.cnt_base = cbase; d.seg_base = sgb;
             d.total = o.total; d.unknown = o.unknown;
             d.key_ctx = o.key_ctx; d.key_node = o.key_node; d.key_stall = o.key_stall; d.val = o.val;
             d.n_keys = o.n_keys; d.capacity = o.capacity;
@@ -588,9 +603,12 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
             htile[k] = tb;
             hgrp[k] = gb;
             hpart[k] = pbase;
+            hseg[k] = sgb;
             const uint64_t pb = (s.n + u.part_len - 1) / u.part_len;
+            const uint32_t nbin = (s.n_ctx + (1u << u.shift) - 1) >> u.shift;
             pbase += pb;
-            cbase += pb * s.n_ctx;
+            cbase += pb * nbin;
+            sgb += nbin;
             tb += (s.n + TILE - 1) / TILE;
             gb += s.n_ctx;
             o.n_ctx = s.n_ctx;
@@ -600,6 +618,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         htile[nk] = tb;
         hgrp[nk] = gb;
         hpart[nk] = pbase;
+        hseg[nk] = sgb;
         AggWork w = w0;
         w.G = (uint32_t)u.G;
         w.n_buf = nk;
@@ -611,17 +630,21 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         w.emit_totals = 1;
         w.small_leaves = opt.small_leaves == 2 || (opt.small_leaves == 0 && u.N < 64 * u.G);
         w.leaf_hash = opt.leaf_hash;
-        if (u.part) {
-            w.part_mode = 1;
-            w.part_ctx_max = u.ctx_max;
+        if (u.mode) {
+            w.part_mode = u.mode;
+            w.part_ctx_max = u.nbin_max;
+            w.part_shift = u.shift;
             w.part_len = u.part_len;
             w.n_parts = u.n_parts;
             w.n_cnt = u.n_cnt;
+            w.n_seg = (uint32_t)u.n_seg;
+            w.n_cnt2 = u.n_cnt2;
         }
         w.bufs = (const BufDev*)dev_of(hb + u.b0);
         w.buf_tile = (const uint64_t*)dev_of(htile);
         w.buf_grp = (const uint32_t*)dev_of(hgrp);
         w.buf_part = (const uint64_t*)dev_of(hpart);
+        w.buf_seg = (const uint32_t*)dev_of(hseg);
         ws.push_back(w);
     }
     const size_t used = hs.off;
@@ -654,6 +677,7 @@ hpa_status hpa_handle::launch_graph(const std::vector<AggWork>& ws, size_t stage
         key = mix64(key, w.sb); key = mix64(key, w.sbits); key = mix64(key, w.L_max); key = mix64(key, w.has_cnt);
         key = mix64(key, w.cur_shift); key = mix64(key, (uint64_t)(uintptr_t)w.grp_hist);
         key = mix64(key, w.part_mode); key = mix64(key, w.part_len); key = mix64(key, w.n_parts);
+        key = mix64(key, w.part_shift);
         key = mix64(key, w.sort_mode); key = mix64(key, w.small_leaves); key = mix64(key, w.leaf_hash);
     }
     key = mix64(key, staged_bytes);
@@ -706,7 +730,7 @@ extern "C" hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t 
     const uint64_t L = G + 6 * (N / LEAF_CAP_SMALL + 1) + 300;
     const uint64_t C = std::min<uint64_t>(PART_CNT_MAX, G * ((uint64_t)h->sms * 8 + 2));   // part counters
     size_t bytes = (G + 1) * 4 * 12 + L * 4 * 5 + (N + TILE + 1) * (4 * 6 + 8) + 256 * 40 + (C + 1) * 4 +
-                   scan_tmp_words(std::max(std::max(G, L), C)) * 4;
+                   scan_tmp_words(std::max(std::max(G, L), C)) * 4 + N + (64ull << 20);   // two-level partition
     return h->ensure_scratch(bytes + (1 << 20));
 }
 

@@ -126,7 +126,9 @@ struct hpa_handle {
                             const hpa_samples* in);
     hpa_status carve_work(hpa::AggWork& w, uint64_t N, uint64_t G, uint32_t n_buf, uint32_t cap, uint32_t sb,
                           uint32_t sbits, bool has_cnt, bool val64, uint64_t staged = 0,
-                          uint64_t cnt_words = 0);   // part counters incl. the scan total (0: none)
+                          uint64_t cnt_words = 0,    // part counters incl. the scan total (0: none)
+                          uint64_t seg_words = 0,    // bucket segments + 2 (two-level partition; 0: none)
+                          uint64_t cnt2_words = 0);  // second-pass counters incl. the scan total
     // descriptors of single-output pipelines (expansion, union) in the staging area
     hpa_status stage_single_output(hpa::AggWork& w, uint32_t bin, uint32_t n_ctx, const hpa_profile& out);
 };

@@ -24,7 +24,9 @@ struct BufDev {
     uint32_t first_leaf_item;   // (filled on device) unused by the host
     uint32_t pad;
     uint64_t part_base;         // first global part of this buffer (partition path)
-    uint64_t cnt_base;          // first part counter of this buffer: sum of n_ctx * parts before it
+    uint64_t cnt_base;          // first part counter of this buffer: sum of bins * parts before it
+    uint32_t seg_base;          // first bucket segment of this buffer (part_mode 2)
+    uint32_t pad2;
     uint64_t* total;            // per-stall totals (may be null)
     uint64_t* unknown;
     // outputs
@@ -80,8 +82,15 @@ struct AggWork {
     const DevBinary* bins;
     DevStatus* status;
     // partition path (every buffer's contexts fit in shared memory)
-    uint32_t part_mode;
-    uint32_t part_ctx_max;        // largest n_ctx of the call
+    uint32_t part_mode;           // 0 per-context cursors, 1 bins = contexts, 2 bins = buckets + second pass
+    uint32_t part_ctx_max;        // largest number of bins of a buffer
+    uint32_t part_shift;          // a bin holds 2^part_shift consecutive contexts
+    uint32_t n_seg;               // part_mode 2: bucket segments of the call
+    const uint32_t* buf_seg;      // [n_buf + 1] segment prefix
+    uint32_t* seg_chunk;          // [n_seg + 1] chunks per segment -> exclusive scan
+    uint32_t* cnt2;               // [n_cnt2 + 1] second-pass counters -> exclusive scan
+    uint64_t n_cnt2;              // upper bound of the second-pass counters
+    uint8_t* rec2_dig;            // [N] low context bits of the bucket-grouped records
     uint64_t part_len;            // samples per part
     uint64_t n_parts;
     uint64_t n_cnt;               // part counters: sum over buffers of n_ctx * parts
@@ -111,6 +120,8 @@ constexpr uint32_t PART_CTX_MAX = 4096;      // contexts per buffer on the parti
                                              // per-context cursor path is faster
 constexpr uint64_t PART_CNT_MAX = 1ull << 26; // part counters per call on the partition path
 constexpr int PART_SCAN_EPT = (int)((PART_CTX_MAX + 1 + PART_THREADS - 1) / PART_THREADS);
+constexpr uint32_t PART2_CTX_MAX = 65536;    // contexts per buffer on the two-level partition path
+constexpr uint64_t PART2_LEN = 32768;        // records per chunk of the second pass
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_EPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_EPT;

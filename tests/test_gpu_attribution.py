@@ -328,3 +328,30 @@ def test_hash_leaves_agree(plain, large_bin, small):
         h.sync()
         assert_same_keys(out, oracle.attribute_samples(B, S))
     h.close()
+
+
+@pytest.mark.parametrize("n_ctx", [4097, 20_000, 65_536, 70_000])
+def test_two_level_grouping(H, plain, large_bin, n_ctx):
+    """More contexts than one partition pass takes: buckets of contexts,
+    then each bucket by context (up to 65,536 contexts), else cursors."""
+    B1, b1 = plain
+    B2, b2 = large_bin
+    for B, bid, counts in ((B1, b1, False), (B2, b2, True)):
+        S = synth.make_samples(81 + n_ctx % 97, B, 1_300_000, n_ctx, 1.0, counts=counts, device="cuda")
+        out = run(H, bid, S)
+        assert_same_keys(out, oracle.attribute_samples(B, S))
+
+
+def test_two_level_in_a_mixed_batch(H, plain, large_bin):
+    """A batch whose largest buffer needs two passes, with small and empty
+    buffers beside it."""
+    B1, b1 = plain
+    B2, b2 = large_bin
+    spec = [(B2, b2, 900_000, 30_000), (B1, b1, 0, 10), (B1, b1, 5_000, 3), (B2, b2, 250_000, 5_000),
+            (B1, b1, 77_777, 65_536)]
+    ss = [synth.make_samples(90 + i, B, n, c, 1.0, counts=(i % 2 == 0), device="cuda")
+          for i, (B, _, n, c) in enumerate(spec)]
+    outs = H.attribute_batch([bid for _, bid, _, _ in spec], ss)
+    H.sync()
+    for o, S, (B, _, _, _) in zip(outs, ss, spec):
+        assert_same_keys(o, oracle.attribute_samples(B, S))
