@@ -573,7 +573,16 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     if (st) return st;
 
     // descriptors: every buffer's BufDev, then per sub-batch its prefix arrays
-    const size_t desc_bytes = n * sizeof(BufDev) + (n + subs.size()) * 28 + 64 * subs.size() + 512;
+    // exact size of the layout below (every take is 256-byte aligned)
+    Carve probe{nullptr};
+    probe.take<BufDev>(n);
+    for (const Sub& u : subs) {
+        probe.take<uint64_t>(u.b1 - u.b0 + 1);
+        probe.take<uint32_t>(u.b1 - u.b0 + 1);
+        probe.take<uint64_t>(u.b1 - u.b0 + 1);
+        probe.take<uint32_t>(u.b1 - u.b0 + 1);
+    }
+    const size_t desc_bytes = probe.off + 256;
     if ((st = ensure_staging(desc_bytes))) return st;
     Carve hs{(char*)staging};
     BufDev* hb = hs.take<BufDev>(n);
@@ -648,6 +657,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         ws.push_back(w);
     }
     const size_t used = hs.off;
+    if (used > desc_bytes) return fail(HPA_E_INTERNAL, "descriptor layout overflows its staging area");
     if (use_graph && !timing) return launch_graph(ws, used, n, in);
     if ((st = upload_staging(used))) return st;
     for (uint32_t b = 0; b < n; ++b) {

@@ -355,3 +355,16 @@ def test_two_level_in_a_mixed_batch(H, plain, large_bin):
     H.sync()
     for o, S, (B, _, _, _) in zip(outs, ss, spec):
         assert_same_keys(o, oracle.attribute_samples(B, S))
+
+
+def test_batch_with_many_sub_batches(H, plain):
+    """70 buffers of 1.1M contexts each: one sub-batch per buffer, so the
+    descriptors of the call need more than the smallest staging area."""
+    B, bid = plain
+    ss = [synth.make_samples(200 + i, B, 2_000 + 37 * i, 1_100_000, 1.1, counts=(i % 2 == 0), device="cuda")
+          for i in range(70)]
+    for rep in range(2):                                   # capture, then replay
+        outs = H.attribute_batch([bid] * len(ss), ss)
+        H.sync()
+        for o, S in zip(outs, ss):
+            assert_same_keys(o, oracle.attribute_samples(B, S))
