@@ -45,7 +45,7 @@ def workload(name: str):
 # the kernel that dominates each phase, from one ncu capture of the 2e7-sample
 # case (profiles/k_leaf_plain-large-20M.md), keyed by a
 # hash of the kernel sources it was taken on: a changed kernel reports null.
-KERNEL_SOURCES = ("hpa_agg.cu", "hpa_leaf.cu", "hpa_dev.cuh", "hpa_internal.h")
+KERNEL_SOURCES = ("hpa_leaf.cu", "hpa_dev.cuh", "hpa_internal.h")     # the leaf kernel's sources
 TRAFFIC = {
     "leaf sort/reduce": {"kernel": "k_leaf", "bytes_per_sample": 15.439, "sources": "84d93f0f21a02f86"},
 }
