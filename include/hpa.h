@@ -331,6 +331,18 @@ hpa_status hpa_apportion_callgraph(hpa_handle* h, uint32_t binary_id, const hpa_
 hpa_status hpa_propagate_inclusive(hpa_handle* h, uint32_t binary_id, const hpa_profile* p,
                                    hpa_profile* tree_out, const hpa_cct* cct, uint64_t* cct_out);
 
+/* Flat view of a profile (Section 7: costs shown by static program structure
+ * alone, regardless of calling context): out keys (ctx = 0, node, stall, val)
+ * with val = the sum over every context of p's values for that (node, stall),
+ * ascending by (node, stall), UNKNOWN last; totals / unknown summed likewise.
+ * p: a profile of this binary (device keys); out: device arrays as for
+ * hpa_attribute_samples, n_ctx = 1.  Apportioning this profile with context
+ * 0 requested gives the GPU calling context tree of all contexts pooled.
+ * Needs (n_nodes + 1) * 2^stall_bits <= 2^28 (a dense accumulator of that
+ * many uint64 in the handle's scratch); HPA_E_CAPACITY (at hpa_sync) when
+ * out->capacity is too small, with *out->n_keys the size needed.            */
+hpa_status hpa_flat_profile(hpa_handle* h, uint32_t binary_id, const hpa_profile* p, hpa_profile* out);
+
 /* Derived metrics over n_profiles profiles (Section 4.5) and the warp issue
  * rate per context (Section 7, W = (S - S_stall) / S with the handle's
  * issued_mask).  ps: HOST array of profile descriptors with DEVICE data.    */

@@ -47,6 +47,8 @@ def load(path: str):
     L.orc_attribute.argtypes = [u64, vp, vp, vp, u64, vp, vp, vp, vp, u32, u32]
     L.orc_inclusive_structure.restype = vp
     L.orc_inclusive_structure.argtypes = [u32, vp, u64, vp, vp, vp, vp]
+    L.orc_flat.restype = vp
+    L.orc_flat.argtypes = [u32, u64, vp, vp, vp]
     L.orc_inclusive_cct.restype = i32
     L.orc_inclusive_cct.argtypes = [u32, vp, u32, u64, vp, vp, vp, vp]
     L.orc_derive.restype = vp
@@ -128,6 +130,14 @@ def inclusive_structure(node_parent, keys: KeyList) -> KeyList:
     k = [_c(keys.ctx, np.uint32), _c(keys.node, np.uint32), _c(keys.stall, np.uint8), _c(keys.val, np.uint64)]
     h = L.orc_inclusive_structure(par.shape[0], _p(par), k[0].shape[0], *[_p(x) for x in k])
     return _take(L, h, 0, False)
+
+
+def flat(n_stall: int, keys: KeyList) -> KeyList:
+    """Flat view (Section 7): values summed over contexts per (node, stall)."""
+    L = lib()
+    k = [_c(keys.node, np.uint32), _c(keys.stall, np.uint8), _c(keys.val, np.uint64)]
+    h = L.orc_flat(n_stall, k[0].shape[0], *[_p(x) for x in k])
+    return _take(L, h, n_stall, True)
 
 
 def inclusive_cct(cct_parent, n_stall: int, keys: KeyList) -> np.ndarray:

@@ -131,6 +131,30 @@ void* orc_inclusive_structure(uint32_t n_nodes, const uint32_t* node_parent, uin
     return out;
 }
 
+// Flat view (Section 7: costs by static structure regardless of calling
+// context): the values of all keys summed per (node, stall), every context
+// pooled into context 0; per-stall totals and UNKNOWN totals of the result.
+void* orc_flat(uint32_t n_stall, uint64_t k, const uint32_t* knode, const uint8_t* kstall, const uint64_t* kval) {
+    KeyList* out = new KeyList();
+    std::map<std::pair<uint32_t, uint32_t>, uint64_t> agg;
+    for (uint64_t i = 0; i < k; ++i) {
+        if (kstall[i] >= n_stall) { out->status = INVALID_ARG; return out; }
+        agg[std::make_pair(knode[i], (uint32_t)kstall[i])] += kval[i];
+    }
+    out->total.assign(n_stall, 0);
+    out->unknown.assign(n_stall, 0);
+    for (auto& kv : agg) {
+        if (!kv.second) continue;                  // a key whose values sum to 0 is omitted
+        out->ctx.push_back(0);
+        out->node.push_back(kv.first.first);
+        out->stall.push_back(kv.first.second);
+        out->val.push_back(kv.second);
+        out->total[kv.first.second] += kv.second;
+        if (kv.first.first == UNKNOWN) out->unknown[kv.first.second] += kv.second;
+    }
+    return out;
+}
+
 // O4(b): inclusive metrics over the host calling-context tree (Section 6.1).
 // Launch context c is CCT node c.  host[h][r] = sum of the values of all keys
 // (UNKNOWN included) whose context lies in the subtree of h: each key's value

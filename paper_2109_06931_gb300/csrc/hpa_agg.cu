@@ -421,7 +421,7 @@ __global__ void k_part_seg(AggWork w) {
 // part, the tile's per-bin counts / offsets, and the tile's records staged in
 // bin order (record + bin).
 __host__ __device__ inline size_t part_scatter_smem(uint32_t nb) {
-    return (size_t)nb * 4 + ((size_t)nb + 1) * 4 + 8 + (size_t)PART_TILE * (8 + 2);
+    return (size_t)nb * 4 + ((size_t)nb + 1) * 4 + 8 + (size_t)PSC_TILE * (8 + 2);
 }
 
 // Each part is processed in tiles of PART_TILE samples: the tile's records
@@ -430,8 +430,9 @@ __host__ __device__ inline size_t part_scatter_smem(uint32_t nb) {
 // bin (coalesced runs instead of lone 8-byte stores, which the L2 would have
 // to merge with DRAM data when it evicts partly written sectors).
 template <bool HAS_CNT, int U>
-__global__ void __launch_bounds__(PART_THREADS, 2) k_part_scatter(AggWork w) {
-    static_assert(PART_TILE == PART_THREADS * U, "one tile = U samples per thread");
+__global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(AggWork w) {
+    static_assert(PSC_TILE == PSC_THREADS * U, "one tile = U samples per thread");
+    constexpr int PART_THREADS = PSC_THREADS, PART_TILE = PSC_TILE;
     extern __shared__ __align__(16) unsigned char psm[];
     __shared__ uint32_t sw[33];
     const uint32_t nbmax = w.part_ctx_max;
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part_scatter(AggWork w) {
             for (int u = 0; u < U; ++u)
                 if (ok[u]) rk[u] = atomicAdd(&th[cx[u] >> shift], 1u);
             __syncthreads();
-            const uint32_t tot = block_scan_array<uint32_t, PART_THREADS, PART_SCAN_EPT>(th, (int)nbin, sw);
+            const uint32_t tot = block_scan_array<uint32_t, PSC_THREADS, PSC_SCAN_EPT>(th, (int)nbin, sw);
             if (threadIdx.x == 0) th[nbin] = tot;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -877,11 +878,12 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
         if (!attr) {
             const int mx = (int)PART_CTX_MAX * 4, mxs = (int)part_scatter_smem(PART_CTX_MAX);
             cudaFuncSetAttribute(k_part_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-            cudaFuncSetAttribute(k_part_scatter<true, PART_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs);
-            cudaFuncSetAttribute(k_part_scatter<false, PART_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs);
+            cudaFuncSetAttribute(k_part_scatter<true, PSC_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs);
+            cudaFuncSetAttribute(k_part_scatter<false, PSC_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs);
             attr = true;
         }
         const int pb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * 2));
+        const int psb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * PSC_MIN_BLOCKS));
         k_part_hist<<<pb, PART_THREADS, csm, s>>>(w);
         scan_u32(w.part_cnt, w.part_cnt, w.n_cnt, w.scan_tmp, s, launches);
         *launches += 1;
@@ -891,14 +893,14 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
             *launches += 1;
             run_plan(w, s, sms, launches, true);
             if (ev) cudaEventRecord(ev[1], s);
-            if (w.has_cnt) k_part_scatter<true, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
-            else k_part_scatter<false, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
+            if (w.has_cnt) k_part_scatter<true, PSC_U><<<psb, PSC_THREADS, ssm, s>>>(w);
+            else k_part_scatter<false, PSC_U><<<psb, PSC_THREADS, ssm, s>>>(w);
             *launches += 1;
         } else {
             // first pass into buckets, then each bucket by context
             if (ev) cudaEventRecord(ev[1], s);
-            if (w.has_cnt) k_part_scatter<true, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
-            else k_part_scatter<false, PART_U><<<pb, PART_THREADS, ssm, s>>>(w);
+            if (w.has_cnt) k_part_scatter<true, PSC_U><<<psb, PSC_THREADS, ssm, s>>>(w);
+            else k_part_scatter<false, PSC_U><<<psb, PSC_THREADS, ssm, s>>>(w);
             const int sg = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.n_seg + 255) / 256, (uint64_t)sms * 4));
             k_seg_chunks<<<sg, 256, 0, s>>>(w);
             scan_u32(w.seg_chunk, w.seg_chunk, w.n_seg, w.scan_tmp, s, launches);

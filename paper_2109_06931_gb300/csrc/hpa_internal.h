@@ -114,12 +114,19 @@ constexpr int BIG_THREADS = 512;
 constexpr int BIG_EPT = ((1 << BIG_FINE_MAX_LOG) + 1 + BIG_THREADS - 1) / BIG_THREADS;
 constexpr int PART_THREADS = 512;
 constexpr int PART_U = 4;                    // samples in flight per thread in k_part_scatter
-constexpr int PART_TILE = PART_THREADS * PART_U;   // samples staged per tile in k_part_scatter
+constexpr int PART_TILE = PART_THREADS * PART_U;   // records staged per tile in k_part2_scatter
+// k_part_scatter (attribution + first partition pass): CTA size, samples in
+// flight per thread, CTAs per SM
+constexpr int PSC_THREADS = 512;
+constexpr int PSC_U = 4;
+constexpr int PSC_MIN_BLOCKS = 2;
+constexpr int PSC_TILE = PSC_THREADS * PSC_U;
 constexpr uint32_t PART_CTX_MAX = 4096;      // contexts per buffer on the partition path; with more, the
                                              // (context, part) regions written at once overflow L2 and the
                                              // per-context cursor path is faster
 constexpr uint64_t PART_CNT_MAX = 1ull << 26; // part counters per call on the partition path
 constexpr int PART_SCAN_EPT = (int)((PART_CTX_MAX + 1 + PART_THREADS - 1) / PART_THREADS);
+constexpr int PSC_SCAN_EPT = (int)((PART_CTX_MAX + 1 + PSC_THREADS - 1) / PSC_THREADS);
 constexpr uint32_t PART2_CTX_MAX = 65536;    // contexts per buffer on the two-level partition path
 constexpr uint64_t PART2_LEN = 32768;        // records per chunk of the second pass
 constexpr int SCAN_THREADS = 512;

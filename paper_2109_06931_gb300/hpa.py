@@ -120,6 +120,7 @@ def lib(build_if_needed: bool = True):
         L.hpa_attribute_samples.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_attribute_samples_host.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_attribute_batch.argtypes = [H, C.c_uint32, u32p, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
+        L.hpa_flat_profile.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile)]
         L.hpa_tune.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile), C.c_uint32,
                                C.POINTER(hpa_options), vp]
         L.hpa_apportion_callgraph.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_gpucct)]
@@ -388,6 +389,17 @@ class Hpa:
         self.check(self.L.hpa_apportion_callgraph(self.h, bid, C.byref(pc), C.byref(g)))
         self._keep = [req]
         return incl, a, flags
+
+    def flat_profile(self, bid: int, p: Profile, capacity: int | None = None) -> Profile:
+        """hpa_flat_profile: the profile summed over contexts, keys (0, node, stall)."""
+        k = p.count()
+        pin = p.c()
+        pin.capacity = k
+        out = new_profile(max(1, k if capacity is None else capacity), p.n_stall, self.device)
+        co = out.c()
+        self.check(self.L.hpa_flat_profile(self.h, bid, C.byref(pin), C.byref(co)))
+        out.n_ctx, out.n_stall, out.n_nodes = 1, p.n_stall, co.n_nodes
+        return out
 
     def derive_metrics(self, profiles, n_ctx: int | None = None, capacity: int | None = None):
         """Cross-profile statistics (Section 4.5) and per-context warp issue rate (Section 7)."""
