@@ -176,6 +176,28 @@ typedef struct {
     uint8_t* flags;
 } hpa_gpucct;
 
+/* One context's GPU calling context tree materialised as a tree (Section
+ * 6.3, step 4: apportioning the condensed call graph equals splitting it
+ * into a tree whose call paths carry the product of the call-site ratios).
+ * DEVICE arrays of `budget` entries, filled breadth-first: roots are the
+ * condensed nodes without external callers (node order); the children of a
+ * tree node for condensed node v at scale s are, for each external call site
+ * e of v in call-site order, callee node h at scale s * r(e) with
+ * r(e) = a(e) / incl(h) (total column), omitted when that scale or incl(h)
+ * is zero.  incl[t][n_stall + 1] = incl(h) * scale.  parent / edge of a root
+ * are HPA_NO_PARENT.  *n_nodes: nodes written; *truncated: 1 when the budget
+ * cut the tree (the last level is cut in order).                            */
+typedef struct {
+    uint32_t budget;
+    uint32_t* parent;
+    uint32_t* cnode;
+    uint32_t* edge;
+    float* scale;
+    float* incl;
+    uint64_t* n_nodes;
+    uint32_t* truncated;
+} hpa_cct_tree;
+
 /* Host calling context tree: DEVICE parent array (parent[v] < n_nodes or
  * HPA_NO_PARENT).  Launch context c is CCT node c (n_ctx <= n_nodes).        */
 typedef struct {
@@ -330,6 +352,12 @@ hpa_status hpa_apportion_callgraph(hpa_handle* h, uint32_t binary_id, const hpa_
  *    = sum of p's values whose context lies in CCT node v's subtree.        */
 hpa_status hpa_propagate_inclusive(hpa_handle* h, uint32_t binary_id, const hpa_profile* p,
                                    hpa_profile* tree_out, const hpa_cct* cct, uint64_t* cct_out);
+
+/* Materialise the GPU calling context tree of requested context q of an
+ * apportioning result g (hpa_apportion_callgraph of this binary with
+ * n_stall stall reasons); see hpa_cct_tree.  Scales accumulate in FP64.    */
+hpa_status hpa_expand_gpucct(hpa_handle* h, uint32_t binary_id, const hpa_gpucct* g, uint32_t n_stall,
+                             uint32_t q, hpa_cct_tree* out);
 
 /* Flat view of a profile (Section 7: costs shown by static program structure
  * alone, regardless of calling context): out keys (ctx = 0, node, stall, val)

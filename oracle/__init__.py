@@ -47,6 +47,12 @@ def load(path: str):
     L.orc_attribute.argtypes = [u64, vp, vp, vp, u64, vp, vp, vp, vp, u32, u32]
     L.orc_inclusive_structure.restype = vp
     L.orc_inclusive_structure.argtypes = [u32, vp, u64, vp, vp, vp, vp]
+    L.orc_expand.restype = vp
+    L.orc_expand.argtypes = [u32, u32, u32, vp, vp, vp, u32, vp, vp, u32]
+    L.orc_expand_size.restype = u64; L.orc_expand_size.argtypes = [vp]
+    L.orc_expand_truncated.restype = i32; L.orc_expand_truncated.argtypes = [vp]
+    L.orc_expand_fetch.argtypes = [vp] * 6
+    L.orc_expand_free.argtypes = [vp]
     L.orc_flat.restype = vp
     L.orc_flat.argtypes = [u32, u64, vp, vp, vp]
     L.orc_inclusive_cct.restype = i32
@@ -219,3 +225,30 @@ def apportion(binary, n_stall: int, keys: KeyList, req_ctx) -> GpuCct:
     L.orc_apportion_fetch(h, _p(g.cnode_of_func), _p(g.incl), _p(g.a), _p(g.flags))
     L.orc_apportion_free(h)
     return g
+
+
+@dataclass
+class Tree:
+    parent: np.ndarray
+    cnode: np.ndarray
+    edge: np.ndarray
+    scale: np.ndarray
+    incl: np.ndarray        # [n, n_stall + 1]
+    truncated: bool
+
+
+def expand(binary, g: "GpuCct", q: int, budget: int) -> Tree:
+    """Context q of an apportioning result as a tree (Section 6.3, step 4)."""
+    L = lib()
+    cof = _c(g.cnode_of_func, np.uint32)
+    cc, ce = _c(binary.cs_caller, np.uint32), _c(binary.cs_callee, np.uint32)
+    inc, a = _c(g.incl[q], np.float64), _c(g.a[q], np.float64)
+    M = int(inc.shape[1])
+    h = L.orc_expand(int(binary.n_funcs), int(g.V), int(cc.shape[0]), _p(cof), _p(cc), _p(ce), M,
+                     _p(inc), _p(a), int(budget))
+    n = int(L.orc_expand_size(h))
+    t = Tree(np.empty(n, np.uint32), np.empty(n, np.uint32), np.empty(n, np.uint32), np.empty(n),
+             np.empty((n, M)), bool(L.orc_expand_truncated(h)))
+    L.orc_expand_fetch(h, _p(t.parent), _p(t.cnode), _p(t.edge), _p(t.scale), _p(t.incl))
+    L.orc_expand_free(h)
+    return t

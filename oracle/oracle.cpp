@@ -467,6 +467,63 @@ void* orc_apportion(uint32_t n_nodes, const uint32_t* node_func, uint32_t F, uin
 int orc_status(void* p) { return ((KeyList*)p)->status; }
 uint64_t orc_bad(void* p) { return ((KeyList*)p)->bad; }
 uint64_t orc_size(void* p) { return ((KeyList*)p)->val.size(); }
+// The GPU calling context tree of one context as a tree (Section 6.3, step
+// 4): every call path from a root of the condensed graph, breadth-first,
+// carrying the product of the ratios r(e) = a(e) / incl(callee) (total
+// column) of its call sites; children in call-site order; paths whose
+// product or whose node's cost is zero are left out; at most `budget` nodes.
+struct Tree {
+    std::vector<uint32_t> parent, cnode, edge;
+    std::vector<double> scale, incl;
+    int truncated = 0;
+};
+
+void* orc_expand(uint32_t F, uint32_t V, uint32_t E, const uint32_t* cnode_of_func, const uint32_t* cs_caller,
+                 const uint32_t* cs_callee, uint32_t M, const double* incl, const double* a, uint32_t budget) {
+    Tree* t = new Tree();
+    std::vector<uint8_t> live(V, 0), has_caller(V, 0);
+    for (uint32_t f = 0; f < F; ++f) live[cnode_of_func[f]] = 1;
+    std::vector<std::vector<uint32_t>> calls(V);             // external call sites of each condensed node
+    for (uint32_t e = 0; e < E; ++e) {
+        const uint32_t g = cnode_of_func[cs_caller[e]], h = cnode_of_func[cs_callee[e]];
+        if (g == h) continue;
+        calls[g].push_back(e);
+        has_caller[h] = 1;
+    }
+    auto add = [&](uint32_t par, uint32_t v, uint32_t e, double sc) {
+        if (t->cnode.size() >= budget) { t->truncated = 1; return; }
+        t->parent.push_back(par); t->cnode.push_back(v); t->edge.push_back(e); t->scale.push_back(sc);
+        for (uint32_t r = 0; r < M; ++r) t->incl.push_back(incl[(size_t)v * M + r] * sc);
+    };
+    for (uint32_t v = 0; v < V; ++v)
+        if (live[v] && !has_caller[v] && incl[(size_t)v * M + M - 1] > 0.0) add(0xFFFFFFFFu, v, 0xFFFFFFFFu, 1.0);
+    size_t begin = 0;
+    while (begin < t->cnode.size()) {                        // one level per round
+        const size_t end = t->cnode.size();
+        for (size_t i = begin; i < end; ++i) {
+            for (uint32_t e : calls[t->cnode[i]]) {
+                const uint32_t h = cnode_of_func[cs_callee[e]];
+                const double ih = incl[(size_t)h * M + M - 1];
+                const double r = ih > 0.0 ? a[(size_t)e * M + M - 1] / ih : 0.0;
+                const double sc = t->scale[i] * r;
+                if (sc > 0.0) add((uint32_t)i, h, e, sc);
+            }
+        }
+        begin = end;
+    }
+    return t;
+}
+uint64_t orc_expand_size(void* p) { return ((Tree*)p)->cnode.size(); }
+int orc_expand_truncated(void* p) { return ((Tree*)p)->truncated; }
+void orc_expand_fetch(void* p, uint32_t* parent, uint32_t* cnode, uint32_t* edge, double* scale, double* incl) {
+    Tree* t = (Tree*)p;
+    for (size_t i = 0; i < t->cnode.size(); ++i) {
+        parent[i] = t->parent[i]; cnode[i] = t->cnode[i]; edge[i] = t->edge[i]; scale[i] = t->scale[i];
+    }
+    for (size_t i = 0; i < t->incl.size(); ++i) incl[i] = t->incl[i];
+}
+void orc_expand_free(void* p) { delete (Tree*)p; }
+
 void orc_fetch(void* p, uint32_t* ctx, uint32_t* node, uint8_t* stall, uint64_t* val,
                uint64_t* total, uint64_t* unknown) {
     KeyList* k = (KeyList*)p;

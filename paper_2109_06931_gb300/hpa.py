@@ -78,6 +78,11 @@ class hpa_server_stats(C.Structure):
                 ("max_ms", C.c_double), ("mean_ms", C.c_double), ("busy_s", C.c_double)]
 
 
+class hpa_cct_tree(C.Structure):
+    _fields_ = [("budget", C.c_uint32), ("parent", vp), ("cnode", vp), ("edge", vp), ("scale", vp), ("incl", vp),
+                ("n_nodes", vp), ("truncated", vp)]
+
+
 class hpa_derived(C.Structure):
     _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp),
                 ("sum", vp), ("min", vp), ("max", vp), ("mean", vp), ("std", vp), ("cov", vp),
@@ -120,6 +125,8 @@ def lib(build_if_needed: bool = True):
         L.hpa_attribute_samples.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_attribute_samples_host.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_attribute_batch.argtypes = [H, C.c_uint32, u32p, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
+        L.hpa_expand_gpucct.argtypes = [H, C.c_uint32, C.POINTER(hpa_gpucct), C.c_uint32, C.c_uint32,
+                                         C.POINTER(hpa_cct_tree)]
         L.hpa_flat_profile.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile)]
         L.hpa_tune.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile), C.c_uint32,
                                C.POINTER(hpa_options), vp]
@@ -389,6 +396,23 @@ class Hpa:
         self.check(self.L.hpa_apportion_callgraph(self.h, bid, C.byref(pc), C.byref(g)))
         self._keep = [req]
         return incl, a, flags
+
+    def expand_gpucct(self, bid: int, res, req_ctx, n_stall: int, q: int, budget: int):
+        """hpa_expand_gpucct on an apportion_callgraph result `res` = (incl, a, flags)
+        for the requested contexts req_ctx: context q's GPU CCT as a tree."""
+        incl, a, flags = res
+        req = torch.as_tensor(np.asarray(req_ctx, np.uint32).view(np.int32), device=self.device)
+        g = hpa_gpucct(int(req.shape[0]), _ptr(req), _ptr(incl), _ptr(a), _ptr(flags))
+        d = self.device
+        out = dict(parent=torch.empty(budget, dtype=torch.int32, device=d), cnode=torch.empty(budget, dtype=torch.int32, device=d),
+                   edge=torch.empty(budget, dtype=torch.int32, device=d), scale=torch.empty(budget, dtype=torch.float32, device=d),
+                   incl=torch.empty((budget, n_stall + 1), dtype=torch.float32, device=d),
+                   n=torch.zeros(1, dtype=torch.int64, device=d), truncated=torch.zeros(1, dtype=torch.int32, device=d))
+        t = hpa_cct_tree(budget, _ptr(out["parent"]), _ptr(out["cnode"]), _ptr(out["edge"]), _ptr(out["scale"]),
+                         _ptr(out["incl"]), _ptr(out["n"]), _ptr(out["truncated"]))
+        self.check(self.L.hpa_expand_gpucct(self.h, bid, C.byref(g), n_stall, q, C.byref(t)))
+        self._keep = [req]
+        return out
 
     def flat_profile(self, bid: int, p: Profile, capacity: int | None = None) -> Profile:
         """hpa_flat_profile: the profile summed over contexts, keys (0, node, stall)."""

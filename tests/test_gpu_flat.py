@@ -61,3 +61,32 @@ def test_global_gpu_cct_is_apportioning_of_the_flat_profile(H):
     H.sync()
     ref = oracle.apportion(B, 16, oracle.flat(16, oracle.attribute_samples(B, S)), np.array([0], np.uint32))
     check(res, ref)
+
+
+@pytest.mark.parametrize("which,ctxs,budget", [("plain", [0, 7, 499], 1 << 20), ("large", [3, 12_345], 1 << 20),
+                                               ("plain", [5], 300)])
+def test_expanded_gpu_cct(H, which, ctxs, budget):
+    """Context q's GPU CCT as a tree: the same nodes, parents and call sites
+    as the oracle's expansion of its own apportioning, scales and inclusive
+    costs within 1e-5."""
+    w = synth.PLAIN if which == "plain" else synth.LARGE
+    B = w.binary()
+    bid = H.load_structure(B)
+    S = w.samples(B, device="cuda", n=min(w.n_samples, 3_000_000))
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    res = H.apportion_callgraph(bid, p, ctxs)
+    H.sync()
+    g = oracle.apportion(B, 16, oracle.attribute_samples(B, S), np.array(ctxs, np.uint32))
+    for q in range(len(ctxs)):
+        t = H.expand_gpucct(bid, res, ctxs, 16, q, budget)
+        H.sync()
+        ref = oracle.expand(B, g, q, budget)
+        n = int(t["n"].item())
+        assert n == len(ref.cnode) and bool(t["truncated"].item()) == ref.truncated
+        assert np.array_equal(t["cnode"][:n].cpu().numpy().view(np.uint32), ref.cnode)
+        assert np.array_equal(t["parent"][:n].cpu().numpy().view(np.uint32), ref.parent)
+        assert np.array_equal(t["edge"][:n].cpu().numpy().view(np.uint32), ref.edge)
+        np.testing.assert_allclose(t["scale"][:n].cpu().numpy(), ref.scale, rtol=1e-5, atol=1e-30)
+        got = t["incl"][:n].cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(got - ref.incl) <= 1e-5 * np.abs(ref.incl) + 1e-30)

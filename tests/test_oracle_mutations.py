@@ -10,6 +10,7 @@ import pytest
 import oracle
 import test_oracle_apportion as TA
 import test_oracle_attribution as TT
+import test_oracle_expand as TX
 import test_oracle_flat as TF
 import test_oracle_inclusive_derive as TI
 
@@ -38,6 +39,8 @@ MUTATIONS = [
      [lambda o: TI.test_structure_inclusive_brute(o)]),
     ("cct-skip-self", "while (h != NO_PARENT) {\n            host", "h = cct_parent[h];\n        while (h != NO_PARENT) {\n            host",
      [lambda o: TI.test_cct_inclusive(o)]),
+    ("expand-no-product", "const double sc = t->scale[i] * r;", "const double sc = r;",
+     [lambda o: TX.test_ratios_are_call_site_weights(o, 1)]),
     ("flat-drops-unknown", "agg[std::make_pair(knode[i], (uint32_t)kstall[i])] += kval[i];",
      "if (knode[i] != UNKNOWN) agg[std::make_pair(knode[i], (uint32_t)kstall[i])] += kval[i];",
      [lambda o: TF.test_hand_computed_example(o), lambda o: TF.test_conservation_and_order_on_a_profile(o)]),
