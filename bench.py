@@ -170,6 +170,19 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     k2 = p2.count()
     ms = timed(stream, lambda: (h.propagate_inclusive(bid, p2), h.sync()), reps=2)
     out["inclusive_tree"] = {"ms": ms, "keys": k2, "keys_per_s": k2 / (ms / 1e3)}
+    # flat view of the full profile, and one context's GPU CCT as a tree
+    ms = timed(stream, lambda: (h.flat_profile(bid, prof), h.sync()), reps=2)
+    fp = h.flat_profile(bid, prof)
+    h.sync()
+    out["flat_view"] = {"ms": ms, "keys_in": K, "keys_out": fp.count(), "keys_per_s": K / (ms / 1e3)}
+    res = h.apportion_callgraph(bid, prof, req[:1])
+    h.sync()
+    budget = 1 << 20
+    ms = timed(stream, lambda: (h.expand_gpucct(bid, res, req[:1], w.n_stall, 0, budget), h.sync()), reps=2)
+    t = h.expand_gpucct(bid, res, req[:1], w.n_stall, 0, budget)
+    h.sync()
+    out["gpucct_tree"] = {"ms": ms, "nodes": int(t["n"].item()), "truncated": bool(t["truncated"].item()),
+                          "budget": budget}
     profs = [p2]
     for i in range(3):
         Si = w.samples(B, device=dev, n=w.n_samples // 10, start=(i + 1) * w.n_samples)
@@ -179,6 +192,11 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     kk = sum(p.count() for p in profs)
     ms = timed(stream, lambda: (h.derive_metrics(profs), h.sync()), reps=2)
     out["derive"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
+    # sparse layouts of the same profiles (context-major and profile-major)
+    ms = timed(stream, lambda: (h.build_cms(profs), h.sync()), reps=2)
+    out["cms"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
+    ms = timed(stream, lambda: (h.build_pms(profs), h.sync()), reps=2)
+    out["pms"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
     return out
 
 

@@ -371,6 +371,49 @@ hpa_status hpa_expand_gpucct(hpa_handle* h, uint32_t binary_id, const hpa_gpucct
  * out->capacity is too small, with *out->n_keys the size needed.            */
 hpa_status hpa_flat_profile(hpa_handle* h, uint32_t binary_id, const hpa_profile* p, hpa_profile* out);
 
+/* Sparse layouts of several profiles (Section 6.2), built on the device.  A
+ * calling context is a (launch context, structure node) pair, a metric a
+ * stall reason, a profile one input key list (device keys of one binary, as
+ * produced by hpa_attribute_samples).  Outputs are caller-allocated DEVICE
+ * arrays with capacities; counts (DEVICE) receives the sizes needed, and
+ * HPA_E_CAPACITY (at hpa_sync) reports an array too small.
+ *
+ * CMS, context-major: planes = contexts of the union of the profiles in
+ * (ctx, node) order; plane_off[i] .. plane_off[i + 1] index the plane's
+ * non-empty metrics (metric_id, ascending), the sparse metric index;
+ * metric_off[k] .. metric_off[k + 1] index its (pid, val) entries, one per
+ * profile holding that (context, metric), ascending by profile.
+ * counts[0..2] = planes, metric entries, values.  Needs
+ * (n_nodes + 1) * 2^stall_bits * 2^ceil(log2 n_profiles) <= 2^32.          */
+typedef struct {
+    uint64_t cap_planes, cap_metrics, cap_values;
+    uint32_t* plane_ctx;
+    uint32_t* plane_node;
+    uint64_t* plane_off;      /* [cap_planes + 1]  */
+    uint8_t* metric_id;
+    uint64_t* metric_off;     /* [cap_metrics + 1] */
+    uint32_t* pid;
+    uint64_t* val;
+    uint64_t* counts;         /* [3] */
+} hpa_cms;
+hpa_status hpa_build_cms(hpa_handle* h, const hpa_profile* const* ps, uint32_t n_profiles, hpa_cms* out);
+
+/* PMS, profile-major: prof_off[p] .. prof_off[p + 1] index profile p's
+ * planes (its contexts in (ctx, node) order); plane_off[i] .. plane_off[i +
+ * 1] index the plane's (metric_id, val) entries, ascending by metric.
+ * counts[0..1] = planes, values.                                            */
+typedef struct {
+    uint64_t cap_planes, cap_values;
+    uint64_t* prof_off;       /* [n_profiles + 1]  */
+    uint32_t* plane_ctx;
+    uint32_t* plane_node;
+    uint64_t* plane_off;      /* [cap_planes + 1]  */
+    uint8_t* metric_id;
+    uint64_t* val;
+    uint64_t* counts;         /* [2] */
+} hpa_pms;
+hpa_status hpa_build_pms(hpa_handle* h, const hpa_profile* const* ps, uint32_t n_profiles, hpa_pms* out);
+
 /* Derived metrics over n_profiles profiles (Section 4.5) and the warp issue
  * rate per context (Section 7, W = (S - S_stall) / S with the handle's
  * issued_mask).  ps: HOST array of profile descriptors with DEVICE data.    */

@@ -53,6 +53,13 @@ def load(path: str):
     L.orc_expand_truncated.restype = i32; L.orc_expand_truncated.argtypes = [vp]
     L.orc_expand_fetch.argtypes = [vp] * 6
     L.orc_expand_free.argtypes = [vp]
+    L.orc_cms.restype = vp
+    L.orc_cms.argtypes = [u64, vp, vp, vp, vp, vp]
+    L.orc_pms.restype = vp
+    L.orc_pms.argtypes = [u32, u64, vp, vp, vp, vp, vp]
+    L.orc_sparse_sizes.argtypes = [vp, vp]
+    L.orc_sparse_fetch.argtypes = [vp] * 9
+    L.orc_sparse_free.argtypes = [vp]
     L.orc_flat.restype = vp
     L.orc_flat.argtypes = [u32, u64, vp, vp, vp]
     L.orc_inclusive_cct.restype = i32
@@ -252,3 +259,48 @@ def expand(binary, g: "GpuCct", q: int, budget: int) -> Tree:
     L.orc_expand_fetch(h, _p(t.parent), _p(t.cnode), _p(t.edge), _p(t.scale), _p(t.incl))
     L.orc_expand_free(h)
     return t
+
+
+@dataclass
+class Sparse:
+    prof_off: np.ndarray      # PMS only
+    plane_ctx: np.ndarray
+    plane_node: np.ndarray
+    plane_off: np.ndarray
+    metric_id: np.ndarray
+    metric_off: np.ndarray    # CMS only
+    pid: np.ndarray           # CMS only
+    val: np.ndarray
+
+
+def _flatten(profiles):
+    pid = np.concatenate([np.full(len(k), p, np.uint32) for p, k in enumerate(profiles)])
+    cat = lambda f, dt: _c(np.concatenate([getattr(k, f) for k in profiles]).astype(dt), dt)
+    return _c(pid, np.uint32), cat("ctx", np.uint32), cat("node", np.uint32), cat("stall", np.uint8), cat("val", np.uint64)
+
+
+def _sparse(L, h):
+    sz = np.zeros(4, np.uint64)
+    L.orc_sparse_sizes(h, _p(sz))
+    npl, nm, nv, npo = (int(x) for x in sz)
+    o = Sparse(np.zeros(npo, np.uint64), np.zeros(npl, np.uint32), np.zeros(npl, np.uint32), np.zeros(npl + 1, np.uint64),
+               np.zeros(nm, np.uint32), np.zeros(nm + 1 if nm or nv else 1, np.uint64), np.zeros(nv, np.uint32),
+               np.zeros(nv, np.uint64))
+    L.orc_sparse_fetch(h, _p(o.prof_off), _p(o.plane_ctx), _p(o.plane_node), _p(o.plane_off), _p(o.metric_id),
+                       _p(o.metric_off), _p(o.pid), _p(o.val))
+    L.orc_sparse_free(h)
+    return o
+
+
+def cms(profiles) -> Sparse:
+    """Context-major sparse layout of several key lists (Section 6.2)."""
+    L = lib()
+    a = _flatten(profiles)
+    return _sparse(L, L.orc_cms(a[0].shape[0], *[_p(x) for x in a]))
+
+
+def pms(profiles) -> Sparse:
+    """Profile-major sparse layout of several key lists (Section 6.2)."""
+    L = lib()
+    a = _flatten(profiles)
+    return _sparse(L, L.orc_pms(len(profiles), a[0].shape[0], *[_p(x) for x in a]))

@@ -524,6 +524,79 @@ void orc_expand_fetch(void* p, uint32_t* parent, uint32_t* cnode, uint32_t* edge
 }
 void orc_expand_free(void* p) { delete (Tree*)p; }
 
+// Sparse layouts of several profiles (Section 6.2).  Input: the keys of all
+// profiles flattened, with each key's profile index.  CMS orders everything
+// by (context = (ctx, node), metric = stall, profile); PMS by (profile,
+// context, metric).  Offsets are CSR-style, with one extra closing entry.
+struct Sparse {
+    std::vector<uint64_t> prof_off, plane_off, metric_off;
+    std::vector<uint32_t> plane_ctx, plane_node, pid;
+    std::vector<uint32_t> metric_id;
+    std::vector<uint64_t> val;
+};
+
+void* orc_cms(uint64_t n, const uint32_t* kp, const uint32_t* kctx, const uint32_t* knode, const uint8_t* kstall,
+              const uint64_t* kval) {
+    Sparse* o = new Sparse();
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, uint64_t> m;   // (ctx, node, stall, p)
+    for (uint64_t i = 0; i < n; ++i) m[std::make_tuple(kctx[i], knode[i], (uint32_t)kstall[i], kp[i])] = kval[i];
+    bool first = true;
+    uint32_t pc = 0, pn = 0, ps = 0;
+    for (auto& kv : m) {
+        const uint32_t c = std::get<0>(kv.first), nd = std::get<1>(kv.first), r = std::get<2>(kv.first);
+        const bool new_plane = first || c != pc || nd != pn;
+        const bool new_metric = new_plane || r != ps;
+        if (new_plane) { o->plane_ctx.push_back(c); o->plane_node.push_back(nd); o->plane_off.push_back(o->metric_id.size()); }
+        if (new_metric) { o->metric_id.push_back(r); o->metric_off.push_back(o->val.size()); }
+        o->pid.push_back(std::get<3>(kv.first));
+        o->val.push_back(kv.second);
+        first = false; pc = c; pn = nd; ps = r;
+    }
+    o->plane_off.push_back(o->metric_id.size());
+    o->metric_off.push_back(o->val.size());
+    return o;
+}
+
+void* orc_pms(uint32_t P, uint64_t n, const uint32_t* kp, const uint32_t* kctx, const uint32_t* knode,
+              const uint8_t* kstall, const uint64_t* kval) {
+    Sparse* o = new Sparse();
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, uint64_t> m;   // (p, ctx, node, stall)
+    for (uint64_t i = 0; i < n; ++i) m[std::make_tuple(kp[i], kctx[i], knode[i], (uint32_t)kstall[i])] = kval[i];
+    o->prof_off.assign(P + 1, 0);
+    bool first = true;
+    uint32_t pp = 0, pc = 0, pn = 0;
+    for (auto& kv : m) {
+        const uint32_t p = std::get<0>(kv.first), c = std::get<1>(kv.first), nd = std::get<2>(kv.first);
+        if (first || p != pp || c != pc || nd != pn) {
+            o->plane_ctx.push_back(c); o->plane_node.push_back(nd); o->plane_off.push_back(o->val.size());
+            o->prof_off[p + 1] = o->plane_ctx.size();
+        }
+        o->metric_id.push_back(std::get<3>(kv.first));
+        o->val.push_back(kv.second);
+        first = false; pp = p; pc = c; pn = nd;
+    }
+    for (uint32_t p = 1; p <= P; ++p) o->prof_off[p] = std::max(o->prof_off[p], o->prof_off[p - 1]);
+    o->plane_off.push_back(o->val.size());
+    return o;
+}
+
+void orc_sparse_sizes(void* p, uint64_t* sz) {
+    Sparse* o = (Sparse*)p;
+    sz[0] = o->plane_ctx.size(); sz[1] = o->metric_id.size(); sz[2] = o->val.size(); sz[3] = o->prof_off.size();
+}
+void orc_sparse_fetch(void* p, uint64_t* prof_off, uint32_t* plane_ctx, uint32_t* plane_node, uint64_t* plane_off,
+                      uint32_t* metric_id, uint64_t* metric_off, uint32_t* pid, uint64_t* val) {
+    Sparse* o = (Sparse*)p;
+    for (size_t i = 0; i < o->prof_off.size(); ++i) prof_off[i] = o->prof_off[i];
+    for (size_t i = 0; i < o->plane_ctx.size(); ++i) { plane_ctx[i] = o->plane_ctx[i]; plane_node[i] = o->plane_node[i]; }
+    for (size_t i = 0; i < o->plane_off.size(); ++i) plane_off[i] = o->plane_off[i];
+    for (size_t i = 0; i < o->metric_id.size(); ++i) metric_id[i] = o->metric_id[i];
+    for (size_t i = 0; i < o->metric_off.size(); ++i) metric_off[i] = o->metric_off[i];
+    for (size_t i = 0; i < o->pid.size(); ++i) pid[i] = o->pid[i];
+    for (size_t i = 0; i < o->val.size(); ++i) val[i] = o->val[i];
+}
+void orc_sparse_free(void* p) { delete (Sparse*)p; }
+
 void orc_fetch(void* p, uint32_t* ctx, uint32_t* node, uint8_t* stall, uint64_t* val,
                uint64_t* total, uint64_t* unknown) {
     KeyList* k = (KeyList*)p;

@@ -83,6 +83,17 @@ class hpa_cct_tree(C.Structure):
                 ("n_nodes", vp), ("truncated", vp)]
 
 
+class hpa_cms(C.Structure):
+    _fields_ = [("cap_planes", C.c_uint64), ("cap_metrics", C.c_uint64), ("cap_values", C.c_uint64),
+                ("plane_ctx", vp), ("plane_node", vp), ("plane_off", vp), ("metric_id", vp), ("metric_off", vp),
+                ("pid", vp), ("val", vp), ("counts", vp)]
+
+
+class hpa_pms(C.Structure):
+    _fields_ = [("cap_planes", C.c_uint64), ("cap_values", C.c_uint64), ("prof_off", vp), ("plane_ctx", vp),
+                ("plane_node", vp), ("plane_off", vp), ("metric_id", vp), ("val", vp), ("counts", vp)]
+
+
 class hpa_derived(C.Structure):
     _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp),
                 ("sum", vp), ("min", vp), ("max", vp), ("mean", vp), ("std", vp), ("cov", vp),
@@ -127,6 +138,8 @@ def lib(build_if_needed: bool = True):
         L.hpa_attribute_batch.argtypes = [H, C.c_uint32, u32p, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_expand_gpucct.argtypes = [H, C.c_uint32, C.POINTER(hpa_gpucct), C.c_uint32, C.c_uint32,
                                          C.POINTER(hpa_cct_tree)]
+        L.hpa_build_cms.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_cms)]
+        L.hpa_build_pms.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_pms)]
         L.hpa_flat_profile.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile)]
         L.hpa_tune.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile), C.c_uint32,
                                C.POINTER(hpa_options), vp]
@@ -412,6 +425,42 @@ class Hpa:
                          _ptr(out["incl"]), _ptr(out["n"]), _ptr(out["truncated"]))
         self.check(self.L.hpa_expand_gpucct(self.h, bid, C.byref(g), n_stall, q, C.byref(t)))
         self._keep = [req]
+        return out
+
+    def _profile_array(self, profiles):
+        cps = [p.c() for p in profiles]
+        for c, p in zip(cps, profiles):
+            c.capacity = p.count()
+        return cps, (C.POINTER(hpa_profile) * len(cps))(*[C.pointer(c) for c in cps])
+
+    def build_cms(self, profiles):
+        """hpa_build_cms: context-major sparse layout (Section 6.2) of the profiles."""
+        total = sum(p.count() for p in profiles)
+        d, n = self.device, max(1, total)
+        t = lambda m, dt: torch.empty(m, dtype=dt, device=d)
+        out = dict(plane_ctx=t(n, torch.int32), plane_node=t(n, torch.int32), plane_off=t(n + 1, torch.int64),
+                   metric_id=t(n, torch.uint8), metric_off=t(n + 1, torch.int64), pid=t(n, torch.int32),
+                   val=t(n, torch.int64), counts=torch.zeros(3, dtype=torch.int64, device=d))
+        o = hpa_cms(n, n, n, *[_ptr(out[k]) for k in ("plane_ctx", "plane_node", "plane_off", "metric_id",
+                                                        "metric_off", "pid", "val", "counts")])
+        cps, arr = self._profile_array(profiles)
+        self.check(self.L.hpa_build_cms(self.h, arr, len(cps), C.byref(o)))
+        self._keep = [cps, arr]
+        return out
+
+    def build_pms(self, profiles):
+        """hpa_build_pms: profile-major sparse layout (Section 6.2) of the profiles."""
+        total = sum(p.count() for p in profiles)
+        d, n = self.device, max(1, total)
+        t = lambda m, dt: torch.empty(m, dtype=dt, device=d)
+        out = dict(prof_off=t(len(profiles) + 1, torch.int64), plane_ctx=t(n, torch.int32), plane_node=t(n, torch.int32),
+                   plane_off=t(n + 1, torch.int64), metric_id=t(n, torch.uint8), val=t(n, torch.int64),
+                   counts=torch.zeros(2, dtype=torch.int64, device=d))
+        o = hpa_pms(n, n, *[_ptr(out[k]) for k in ("prof_off", "plane_ctx", "plane_node", "plane_off", "metric_id",
+                                                    "val", "counts")])
+        cps, arr = self._profile_array(profiles)
+        self.check(self.L.hpa_build_pms(self.h, arr, len(cps), C.byref(o)))
+        self._keep = [cps, arr]
         return out
 
     def flat_profile(self, bid: int, p: Profile, capacity: int | None = None) -> Profile:

@@ -13,6 +13,7 @@ import test_oracle_attribution as TT
 import test_oracle_expand as TX
 import test_oracle_flat as TF
 import test_oracle_inclusive_derive as TI
+import test_oracle_sparse as TS
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")
 
@@ -41,6 +42,9 @@ MUTATIONS = [
      [lambda o: TI.test_cct_inclusive(o)]),
     ("expand-no-product", "const double sc = t->scale[i] * r;", "const double sc = r;",
      [lambda o: TX.test_ratios_are_call_site_weights(o, 1)]),
+    ("cms-profile-major-order", "m[std::make_tuple(kctx[i], knode[i], (uint32_t)kstall[i], kp[i])] = kval[i];",
+     "m[std::make_tuple(kctx[i], knode[i], kp[i], (uint32_t)kstall[i])] = kval[i];",
+     [lambda o: TS.test_hand_computed_cms(o), lambda o: TS.test_cms_reconstructs_every_profile(o)]),
     ("flat-drops-unknown", "agg[std::make_pair(knode[i], (uint32_t)kstall[i])] += kval[i];",
      "if (knode[i] != UNKNOWN) agg[std::make_pair(knode[i], (uint32_t)kstall[i])] += kval[i];",
      [lambda o: TF.test_hand_computed_example(o), lambda o: TF.test_conservation_and_order_on_a_profile(o)]),
@@ -65,7 +69,7 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new, pins):
         for pin in pins:
             try:
                 pin(oracle)
-            except (AssertionError, ValueError, KeyError):
+            except (AssertionError, ValueError, KeyError, IndexError):
                 caught += 1
         assert caught >= 1, f"planted mistake '{name}' passed every pin"
     finally:
