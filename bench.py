@@ -150,7 +150,9 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     """Timings of the other rows of the path on the benchmark's profile:
     GPU calling-context trees (64 contexts), inclusive propagation over the
     host CCT (all contexts) and over the structure tree (a 10 % sample of the
-    profile, to bound scratch), derived metrics over 4 profiles."""
+    profile, to bound scratch), derived metrics over 4 profiles, the flat
+    view, one context's GPU CCT as a tree, both sparse layouts, and the
+    unification of 16 profiles' calling context trees."""
     from paper_2109_06931_gb300 import hpa as H
     out = {}
     K = prof.count()
@@ -197,6 +199,16 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     out["cms"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
     ms = timed(stream, lambda: (h.build_pms(profs), h.sync()), reps=2)
     out["pms"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
+    # calling context trees of 16 profiles (subsets of a 2M-node master tree) unified
+    ccts = [tuple(torch.from_numpy(a.view(t)).to(dev) for a, t in zip(c, (np.int32, np.int16, np.int64)))
+            for c in synth.make_profile_ccts(3, 2_000_000, 64, 16, 0.25)]
+    torch.cuda.synchronize()
+    nin = sum(int(c[0].shape[0]) for c in ccts)
+    ms = timed(stream, lambda: (h.unify_ccts(ccts), h.sync()), reps=2)
+    u = h.unify_ccts(ccts)
+    h.sync()
+    out["unify"] = {"ms": ms, "profiles": len(ccts), "nodes_in": nin, "nodes_out": int(u["n"].item()),
+                    "nodes_per_s": nin / (ms / 1e3)}
     return out
 
 

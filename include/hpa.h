@@ -414,6 +414,36 @@ typedef struct {
 } hpa_pms;
 hpa_status hpa_build_pms(hpa_handle* h, const hpa_profile* const* ps, uint32_t n_profiles, hpa_pms* out);
 
+/* Call-path profile unification (Section 6.1): the calling context trees of
+ * several profiles merged into one.  Input CCT p: DEVICE arrays of n_nodes
+ * entries -- parent (index in the same CCT, smaller than the node's own, or
+ * HPA_NO_PARENT for a root), load module (< 0xFFFF) and offset (< 2^48) of
+ * the node's call site.  A merged node is identified by its merged parent
+ * and its (module, offset).  Output (DEVICE): uid[i] for every input node,
+ * the CCTs concatenated in order; the merged tree's parent / module / offset
+ * (capacity entries), numbered in the order of first occurrence in that
+ * concatenation (so parents come before their children); *n_unified its
+ * size.  Total nodes in [1, 2^31).  The call waits once on the handle's
+ * stream (it reads the deepest level back to size the level loop), so it
+ * cannot be captured into a graph.  Errors at hpa_sync: HPA_E_INVALID_TABLE
+ * for a parent that does not precede its node or a site out of range (the
+ * outputs are then unspecified), HPA_E_CAPACITY for a small capacity.       */
+typedef struct {
+    uint32_t n_nodes;
+    const uint32_t* parent;
+    const uint16_t* module;
+    const uint64_t* offset;
+} hpa_cct_nodes;
+typedef struct {
+    uint32_t capacity;
+    uint32_t* uid;
+    uint32_t* parent;
+    uint16_t* module;
+    uint64_t* offset;
+    uint64_t* n_unified;
+} hpa_cct_unified;
+hpa_status hpa_unify_ccts(hpa_handle* h, const hpa_cct_nodes* ccts, uint32_t n, hpa_cct_unified* out);
+
 /* Derived metrics over n_profiles profiles (Section 4.5) and the warp issue
  * rate per context (Section 7, W = (S - S_stall) / S with the handle's
  * issued_mask).  ps: HOST array of profile descriptors with DEVICE data.    */

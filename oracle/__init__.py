@@ -53,6 +53,12 @@ def load(path: str):
     L.orc_expand_truncated.restype = i32; L.orc_expand_truncated.argtypes = [vp]
     L.orc_expand_fetch.argtypes = [vp] * 6
     L.orc_expand_free.argtypes = [vp]
+    L.orc_unify.restype = vp
+    L.orc_unify.argtypes = [u32, vp, vp, vp, vp]
+    L.orc_unify_size.restype = u64; L.orc_unify_size.argtypes = [vp]
+    L.orc_unify_status.restype = i32; L.orc_unify_status.argtypes = [vp]
+    L.orc_unify_fetch.argtypes = [vp] * 5
+    L.orc_unify_free.argtypes = [vp]
     L.orc_cms.restype = vp
     L.orc_cms.argtypes = [u64, vp, vp, vp, vp, vp]
     L.orc_pms.restype = vp
@@ -304,3 +310,26 @@ def pms(profiles) -> Sparse:
     L = lib()
     a = _flatten(profiles)
     return _sparse(L, L.orc_pms(len(profiles), a[0].shape[0], *[_p(x) for x in a]))
+
+
+def unify(ccts):
+    """Call-path profile unification (Section 6.1).  ccts: [(parent, module,
+    offset)] per profile.  Returns (uid per input node, concatenated; merged
+    parent, module, offset)."""
+    L = lib()
+    base = np.zeros(len(ccts) + 1, np.uint64)
+    base[1:] = np.cumsum([len(c[0]) for c in ccts])
+    par = _c(np.concatenate([c[0] for c in ccts]), np.uint32)
+    mod = _c(np.concatenate([c[1] for c in ccts]), np.uint16)
+    off = _c(np.concatenate([c[2] for c in ccts]), np.uint64)
+    h = L.orc_unify(len(ccts), _p(base), _p(par), _p(mod), _p(off))
+    st = L.orc_unify_status(h)
+    if st:
+        L.orc_unify_free(h)
+        raise ValueError(f"oracle unify status {st}")
+    n = int(L.orc_unify_size(h))
+    uid = np.empty(par.shape[0], np.uint32)
+    up, um, uo = np.empty(n, np.uint32), np.empty(n, np.uint16), np.empty(n, np.uint64)
+    L.orc_unify_fetch(h, _p(uid), _p(up), _p(um), _p(uo))
+    L.orc_unify_free(h)
+    return uid, up, um, uo

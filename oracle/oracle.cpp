@@ -597,6 +597,52 @@ void orc_sparse_fetch(void* p, uint64_t* prof_off, uint32_t* plane_ctx, uint32_t
 }
 void orc_sparse_free(void* p) { delete (Sparse*)p; }
 
+// Call-path profile unification (Section 6.1): the nodes of all CCTs in
+// order; a node is identified by its merged parent and its (module, offset);
+// a new identity gets the next merged id.
+struct Unified {
+    std::vector<uint32_t> uid, parent, module;
+    std::vector<uint64_t> offset;
+    int status = OK;
+};
+
+void* orc_unify(uint32_t n_cct, const uint64_t* base, const uint32_t* parent, const uint16_t* module,
+                const uint64_t* offset) {
+    Unified* u = new Unified();
+    std::map<std::tuple<uint32_t, uint32_t, uint64_t>, uint32_t> ids;
+    const uint64_t N = base[n_cct];
+    u->uid.assign(N, 0);
+    for (uint32_t p = 0; p < n_cct; ++p)
+        for (uint64_t i = base[p]; i < base[p + 1]; ++i) {
+            const uint32_t par = parent[i];
+            if (par != 0xFFFFFFFFu && base[p] + par >= i) { u->status = INVALID_ARG; return u; }
+            const uint32_t up = par == 0xFFFFFFFFu ? 0xFFFFFFFFu : u->uid[base[p] + par];
+            const auto key = std::make_tuple(up, (uint32_t)module[i], offset[i]);
+            auto it = ids.find(key);
+            if (it == ids.end()) {
+                const uint32_t id = (uint32_t)u->parent.size();
+                ids[key] = id;
+                u->parent.push_back(up);
+                u->module.push_back(module[i]);
+                u->offset.push_back(offset[i]);
+                u->uid[i] = id;
+            } else {
+                u->uid[i] = it->second;
+            }
+        }
+    return u;
+}
+uint64_t orc_unify_size(void* p) { return ((Unified*)p)->parent.size(); }
+int orc_unify_status(void* p) { return ((Unified*)p)->status; }
+void orc_unify_fetch(void* p, uint32_t* uid, uint32_t* parent, uint16_t* module, uint64_t* offset) {
+    Unified* u = (Unified*)p;
+    for (size_t i = 0; i < u->uid.size(); ++i) uid[i] = u->uid[i];
+    for (size_t i = 0; i < u->parent.size(); ++i) {
+        parent[i] = u->parent[i]; module[i] = (uint16_t)u->module[i]; offset[i] = u->offset[i];
+    }
+}
+void orc_unify_free(void* p) { delete (Unified*)p; }
+
 void orc_fetch(void* p, uint32_t* ctx, uint32_t* node, uint8_t* stall, uint64_t* val,
                uint64_t* total, uint64_t* unknown) {
     KeyList* k = (KeyList*)p;

@@ -94,6 +94,15 @@ class hpa_pms(C.Structure):
                 ("plane_node", vp), ("plane_off", vp), ("metric_id", vp), ("val", vp), ("counts", vp)]
 
 
+class hpa_cct_nodes(C.Structure):
+    _fields_ = [("n_nodes", C.c_uint32), ("parent", vp), ("module", vp), ("offset", vp)]
+
+
+class hpa_cct_unified(C.Structure):
+    _fields_ = [("capacity", C.c_uint32), ("uid", vp), ("parent", vp), ("module", vp), ("offset", vp),
+                ("n_unified", vp)]
+
+
 class hpa_derived(C.Structure):
     _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp),
                 ("sum", vp), ("min", vp), ("max", vp), ("mean", vp), ("std", vp), ("cov", vp),
@@ -138,6 +147,7 @@ def lib(build_if_needed: bool = True):
         L.hpa_attribute_batch.argtypes = [H, C.c_uint32, u32p, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_expand_gpucct.argtypes = [H, C.c_uint32, C.POINTER(hpa_gpucct), C.c_uint32, C.c_uint32,
                                          C.POINTER(hpa_cct_tree)]
+        L.hpa_unify_ccts.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_cct_unified)]
         L.hpa_build_cms.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_cms)]
         L.hpa_build_pms.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_pms)]
         L.hpa_flat_profile.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile)]
@@ -425,6 +435,24 @@ class Hpa:
                          _ptr(out["incl"]), _ptr(out["n"]), _ptr(out["truncated"]))
         self.check(self.L.hpa_expand_gpucct(self.h, bid, C.byref(g), n_stall, q, C.byref(t)))
         self._keep = [req]
+        return out
+
+    def unify_ccts(self, ccts, capacity: int | None = None):
+        """hpa_unify_ccts: ccts = [(parent, module, offset)] device tensors per
+        profile (int32 / int16 / int64).  Returns uid per input node and the
+        merged tree's parent / module / offset and size."""
+        N = sum(int(c[0].shape[0]) for c in ccts)
+        cap = N if capacity is None else capacity
+        d = self.device
+        out = dict(uid=torch.empty(N, dtype=torch.int32, device=d), parent=torch.empty(cap, dtype=torch.int32, device=d),
+                   module=torch.empty(cap, dtype=torch.int16, device=d), offset=torch.empty(cap, dtype=torch.int64, device=d),
+                   n=torch.zeros(1, dtype=torch.int64, device=d))
+        desc = (hpa_cct_nodes * len(ccts))(*[hpa_cct_nodes(int(c[0].shape[0]), _ptr(c[0]), _ptr(c[1]), _ptr(c[2]))
+                                             for c in ccts])
+        o = hpa_cct_unified(cap, _ptr(out["uid"]), _ptr(out["parent"]), _ptr(out["module"]), _ptr(out["offset"]),
+                            _ptr(out["n"]))
+        self.check(self.L.hpa_unify_ccts(self.h, desc, len(ccts), C.byref(o)))
+        self._keep = [ccts, desc]
         return out
 
     def _profile_array(self, profiles):

@@ -362,6 +362,51 @@ def make_cct_levels(seed: int, n_nodes: int, max_depth: int, max_fanout: int) ->
     return out
 
 
+def make_profile_ccts(seed: int, n_master: int, depth: int, n_profiles: int, keep: float, n_sites: int = 0):
+    """Per-profile calling context trees for unification: a master tree whose
+    call sites repeat under different parents, as a callee's call sites do
+    under each of its calling contexts (site = a seeded pick per depth among
+    n_sites // 8 groups, plus the node's rank among its siblings, so that
+    siblings never share one; module = site % 8, offset = 0x1000 + 16 site).
+    Profile p keeps a seeded subset of the master's nodes closed under
+    parents, in master order.  Returns [(parent, module, offset)] with parents
+    as indices within the profile (HPA_NO_PARENT for a root)."""
+    FAN = 8
+    par = make_cct_levels(seed, n_master, depth, FAN)
+    idx = np.arange(n_master)
+    dep = np.zeros(n_master, np.int64)
+    anc = par.astype(np.int64)
+    while True:                                         # depth by walking every node up one step at a time
+        up = anc != NO_PARENT
+        if not up.any():
+            break
+        dep += up
+        anc[up] = par[anc[up]].astype(np.int64)
+    order = np.argsort(par, kind="stable")
+    first = np.searchsorted(par[order], par[order], side="left")
+    rank = np.empty(n_master, np.int64)
+    rank[order] = np.arange(n_master) - first
+    assert rank.max(initial=0) < FAN
+    groups = max(1, (n_sites or max(64, n_master // 4)) // FAN)
+    site = np_below(seed, 503, dep, groups).astype(np.int64) * FAN + rank
+    module = (site % 8).astype(np.uint16)
+    offset = (0x1000 + 16 * site).astype(np.uint64)
+    lv = np.argsort(dep, kind="stable")
+    by_level = np.split(lv, np.searchsorted(dep[lv], np.arange(1, int(dep.max(initial=0)) + 1)))
+    out = []
+    for p in range(n_profiles):
+        kept = np_unif(seed, 510 + p, idx) < keep
+        for d in range(int(dep.max(initial=0)), 0, -1):   # close under parents, deepest level first
+            v = by_level[d]
+            kept[par[v[kept[v]]]] = True
+        local = np.cumsum(kept) - 1
+        sel = np.nonzero(kept)[0]
+        mp = par[sel]
+        lp = np.where(mp == NO_PARENT, NO_PARENT, local[np.minimum(mp, n_master - 1)]).astype(np.uint32)
+        out.append((lp, module[sel], offset[sel]))
+    return out
+
+
 # ---------------------------------------------------------------- samples
 @dataclasses.dataclass
 class Samples:

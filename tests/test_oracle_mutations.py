@@ -14,6 +14,7 @@ import test_oracle_expand as TX
 import test_oracle_flat as TF
 import test_oracle_inclusive_derive as TI
 import test_oracle_sparse as TS
+import test_oracle_unify as TU
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")
 
@@ -45,6 +46,9 @@ MUTATIONS = [
     ("cms-profile-major-order", "m[std::make_tuple(kctx[i], knode[i], (uint32_t)kstall[i], kp[i])] = kval[i];",
      "m[std::make_tuple(kctx[i], knode[i], kp[i], (uint32_t)kstall[i])] = kval[i];",
      [lambda o: TS.test_hand_computed_cms(o), lambda o: TS.test_cms_reconstructs_every_profile(o)]),
+    ("unify-ignores-parent", "const auto key = std::make_tuple(up, (uint32_t)module[i], offset[i]);",
+     "const auto key = std::make_tuple(0u, (uint32_t)module[i], offset[i]);",
+     [lambda o: TU.test_hand_example(o), lambda o: TU.test_paths_are_kept(o)]),
     ("flat-drops-unknown", "agg[std::make_pair(knode[i], (uint32_t)kstall[i])] += kval[i];",
      "if (knode[i] != UNKNOWN) agg[std::make_pair(knode[i], (uint32_t)kstall[i])] += kval[i];",
      [lambda o: TF.test_hand_computed_example(o), lambda o: TF.test_conservation_and_order_on_a_profile(o)]),
