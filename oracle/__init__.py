@@ -59,6 +59,12 @@ def load(path: str):
     L.orc_unify_status.restype = i32; L.orc_unify_status.argtypes = [vp]
     L.orc_unify_fetch.argtypes = [vp] * 5
     L.orc_unify_free.argtypes = [vp]
+    L.orc_bottom_up.restype = vp
+    L.orc_bottom_up.argtypes = [u64, vp, vp, vp, vp, u32, vp, u32, vp, vp, vp, u32]
+    L.orc_bu_status.restype = i32; L.orc_bu_status.argtypes = [vp]
+    L.orc_bu_sizes.argtypes = [vp, vp]
+    L.orc_bu_fetch.argtypes = [vp] * 9
+    L.orc_bu_free.argtypes = [vp]
     L.orc_cms.restype = vp
     L.orc_cms.argtypes = [u64, vp, vp, vp, vp, vp]
     L.orc_pms.restype = vp
@@ -333,3 +339,40 @@ def unify(ccts):
     L.orc_unify_fetch(h, _p(uid), _p(up), _p(um), _p(uo))
     L.orc_unify_free(h)
     return uid, up, um, uo
+
+
+@dataclass
+class BottomUp:
+    """Bottom-up view: nodes (parent, func, module, offset), level_off, and
+    the values (node, stall, val) ascending by (node, stall)."""
+    parent: np.ndarray
+    func: np.ndarray
+    module: np.ndarray
+    offset: np.ndarray
+    level_off: np.ndarray
+    vnode: np.ndarray
+    vstall: np.ndarray
+    val: np.ndarray
+
+
+def bottom_up(node_func, keys: KeyList, cct, levels: int) -> BottomUp:
+    """Bottom-up view (Section 7) of a profile.  cct = (parent, module,
+    offset) of the calling context tree whose node c is launch context c."""
+    L = lib()
+    nf = _c(node_func, np.uint32)
+    k = [_c(keys.ctx, np.uint32), _c(keys.node, np.uint32), _c(keys.stall, np.uint8), _c(keys.val, np.uint64)]
+    par, mod, off = _c(cct[0], np.uint32), _c(cct[1], np.uint16), _c(cct[2], np.uint64)
+    h = L.orc_bottom_up(k[0].shape[0], *[_p(x) for x in k], nf.shape[0], _p(nf), par.shape[0], _p(par), _p(mod),
+                        _p(off), levels)
+    st = L.orc_bu_status(h)
+    if st:
+        L.orc_bu_free(h)
+        raise ValueError(f"oracle bottom_up status {st}")
+    n = np.zeros(3, np.uint64)
+    L.orc_bu_sizes(h, _p(n))
+    nn, nv, nl = (int(x) for x in n)
+    b = BottomUp(np.empty(nn, np.uint32), np.empty(nn, np.uint32), np.empty(nn, np.uint16), np.empty(nn, np.uint64),
+                 np.empty(nl, np.uint64), np.empty(nv, np.uint32), np.empty(nv, np.uint8), np.empty(nv, np.uint64))
+    L.orc_bu_fetch(h, *[_p(x) for x in (b.parent, b.func, b.module, b.offset, b.level_off, b.vnode, b.vstall, b.val)])
+    L.orc_bu_free(h)
+    return b

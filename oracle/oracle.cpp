@@ -38,7 +38,7 @@ namespace {
 const uint32_t UNKNOWN = 0xFFFFFFFFu;   // attribution of a PC in no range
 const uint32_t NO_PARENT = 0xFFFFFFFFu;
 
-const int OK = 0, INVALID_ARG = 1, INVALID_SAMPLE = 3;
+const int OK = 0, INVALID_ARG = 1, INVALID_TABLE = 2, INVALID_SAMPLE = 3;
 
 typedef std::tuple<uint32_t, uint32_t, uint32_t> Key;   // (ctx, node, stall)
 
@@ -632,6 +632,91 @@ void* orc_unify(uint32_t n_cct, const uint64_t* base, const uint32_t* parent, co
         }
     return u;
 }
+// Bottom-up view (Section 7): the costs of a function divided among the
+// calling contexts in which it is called.  Its roots are the functions of
+// the keys' structure nodes (UNKNOWN keys belong to no function).  Below a
+// function, each node stands for one caller chain: the call sites met when
+// walking up the calling context tree from a key's launch context -- the
+// context's own call site first, then its parent's, up to the root's -- cut
+// after `levels` sites; level k holds the chains of k sites.  A node's value
+// per stall reason is the sum of the values of the keys of its function
+// whose context's chain begins with the node's chain.  Nodes are numbered
+// level by level and, within a level, in the order of the first key (in
+// profile order) that reaches them.  Roots carry module 0xFFFF, offset 0.
+struct BottomUp {
+    std::vector<uint32_t> parent, func, module;
+    std::vector<uint64_t> offset, level_off;
+    std::vector<uint32_t> vnode, vstall;
+    std::vector<uint64_t> val;
+    int status = OK;
+};
+
+void* orc_bottom_up(uint64_t k, const uint32_t* kctx, const uint32_t* knode, const uint8_t* kstall,
+                    const uint64_t* kval, uint32_t n_nodes, const uint32_t* node_func, uint32_t n_cct,
+                    const uint32_t* cct_parent, const uint16_t* cct_module, const uint64_t* cct_offset,
+                    uint32_t levels) {
+    BottomUp* b = new BottomUp();
+    for (uint32_t v = 0; v < n_cct; ++v)
+        if ((cct_parent[v] != NO_PARENT && cct_parent[v] >= v) || cct_module[v] == 0xFFFFu ||
+            (cct_offset[v] >> 48)) { b->status = INVALID_TABLE; return b; }
+    // every key's chain of labels: its function, then the call sites upward
+    std::vector<std::vector<std::pair<uint32_t, uint64_t>>> chain(k);
+    for (uint64_t i = 0; i < k; ++i) {
+        if (kctx[i] >= n_cct || (knode[i] != UNKNOWN && knode[i] >= n_nodes)) { b->status = INVALID_ARG; return b; }
+        if (knode[i] == UNKNOWN) continue;
+        chain[i].push_back(std::make_pair(0xFFFFu, (uint64_t)node_func[knode[i]]));
+        for (uint32_t c = kctx[i]; c != NO_PARENT && chain[i].size() <= levels; c = cct_parent[c])
+            chain[i].push_back(std::make_pair((uint32_t)cct_module[c], cct_offset[c]));
+    }
+    std::vector<uint32_t> at(k, NO_PARENT);        // each key's node at the previous level
+    std::map<std::pair<uint32_t, uint32_t>, uint64_t> cost;
+    b->level_off.push_back(0);
+    for (uint32_t lev = 0; lev <= levels; ++lev) {
+        std::map<std::tuple<uint32_t, uint32_t, uint64_t>, uint32_t> ids;
+        for (uint64_t i = 0; i < k; ++i) {
+            if (chain[i].size() <= lev) continue;
+            const auto lab = chain[i][lev];
+            const auto key = std::make_tuple(at[i], lab.first, lab.second);
+            auto it = ids.find(key);
+            uint32_t id;
+            if (it == ids.end()) {
+                id = (uint32_t)b->parent.size();
+                ids[key] = id;
+                b->parent.push_back(at[i]);
+                b->func.push_back(node_func[knode[i]]);
+                b->module.push_back(lab.first);
+                b->offset.push_back(lev == 0 ? 0 : lab.second);
+            } else {
+                id = it->second;
+            }
+            cost[std::make_pair(id, (uint32_t)kstall[i])] += kval[i];
+            at[i] = id;
+        }
+        b->level_off.push_back(b->parent.size());
+    }
+    for (auto& kv : cost) {
+        b->vnode.push_back(kv.first.first);
+        b->vstall.push_back(kv.first.second);
+        b->val.push_back(kv.second);
+    }
+    return b;
+}
+int orc_bu_status(void* p) { return ((BottomUp*)p)->status; }
+void orc_bu_sizes(void* p, uint64_t* n) {
+    BottomUp* b = (BottomUp*)p;
+    n[0] = b->parent.size(); n[1] = b->val.size(); n[2] = b->level_off.size();
+}
+void orc_bu_fetch(void* p, uint32_t* parent, uint32_t* func, uint16_t* module, uint64_t* offset, uint64_t* level_off,
+                  uint32_t* vnode, uint8_t* vstall, uint64_t* val) {
+    BottomUp* b = (BottomUp*)p;
+    for (size_t i = 0; i < b->parent.size(); ++i) {
+        parent[i] = b->parent[i]; func[i] = b->func[i]; module[i] = (uint16_t)b->module[i]; offset[i] = b->offset[i];
+    }
+    std::copy(b->level_off.begin(), b->level_off.end(), level_off);
+    for (size_t i = 0; i < b->val.size(); ++i) { vnode[i] = b->vnode[i]; vstall[i] = (uint8_t)b->vstall[i]; val[i] = b->val[i]; }
+}
+void orc_bu_free(void* p) { delete (BottomUp*)p; }
+
 uint64_t orc_unify_size(void* p) { return ((Unified*)p)->parent.size(); }
 int orc_unify_status(void* p) { return ((Unified*)p)->status; }
 void orc_unify_fetch(void* p, uint32_t* uid, uint32_t* parent, uint16_t* module, uint64_t* offset) {

@@ -362,19 +362,15 @@ def make_cct_levels(seed: int, n_nodes: int, max_depth: int, max_fanout: int) ->
     return out
 
 
-def make_profile_ccts(seed: int, n_master: int, depth: int, n_profiles: int, keep: float, n_sites: int = 0):
-    """Per-profile calling context trees for unification: a master tree whose
-    call sites repeat under different parents, as a callee's call sites do
-    under each of its calling contexts (site = a seeded pick per depth among
-    n_sites // 8 groups, plus the node's rank among its siblings, so that
-    siblings never share one; module = site % 8, offset = 0x1000 + 16 site).
-    Profile p keeps a seeded subset of the master's nodes closed under
-    parents, in master order.  Returns [(parent, module, offset)] with parents
-    as indices within the profile (HPA_NO_PARENT for a root)."""
-    FAN = 8
-    par = make_cct_levels(seed, n_master, depth, FAN)
-    idx = np.arange(n_master)
-    dep = np.zeros(n_master, np.int64)
+def cct_sites(seed: int, par: np.ndarray, n_sites: int = 0, fan: int = 8):
+    """Call sites (module, offset) of the nodes of a calling context tree
+    (parent < child) that repeat under different parents, as a callee's call
+    sites do under each of its calling contexts: site = a seeded pick per
+    depth among n_sites // fan groups, plus the node's rank among its
+    siblings, so that siblings never share one; module = site % 8, offset =
+    0x1000 + 16 site.  Returns (module u16, offset u64, depth i64)."""
+    n = par.shape[0]
+    dep = np.zeros(n, np.int64)
     anc = par.astype(np.int64)
     while True:                                         # depth by walking every node up one step at a time
         up = anc != NO_PARENT
@@ -384,13 +380,23 @@ def make_profile_ccts(seed: int, n_master: int, depth: int, n_profiles: int, kee
         anc[up] = par[anc[up]].astype(np.int64)
     order = np.argsort(par, kind="stable")
     first = np.searchsorted(par[order], par[order], side="left")
-    rank = np.empty(n_master, np.int64)
-    rank[order] = np.arange(n_master) - first
-    assert rank.max(initial=0) < FAN
-    groups = max(1, (n_sites or max(64, n_master // 4)) // FAN)
-    site = np_below(seed, 503, dep, groups).astype(np.int64) * FAN + rank
-    module = (site % 8).astype(np.uint16)
-    offset = (0x1000 + 16 * site).astype(np.uint64)
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n) - first
+    assert rank.max(initial=0) < fan
+    groups = max(1, (n_sites or max(64, n // 4)) // fan)
+    site = np_below(seed, 503, dep, groups).astype(np.int64) * fan + rank
+    return (site % 8).astype(np.uint16), (0x1000 + 16 * site).astype(np.uint64), dep
+
+
+def make_profile_ccts(seed: int, n_master: int, depth: int, n_profiles: int, keep: float, n_sites: int = 0):
+    """Per-profile calling context trees for unification: a master tree whose
+    call sites repeat under different parents (cct_sites); profile p keeps a
+    seeded subset of the master's nodes closed under parents, in master
+    order.  Returns [(parent, module, offset)] with parents as indices within
+    the profile (HPA_NO_PARENT for a root)."""
+    par = make_cct_levels(seed, n_master, depth, 8)
+    idx = np.arange(n_master)
+    module, offset, dep = cct_sites(seed, par, n_sites)
     lv = np.argsort(dep, kind="stable")
     by_level = np.split(lv, np.searchsorted(dep[lv], np.arange(1, int(dep.max(initial=0)) + 1)))
     out = []

@@ -10,6 +10,7 @@ import pytest
 import oracle
 import test_oracle_apportion as TA
 import test_oracle_attribution as TT
+import test_oracle_bottom_up as TB
 import test_oracle_expand as TX
 import test_oracle_flat as TF
 import test_oracle_inclusive_derive as TI
@@ -46,6 +47,15 @@ MUTATIONS = [
     ("cms-profile-major-order", "m[std::make_tuple(kctx[i], knode[i], (uint32_t)kstall[i], kp[i])] = kval[i];",
      "m[std::make_tuple(kctx[i], knode[i], kp[i], (uint32_t)kstall[i])] = kval[i];",
      [lambda o: TS.test_hand_computed_cms(o), lambda o: TS.test_cms_reconstructs_every_profile(o)]),
+    ("bottom-up-ignores-parent", "const auto key = std::make_tuple(at[i], lab.first, lab.second);",
+     "const auto key = std::make_tuple(0u, lab.first, lab.second);",
+     [lambda o: TB.test_hand_example(o), lambda o: TB.test_brute_force(o, 20, 16)]),
+    ("bottom-up-context-not-site", "chain[i].push_back(std::make_pair((uint32_t)cct_module[c], cct_offset[c]));",
+     "chain[i].push_back(std::make_pair((uint32_t)cct_module[c], (uint64_t)c));",
+     [lambda o: TB.test_hand_example(o), lambda o: TB.test_brute_force(o, 20, 16)]),
+    ("bottom-up-skips-launch-site", "for (uint32_t c = kctx[i]; c != NO_PARENT && chain[i].size() <= levels; c = cct_parent[c])",
+     "for (uint32_t c = cct_parent[kctx[i]]; c != NO_PARENT && chain[i].size() <= levels; c = cct_parent[c])",
+     [lambda o: TB.test_hand_example(o), lambda o: TB.test_brute_force(o, 20, 16)]),
     ("unify-ignores-parent", "const auto key = std::make_tuple(up, (uint32_t)module[i], offset[i]);",
      "const auto key = std::make_tuple(0u, (uint32_t)module[i], offset[i]);",
      [lambda o: TU.test_hand_example(o), lambda o: TU.test_paths_are_kept(o)]),
