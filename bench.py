@@ -151,8 +151,8 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     GPU calling-context trees (64 contexts), inclusive propagation over the
     host CCT (all contexts) and over the structure tree (a 10 % sample of the
     profile, to bound scratch), derived metrics over 4 profiles, the flat
-    view, one context's GPU CCT as a tree, both sparse layouts, and the
-    unification of 16 profiles' calling context trees."""
+    view, one context's GPU CCT as a tree, both sparse layouts, the
+    bottom-up view, and the unification of 16 profiles' calling context trees."""
     from paper_2109_06931_gb300 import hpa as H
     out = {}
     K = prof.count()
@@ -199,6 +199,18 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     out["cms"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
     ms = timed(stream, lambda: (h.build_pms(profs), h.sync()), reps=2)
     out["pms"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
+    # bottom-up view of the 10 % profile over the contexts' tree, every level
+    cpar = w.cct()
+    cmod, coff, cdep = synth.cct_sites(w.seed, cpar, 0, fan=w.cct_fanout)
+    cct = tuple(torch.from_numpy(a.view(t)).to(dev) for a, t in zip((cpar, cmod, coff), (np.int32, np.int16, np.int64)))
+    torch.cuda.synchronize()
+    lv = int(cdep.max()) + 1
+    bu = h.bottom_up(bid, p2, cct, lv)
+    h.sync()
+    nn, nv = (int(x) for x in bu["counts"].tolist())
+    ms = timed(stream, lambda: (h.bottom_up(bid, p2, cct, lv, nn, nv), h.sync()), reps=2)
+    out["bottom_up"] = {"ms": ms, "keys_in": k2, "levels": lv, "nodes": nn, "values": nv,
+                        "keys_per_s": k2 / (ms / 1e3)}
     # calling context trees of 16 profiles (subsets of a 2M-node master tree) unified
     ccts = [tuple(torch.from_numpy(a.view(t)).to(dev) for a, t in zip(c, (np.int32, np.int16, np.int64)))
             for c in synth.make_profile_ccts(3, 2_000_000, 64, 16, 0.25)]

@@ -444,6 +444,45 @@ typedef struct {
 } hpa_cct_unified;
 hpa_status hpa_unify_ccts(hpa_handle* h, const hpa_cct_nodes* ccts, uint32_t n, hpa_cct_unified* out);
 
+/* Bottom-up view of a profile (Section 7): the costs of each function
+ * divided among the calling contexts in which it is called.  The view's
+ * roots are the functions of p's structure nodes (UNKNOWN keys belong to no
+ * function).  Below a function, one node per caller chain: the call sites
+ * met walking up `cct` from a key's launch context c (CCT node c: its own
+ * call site first, then its parent's, up to the root's), cut after `levels`
+ * sites; level k (0 = the functions) holds the chains of k sites, and a
+ * node's children extend its chain by one site.  A node's value per stall
+ * reason is the sum of p's values of its function over the contexts whose
+ * chain begins with the node's chain (exact, 64-bit).
+ * cct: DEVICE arrays as for hpa_unify_ccts (a parent precedes its node;
+ * module < 0xFFFF, offset < 2^48), n_nodes >= p->n_ctx.  Output, DEVICE:
+ * nodes level by level and within a level in the order of the first key of
+ * p that reaches them; parent (HPA_NO_PARENT for a function), func, and the
+ * call site (module, offset) of the chain's last site (0xFFFF, 0 for a
+ * function); level_off[k] .. level_off[k + 1] (may be NULL; levels + 2
+ * entries) are level k's nodes; values (val_node, val_stall, val) ascending
+ * by (node, stall), zero values omitted.  counts[0..1] = nodes, values
+ * needed; HPA_E_CAPACITY (at hpa_sync) for an array too small, after which
+ * the arrays hold a prefix.  HPA_E_INVALID_TABLE (at hpa_sync) for a tree
+ * that breaks the rules above.  Scratch: about 24 B per key of p's capacity
+ * plus a table of 12 B per slot for a power of two >= 2 max(keys, tree
+ * nodes).  No host synchronisation.                                         */
+typedef struct {
+    uint32_t levels;          /* call sites per chain, <= 1024 */
+    uint64_t cap_nodes, cap_values;
+    uint32_t* parent;         /* [cap_nodes] */
+    uint32_t* func;
+    uint16_t* module;
+    uint64_t* offset;
+    uint64_t* level_off;      /* [levels + 2] or NULL */
+    uint32_t* val_node;       /* [cap_values] */
+    uint8_t* val_stall;
+    uint64_t* val;
+    uint64_t* counts;         /* [2] */
+} hpa_bottom_up;
+hpa_status hpa_bottom_up_view(hpa_handle* h, uint32_t binary_id, const hpa_profile* p, const hpa_cct_nodes* cct,
+                              hpa_bottom_up* out);
+
 /* Derived metrics over n_profiles profiles (Section 4.5) and the warp issue
  * rate per context (Section 7, W = (S - S_stall) / S with the handle's
  * issued_mask).  ps: HOST array of profile descriptors with DEVICE data.    */

@@ -12,6 +12,7 @@
 // parent's representative is final before its children are keyed.  Merged
 // ids are the ranks of the representatives: the order of first occurrence.
 
+#include "hpa_hash.cuh"
 #include "hpa_host.h"
 
 namespace hpa {
@@ -42,45 +43,6 @@ struct UnifyArgs {
     uint32_t* maxdep;
     DevStatus* status;
 };
-
-constexpr unsigned long long UEMPTY = ~0ull;
-
-__device__ __forceinline__ uint32_t uhash(unsigned long long k, uint32_t mask) {
-    k ^= k >> 33;
-    k *= 0xff51afd7ed558ccdull;
-    k ^= k >> 33;
-    k *= 0xc4ceb9fe1a85ec53ull;
-    k ^= k >> 33;
-    return (uint32_t)k & mask;
-}
-
-__device__ __forceinline__ bool ut_insert(unsigned long long* keys, uint32_t* vals, uint32_t mask,
-                                          unsigned long long key, uint32_t idx) {
-    uint32_t h = uhash(key, mask);
-    volatile unsigned long long* vk = keys;
-    for (uint32_t t = 0; t <= mask; ++t) {
-        unsigned long long cur = vk[h];
-        if (cur == UEMPTY) {
-            cur = atomicCAS(&keys[h], UEMPTY, key);
-            if (cur == UEMPTY) cur = key;
-        }
-        if (cur == key) { atomicMin(&vals[h], idx); return true; }
-        h = (h + 1) & mask;
-    }
-    return false;
-}
-
-__device__ __forceinline__ uint32_t ut_find(const unsigned long long* keys, const uint32_t* vals, uint32_t mask,
-                                            unsigned long long key) {
-    uint32_t h = uhash(key, mask);
-    for (uint32_t t = 0; t <= mask; ++t) {
-        const unsigned long long cur = keys[h];
-        if (cur == key) return vals[h];
-        if (cur == UEMPTY) return 0xFFFFFFFFu;
-        h = (h + 1) & mask;
-    }
-    return 0xFFFFFFFFu;
-}
 
 __global__ void k_un_init(UnifyArgs a) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.N; i += (uint64_t)gridDim.x * blockDim.x) {

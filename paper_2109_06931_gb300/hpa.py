@@ -103,6 +103,12 @@ class hpa_cct_unified(C.Structure):
                 ("n_unified", vp)]
 
 
+class hpa_bottom_up(C.Structure):
+    _fields_ = [("levels", C.c_uint32), ("cap_nodes", C.c_uint64), ("cap_values", C.c_uint64),
+                ("parent", vp), ("func", vp), ("module", vp), ("offset", vp), ("level_off", vp),
+                ("val_node", vp), ("val_stall", vp), ("val", vp), ("counts", vp)]
+
+
 class hpa_derived(C.Structure):
     _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp),
                 ("sum", vp), ("min", vp), ("max", vp), ("mean", vp), ("std", vp), ("cov", vp),
@@ -147,6 +153,8 @@ def lib(build_if_needed: bool = True):
         L.hpa_attribute_batch.argtypes = [H, C.c_uint32, u32p, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
         L.hpa_expand_gpucct.argtypes = [H, C.c_uint32, C.POINTER(hpa_gpucct), C.c_uint32, C.c_uint32,
                                          C.POINTER(hpa_cct_tree)]
+        L.hpa_bottom_up_view.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_cct_nodes),
+                                         C.POINTER(hpa_bottom_up)]
         L.hpa_unify_ccts.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_cct_unified)]
         L.hpa_build_cms.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_cms)]
         L.hpa_build_pms.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_pms)]
@@ -435,6 +443,37 @@ class Hpa:
                          _ptr(out["incl"]), _ptr(out["n"]), _ptr(out["truncated"]))
         self.check(self.L.hpa_expand_gpucct(self.h, bid, C.byref(g), n_stall, q, C.byref(t)))
         self._keep = [req]
+        return out
+
+    def bottom_up(self, bid: int, p: Profile, cct, levels: int, cap_nodes: int | None = None,
+                  cap_values: int | None = None):
+        """hpa_bottom_up_view: cct = (parent, module, offset) device tensors
+        (int32 / int16 / int64).  Without capacities, a first call sizes the
+        output.  Returns the node arrays, level_off, the (node, stall, val)
+        values and the counts tensor (nodes, values needed)."""
+        d = self.device
+        pin = p.c()
+        pin.capacity = max(1, p.count())
+        desc = hpa_cct_nodes(int(cct[0].shape[0]), _ptr(cct[0]), _ptr(cct[1]), _ptr(cct[2]))
+        if cap_nodes is None or cap_values is None:
+            counts = torch.zeros(2, dtype=torch.int64, device=d)
+            o = hpa_bottom_up(levels, 0, 0, None, None, None, None, None, None, None, None, _ptr(counts))
+            self.check(self.L.hpa_bottom_up_view(self.h, bid, C.byref(pin), C.byref(desc), C.byref(o)))
+            st, _ = self.sync_status()
+            if st not in (HPA_OK, HPA_E_CAPACITY):
+                raise HpaError(st, self.L.hpa_last_error(self.h).decode())
+            n = counts.tolist()
+            cap_nodes = n[0] if cap_nodes is None else cap_nodes
+            cap_values = n[1] if cap_values is None else cap_values
+        e = lambda n, dt: torch.empty(max(1, n), dtype=dt, device=d)
+        out = dict(parent=e(cap_nodes, torch.int32), func=e(cap_nodes, torch.int32), module=e(cap_nodes, torch.int16),
+                   offset=e(cap_nodes, torch.int64), level_off=e(levels + 2, torch.int64),
+                   val_node=e(cap_values, torch.int32), val_stall=e(cap_values, torch.uint8),
+                   val=e(cap_values, torch.int64), counts=torch.zeros(2, dtype=torch.int64, device=d))
+        o = hpa_bottom_up(levels, cap_nodes, cap_values, *[_ptr(out[k]) for k in
+                          ("parent", "func", "module", "offset", "level_off", "val_node", "val_stall", "val", "counts")])
+        self.check(self.L.hpa_bottom_up_view(self.h, bid, C.byref(pin), C.byref(desc), C.byref(o)))
+        self._keep = [p, cct, out]
         return out
 
     def unify_ccts(self, ccts, capacity: int | None = None):
