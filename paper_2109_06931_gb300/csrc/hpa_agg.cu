@@ -715,6 +715,8 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_partition(AggWork w) {
 // buffer are summed here over its keys (every valid record lies in exactly
 // one key): per-thread slots in shared memory, flushed when the CTA moves to
 // another buffer.
+constexpr int EMIT_U = 4;
+
 __global__ void __launch_bounds__(256) k_emit(AggWork w) {
     extern __shared__ unsigned long long acc[];          // [2^sb][256] per-thread totals (emit_totals)
     __shared__ unsigned long long unk[HPA_MAX_STALL_DEV];
@@ -760,23 +762,39 @@ __global__ void __launch_bounds__(256) k_emit(AggWork w) {
         const uint32_t g0 = w.leaf_grp0[l];
         const uint64_t o0 = (uint64_t)leaf_out[l] - leaf_out[w.buf_first_leaf[b]];
         const uint32_t gctx0 = g0 - B.grp_base;
-        for (uint32_t i = tid; i < d; i += blockDim.x) {
-            const uint64_t pos = o0 + i;
-            const uint32_t k = w.tmp_key[start + i];
-            const unsigned long long v = w.tmp_val[start + i];
-            const uint32_t sub = k & smask;
-            const uint32_t node = sub >> w.sb;
-            const uint32_t stall = sub & stmask;
-            if (tot) {
-                acc[stall * 256 + tid] += v;
-                if (node == M) atomicAdd(&unk[stall], v);
+        // EMIT_U keys per thread loaded before any is processed: more bytes in flight
+        for (uint32_t i0 = tid; i0 < d; i0 += EMIT_U * 256) {
+            uint32_t kk[EMIT_U];
+            unsigned long long vv[EMIT_U];
+#pragma unroll
+            for (int u = 0; u < EMIT_U; ++u) {
+                const uint32_t i = i0 + u * 256;
+                if (i < d) {
+                    kk[u] = __ldcs(&w.tmp_key[start + i]);
+                    vv[u] = __ldcs((const unsigned long long*)&w.tmp_val[start + i]);
+                }
             }
-            if (pos < B.capacity) {
-                const uint32_t gl = (w.sbits >= 32) ? 0u : (k >> w.sbits);
-                B.key_ctx[pos] = gctx0 + gl;
-                B.key_node[pos] = (node == M) ? UNKNOWN : node;
-                B.key_stall[pos] = (uint8_t)stall;
-                B.val[pos] = v;
+#pragma unroll
+            for (int u = 0; u < EMIT_U; ++u) {
+                const uint32_t i = i0 + u * 256;
+                if (i >= d) break;
+                const uint64_t pos = o0 + i;
+                const uint32_t k = kk[u];
+                const unsigned long long v = vv[u];
+                const uint32_t sub = k & smask;
+                const uint32_t node = sub >> w.sb;
+                const uint32_t stall = sub & stmask;
+                if (tot) {
+                    acc[stall * 256 + tid] += v;
+                    if (node == M) atomicAdd(&unk[stall], v);
+                }
+                if (pos < B.capacity) {
+                    const uint32_t gl = (w.sbits >= 32) ? 0u : (k >> w.sbits);
+                    __stcs(&B.key_ctx[pos], gctx0 + gl);
+                    __stcs(&B.key_node[pos], (node == M) ? UNKNOWN : node);
+                    B.key_stall[pos] = (uint8_t)stall;
+                    __stcs((unsigned long long*)&B.val[pos], v);
+                }
             }
         }
     }

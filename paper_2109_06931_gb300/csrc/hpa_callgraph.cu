@@ -114,6 +114,8 @@ hpa_status build_callgraph(hpa_handle* h, Binary* B) {
     std::vector<uint32_t> cin_off, cin_edge, cout_off, cout_edge;
     csr(V, ckey_in, citems_in, cin_off, cin_edge);
     csr(V, ckey_out, citems_out, cout_off, cout_edge);
+    std::vector<uint32_t> cout_head(cout_edge.size());
+    for (size_t i = 0; i < cout_edge.size(); ++i) cout_head[i] = cof[B->cs_callee[cout_edge[i]]];
     // heights: components complete callees-first, so one pass in completion order
     std::vector<std::vector<uint32_t>> members(C);
     for (uint32_t f = 0; f < F; ++f) members[comp[f]].push_back(f);
@@ -147,18 +149,19 @@ hpa_status build_callgraph(hpa_handle* h, Binary* B) {
     DevCallGraph& g = B->cg;
     g.F = F; g.E = E; g.V = V; g.n_levels = n_levels; g.M = M;
     hpa_status st;
-    uint32_t *p0, *p1, *p2, *p3, *p4, *p5, *p6, *p7, *p8, *p9, *p10, *p11, *p12;
+    uint32_t *p0, *p1, *p2, *p3, *p4, *p5, *p6, *p7, *p8, *p9, *p10, *p11, *p12, *p13;
     uint8_t *q0, *q1;
     if ((st = upload(h, B, B->node_func, &p0)) || (st = upload(h, B, node_cs, &p1)) ||
         (st = upload(h, B, B->cs_caller, &p2)) || (st = upload(h, B, B->cs_callee, &p3)) ||
         (st = upload(h, B, cof, &p4)) || (st = upload(h, B, fin_off, &p5)) || (st = upload(h, B, fin_edge, &p6)) ||
         (st = upload(h, B, cin_off, &p7)) || (st = upload(h, B, cin_edge, &p8)) ||
         (st = upload(h, B, cout_off, &p9)) || (st = upload(h, B, cout_edge, &p10)) ||
+        (st = upload(h, B, cout_head, &p13)) ||
         (st = upload(h, B, level_off, &p11)) || (st = upload(h, B, level_node, &p12)) ||
         (st = upload(h, B, intra, &q0)) || (st = upload(h, B, live, &q1)))
         return st;
     g.node_func = p0; g.node_cs = p1; g.cs_caller = p2; g.cs_callee = p3; g.cnode_of_func = p4;
-    g.fin_off = p5; g.fin_edge = p6; g.cin_off = p7; g.cin_edge = p8; g.cout_off = p9; g.cout_edge = p10;
+    g.fin_off = p5; g.fin_edge = p6; g.cin_off = p7; g.cin_edge = p8; g.cout_off = p9; g.cout_edge = p10; g.cout_head = p13;
     g.level_off = p11; g.level_node = p12; g.edge_intra = q0; g.cnode_live = q1;
     uint32_t* par;
     if ((st = upload(h, B, B->node_parent, &par))) return st;

@@ -13,8 +13,9 @@
 //          again on the condensed graph (FIXUP2);
 //  step 4  bottom-up over the condensed DAG's levels (sinks first):
 //          incl(v) = excl(v) + sum_{e out of v} w(e)/W(head(e)) * incl(head(e)),
-//          a(e) = w(e)/W(head(e)) * incl(head(e)); one warp per node, one lane
-//          per stall reason.
+//          a(e) = w(e)/W(head(e)) * incl(head(e)); the ratio of each edge is
+//          computed once, then one thread per (node of the level, stall
+//          reason), then one per node for its total column.
 // Counts are accumulated exactly (integers in FP64, < 2^53); ratios and
 // products are FP64; results are rounded once to FP32.
 
@@ -24,12 +25,15 @@
 
 namespace hpa {
 
+constexpr int GPUCCT_THREADS = 1024;   // one CTA per requested context (per SM)
+
 struct CctSlot {
     double* incl;        // [V][M]
     unsigned long long* fS;   // [F]
     unsigned long long* w;    // [E] measured
     unsigned long long* w2;   // [E] after fix-ups
     unsigned long long* W;    // [V]
+    double* ratio;       // [E] w(e) / W(head(e)) of external edges
     uint8_t* flags;      // [E]
     uint32_t* inZ;       // [F]
     uint8_t* meas_in;    // [F]
@@ -71,6 +75,7 @@ __host__ __device__ inline size_t slot_layout(const DevCallGraph& g, uint32_t M,
     t.w = (unsigned long long*)take((size_t)g.E * 8);
     t.w2 = (unsigned long long*)take((size_t)g.E * 8);
     t.W = (unsigned long long*)take((size_t)g.V * 8);
+    t.ratio = (double*)take((size_t)g.E * 8);
     t.flags = (uint8_t*)take(g.E);
     t.inZ = (uint32_t*)take((size_t)g.F * 4);
     t.meas_in = (uint8_t*)take(g.F);
@@ -89,8 +94,7 @@ __global__ void __launch_bounds__(THREADS) k_gpucct(CctArgs A) {
     __shared__ uint64_t s_range[2];
     CctSlot T;
     slot_layout(g, A.M, A.slots + (size_t)blockIdx.x * A.slot_bytes, &T);
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
-    constexpr uint32_t NW = THREADS / 32;
+    const uint32_t tid = threadIdx.x;
     const uint64_t K = min(*A.n_keys, A.key_cap);
 
     for (uint32_t q = blockIdx.x; q < A.n_req; q += gridDim.x) {
@@ -201,33 +205,41 @@ __global__ void __launch_bounds__(THREADS) k_gpucct(CctArgs A) {
             }
             __syncthreads();
         }
-        // step 4: bottom-up sweep, one warp per condensed node
+        // step 4: the ratio of every external edge once, then the levels
+        // bottom-up: one thread per (node of the level, stall reason), then one
+        // per node for its total column and its edges' total shares
+        for (uint32_t e = tid; e < g.E; e += THREADS) {
+            if (g.edge_intra[e]) continue;
+            const uint32_t hd = g.cnode_of_func[g.cs_callee[e]];
+            T.ratio[e] = T.W[hd] ? (double)T.w2[e] / (double)T.W[hd] : 0.0;
+        }
+        __syncthreads();
         float* outA = A.out_a + (size_t)q * g.E * A.M;
+        const uint32_t S = A.S;
         for (uint32_t lev = 0; lev < g.n_levels; ++lev) {
-            for (uint32_t k = g.level_off[lev] + warp; k < g.level_off[lev + 1]; k += NW) {
-                const uint32_t v = g.level_node[k];
-                double* iv = T.incl + (size_t)v * A.M;
-                double acc0 = lane < A.S ? iv[lane] : 0.0;
-                double acc1 = lane + 32 < A.S ? iv[lane + 32] : 0.0;
+            const uint32_t k0 = g.level_off[lev], nk = g.level_off[lev + 1] - k0;
+            for (uint32_t it = tid; it < nk * S; it += THREADS) {
+                const uint32_t v = g.level_node[k0 + it / S], r = it % S;
+                double acc = T.incl[(size_t)v * A.M + r];
                 for (uint32_t j = g.cout_off[v]; j < g.cout_off[v + 1]; ++j) {
                     const uint32_t e = g.cout_edge[j];
-                    const uint32_t hd = g.cnode_of_func[g.cs_callee[e]];
-                    const double ratio = T.W[hd] ? (double)T.w2[e] / (double)T.W[hd] : 0.0;
-                    const double* ih = T.incl + (size_t)hd * A.M;
-                    const double x0 = lane < A.S ? ratio * ih[lane] : 0.0;
-                    const double x1 = lane + 32 < A.S ? ratio * ih[lane + 32] : 0.0;
-                    acc0 += x0;
-                    acc1 += x1;
-                    float* ae = outA + (size_t)e * A.M;
-                    if (lane < A.S) ae[lane] = (float)x0;
-                    if (lane + 32 < A.S) ae[lane + 32] = (float)x1;
-                    const double tot = warp_sum(x0 + x1);
-                    if (lane == 0) ae[A.S] = (float)tot;
+                    const double x = T.ratio[e] * T.incl[(size_t)g.cout_head[j] * A.M + r];
+                    acc += x;
+                    outA[(size_t)e * A.M + r] = (float)x;
                 }
-                if (lane < A.S) iv[lane] = acc0;
-                if (lane + 32 < A.S) iv[lane + 32] = acc1;
-                const double tot = warp_sum(acc0 + acc1);
-                if (lane == 0) iv[A.S] = tot;
+                T.incl[(size_t)v * A.M + r] = acc;
+            }
+            __syncthreads();
+            for (uint32_t k = k0 + tid; k < k0 + nk; k += THREADS) {
+                const uint32_t v = g.level_node[k];
+                double* iv = T.incl + (size_t)v * A.M;
+                double tot = 0.0;
+                for (uint32_t r = 0; r < S; ++r) tot += iv[r];
+                iv[S] = tot;
+                for (uint32_t j = g.cout_off[v]; j < g.cout_off[v + 1]; ++j) {
+                    const uint32_t e = g.cout_edge[j];
+                    outA[(size_t)e * A.M + S] = (float)(T.ratio[e] * T.incl[(size_t)g.cout_head[j] * A.M + S]);
+                }
             }
             __syncthreads();
         }
@@ -271,11 +283,11 @@ extern "C" hpa_status hpa_apportion_callgraph(hpa_handle* h, uint32_t binary_id,
     A.out_incl = out->incl; A.out_a = out->a; A.out_flags = out->flags;
     A.status = h->d_status;
     A.slot_bytes = slot_layout(g, A.M, nullptr, nullptr);
-    const uint32_t grid = std::min<uint32_t>(out->n_req, (uint32_t)h->sms * 2);
+    const uint32_t grid = std::min<uint32_t>(out->n_req, (uint32_t)h->sms);
     hpa_status st = h->ensure_scratch(A.slot_bytes * grid + 256);
     if (st) return st;
     A.slots = (char*)h->scratch;
-    k_gpucct<256><<<grid, 256, 0, h->stream>>>(A);
+    k_gpucct<GPUCCT_THREADS><<<grid, GPUCCT_THREADS, 0, h->stream>>>(A);
     h->launches += 1;
     return h->cuda(cudaGetLastError(), "apportion launch");
 }

@@ -24,6 +24,7 @@ struct DevCallGraph {
     const uint32_t* cin_edge;
     const uint32_t* cout_off;    // [V+1] external out-edges of each condensed node
     const uint32_t* cout_edge;
+    const uint32_t* cout_head;   // condensed callee of each cout_edge entry
     const uint32_t* level_off;   // [n_levels+1] condensed nodes by height (sinks first)
     const uint32_t* level_node;
     const uint8_t* edge_intra;   // [E] 1 if the edge lies inside one SCC
