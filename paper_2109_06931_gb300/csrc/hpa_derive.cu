@@ -6,12 +6,13 @@
 // with the shared plan / partition stages; a run of equal keys holds at most
 // one value per profile.  Per key: present count, sum, exact sum of squares
 // (128-bit), min and max; absent profiles count as 0:
-//   mean = sum / P, var = (P * sumsq - sum^2) / P^2 (exact integers, one
-//   rounding), std = sqrt(var), cov = std / mean.
+//   mean = sum / P, var = (P * sumsq - sum^2) / P^2 (exact integer
+//   numerator, FP32 from there), std = sqrt(var), cov = std / mean.
 
 #include <algorithm>
 
 #include "hpa_host.h"
+#include "hpa_warpagg.cuh"
 
 namespace hpa {
 
@@ -58,51 +59,72 @@ __device__ __forceinline__ bool fetch(const DeriveArgs& A, uint64_t i, uint32_t&
     return c < A.n_ctx && (n == UNKNOWN || n < A.M);
 }
 
+// Both passes walk the flattened keys warp by warp (the loop is uniform in
+// a warp) and count with warp-aggregated atomics: the profiles are sorted by
+// context, so the lanes of a warp mostly share one.
 __global__ void k_union_hist(AggWork w, DeriveArgs A) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < A.total; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t c, sub;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); i0 < A.total; i0 += stride) {
+        const uint64_t i = i0 + (threadIdx.x & 31u);
+        uint32_t c = 0, sub;
         uint64_t v;
-        if (fetch(A, i, c, sub, v, w.sb)) atomicAdd(&w.grp_hist[c], 1u);
-        else {
-            const uint32_t p = upper_index<uint64_t>(A.prof_base, A.P, i);
-            if (i - A.prof[p].base < min(*A.prof[p].n_keys, A.prof[p].cap)) atomicAdd(&w.buf_bad[0], 1ull);
+        bool ok = false;
+        if (i < A.total) {
+            ok = fetch(A, i, c, sub, v, w.sb);
+            if (!ok) {
+                const uint32_t p = upper_index<uint64_t>(A.prof_base, A.P, i);
+                if (i - A.prof[p].base < min(*A.prof[p].n_keys, A.prof[p].cap)) atomicAdd(&w.buf_bad[0], 1ull);
+            }
         }
+        warp_agg_inc(ok ? &w.grp_hist[c] : nullptr);
     }
 }
 
 __global__ void k_union_scatter(AggWork w, DeriveArgs A) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < A.total; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t c, sub;
-        uint64_t v;
-        if (!fetch(A, i, c, sub, v, w.sb)) continue;
-        const uint32_t slot = atomicAdd(&w.grp_cursor[(size_t)c << w.cur_shift], 1u);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); i0 < A.total; i0 += stride) {
+        const uint64_t i = i0 + (threadIdx.x & 31u);
+        uint32_t c = 0, sub = 0;
+        uint64_t v = 0;
+        const bool ok = i < A.total && fetch(A, i, c, sub, v, w.sb);
+        const uint32_t slot = warp_agg_inc(ok ? &w.grp_cursor[(size_t)c << w.cur_shift] : nullptr);
+        if (!ok) continue;
         w.rec_sub[slot] = sub;
         w.rec_v64[slot] = v;
     }
 }
 
+// Statistics of one key from its exact integer sums.  The variance's
+// numerator P * sumsq - sum^2 is exact (128-bit); the divisions and the
+// square root are FP32, the precision of the outputs (a few ulp of error).
 __device__ __forceinline__ void key_stats(uint32_t P, uint32_t cnt, unsigned long long sum, unsigned long long sql,
                                           unsigned long long sqh, unsigned long long mn, unsigned long long mx,
                                           const StatOut& o, size_t at) {
     const unsigned __int128 sq = ((unsigned __int128)sqh << 64) | sql;
     const unsigned __int128 num = (unsigned __int128)P * sq - (unsigned __int128)sum * sum;
-    const double var = (double)num / ((double)P * (double)P);
-    const double sd = sqrt(var);
-    const double mean = (double)sum / (double)P;
+    const float numf = __fmaf_rn(__ull2float_rn((unsigned long long)(num >> 64)), 18446744073709551616.0f,
+                                 __ull2float_rn((unsigned long long)num));
+    const float pf = (float)P;
+    const float var = numf / (pf * pf);
+    const float sd = sqrtf(var);
+    const float mean = __ull2float_rn(sum) / pf;
     o.mn[at] = cnt < P ? 0ull : mn;
     o.mx[at] = mx;
-    o.mean[at] = (float)mean;
-    o.sd[at] = (float)sd;
-    o.cov[at] = (float)(sd / mean);
+    o.mean[at] = mean;
+    o.sd[at] = sd;
+    o.cov[at] = sd / mean;
 }
 
-constexpr int DS_THREADS = 256;
+constexpr int DS_THREADS = 512;
 constexpr int DS_CAP = LEAF_CAP_SMALL;
 constexpr int DS_WIN = 1024;    // keys per dense window of the oversized path
 
+// Leaf of the union: the records' keys are sorted with their index within
+// the leaf in the upper 32 bits of each element (9-bit digits), and the
+// values are gathered by index afterwards, run by run.
 template <int THREADS, int CAP>
-__global__ void __launch_bounds__(THREADS) k_leaf_stats(AggWork w, DeriveArgs A) {
-    using Sort = BlockRadix<THREADS, CAP, 8, uint64_t, true>;
+__global__ void __launch_bounds__(THREADS, 2) k_leaf_stats(AggWork w, DeriveArgs A) {
+    using Sort = PackedRadix<THREADS, CAP, uint64_t>;
     constexpr int EPT = (CAP + THREADS - 1) / THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename Sort::Smem& S = *reinterpret_cast<typename Sort::Smem*>(smem_raw);
@@ -136,31 +158,30 @@ __global__ void __launch_bounds__(THREADS) k_leaf_stats(AggWork w, DeriveArgs A)
                 for (uint32_t j = threadIdx.x; j <= ng; j += THREADS) gb[j] = seg[g0 + j] - start;
                 __syncthreads();
             }
-            for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
-                S.key[0][i] = src_sub[start + i];
-                S.val[0][i] = src_val[start + i];
-            }
+            for (uint32_t i = threadIdx.x; i < n; i += THREADS)
+                S.el[0][i] = (uint64_t)src_sub[start + i] | ((uint64_t)i << 32);
             __syncthreads();
             if (ng > 1) {
                 for (uint32_t j = threadIdx.x; j < ng; j += THREADS) {
                     const uint32_t a = gb[j], e = min(gb[j + 1], n);
-                    for (uint32_t i = a; i < e; ++i) S.key[0][i] |= j << w.sbits;
+                    for (uint32_t i = a; i < e; ++i) S.el[0][i] |= (uint64_t)(j << w.sbits);
                 }
                 __syncthreads();
             }
             const int cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
+            const uint64_t* el = S.el[cur];
             const int c0 = threadIdx.x * EPT, c1 = min((int)n, c0 + EPT);
             uint32_t heads = 0;
-            for (int i = c0; i < c1; ++i) heads += (i == 0) || (S.key[cur][i] != S.key[cur][i - 1]);
+            for (int i = c0; i < c1; ++i) heads += (i == 0) || ((uint32_t)el[i] != (uint32_t)el[i - 1]);
             uint32_t n_runs;
             uint32_t run = block_exclusive_scan<uint32_t, THREADS>(heads, sw, &n_runs);
             for (int i = c0; i < c1; ++i) {
-                const uint32_t k = S.key[cur][i];
-                if (!(i == 0 || k != S.key[cur][i - 1])) continue;
+                const uint32_t k = (uint32_t)el[i];
+                if (!(i == 0 || k != (uint32_t)el[i - 1])) continue;
                 uint32_t cnt = 0;
                 unsigned long long sum = 0, sql = 0, sqh = 0, mn = ~0ull, mx = 0;
-                for (int j = i; j < (int)n && S.key[cur][j] == k; ++j) {
-                    const unsigned long long x = S.val[cur][j];
+                for (int j = i; j < (int)n && (uint32_t)el[j] == k; ++j) {
+                    const unsigned long long x = src_val[start + (uint32_t)(el[j] >> 32)];
                     ++cnt;
                     sum += x;
                     const unsigned long long lo2 = x * x, hi2 = __umul64hi(x, x);
@@ -409,10 +430,10 @@ extern "C" hpa_status hpa_derive_metrics(hpa_handle* h, const hpa_profile* const
     run_plan(w, s, sms, &h->launches, false);
     k_union_scatter<<<blocks, 256, 0, s>>>(w, A);
     launch_big_partition(w, s, sms, &h->launches);
-    using Sort = BlockRadix<DS_THREADS, DS_CAP, 8, uint64_t, true>;
+    using Sort = PackedRadix<DS_THREADS, DS_CAP, uint64_t>;
     const size_t smem = std::max(sizeof(typename Sort::Smem), (size_t)DS_WIN * 44);
     cudaFuncSetAttribute(k_leaf_stats<DS_THREADS, DS_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_leaf_stats<DS_THREADS, DS_CAP><<<sms, DS_THREADS, smem, s>>>(w, A);
+    k_leaf_stats<DS_THREADS, DS_CAP><<<sms * 2, DS_THREADS, smem, s>>>(w, A);
     scan_u32(w.leaf_d, w.leaf_d, w.L_max, w.scan_tmp, s, &h->launches);
     k_emit_stats<<<sms * 8, 256, 0, s>>>(w, A, o);
     launch_finalize(w, s, &h->launches);

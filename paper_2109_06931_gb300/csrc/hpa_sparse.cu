@@ -16,6 +16,7 @@
 // and scans over that order give the planes and the metric index.
 
 #include "hpa_host.h"
+#include "hpa_warpagg.cuh"
 
 namespace hpa {
 
@@ -51,33 +52,45 @@ __device__ __forceinline__ bool sp_fetch(const SpArgs& A, uint64_t i, uint32_t& 
 }
 
 // ---- CMS
+// Both passes walk the flattened keys warp by warp (the loop is uniform in
+// a warp) and count with warp-aggregated atomics: the profiles are sorted by
+// context, so the lanes of a warp mostly share one.
 __global__ void k_cms_hist(AggWork w, SpArgs A) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < A.total; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); i0 < A.total; i0 += stride) {
+        const uint64_t i = i0 + (threadIdx.x & 31u);
+        uint32_t* ctr = nullptr;
         uint32_t p;
         uint64_t j;
-        if (!sp_fetch(A, i, p, j)) continue;
-        const SpDesc& d = A.prof[p];
-        const uint32_t c = d.ctx[j], n = d.node[j];
-        if (c >= A.n_ctx || d.stall[j] >= A.n_stall || (n != UNKNOWN && n >= A.M)) {
-            atomicAdd(&w.buf_bad[0], 1ull);
-            continue;
+        if (i < A.total && sp_fetch(A, i, p, j)) {
+            const SpDesc& d = A.prof[p];
+            const uint32_t c = d.ctx[j], n = d.node[j];
+            if (c >= A.n_ctx || d.stall[j] >= A.n_stall || (n != UNKNOWN && n >= A.M)) atomicAdd(&w.buf_bad[0], 1ull);
+            else ctr = &w.grp_hist[c];
         }
-        atomicAdd(&w.grp_hist[c], 1u);
+        warp_agg_inc(ctr);
     }
 }
 
 __global__ void k_cms_scatter(AggWork w, SpArgs A) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < A.total; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t p;
-        uint64_t j;
-        if (!sp_fetch(A, i, p, j)) continue;
-        const SpDesc& d = A.prof[p];
-        const uint32_t c = d.ctx[j], n = d.node[j], r = d.stall[j];
-        if (c >= A.n_ctx || r >= A.n_stall || (n != UNKNOWN && n >= A.M)) continue;
-        const uint32_t sub = (((n == UNKNOWN ? A.M : n) << A.sb) | r);
-        const uint32_t slot = atomicAdd(&w.grp_cursor[(size_t)c << w.cur_shift], 1u);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); i0 < A.total; i0 += stride) {
+        const uint64_t i = i0 + (threadIdx.x & 31u);
+        uint32_t* ctr = nullptr;
+        uint32_t p = 0, sub = 0;
+        uint64_t j = 0;
+        if (i < A.total && sp_fetch(A, i, p, j)) {
+            const SpDesc& d = A.prof[p];
+            const uint32_t c = d.ctx[j], n = d.node[j], r = d.stall[j];
+            if (c < A.n_ctx && r < A.n_stall && (n == UNKNOWN || n < A.M)) {
+                sub = (((n == UNKNOWN ? A.M : n) << A.sb) | r);
+                ctr = &w.grp_cursor[(size_t)c << w.cur_shift];
+            }
+        }
+        const uint32_t slot = warp_agg_inc(ctr);
+        if (!ctr) continue;
         w.rec_sub[slot] = (sub << A.pbits) | p;
-        w.rec_v64[slot] = d.val[j];
+        w.rec_v64[slot] = A.prof[p].val[j];
     }
 }
 
