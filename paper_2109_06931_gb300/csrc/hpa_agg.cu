@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "hpa_bulk.cuh"
 #include "hpa_internal.h"
 
 namespace hpa {
@@ -420,28 +421,47 @@ __global__ void k_part_seg(AggWork w) {
 // Shared memory of k_part_scatter for up to nb bins: per-bin cursors of the
 // part, the tile's per-bin counts / offsets, and the tile's records staged in
 // bin order (record + bin).
+// Ahead of them sits the stage of the next tile's samples (pc, ctx, count,
+// stall), filled by bulk copies while the current tile is processed.
+constexpr size_t PSC_STAGE_PC = 0, PSC_STAGE_CTX = PSC_TILE * 8, PSC_STAGE_CNT = PSC_TILE * 12,
+                 PSC_STAGE_ST = PSC_TILE * 16, PSC_STAGE = ((size_t)PSC_TILE * 17 + 127) & ~(size_t)127;
+
 __host__ __device__ inline size_t part_scatter_smem(uint32_t nb) {
-    return (size_t)nb * 4 + ((size_t)nb + 1) * 4 + 8 + (size_t)PSC_TILE * (8 + 2);
+    return PSC_STAGE + (size_t)nb * 4 + ((size_t)nb + 1) * 4 + 8 + (size_t)PSC_TILE * (8 + 2);
 }
 
 // Each part is processed in tiles of PART_TILE samples: the tile's records
 // are ranked by bin with shared-memory atomics, staged in bin order, and
 // then written so that consecutive threads store consecutive records of a
 // bin (coalesced runs instead of lone 8-byte stores, which the L2 would have
-// to merge with DRAM data when it evicts partly written sectors).
+// to merge with DRAM data when it evicts partly written sectors).  A full
+// tile whose arrays are 16-byte aligned arrives by bulk copies (TMA) into the
+// stage, issued by one thread as soon as every thread has read the previous
+// tile from it, so the next tile's loads overlap this tile's lookups and
+// stores; other tiles are loaded by the threads themselves.
 template <bool HAS_CNT, int U>
 __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(AggWork w) {
     static_assert(PSC_TILE == PSC_THREADS * U, "one tile = U samples per thread");
     constexpr int PART_THREADS = PSC_THREADS, PART_TILE = PSC_TILE;
-    extern __shared__ __align__(16) unsigned char psm[];
+    extern __shared__ __align__(128) unsigned char psm[];
     __shared__ uint32_t sw[33];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_abort;
     const uint32_t nbmax = w.part_ctx_max;
-    uint32_t* cur = reinterpret_cast<uint32_t*>(psm);                 // [nbmax] cursors of the part
+    uint64_t* spc = reinterpret_cast<uint64_t*>(psm + PSC_STAGE_PC);
+    uint32_t* sctx = reinterpret_cast<uint32_t*>(psm + PSC_STAGE_CTX);
+    uint32_t* scnt = reinterpret_cast<uint32_t*>(psm + PSC_STAGE_CNT);
+    uint8_t* sst = psm + PSC_STAGE_ST;
+    uint32_t* cur = reinterpret_cast<uint32_t*>(psm + PSC_STAGE);      // [nbmax] cursors of the part
     uint32_t* th = cur + nbmax;                                         // [nbmax + 1] tile counts -> offsets
-    uint2* srec = reinterpret_cast<uint2*>(psm + (((size_t)nbmax * 4 + ((size_t)nbmax + 1) * 4 + 7) & ~(size_t)7));
+    uint2* srec = reinterpret_cast<uint2*>(psm + PSC_STAGE + (((size_t)nbmax * 4 + ((size_t)nbmax + 1) * 4 + 7) & ~(size_t)7));
     uint16_t* sbin = reinterpret_cast<uint16_t*>(srec + PART_TILE);
     const uint64_t keep = policy_evict_last();
-    for (uint64_t p = blockIdx.x; p < w.n_parts; p += gridDim.x) {
+    const uint32_t limit = w.timeout_iters ? w.timeout_iters : (1u << 22);
+    if (threadIdx.x == 0) { mbar_init(&bar); s_abort = 0; }
+    uint32_t phase = 0;
+    bool aborted = false;
+    for (uint64_t p = blockIdx.x; p < w.n_parts && !aborted; p += gridDim.x) {
         const uint32_t b = upper_index<uint64_t>(w.buf_part, w.n_buf, p);
         const BufDev B = w.bufs[b];
         const DevBinary bin = w.bins[B.bin];
@@ -455,23 +475,55 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
         const bool two = w.part_mode == 2;
         const uint32_t* first = w.part_cnt + B.cnt_base + pl;
         for (uint32_t c = threadIdx.x; c < nbin; c += PART_THREADS) cur[c] = first[(uint64_t)c * parts];
+        const bool cnt_in = HAS_CNT && B.count;
+        // a full tile whose four source ranges start on 16-byte boundaries (all
+        // sizes are multiples of 16 bytes)
+        auto staged = [&](uint64_t t) {
+            return t + PART_TILE <= i1 && aligned16(B.pc + t) && aligned16(B.ctx + t) && aligned16(B.stall + t) &&
+                   (!cnt_in || aligned16(B.count + t));
+        };
+        auto issue = [&](uint64_t t) {                  // one thread; every thread is done with the stage
+            fence_proxy_async();
+            mbar_expect_tx(&bar, PART_TILE * (cnt_in ? 8u + 4u + 1u + 4u : 8u + 4u + 1u));
+            bulk_g2s(spc, B.pc + t, PART_TILE * 8, &bar);
+            bulk_g2s(sctx, B.ctx + t, PART_TILE * 4, &bar);
+            bulk_g2s(sst, B.stall + t, PART_TILE, &bar);
+            if (cnt_in) bulk_g2s(scnt, B.count + t, PART_TILE * 4, &bar);
+        };
+        if (threadIdx.x == 0 && staged(i0)) issue(i0);
         uint32_t bad = 0;
         for (uint64_t t0 = i0; t0 < i1; t0 += PART_TILE) {
             for (uint32_t c = threadIdx.x; c <= nbin; c += PART_THREADS) th[c] = 0;
+            const bool from_stage = staged(t0);
+            if (from_stage) {
+                if (!mbar_wait(&bar, phase, limit)) {
+                    s_abort = 1;
+                    raise_status(w.status, 7 /* HPA_E_TIMEOUT */, 1);
+                }
+                phase ^= 1u;
+            }
             __syncthreads();
+            if (s_abort) { aborted = true; break; }
             uint64_t pc[U];
             uint32_t st[U], cnt[U], cx[U], nd[U], rk[U];
             bool ok[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint64_t i = t0 + (uint64_t)u * PART_THREADS + threadIdx.x;
+                const uint32_t k = (uint32_t)u * PART_THREADS + threadIdx.x;
+                const uint64_t i = t0 + k;
                 ok[u] = i < i1;
                 pc[u] = 0; st[u] = 0; cnt[u] = 1u; cx[u] = 0xFFFFFFFFu;
-                if (ok[u]) {
+                if (from_stage) {
+                    cx[u] = sctx[k];
+                    st[u] = sst[k];
+                    pc[u] = spc[k];
+                    if (cnt_in) cnt[u] = scnt[k];
+                    ok[u] = cx[u] < n_ctx;
+                } else if (ok[u]) {
                     cx[u] = ld_stream(&B.ctx[i]);
                     st[u] = ld_stream(&B.stall[i]);
                     pc[u] = ld_stream((const unsigned long long*)&B.pc[i]);
-                    if (HAS_CNT && B.count) cnt[u] = ld_stream(&B.count[i]);
+                    if (cnt_in) cnt[u] = ld_stream(&B.count[i]);
                     ok[u] = cx[u] < n_ctx;                  // counted as invalid by k_part_hist
                 }
             }
@@ -480,6 +532,7 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
             for (int u = 0; u < U; ++u)
                 if (ok[u]) rk[u] = atomicAdd(&th[cx[u] >> shift], 1u);
             __syncthreads();
+            if (threadIdx.x == 0 && staged(t0 + PART_TILE)) issue(t0 + PART_TILE);
             const uint32_t tot = block_scan_array<uint32_t, PSC_THREADS, PSC_SCAN_EPT>(th, (int)nbin, sw);
             if (threadIdx.x == 0) th[nbin] = tot;
 #pragma unroll
@@ -512,6 +565,9 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
         }
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
     }
+    // after a wait gave up, the copies of that tile may still be in flight:
+    // wait for them (bounded again) before the CTA's shared memory goes away
+    if (aborted) mbar_wait(&bar, phase ^ 1u, limit);
 }
 
 // ------------------------------------------------------------------ second pass (part_mode 2)

@@ -637,6 +637,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         w.span_log = std::min<uint32_t>(10, 32 - u.sbits);
         w.n_tiles = u.tiles;
         w.emit_totals = 1;
+        w.timeout_iters = opt.timeout_iters;
         w.small_leaves = opt.small_leaves == 2 || (opt.small_leaves == 0 && u.N < 64 * u.G);
         w.leaf_hash = opt.leaf_hash;
         if (u.mode) {

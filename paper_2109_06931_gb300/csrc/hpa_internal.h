@@ -99,6 +99,7 @@ struct AggWork {
     uint32_t emit_totals;         // k_emit sums the per-stall and UNKNOWN totals
     uint32_t small_leaves;        // leaves of <= SMALL_LEAF_CAP records go to the small-leaf kernel
     uint32_t leaf_hash;           // leaves aggregate in a shared-memory hash table before sorting
+    uint32_t timeout_iters;       // polls of a bounded device wait (0 = 1 << 22)
 };
 
 constexpr int TILE = 4096;            // samples per tile of the sample-reading kernels

@@ -87,6 +87,7 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
     w.cur_shift = 0;
     w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt; w.val64 = false;
     w.emit_totals = 1;
+    w.timeout_iters = h->opt.timeout_iters;
     w.n_tiles = (N + TILE - 1) / TILE;
     BufDev* d_buf = nullptr;
     uint64_t* d_tile = nullptr;

@@ -368,3 +368,17 @@ def test_batch_with_many_sub_batches(H, plain):
         H.sync()
         for o, S in zip(outs, ss):
             assert_same_keys(o, oracle.attribute_samples(B, S))
+
+
+@pytest.mark.parametrize("n_ctx,counts", [(300, True), (300, False), (20_000, True)])
+@pytest.mark.parametrize("off", [1, 3])
+def test_unaligned_sample_arrays(H, plain, n_ctx, counts, off):
+    """Sample arrays that do not start on a 16-byte boundary (slices of
+    larger tensors): tiles are then loaded by the threads instead of bulk
+    copies, with the same result."""
+    B, bid = plain
+    S = synth.make_samples(91 + off, B, 700_000 + off, n_ctx, 1.1, counts=counts, device="cuda")
+    T = synth.Samples(S.pc[off:], S.ctx[off:], S.stall[off:], None if S.count is None else S.count[off:],
+                      S.n_ctx, S.n_stall)
+    out = run(H, bid, T)
+    assert_same_keys(out, oracle.attribute_samples(B, T))
