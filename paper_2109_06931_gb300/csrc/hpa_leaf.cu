@@ -22,11 +22,13 @@ namespace hpa {
 
 template <int THREADS, int CAP, bool HAS_CNT, typename V, bool HASH>
 struct LeafCfg {
-    // 32-bit counts (or none): packed elements, digits up to 9 bits;
-    // 64-bit values: key and value arrays, 8-bit digits
+    // 32-bit counts (or none): packed (count, key) elements, digits up to 9
+    // bits; 64-bit values: packed (record index, key) elements sorted the
+    // same way, the values gathered by index when the runs are summed
     static constexpr bool PACKED = sizeof(V) == 4;
+    static constexpr bool IDX = !PACKED && HAS_CNT;
     using E = std::conditional_t<HAS_CNT, uint64_t, uint32_t>;
-    using Sort = std::conditional_t<PACKED, PackedRadix<THREADS, CAP, E>, BlockRadix<THREADS, CAP, 8, V, HAS_CNT>>;
+    using Sort = std::conditional_t<PACKED || IDX, PackedRadix<THREADS, CAP, E>, BlockRadix<THREADS, CAP, 8, V, HAS_CNT>>;
     static constexpr int EPT = (CAP + THREADS - 1) / THREADS;
     static constexpr size_t SORT_BYTES = sizeof(typename Sort::Smem);
     static constexpr int WD = 8192;                              // dense window (uint64 counters)
@@ -352,6 +354,13 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
                         zero |= v == 0;
                         vmax = max(vmax, (unsigned long long)v);
                     }
+            } else if constexpr (Cfg::IDX) {
+                for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
+                    const unsigned long long v = src_v64[start + i];
+                    S.el[0][i] = (uint64_t)src_sub[start + i] | ((uint64_t)i << 32);
+                    zero |= v == 0;
+                    vmax = max(vmax, v);
+                }
             } else {
                 for (uint32_t i = threadIdx.x; i < n; i += THREADS) {
                     uint32_t k;
@@ -369,22 +378,25 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
                 for (uint32_t j = threadIdx.x; j < ng; j += THREADS) {
                     const uint32_t a = gb[j], e = min(gb[j + 1], n);
                     for (uint32_t i = a; i < e; ++i) {
-                        if constexpr (Cfg::PACKED) S.el[0][i] |= (typename Cfg::E)(j << w.sbits);
+                        if constexpr (Cfg::PACKED || Cfg::IDX) S.el[0][i] |= (typename Cfg::E)(j << w.sbits);
                         else S.key[0][i] |= j << w.sbits;
                     }
                 }
             }
             __syncthreads();
             int cur;
-            if constexpr (Cfg::PACKED) cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits), (int)w.sort_mode);
+            if constexpr (Cfg::PACKED || Cfg::IDX) cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits), (int)w.sort_mode);
             else cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
             auto Kc = [&S, cur](int i) -> uint32_t {
-                if constexpr (Cfg::PACKED) return Sort::key_of(S.el[cur][i]);
+                if constexpr (Cfg::PACKED || Cfg::IDX) return Sort::key_of(S.el[cur][i]);
                 else return S.key[cur][i];
             };
-            auto Vc = [&S, cur](int i) -> unsigned long long {
+            const uint64_t* vsrc = src_v64 + start;
+            auto Vc = [&S, cur, vsrc](int i) -> unsigned long long {
                 if constexpr (Cfg::PACKED) {
                     return (unsigned long long)Sort::val_of(S.el[cur][i]);
+                } else if constexpr (Cfg::IDX) {
+                    return (unsigned long long)vsrc[(uint32_t)(S.el[cur][i] >> 32)];
                 } else {
                     if constexpr (HAS_CNT) return (unsigned long long)S.val[cur][i];
                     else return 1ull;
@@ -501,7 +513,7 @@ static void launch_packed_leaves(const AggWork& w, cudaStream_t s, int sms) {
 
 void launch_leaves(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
     if (w.val64) {
-        launch_leaf<256, LEAF_CAP_SMALL, true, uint64_t, false>(w, s, sms, 1);
+        launch_leaf<256, LEAF_CAP_SMALL, true, uint64_t, false>(w, s, sms, 2);
         *launches += 1;
         return;
     }
