@@ -64,9 +64,12 @@ __global__ void k_bu_sites(BuArgs a, int pass) {
             const uint32_t p = a.cparent[v];
             if ((p != HPA_NO_PARENT && p >= v) || a.cmodule[v] == 0xFFFFu || (a.coffset[v] >> 48))
                 raise_status(a.status, 2 /* HPA_E_INVALID_TABLE */, (int32_t)v);
-            if (!ut_insert(a.tkeys, a.tvals, a.tmask, key, v)) raise_status(a.status, 8 /* HPA_E_INTERNAL */, 3);
+            const uint32_t slot = ut_insert(a.tkeys, a.tvals, a.tmask, key, v);
+            if (slot > a.tmask) raise_status(a.status, 8 /* HPA_E_INTERNAL */, 3);
+            a.site_rep[v] = slot;
         } else {
-            const uint32_t r = ut_find(a.tkeys, a.tvals, a.tmask, key);
+            const uint32_t slot = a.site_rep[v];
+            const uint32_t r = slot <= a.tmask ? a.tvals[slot] : v;
             a.site_rep[v] = r < a.n_cct ? r : v;
         }
     }
@@ -102,21 +105,26 @@ __device__ __forceinline__ bool bu_live(const BuArgs& a, uint64_t i, uint32_t le
     return true;
 }
 
+// insertion keeps each key's slot in rep[]; the next pass reads the slot's
+// representative (the smallest key index inserted there)
 __global__ void k_bu_insert(BuArgs a, uint32_t lev) {
     const uint64_t Kd = bu_keys(a);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < Kd; i += (uint64_t)gridDim.x * blockDim.x) {
         unsigned long long key;
-        if (!bu_live(a, i, lev, &key)) continue;
-        if (!ut_insert(a.tkeys, a.tvals, a.tmask, key, (uint32_t)i)) raise_status(a.status, 8, 4);
+        uint32_t slot = HPA_NO_PARENT;
+        if (bu_live(a, i, lev, &key)) {
+            slot = ut_insert(a.tkeys, a.tvals, a.tmask, key, (uint32_t)i);
+            if (slot > a.tmask) raise_status(a.status, 8, 4);
+        }
+        a.rep[i] = slot;
     }
 }
 
 __global__ void k_bu_find(BuArgs a, uint32_t lev) {
     const uint64_t Kd = bu_keys(a);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.K; i += (uint64_t)gridDim.x * blockDim.x) {
-        unsigned long long key;
-        uint32_t r = HPA_NO_PARENT;
-        if (i < Kd && bu_live(a, i, lev, &key)) r = ut_find(a.tkeys, a.tvals, a.tmask, key);
+        const uint32_t slot = i < Kd ? a.rep[i] : HPA_NO_PARENT;
+        const uint32_t r = slot <= a.tmask ? a.tvals[slot] : HPA_NO_PARENT;
         a.rep[i] = r;
         a.rank[i] = r == (uint32_t)i;
     }

@@ -22,8 +22,10 @@ __device__ __forceinline__ uint32_t uhash(unsigned long long k, uint32_t mask) {
     return (uint32_t)k & mask;
 }
 
-__device__ __forceinline__ bool ut_insert(unsigned long long* keys, uint32_t* vals, uint32_t mask,
-                                          unsigned long long key, uint32_t idx) {
+// Returns the key's slot, or 0xFFFFFFFF when the table is full; once every
+// insertion has finished, vals[slot] is the key's representative.
+__device__ __forceinline__ uint32_t ut_insert(unsigned long long* keys, uint32_t* vals, uint32_t mask,
+                                              unsigned long long key, uint32_t idx) {
     uint32_t h = uhash(key, mask);
     volatile unsigned long long* vk = keys;
     for (uint32_t t = 0; t <= mask; ++t) {
@@ -32,10 +34,10 @@ __device__ __forceinline__ bool ut_insert(unsigned long long* keys, uint32_t* va
             cur = atomicCAS(&keys[h], UEMPTY, key);
             if (cur == UEMPTY) cur = key;
         }
-        if (cur == key) { atomicMin(&vals[h], idx); return true; }
+        if (cur == key) { atomicMin(&vals[h], idx); return h; }
         h = (h + 1) & mask;
     }
-    return false;
+    return 0xFFFFFFFFu;
 }
 
 __device__ __forceinline__ uint32_t ut_find(const unsigned long long* keys, const uint32_t* vals, uint32_t mask,

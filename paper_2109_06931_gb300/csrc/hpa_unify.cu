@@ -82,11 +82,14 @@ __global__ void k_un_sites(UnifyArgs a, int pass, int cur) {
         const UnifyDesc& d = a.ccts[p];
         const uint64_t j = i - d.base;
         const unsigned long long key = ((unsigned long long)d.module[j] << 48) | (d.offset[j] & 0xFFFFFFFFFFFFull);
-        if (pass == 0) {
-            if (!ut_insert(a.skeys, a.svals, a.tmask, key, (uint32_t)i)) raise_status(a.status, 8 /* HPA_E_INTERNAL */, 1);
+        if (pass == 0) {                                // the slot waits in site_rep for pass 1
+            const uint32_t slot = ut_insert(a.skeys, a.svals, a.tmask, key, (uint32_t)i);
+            if (slot > a.tmask) raise_status(a.status, 8 /* HPA_E_INTERNAL */, 1);
+            a.site_rep[i] = slot;
             atomicMax(a.maxdep, a.dep[cur][i]);
         } else {
-            a.site_rep[i] = ut_find(a.skeys, a.svals, a.tmask, key);
+            const uint32_t slot = a.site_rep[i];
+            a.site_rep[i] = slot <= a.tmask ? a.svals[slot] : 0xFFFFFFFFu;
         }
     }
 }
@@ -98,10 +101,13 @@ __global__ void k_un_level(UnifyArgs a, uint32_t level, int cur, int pass) {
         const uint32_t pk = g == HPA_NO_PARENT ? 0xFFFFFFFFu : a.rep[g];
         if (a.site_rep[i] >= a.N) { if (pass) a.rep[i] = HPA_NO_PARENT; continue; }   // only after a raised status
         const unsigned long long key = ((unsigned long long)pk << 32) | a.site_rep[i];
-        if (pass == 0) {
-            if (!ut_insert(a.nkeys, a.nvals, a.tmask, key, (uint32_t)i)) raise_status(a.status, 8, 2);
+        if (pass == 0) {                                // the slot waits in rep for pass 1
+            const uint32_t slot = ut_insert(a.nkeys, a.nvals, a.tmask, key, (uint32_t)i);
+            if (slot > a.tmask) raise_status(a.status, 8, 2);
+            a.rep[i] = slot;
         } else {
-            a.rep[i] = ut_find(a.nkeys, a.nvals, a.tmask, key);
+            const uint32_t slot = a.rep[i];
+            a.rep[i] = slot <= a.tmask ? a.nvals[slot] : HPA_NO_PARENT;
         }
     }
 }
