@@ -699,8 +699,14 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part2_scatter(AggWork w) {
 
 // ------------------------------------------------------------------ K10: split big groups
 // One CTA per big group: fine-bin histogram, offsets, leaf boundaries (runs
-// of bins, see big_leaf_head) and a stable-per-bin scatter into rec2.
-__global__ void __launch_bounds__(BIG_THREADS) k_big_partition(AggWork w) {
+// of bins, see big_leaf_head) and a scatter by bin into rec2 (the order
+// within a bin is free: its leaf sorts it).  Both passes load BIG_U records
+// per thread before their shared-memory atomics, to keep loads in flight.
+// (Warp-aggregating those atomics with __match_any_sync made the pass 2.6x
+// slower: hot bins are not what limits it.)
+constexpr int BIG_U = 4;
+
+__global__ void __launch_bounds__(BIG_THREADS, 2) k_big_partition(AggWork w) {
     extern __shared__ uint32_t off[];            // 2^h + 1 bin counts, then offsets, then cursors
     __shared__ uint32_t sw[33];
     const uint32_t n_items = w.item_id[w.G];
@@ -717,8 +723,17 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_partition(AggWork w) {
         if (n <= w.cap) continue;                 // uniform across the block
         for (uint32_t j = threadIdx.x; j <= nb; j += BIG_THREADS) off[j] = 0;
         __syncthreads();
-        for (uint32_t i = s0 + threadIdx.x; i < s1; i += BIG_THREADS)
-            atomicAdd(&off[(pair ? w.rec_pair[i].x : w.rec_sub[i]) >> shift], 1u);
+        for (uint32_t i0 = s0 + threadIdx.x; i0 < s1; i0 += BIG_THREADS * BIG_U) {
+            uint32_t k[BIG_U];
+#pragma unroll
+            for (int u = 0; u < BIG_U; ++u) {
+                const uint32_t i = i0 + u * BIG_THREADS;
+                if (i < s1) k[u] = pair ? w.rec_pair[i].x : w.rec_sub[i];
+            }
+#pragma unroll
+            for (int u = 0; u < BIG_U; ++u)
+                if (i0 + u * BIG_THREADS < s1) atomicAdd(&off[k[u] >> shift], 1u);
+        }
         __syncthreads();
         block_scan_array<uint32_t, BIG_THREADS, BIG_EPT>(off, nb + 1, sw);   // off[nb] = n
         // leaf boundaries
@@ -750,15 +765,27 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_partition(AggWork w) {
             w.leaf_info[l0 + k] = (b << 8) | 1u;
         }
         __syncthreads();
-        for (uint32_t i = s0 + threadIdx.x; i < s1; i += BIG_THREADS) {
-            if (pair) {
-                const uint2 r = w.rec_pair[i];
-                w.rec2_pair[s0 + atomicAdd(&off[r.x >> shift], 1u)] = r;
-            } else {
-                const uint32_t sub = w.rec_sub[i];
-                const uint32_t p = s0 + atomicAdd(&off[sub >> shift], 1u);
-                w.rec2_sub[p] = sub;
-                if (w.val64) w.rec2_v64[p] = w.rec_v64[i];
+        for (uint32_t i0 = s0 + threadIdx.x; i0 < s1; i0 += BIG_THREADS * BIG_U) {
+            uint2 r[BIG_U];
+#pragma unroll
+            for (int u = 0; u < BIG_U; ++u) {
+                const uint32_t i = i0 + u * BIG_THREADS;
+                if (i < s1) {
+                    if (pair) r[u] = w.rec_pair[i];
+                    else r[u].x = w.rec_sub[i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < BIG_U; ++u) {
+                const uint32_t i = i0 + u * BIG_THREADS;
+                if (i >= s1) break;
+                const uint32_t p = s0 + atomicAdd(&off[r[u].x >> shift], 1u);
+                if (pair) {
+                    w.rec2_pair[p] = r[u];
+                } else {
+                    w.rec2_sub[p] = r[u].x;
+                    if (w.val64) w.rec2_v64[p] = w.rec_v64[i];
+                }
             }
         }
         __syncthreads();
