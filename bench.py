@@ -401,9 +401,18 @@ def max_over_ranks(x: float, world: int, device) -> float:
     if world == 1:
         return x
     import torch.distributed as dist
+    if dist.get_backend() != "nccl":
+        device = "cpu"
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_start(rank: int, n: int) -> int:
+    """First sample (or buffer) index of rank's shard: replicas process
+    disjoint slices of the same seeded streams, so the units of all ranks
+    are distinct."""
+    return rank * n
 
 
 def barrier(world):
@@ -457,7 +466,8 @@ def run_batched(args, world, rank, local):
         n_each = max(1, args.samples // w.n_buffers) if args.samples else w.n_samples
         bins = [w.binary()]
         ids = [h.load_structure(bins[0])]
-        bufs = [w.buffer(i, bins[0], n_each, device=dev) for i in range(w.n_buffers)]
+        b0 = shard_start(rank, w.n_buffers)
+        bufs = [w.buffer(b0 + i, bins[0], n_each, device=dev) for i in range(w.n_buffers)]
         bids = [ids[0]] * len(bufs)
         outs = [H.new_profile(min(b.n, w.n_tuples), b.n_stall, dev) for b in bufs]
         extra = {"cct_nodes": w.cct_nodes, "tuples_per_buffer": w.n_tuples}
@@ -468,7 +478,8 @@ def run_batched(args, world, rank, local):
             sizes = np.maximum(1, (sizes * (args.samples / sizes.sum())).astype(np.int64))
         bins = w.binaries()
         ids = [h.load_structure(b) for b in bins]
-        bufs = [w.buffer(i, bins[i % len(bins)], int(n), device=dev) for i, n in enumerate(sizes)]
+        b0 = shard_start(rank, w.n_buffers)
+        bufs = [w.buffer(b0 + i, bins[i % len(bins)], int(n), device=dev) for i, n in enumerate(sizes)]
         bids = [ids[i % len(ids)] for i in range(len(bufs))]
         outs = [H.new_profile(b.n, b.n_stall, dev) for b in bufs]
     N = int(sum(b.n for b in bufs))
@@ -595,7 +606,7 @@ def main():
         import dataclasses
         w = dataclasses.replace(w, n_ctx=args.contexts)
     B = w.binary()
-    S = w.samples(B, device=dev)
+    S = w.samples(B, device=dev, start=shard_start(rank, w.n_samples))
     N = S.n
     stream = torch.cuda.Stream(dev)
     h = H.Hpa(local, stream=stream, cursor_shift=args.cursor_shift, sort_mode=args.sort_mode,
