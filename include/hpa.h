@@ -248,6 +248,16 @@ hpa_status hpa_sync(hpa_handle* h, uint64_t* bad);
  * contexts (summed over a batch), so that later calls allocate nothing (as
  * stream capture requires).  Calls grow the scratch themselves otherwise.     */
 hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t max_groups);
+/* Bounded device wait (failure detection): enqueue on the handle's stream a
+ * kernel that polls the DEVICE word *flag until it equals `value`, at most
+ * opt.timeout_iters times with about a microsecond of sleep between polls.
+ * If the word never takes the value, the kernel records HPA_E_TIMEOUT
+ * (reported by hpa_sync) and returns, so the stream moves on and the context
+ * stays usable.  Use: the handle's work on a buffer waits for the ready flag
+ * of whatever produced it -- set by work ordered before the wait, or by the
+ * host in mapped memory.  It must not wait for a kernel that only runs
+ * after it (nothing guarantees two kernels run at the same time).          */
+hpa_status hpa_wait_flag(hpa_handle* h, const uint32_t* flag, uint32_t value);
 /* Number of kernels the handle has launched so far. */
 uint64_t hpa_kernel_launches(hpa_handle* h);
 /* Per-phase timing of the aggregation pipeline with CUDA events recorded on

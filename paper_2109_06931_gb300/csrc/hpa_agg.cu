@@ -566,8 +566,9 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
         if (bad) atomicAdd(&w.buf_bad[b], (unsigned long long)bad);
     }
     // after a wait gave up, the copies of that tile may still be in flight:
-    // wait for them (bounded again) before the CTA's shared memory goes away
-    if (aborted) mbar_wait(&bar, phase ^ 1u, limit);
+    // wait for them (bounded again, by at least 2^22 polls whatever the
+    // option says) before the CTA's shared memory goes away
+    if (aborted) mbar_wait(&bar, phase ^ 1u, max(limit, 1u << 22));
 }
 
 // ------------------------------------------------------------------ second pass (part_mode 2)

@@ -846,3 +846,25 @@ extern "C" hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_
     out->n_nodes = d.n_nodes;
     return hpa_sync(h, nullptr);
 }
+
+namespace hpa {
+
+// polls with a sleep between reads; records a timeout instead of spinning on
+__global__ void k_wait_flag(const uint32_t* flag, uint32_t value, uint32_t limit, DevStatus* st) {
+    const volatile uint32_t* f = flag;
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (*f == value) return;
+        __nanosleep(1000);
+    }
+    raise_status(st, 7 /* HPA_E_TIMEOUT */, 0);
+}
+
+}  // namespace hpa
+
+extern "C" hpa_status hpa_wait_flag(hpa_handle* h, const uint32_t* flag, uint32_t value) {
+    if (!h || !flag) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    hpa::k_wait_flag<<<1, 1, 0, h->stream>>>(flag, value, h->opt.timeout_iters, h->d_status);
+    h->launches += 1;
+    return h->cuda(cudaGetLastError(), "wait launch");
+}

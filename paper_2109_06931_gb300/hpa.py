@@ -155,6 +155,7 @@ def lib(build_if_needed: bool = True):
                                          C.POINTER(hpa_cct_tree)]
         L.hpa_bottom_up_view.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_cct_nodes),
                                          C.POINTER(hpa_bottom_up)]
+        L.hpa_wait_flag.argtypes = [H, vp, C.c_uint32]
         L.hpa_unify_ccts.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_cct_unified)]
         L.hpa_build_cms.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_cms)]
         L.hpa_build_pms.argtypes = [H, vp, C.c_uint32, C.POINTER(hpa_pms)]
@@ -241,14 +242,14 @@ class Hpa:
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, issued_mask: int = 1,
                  leaf_capacity: int = 0, cursor_shift: int | None = None,
                  sort_mode: int | None = None, partition: bool = True, small_leaves: int = 0,
-                 leaf_hash: int = 0):
+                 leaf_hash: int = 0, timeout_iters: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("hpa needs a CUDA device; there is no CPU implementation")
         self.L = lib()
         self.device = torch.device("cuda", device)
         self.stream = stream or torch.cuda.current_stream(self.device)
         self.h = C.c_void_p()
-        opt = hpa_options(issued_mask, leaf_capacity, 0)
+        opt = hpa_options(issued_mask, leaf_capacity, timeout_iters)
         if cursor_shift is not None:
             opt.cursor_pad = cursor_shift + 1
         if sort_mode is not None:
@@ -290,6 +291,10 @@ class Hpa:
         bad = C.c_uint64(0)
         st = self.L.hpa_sync(self.h, C.byref(bad))
         return int(st), int(bad.value)
+
+    def wait_flag(self, flag: torch.Tensor, value: int):
+        """hpa_wait_flag: the handle's stream waits (bounded) for flag[0] == value."""
+        self.check(self.L.hpa_wait_flag(self.h, _ptr(flag), C.c_uint32(value)))
 
     def launches(self) -> int:
         return int(self.L.hpa_kernel_launches(self.h))
