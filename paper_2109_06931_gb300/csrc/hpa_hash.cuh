@@ -1,7 +1,8 @@
 // Open-addressing hash tables of 64-bit keys with a 32-bit value per slot,
 // for grouping equal keys on the device: insertion claims a slot with a
 // compare-and-swap on the key and keeps the minimum of the inserted values
-// (the representative: the first index, in input order, with that key).
+// (the representative: the first index, in input order, with that key); a
+// second pass reads the representative from the slot the insertion returned.
 // Linear probing; tables hold a power of two of slots, at least twice the
 // keys inserted, keys initialised to all ones (which no key may equal) and
 // values to all ones.
@@ -13,6 +14,7 @@ namespace hpa {
 
 constexpr unsigned long long UEMPTY = ~0ull;
 
+// slot of a key: the 64-bit finalizer of MurmurHash3 (Appleby), masked
 __device__ __forceinline__ uint32_t uhash(unsigned long long k, uint32_t mask) {
     k ^= k >> 33;
     k *= 0xff51afd7ed558ccdull;
@@ -35,18 +37,6 @@ __device__ __forceinline__ uint32_t ut_insert(unsigned long long* keys, uint32_t
             if (cur == UEMPTY) cur = key;
         }
         if (cur == key) { atomicMin(&vals[h], idx); return h; }
-        h = (h + 1) & mask;
-    }
-    return 0xFFFFFFFFu;
-}
-
-__device__ __forceinline__ uint32_t ut_find(const unsigned long long* keys, const uint32_t* vals, uint32_t mask,
-                                            unsigned long long key) {
-    uint32_t h = uhash(key, mask);
-    for (uint32_t t = 0; t <= mask; ++t) {
-        const unsigned long long cur = keys[h];
-        if (cur == key) return vals[h];
-        if (cur == UEMPTY) return 0xFFFFFFFFu;
         h = (h + 1) & mask;
     }
     return 0xFFFFFFFFu;
