@@ -514,12 +514,18 @@ typedef struct hpa_server hpa_server;
 typedef struct {
     uint64_t mem_cap_bytes;  /* device pool for admitted requests; 0 = 60 GiB    */
     uint32_t max_batch;      /* requests per batch; 0 = 64                      */
-    uint32_t reserved[5];
+    uint32_t max_inflight;   /* batches between copy-in and copy-out; 0 = 3     */
+    uint32_t reserved[4];
 } hpa_server_options;
 typedef struct {
     uint64_t submitted, completed, rejected, samples, batches;
     double p50_ms, p99_ms, max_ms, mean_ms;   /* latency: submit -> result in host arrays */
     double busy_s;                            /* first admission -> last completion        */
+    /* per batch, mean milliseconds (CUDA events): samples copied in; waiting
+     * for the device after they arrived; computing; keys ready but not yet
+     * being copied out; copying out.  launch_ms: host time to admit a batch
+     * and enqueue its work.                                                  */
+    double h2d_ms, wait_compute_ms, compute_ms, wait_d2h_ms, d2h_ms, launch_ms;
 } hpa_server_stats;
 
 hpa_status hpa_server_create(hpa_handle* h, const hpa_server_options* opt, hpa_server** out);

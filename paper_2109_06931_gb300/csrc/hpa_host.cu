@@ -57,36 +57,63 @@ hpa_status hpa_handle::ensure_scratch(size_t bytes) {
     return HPA_OK;
 }
 
-hpa_status hpa_handle::ensure_staging(size_t bytes) {
-    if (bytes <= staging_cap) {
-        if (staging_event_live) {
-            hpa_status st = cuda(cudaEventSynchronize(staging_event), "cudaEventSynchronize");
-            if (st) return st;
+hpa_status hpa_handle::ensure_staging(size_t bytes, bool for_graph) {
+    const int k = for_graph ? 0 : staging_next;
+    if (!for_graph) staging_next = staging_next % (N_STAGING - 1) + 1;
+    StagingSlot& sl = stage_slots[k];
+    if (!sl.ev && cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess)
+        return cuda(cudaGetLastError(), "staging event");
+    if (bytes > sl.cap) {
+        if (capturing()) return fail(HPA_E_OOM, "descriptor staging must grow during stream capture");
+        if (sl.live) cudaEventSynchronize(sl.ev);
+        if (sl.host) cudaFreeHost(sl.host);
+        if (sl.dev) cudaFree(sl.dev);
+        sl.host = nullptr; sl.dev = nullptr; sl.cap = 0; sl.live = false;
+        size_t want = std::max<size_t>(bytes, 64 << 10);
+        if (cudaMallocHost(&sl.host, want) != cudaSuccess || cudaMalloc(&sl.dev, want) != cudaSuccess) {
+            cudaGetLastError();
+            if (sl.host) cudaFreeHost(sl.host);
+            if (sl.dev) cudaFree(sl.dev);
+            sl.host = nullptr; sl.dev = nullptr;
+            return fail(HPA_E_OOM, "cannot allocate %zu bytes of descriptor staging", want);
         }
-        return HPA_OK;
+        sl.cap = want;
+        if (k == 0) ++scratch_epoch;           // graphs copy from slot 0's buffers
+        // the other rotating slots come into being with the first one, so one
+        // call prepares them all (for callers that capture later calls)
+        for (int j = 1; j < N_STAGING && k != 0; ++j) {
+            StagingSlot& o = stage_slots[j];
+            if (o.cap || j == k) continue;
+            if (!o.ev && cudaEventCreateWithFlags(&o.ev, cudaEventDisableTiming) != cudaSuccess)
+                return cuda(cudaGetLastError(), "staging event");
+            if (cudaMallocHost(&o.host, want) != cudaSuccess || cudaMalloc(&o.dev, want) != cudaSuccess) {
+                cudaGetLastError();
+                if (o.host) cudaFreeHost(o.host);
+                if (o.dev) cudaFree(o.dev);
+                o.host = nullptr; o.dev = nullptr;
+                return fail(HPA_E_OOM, "cannot allocate %zu bytes of descriptor staging", want);
+            }
+            o.cap = want;
+        }
+    } else if (sl.live) {
+        hpa_status st = cuda(cudaEventSynchronize(sl.ev), "cudaEventSynchronize");
+        if (st) return st;
     }
-    if (capturing()) return fail(HPA_E_OOM, "descriptor staging must grow during stream capture");
-    if (staging_event_live) cudaEventSynchronize(staging_event);
-    if (staging) cudaFreeHost(staging);
-    if (d_staging) cudaFree(d_staging);
-    staging = nullptr; d_staging = nullptr; staging_cap = 0;
-    size_t want = std::max<size_t>(bytes, 64 << 10);
-    if (cudaMallocHost(&staging, want) != cudaSuccess || cudaMalloc(&d_staging, want) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(HPA_E_OOM, "cannot allocate %zu bytes of descriptor staging", want);
-    }
-    staging_cap = want;
-    ++scratch_epoch;
+    staging_slot = k;
+    staging = sl.host;
+    d_staging = sl.dev;
+    staging_cap = sl.cap;
     return HPA_OK;
 }
 
-// upload the staged descriptors; the host must not touch `staging` until the
-// event has completed (ensure_staging waits for it)
+// upload the staged descriptors; the host must not touch the slot's buffer
+// until its event has completed (ensure_staging waits for it)
 hpa_status hpa_handle::upload_staging(size_t bytes) {
     hpa_status st = cuda(cudaMemcpyAsync(d_staging, staging, bytes, cudaMemcpyHostToDevice, stream), "upload descriptors");
     if (st) return st;
-    st = cuda(cudaEventRecord(staging_event, stream), "cudaEventRecord");
-    staging_event_live = true;
+    StagingSlot& sl = stage_slots[staging_slot];
+    st = cuda(cudaEventRecord(sl.ev, stream), "cudaEventRecord");
+    sl.live = true;
     return st;
 }
 
@@ -117,8 +144,7 @@ extern "C" hpa_status hpa_create(hpa_handle** out, int device, void* cuda_stream
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&h->d_status, sizeof(DevStatus)) != cudaSuccess ||
-        cudaMemset(h->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->staging_event, cudaEventDisableTiming) != cudaSuccess) {
+        cudaMemset(h->d_status, 0, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return HPA_E_CUDA;
@@ -131,11 +157,13 @@ hpa_handle::~hpa_handle() {
     cudaStreamSynchronize(stream);
     for (Binary* b : bins) delete b;
     if (scratch) cudaFree(scratch);
-    if (staging) cudaFreeHost(staging);
-    if (d_staging) cudaFree(d_staging);
+    for (StagingSlot& sl : stage_slots) {
+        if (sl.host) cudaFreeHost(sl.host);
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+    }
     if (d_status) cudaFree(d_status);
     if (d_bins) cudaFree(d_bins);
-    if (staging_event) cudaEventDestroy(staging_event);
     for (auto& g : graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
     if (capture_stream) cudaStreamDestroy(capture_stream);
     for (int i = 0; i < N_COPY_STREAMS; ++i) {
@@ -583,7 +611,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         probe.take<uint32_t>(u.b1 - u.b0 + 1);
     }
     const size_t desc_bytes = probe.off + 256;
-    if ((st = ensure_staging(desc_bytes))) return st;
+    if ((st = ensure_staging(desc_bytes, use_graph && !timing))) return st;
     Carve hs{(char*)staging};
     BufDev* hb = hs.take<BufDev>(n);
     char* ds = (char*)d_staging;
@@ -723,8 +751,9 @@ hpa_status hpa_handle::launch_graph(const std::vector<AggWork>& ws, size_t stage
     if ((st = cuda(cudaGraphLaunch(g->exec, stream), "graph launch"))) return st;
     launches += g->kernels;
     ++graph_replays;
-    st = cuda(cudaEventRecord(staging_event, stream), "cudaEventRecord");
-    staging_event_live = true;
+    StagingSlot& sl = stage_slots[staging_slot];
+    st = cuda(cudaEventRecord(sl.ev, stream), "cudaEventRecord");
+    sl.live = true;
     return st;
 }
 

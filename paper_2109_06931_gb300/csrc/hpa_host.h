@@ -82,11 +82,25 @@ struct hpa_handle {
     void* scratch = nullptr;
     size_t scratch_cap = 0;
     uint64_t scratch_epoch = 0;
-    void* staging = nullptr;      // pinned host descriptors
+    // Descriptor staging: pinned host buffers and their device copies.  Slot 0
+    // serves graph calls (a captured graph copies from the buffer it was
+    // captured with); the other calls rotate over the remaining slots, so that
+    // a call waits only for the upload of the call N_STAGING - 1 before it,
+    // not for the previous call's (which may sit behind work still queued).
+    // staging / d_staging / staging_cap name the slot ensure_staging chose.
+    static constexpr int N_STAGING = 4;
+    struct StagingSlot {
+        void* host = nullptr;
+        void* dev = nullptr;
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;
+        bool live = false;
+    };
+    StagingSlot stage_slots[N_STAGING];
+    int staging_slot = 0, staging_next = 1;
+    void* staging = nullptr;      // pinned host descriptors of the current slot
     void* d_staging = nullptr;
     size_t staging_cap = 0;
-    cudaEvent_t staging_event = nullptr;
-    bool staging_event_live = false;
     uint64_t launches = 0;
     std::vector<hpa::CachedGraph> graphs;
     void* host_io = nullptr;
@@ -117,7 +131,7 @@ struct hpa_handle {
     hpa_status cuda(cudaError_t e, const char* what);
     bool capturing() const;
     hpa_status ensure_scratch(size_t bytes);
-    hpa_status ensure_staging(size_t bytes);
+    hpa_status ensure_staging(size_t bytes, bool for_graph = false);
     hpa_status upload_staging(size_t bytes);
     hpa::Binary* binary(uint32_t id);
     hpa_status refresh_bin_table();

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -31,6 +32,8 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+constexpr size_t SLOT_WORDS = 1 + 2 * HPA_MAX_STALL;
+
 struct Req {
     uint64_t ticket = 0;
     uint32_t bin = 0;
@@ -40,7 +43,7 @@ struct Req {
     size_t bytes = 0, off = 0;
     hpa_samples din{};      // device copies (in the ring)
     hpa_profile dout{};
-    uint64_t* h_nkeys = nullptr;   // pinned
+    uint64_t* h_nkeys = nullptr;   // pinned slot: n_keys, then totals and UNKNOWN totals
     hpa_status status = HPA_OK;
     bool done = false;
 };
@@ -48,6 +51,9 @@ struct Req {
 struct Batch {
     std::vector<Req*> reqs;
     cudaEvent_t in_done = nullptr, computed = nullptr, copied = nullptr;
+    // stage timing: copy-in start, compute start and end, copy-out start
+    cudaEvent_t in0 = nullptr, c0 = nullptr, c1 = nullptr, out0 = nullptr;
+    double launch_s = 0;
     int stage = 0;          // 0 computing, 1 copying keys out
 
 };
@@ -68,12 +74,20 @@ struct hpa_server {
     // device ring (FIFO allocation)
     char* ring = nullptr;
     size_t ring_cap = 0, ring_head = 0;
-    cudaStream_t copy_in = nullptr, copy_out = nullptr;
-    uint64_t* pinned = nullptr;    // n_keys slots
+    // copy_meta carries the small result copies (key counts), so that a
+    // batch's count is known as soon as it is computed instead of behind the
+    // previous batch's keys on copy_out
+    cudaStream_t copy_in = nullptr, copy_out = nullptr, copy_meta = nullptr;
+    // pinned slots of SLOT_WORDS words (n_keys, totals, UNKNOWN totals): the
+    // small results land here, so that no copy targets pageable host memory
+    // (such a copy would block the worker until the copy stream reaches it)
+    uint64_t* pinned = nullptr;
     size_t pinned_cap = 0, pinned_next = 0;
     // stats
     std::vector<double> lat;
     uint64_t submitted = 0, completed = 0, rejected = 0, samples_done = 0, batches = 0;
+    double stage_ms[5] = {0, 0, 0, 0, 0}, launch_ms = 0;
+    uint64_t timed_batches = 0;
     double t_first = 0, t_last = 0;
     std::string err;
 
@@ -124,6 +138,7 @@ void hpa_server::retire() {
         if (b->stage == 0) {
             if (cudaEventQuery(b->computed) != cudaSuccess) { cudaGetLastError(); return; }
             // keys are known: copy exactly K of them for every request
+            cudaEventRecord(b->out0, copy_out);
             for (Req* r : b->reqs) {
                 const uint64_t K = std::min<uint64_t>(*r->h_nkeys, r->out.capacity);
                 if (K) {
@@ -132,8 +147,10 @@ void hpa_server::retire() {
                     cudaMemcpyAsync(r->out.key_stall, r->dout.key_stall, K, cudaMemcpyDeviceToHost, copy_out);
                     cudaMemcpyAsync(r->out.val, r->dout.val, K * 8, cudaMemcpyDeviceToHost, copy_out);
                 }
-                if (r->out.total) cudaMemcpyAsync(r->out.total, r->dout.total, 8 * r->in.n_stall, cudaMemcpyDeviceToHost, copy_out);
-                if (r->out.unknown) cudaMemcpyAsync(r->out.unknown, r->dout.unknown, 8 * r->in.n_stall, cudaMemcpyDeviceToHost, copy_out);
+                if (r->out.total) cudaMemcpyAsync(r->h_nkeys + 1, r->dout.total, 8 * r->in.n_stall, cudaMemcpyDeviceToHost, copy_out);
+                if (r->out.unknown)
+                    cudaMemcpyAsync(r->h_nkeys + 1 + HPA_MAX_STALL, r->dout.unknown, 8 * r->in.n_stall,
+                                    cudaMemcpyDeviceToHost, copy_out);
             }
             cudaEventRecord(b->copied, copy_out);
             b->stage = 1;
@@ -144,6 +161,8 @@ void hpa_server::retire() {
             std::lock_guard<std::mutex> lock(mu);
             for (Req* r : b->reqs) {
                 *r->out.n_keys = *r->h_nkeys;
+                if (r->out.total) std::memcpy(r->out.total, r->h_nkeys + 1, 8 * r->in.n_stall);
+                if (r->out.unknown) std::memcpy(r->out.unknown, r->h_nkeys + 1 + HPA_MAX_STALL, 8 * r->in.n_stall);
                 if (r->status == HPA_OK && *r->h_nkeys > r->out.capacity) r->status = HPA_E_CAPACITY;
                 r->t_done = t;
                 r->done = true;
@@ -154,10 +173,21 @@ void hpa_server::retire() {
             t_last = t;
             ring_release(b->reqs.size());
         }
+        {
+            float ms[5] = {0, 0, 0, 0, 0};
+            cudaEventElapsedTime(&ms[0], b->in0, b->in_done);
+            cudaEventElapsedTime(&ms[1], b->in_done, b->c0);
+            cudaEventElapsedTime(&ms[2], b->c0, b->c1);
+            cudaEventElapsedTime(&ms[3], b->c1, b->out0);
+            cudaEventElapsedTime(&ms[4], b->out0, b->copied);
+            cudaGetLastError();
+            std::lock_guard<std::mutex> lock(mu);
+            for (int i = 0; i < 5; ++i) stage_ms[i] += ms[i];
+            launch_ms += b->launch_s * 1e3;
+            ++timed_batches;
+        }
         done_cv.notify_all();
-        cudaEventDestroy(b->in_done);
-        cudaEventDestroy(b->computed);
-        cudaEventDestroy(b->copied);
+        for (cudaEvent_t e : {b->in_done, b->computed, b->copied, b->in0, b->c0, b->c1, b->out0}) cudaEventDestroy(e);
         delete b;
         inflight.pop_front();
     }
@@ -186,11 +216,12 @@ bool hpa_server::admit_and_launch() {
     }
     done_cv.notify_all();
     if (take.empty()) return false;
+    const double t_admit = now_s();
     Batch* b = new Batch();
     b->reqs = take;
-    cudaEventCreateWithFlags(&b->in_done, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&b->computed, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
+    for (cudaEvent_t* e : {&b->in_done, &b->computed, &b->copied, &b->in0, &b->c0, &b->c1, &b->out0})
+        cudaEventCreate(e);
+    cudaEventRecord(b->in0, copy_in);
     std::vector<uint32_t> ids;
     std::vector<hpa_samples> ins;
     std::vector<hpa_profile> outs;
@@ -216,26 +247,29 @@ bool hpa_server::admit_and_launch() {
         cudaMemcpyAsync((void*)r->din.ctx, s.ctx, s.n * 4, cudaMemcpyHostToDevice, copy_in);
         cudaMemcpyAsync((void*)r->din.stall, s.stall, s.n, cudaMemcpyHostToDevice, copy_in);
         if (s.count) cudaMemcpyAsync((void*)r->din.count, s.count, s.n * 4, cudaMemcpyHostToDevice, copy_in);
-        r->h_nkeys = pinned + (pinned_next++ % pinned_cap);
+        r->h_nkeys = pinned + (pinned_next++ % pinned_cap) * SLOT_WORDS;
         ids.push_back(r->bin);
         ins.push_back(r->din);
         outs.push_back(r->dout);
     }
     cudaEventRecord(b->in_done, copy_in);
     cudaStreamWaitEvent(h->stream, b->in_done, 0);
+    cudaEventRecord(b->c0, h->stream);
     hpa_status st = h->aggregate((uint32_t)take.size(), ids.data(), ins.data(), outs.data(), false);
+    cudaEventRecord(b->c1, h->stream);
     if (st) {
         std::lock_guard<std::mutex> lock(mu);
         err = h->err;
         for (Req* r : take) r->status = st;
     }
     cudaEventRecord(b->computed, h->stream);
-    cudaStreamWaitEvent(copy_out, b->computed, 0);
+    cudaStreamWaitEvent(copy_meta, b->computed, 0);
     for (size_t i = 0; i < take.size(); ++i)
-        cudaMemcpyAsync(take[i]->h_nkeys, outs[i].n_keys, 8, cudaMemcpyDeviceToHost, copy_out);
+        cudaMemcpyAsync(take[i]->h_nkeys, outs[i].n_keys, 8, cudaMemcpyDeviceToHost, copy_meta);
     // the computed event must be after the n_keys copies for retire() to read them
-    cudaEventRecord(b->computed, copy_out);
+    cudaEventRecord(b->computed, copy_meta);
     ++batches;
+    b->launch_s = now_s() - t_admit;
     inflight.push_back(b);
     return true;
 }
@@ -244,7 +278,7 @@ void hpa_server::loop() {
     cudaSetDevice(h->device);
     while (true) {
         retire();
-        const bool launched = inflight.size() < 3 && admit_and_launch();
+        const bool launched = inflight.size() < opt.max_inflight && admit_and_launch();
         std::unique_lock<std::mutex> lock(mu);
         if (stop && queue.empty() && inflight.empty()) break;
         if (!launched) {
@@ -265,17 +299,21 @@ extern "C" hpa_status hpa_server_create(hpa_handle* h, const hpa_server_options*
     if (opt) s->opt = *opt;
     if (!s->opt.mem_cap_bytes) s->opt.mem_cap_bytes = 60ull << 30;
     if (!s->opt.max_batch) s->opt.max_batch = 64;
+    if (!s->opt.max_inflight) s->opt.max_inflight = 3;
     s->ring_cap = s->opt.mem_cap_bytes;
-    s->pinned_cap = 1 << 16;
+    // more slots than requests can be in flight
+    s->pinned_cap = std::max<size_t>(4096, 2 * (size_t)s->opt.max_batch * (s->opt.max_inflight + 1));
+    const unsigned long long cap_bytes = s->opt.mem_cap_bytes;
     if (cudaMalloc((void**)&s->ring, s->ring_cap) != cudaSuccess ||
-        cudaMallocHost((void**)&s->pinned, s->pinned_cap * 8) != cudaSuccess ||
+        cudaMallocHost((void**)&s->pinned, s->pinned_cap * SLOT_WORDS * 8) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy_in, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->copy_out, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&s->copy_out, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->copy_meta, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         if (s->ring) cudaFree(s->ring);
         if (s->pinned) cudaFreeHost(s->pinned);
         delete s;
-        return h->fail(HPA_E_OOM, "server: cannot reserve %llu bytes of device memory", (unsigned long long)opt->mem_cap_bytes);
+        return h->fail(HPA_E_OOM, "server: cannot reserve %llu bytes of device memory", cap_bytes);
     }
     s->worker = std::thread([s] { s->loop(); });
     *out = s;
@@ -343,6 +381,15 @@ extern "C" hpa_status hpa_server_stats_get(hpa_server* s, hpa_server_stats* st) 
         for (double x : v) sum += x;
         st->mean_ms = sum / v.size();
     }
+    if (s->timed_batches) {
+        const double k = 1.0 / (double)s->timed_batches;
+        st->h2d_ms = s->stage_ms[0] * k;
+        st->wait_compute_ms = s->stage_ms[1] * k;
+        st->compute_ms = s->stage_ms[2] * k;
+        st->wait_d2h_ms = s->stage_ms[3] * k;
+        st->d2h_ms = s->stage_ms[4] * k;
+        st->launch_ms = s->launch_ms * k;
+    }
     return HPA_OK;
 }
 
@@ -357,8 +404,10 @@ extern "C" hpa_status hpa_server_destroy(hpa_server* s) {
     cudaSetDevice(s->h->device);
     cudaStreamSynchronize(s->copy_in);
     cudaStreamSynchronize(s->copy_out);
+    cudaStreamSynchronize(s->copy_meta);
     cudaStreamDestroy(s->copy_in);
     cudaStreamDestroy(s->copy_out);
+    cudaStreamDestroy(s->copy_meta);
     cudaFree(s->ring);
     cudaFreeHost(s->pinned);
     for (auto& kv : s->reqs) delete kv.second;

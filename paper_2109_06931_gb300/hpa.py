@@ -69,13 +69,16 @@ class hpa_cct(C.Structure):
 
 
 class hpa_server_options(C.Structure):
-    _fields_ = [("mem_cap_bytes", C.c_uint64), ("max_batch", C.c_uint32), ("reserved", C.c_uint32 * 5)]
+    _fields_ = [("mem_cap_bytes", C.c_uint64), ("max_batch", C.c_uint32), ("max_inflight", C.c_uint32),
+                ("reserved", C.c_uint32 * 4)]
 
 
 class hpa_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
                 ("samples", C.c_uint64), ("batches", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
-                ("max_ms", C.c_double), ("mean_ms", C.c_double), ("busy_s", C.c_double)]
+                ("max_ms", C.c_double), ("mean_ms", C.c_double), ("busy_s", C.c_double),
+                ("h2d_ms", C.c_double), ("wait_compute_ms", C.c_double), ("compute_ms", C.c_double),
+                ("wait_d2h_ms", C.c_double), ("d2h_ms", C.c_double), ("launch_ms", C.c_double)]
 
 
 class hpa_cct_tree(C.Structure):
@@ -606,10 +609,10 @@ class Hpa:
 class Server:
     """Request loop over host sample buffers (hpa_server_*)."""
 
-    def __init__(self, h: Hpa, mem_cap_bytes: int = 0, max_batch: int = 0):
+    def __init__(self, h: Hpa, mem_cap_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0):
         self.h = h
         self.s = C.c_void_p()
-        opt = hpa_server_options(mem_cap_bytes, max_batch)
+        opt = hpa_server_options(mem_cap_bytes, max_batch, max_inflight)
         h.check(h.L.hpa_server_create(h.h, C.byref(opt), C.byref(self.s)))
         self._live = {}
 
