@@ -88,7 +88,7 @@ struct hpa_handle {
     // a call waits only for the upload of the call N_STAGING - 1 before it,
     // not for the previous call's (which may sit behind work still queued).
     // staging / d_staging / staging_cap name the slot ensure_staging chose.
-    static constexpr int N_STAGING = 4;
+    static constexpr int N_STAGING = 8;
     struct StagingSlot {
         void* host = nullptr;
         void* dev = nullptr;
