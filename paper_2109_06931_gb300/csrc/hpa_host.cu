@@ -763,6 +763,14 @@ extern "C" hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, c
     return h->aggregate(1, &binary_id, in, out);
 }
 
+// every buffer of the call in one captured CUDA graph (cached per batch shape)
+extern "C" hpa_status hpa_attribute_batch(hpa_handle* h, uint32_t n, const uint32_t* ids, const hpa_samples* in,
+                                          hpa_profile* outs) {
+    if (!h || (n && (!ids || !in || !outs))) return HPA_E_INVALID_ARG;
+    cudaSetDevice(h->device);
+    return h->aggregate(n, ids, in, outs, true);
+}
+
 extern "C" hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t max_groups) {
     if (!h) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
