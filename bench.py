@@ -408,6 +408,34 @@ def max_over_ranks(x: float, world: int, device) -> float:
     return float(t.item())
 
 
+NOMINAL_HBM_GBS = 8000.0      # the nominal HBM3e bandwidth the roofline is also quoted against
+
+
+def step_stats(ts):
+    """Median, p99, min and max of per-step CUDA-event times (ms)."""
+    v = sorted(ts)
+    if not v:
+        return None
+    p99 = v[min(len(v) - 1, max(0, -(-99 * len(v) // 100) - 1))]     # nearest rank
+    return {"p50": statistics.median(v), "p99": p99, "min": v[0], "max": v[-1], "n": len(v)}
+
+
+def host_info():
+    """Host cores and CPU model of the machine that ran the CPU baseline."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, val = line.partition(":")
+            if k.strip() in ("model name", "Model name", "CPU part") and val.strip():
+                model = val.strip()
+                break
+    except OSError:
+        pass
+    import platform
+    return {"host_nproc": os.cpu_count(), "host_cpu": model or platform.processor() or platform.machine(),
+            "host_arch": platform.machine()}
+
+
 def shard_start(rank: int, n: int) -> int:
     """First sample (or buffer) index of rank's shard: replicas process
     disjoint slices of the same seeded streams, so the units of all ranks
@@ -445,7 +473,7 @@ def run_reference(args, world, rank):
             "data": "synthetic",
             "config": {"workload": w.name, "samples_per_step": n, "note": "CPU oracle, bounded sample"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {n} samples of {w.name}"},
+                             "sample": f"first {n} samples of {w.name}", **host_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -498,15 +526,19 @@ def run_batched(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     l0 = h.launches()
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with Clocks(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        marks[0].record(stream)
+        for k in range(args.steps):
             h.attribute_batch(bids, bufs, outs)
+            marks[k + 1].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
     h.sync()
     launches = h.launches() - l0
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    step_ms = step_stats([marks[k].elapsed_time(marks[k + 1]) for k in range(args.steps)])
     # plain form: one launch sequence per buffer
     for _ in range(1):
         for bid, b, o in zip(bids, bufs, outs):
@@ -540,6 +572,13 @@ def run_batched(args, world, rank, local):
     peak, peak_kind = peaks()
     path_bytes = 17 * N + 17 * K
     ach = path_bytes / (ms / 1e3) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        bin_of = [bins[i % len(bins)] for i in range(len(bufs))]
+        rate, n_cpu, dt_cpu, used = batched_cpu_rate(bin_of, bufs, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{used} smallest buffers, the last cut to fit ({n_cpu} samples, {dt_cpu:.1f} s); "
+                         f"the rate applies per sample of the whole batch", **host_info()}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": N * world / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -552,8 +591,34 @@ def run_batched(args, world, rank, local):
                       "form": "one hpa_attribute_samples per buffer"},
             "path_roofline": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                               "peak_kind": peak_kind, "algorithmic_bytes_per_step": path_bytes},
+            "step_ms": step_ms, "cpu_baseline": cpu,
             "phases_ms": ph, "clocks": clk.summary(), "gpu_launches": int(launches), "rows": rows}), flush=True)
     h.close()
+
+
+def batched_cpu_rate(bin_of, bufs, seconds: float):
+    """Samples/s of the oracle on a bounded subset of a batch: buffers in
+    increasing size, the last one cut so that the oracle runs about
+    `seconds`.  Returns (rate, samples, seconds, buffers used)."""
+    import oracle
+    oracle.build()
+    order = sorted(range(len(bufs)), key=lambda i: bufs[i].n)
+    done_n, t_total, used = 0, 0.0, 0
+    for i in order:
+        if t_total >= seconds:
+            break
+        b = bufs[i]
+        rate = done_n / t_total if t_total > 0 else 5e5
+        n = int(min(b.n, max(10_000, (seconds - t_total) * rate)))
+        S = synth.Samples(b.pc[:n], b.ctx[:n], b.stall[:n], None if b.count is None else b.count[:n],
+                          b.n_ctx, b.n_stall).to("cpu")
+        t = time.perf_counter()
+        k = oracle.attribute_samples(bin_of[i], S)
+        t_total += time.perf_counter() - t
+        assert k.status == 0
+        done_n += n
+        used += 1
+    return done_n / max(t_total, 1e-9), done_n, t_total, used
 
 
 def main():
@@ -629,15 +694,19 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     l0 = h.launches()
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with Clocks(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        marks[0].record(stream)
+        for k in range(args.steps):
             h.attribute_samples(bid, S, out=out)
+            marks[k + 1].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
     h.sync()
     launches = (h.launches() - l0) // args.steps
     ms = e0.elapsed_time(e1) / args.steps
+    step_ms = step_stats([marks[k].elapsed_time(marks[k + 1]) for k in range(args.steps)])
     ms = max_over_ranks(ms, world, dev)
     barrier(world)
     value = N * world / (ms / 1e3)
@@ -730,7 +799,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         rate, n_cpu, dt_cpu = cpu_oracle_rate(w, B, args.cpu_seconds, 20_000_000)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n_cpu} samples of {w.name} ({dt_cpu:.1f} s)"}
+               "sample": f"first {n_cpu} samples of {w.name} ({dt_cpu:.1f} s)", **host_info()}
 
     if rank == 0:
         line = {
@@ -743,9 +812,11 @@ def main():
                        "tuned": tuned},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": ach / peak, "peak_kind": peak_kind, "traffic": traffic_per_launch(dom, N),
-                         "algorithmic_bytes_per_launch": algo[dom], "ms_per_launch": ph[dom]},
+                         "algorithmic_bytes_per_launch": algo[dom], "ms_per_launch": ph[dom],
+                         "frac_of_nominal": ach / NOMINAL_HBM_GBS},
             "path_roofline": {"achieved": path_ach, "frac": path_ach / peak, "unit": "GB/s",
-                              "algorithmic_bytes_per_step": path_bytes},
+                              "algorithmic_bytes_per_step": path_bytes, "frac_of_nominal": path_ach / NOMINAL_HBM_GBS},
+            "step_ms": step_ms,
             "phases_ms": ph,
             "clocks": clk.summary(),
             "gpu_launches": int(launches * args.steps),
