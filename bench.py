@@ -432,6 +432,9 @@ def host_info():
     except OSError:
         pass
     import platform
+    arm_parts = {"0xd4f": "Arm Neoverse V2 (part 0xd4f)", "0xd40": "Arm Neoverse V1 (part 0xd40)",
+                 "0xd0c": "Arm Neoverse N1 (part 0xd0c)"}
+    model = arm_parts.get(model, model)
     return {"host_nproc": os.cpu_count(), "host_cpu": model or platform.processor() or platform.machine(),
             "host_arch": platform.machine()}
 
@@ -590,7 +593,8 @@ def run_batched(args, world, rank, local):
             "plain": {"value": N * world / (ms_plain / 1e3), "ms_per_step": ms_plain,
                       "form": "one hpa_attribute_samples per buffer"},
             "path_roofline": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                              "peak_kind": peak_kind, "algorithmic_bytes_per_step": path_bytes},
+                              "peak_kind": peak_kind, "algorithmic_bytes_per_step": path_bytes,
+                              "frac_of_nominal": ach / NOMINAL_HBM_GBS},
             "step_ms": step_ms, "cpu_baseline": cpu,
             "phases_ms": ph, "clocks": clk.summary(), "gpu_launches": int(launches), "rows": rows}), flush=True)
     h.close()
