@@ -37,7 +37,8 @@ def _keys(oracle_lib, rows):
                               a[:, 3].astype(np.uint64))
 
 
-@pytest.mark.parametrize("name", ["gpucct_fig5.json", "gpucct_selfcall.json"])
+@pytest.mark.parametrize("name", ["gpucct_fig5.json", "gpucct_selfcall.json", "gpucct_diamond.json",
+                                  "gpucct_two_cycle.json", "gpucct_scc_two_callers.json"])
 def test_golden(oracle_lib, name):
     g = json.load(open(os.path.join(GOLD, name)))
     F = len(g["functions"])
