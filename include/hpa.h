@@ -279,6 +279,10 @@ hpa_status hpa_phase_times(hpa_handle* h, uint32_t n_max, double* ms, uint64_t* 
  * call graph's strongly connected components (Tarjan's algorithm) and the
  * level order of the condensed graph, which every context shares.            */
 hpa_status hpa_load_structure(hpa_handle* h, const hpa_structure* s, uint32_t* binary_id);
+/* The checks of hpa_load_structure alone, on the host: no handle and no GPU
+ * needed.  HPA_OK, or the status hpa_load_structure would return, with its
+ * reason written to msg (msg_len bytes; msg may be NULL).                   */
+hpa_status hpa_validate_structure(const hpa_structure* s, char* msg, size_t msg_len);
 hpa_status hpa_unload_structure(hpa_handle* h, uint32_t binary_id);
 /* Facts of a loaded binary; cnode_of_func (host uint32[n_funcs], may be NULL)
  * receives each function's condensed node id.                                */

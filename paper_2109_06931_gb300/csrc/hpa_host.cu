@@ -265,6 +265,16 @@ extern "C" hpa_status hpa_sync(hpa_handle* h, uint64_t* bad) {
 
 // ------------------------------------------------------------------ structure
 static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B);
+static hpa_status check_structure(const hpa_structure* s, std::vector<uint32_t>& depth, uint32_t& max_depth,
+                                  char* msg, size_t msg_len);
+
+extern "C" hpa_status hpa_validate_structure(const hpa_structure* s, char* msg, size_t msg_len) {
+    if (msg && msg_len) msg[0] = 0;
+    if (!s) return HPA_E_INVALID_ARG;
+    std::vector<uint32_t> depth;
+    uint32_t max_depth = 0;
+    return check_structure(s, depth, max_depth, msg, msg_len);
+}
 
 extern "C" hpa_status hpa_load_structure(hpa_handle* h, const hpa_structure* s, uint32_t* binary_id) {
     if (!h || !s || !binary_id) return HPA_E_INVALID_ARG;
@@ -317,52 +327,67 @@ Binary::~Binary() {
     for (void* p : dev_allocs) cudaFree(p);
 }
 
-static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B) {
+// Host checks of a structure's tables (no device work): ranges sorted,
+// non-empty, disjoint, spanning < 2^32 bytes; FUNC nodes exactly the roots,
+// one per function; parents in range, of the same function, acyclic; call
+// sites naming existing functions and CALL nodes of the caller.  Fills each
+// node's depth.  On failure returns the status with a message in msg.
+static hpa_status check_structure(const hpa_structure* s, std::vector<uint32_t>& depth, uint32_t& max_depth,
+                                  char* msg, size_t msg_len) {
+    auto bad = [&](hpa_status st, const char* fmt, ...) {
+        if (msg && msg_len) {
+            va_list ap;
+            va_start(ap, fmt);
+            vsnprintf(msg, msg_len, fmt, ap);
+            va_end(ap);
+        }
+        return st;
+    };
     const uint64_t R = s->n_ranges;
     const uint32_t M = s->n_nodes, F = s->n_funcs, E = s->n_calls;
     if (R == 0 || !s->range_lo || !s->range_hi || !s->range_node)
-        return h->fail(HPA_E_INVALID_ARG, "structure needs at least one range");
+        return bad(HPA_E_INVALID_ARG, "structure needs at least one range");
     if (M == 0 || !s->node_parent || !s->node_kind || !s->node_func)
-        return h->fail(HPA_E_INVALID_ARG, "structure needs node tables");
-    if (R >= 0xFFFFFFFFull) return h->fail(HPA_E_INVALID_TABLE, "too many ranges");
-    if (M >= 0x7FFFFFFFu) return h->fail(HPA_E_INVALID_TABLE, "too many nodes");
+        return bad(HPA_E_INVALID_ARG, "structure needs node tables");
+    if (R >= 0xFFFFFFFFull) return bad(HPA_E_INVALID_TABLE, "too many ranges");
+    if (M >= 0x7FFFFFFFu) return bad(HPA_E_INVALID_TABLE, "too many nodes");
     if (E && (!s->cs_caller || !s->cs_callee || !s->cs_node))
-        return h->fail(HPA_E_INVALID_ARG, "call-site tables missing");
+        return bad(HPA_E_INVALID_ARG, "call-site tables missing");
     // ranges: sorted, non-empty, disjoint, span < 2^32
     for (uint64_t i = 0; i < R; ++i) {
         if (s->range_hi[i] <= s->range_lo[i])
-            return h->fail(HPA_E_INVALID_TABLE, "range %llu is empty", (unsigned long long)i);
+            return bad(HPA_E_INVALID_TABLE, "range %llu is empty", (unsigned long long)i);
         if (i && s->range_lo[i] < s->range_hi[i - 1])
-            return h->fail(HPA_E_INVALID_TABLE, "range %llu overlaps or is out of order", (unsigned long long)i);
+            return bad(HPA_E_INVALID_TABLE, "range %llu overlaps or is out of order", (unsigned long long)i);
         if (s->range_node[i] >= M)
-            return h->fail(HPA_E_INVALID_TABLE, "range %llu names node %u >= n_nodes", (unsigned long long)i, s->range_node[i]);
+            return bad(HPA_E_INVALID_TABLE, "range %llu names node %u >= n_nodes", (unsigned long long)i, s->range_node[i]);
     }
     const uint64_t base = s->range_lo[0];
     const uint64_t span = s->range_hi[R - 1] - base;
-    if (span >= (1ull << 32)) return h->fail(HPA_E_INVALID_TABLE, "ranges span %llu bytes (limit 2^32)", (unsigned long long)span);
+    if (span >= (1ull << 32)) return bad(HPA_E_INVALID_TABLE, "ranges span %llu bytes (limit 2^32)", (unsigned long long)span);
     // nodes: FUNC exactly the roots, parents of the same function, no cycles
     for (uint32_t v = 0; v < M; ++v) {
         const uint32_t p = s->node_parent[v];
-        if (s->node_func[v] >= F) return h->fail(HPA_E_INVALID_TABLE, "node %u names function %u >= n_funcs", v, s->node_func[v]);
-        if (s->node_kind[v] > HPA_NODE_CALL) return h->fail(HPA_E_INVALID_TABLE, "node %u has kind %u", v, s->node_kind[v]);
+        if (s->node_func[v] >= F) return bad(HPA_E_INVALID_TABLE, "node %u names function %u >= n_funcs", v, s->node_func[v]);
+        if (s->node_kind[v] > HPA_NODE_CALL) return bad(HPA_E_INVALID_TABLE, "node %u has kind %u", v, s->node_kind[v]);
         const bool root = p == HPA_NO_PARENT;
         if (root != (s->node_kind[v] == HPA_NODE_FUNC))
-            return h->fail(HPA_E_INVALID_TABLE, "node %u: FUNC nodes must be exactly the roots", v);
+            return bad(HPA_E_INVALID_TABLE, "node %u: FUNC nodes must be exactly the roots", v);
         if (!root) {
-            if (p >= M) return h->fail(HPA_E_INVALID_TABLE, "node %u has parent %u >= n_nodes", v, p);
-            if (s->node_func[p] != s->node_func[v]) return h->fail(HPA_E_INVALID_TABLE, "node %u and its parent belong to different functions", v);
+            if (p >= M) return bad(HPA_E_INVALID_TABLE, "node %u has parent %u >= n_nodes", v, p);
+            if (s->node_func[p] != s->node_func[v]) return bad(HPA_E_INVALID_TABLE, "node %u and its parent belong to different functions", v);
         }
     }
-    std::vector<uint32_t> depth(M, 0xFFFFFFFFu);
+    depth.assign(M, 0xFFFFFFFFu);
     std::vector<uint32_t> func_node(F, HPA_NO_PARENT);
     for (uint32_t v = 0; v < M; ++v) {
         if (s->node_parent[v] == HPA_NO_PARENT) {
             if (func_node[s->node_func[v]] != HPA_NO_PARENT)
-                return h->fail(HPA_E_INVALID_TABLE, "function %u has two FUNC nodes", s->node_func[v]);
+                return bad(HPA_E_INVALID_TABLE, "function %u has two FUNC nodes", s->node_func[v]);
             func_node[s->node_func[v]] = v;
         }
     }
-    uint32_t max_depth = 0;
+    max_depth = 0;
     {
         std::vector<uint32_t> path;
         for (uint32_t v = 0; v < M; ++v) {
@@ -370,7 +395,7 @@ static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B) 
             uint32_t x = v;
             while (depth[x] == 0xFFFFFFFFu && s->node_parent[x] != HPA_NO_PARENT) {
                 path.push_back(x);
-                if (path.size() > M) return h->fail(HPA_E_INVALID_TABLE, "structure tree has a cycle");
+                if (path.size() > M) return bad(HPA_E_INVALID_TABLE, "structure tree has a cycle");
                 x = s->node_parent[x];
             }
             if (depth[x] == 0xFFFFFFFFu) depth[x] = 0;
@@ -382,11 +407,24 @@ static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B) 
     // call sites
     for (uint32_t e = 0; e < E; ++e) {
         if (s->cs_caller[e] >= F || s->cs_callee[e] >= F)
-            return h->fail(HPA_E_INVALID_TABLE, "call site %u names a function >= n_funcs", e);
+            return bad(HPA_E_INVALID_TABLE, "call site %u names a function >= n_funcs", e);
         const uint32_t n = s->cs_node[e];
         if (n >= M || s->node_kind[n] != HPA_NODE_CALL || s->node_func[n] != s->cs_caller[e])
-            return h->fail(HPA_E_INVALID_TABLE, "call site %u: cs_node must be a CALL node of the caller", e);
+            return bad(HPA_E_INVALID_TABLE, "call site %u: cs_node must be a CALL node of the caller", e);
     }
+    return HPA_OK;
+}
+
+static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B) {
+    const uint64_t R = s->n_ranges;
+    const uint32_t M = s->n_nodes, F = s->n_funcs, E = s->n_calls;
+    std::vector<uint32_t> depth;
+    uint32_t max_depth = 0;
+    char msg[256] = {0};
+    const hpa_status vst = check_structure(s, depth, max_depth, msg, sizeof msg);
+    if (vst) return h->fail(vst, "%s", msg);
+    const uint64_t base = s->range_lo[0];
+    const uint64_t span = s->range_hi[R - 1] - base;
     B->n_nodes = M; B->n_funcs = F; B->n_calls = E; B->n_ranges = R; B->max_depth = max_depth;
     // attribution tables: ranges as offsets from the segment base, and a
     // bucket directory (at most DIR_MAX_ENTRIES buckets of 2^dshift bytes).

@@ -149,6 +149,7 @@ def lib(build_if_needed: bool = True):
         L.hpa_kernel_launches.argtypes = [H]
         L.hpa_kernel_launches.restype = C.c_uint64
         L.hpa_load_structure.argtypes = [H, C.POINTER(hpa_structure), u32p]
+        L.hpa_validate_structure.argtypes = [C.POINTER(hpa_structure), C.c_char_p, C.c_size_t]
         L.hpa_unload_structure.argtypes = [H, C.c_uint32]
         L.hpa_binary_info_get.argtypes = [H, C.c_uint32, C.POINTER(hpa_binary_info), vp]
         L.hpa_attribute_samples.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile)]
@@ -239,6 +240,31 @@ def new_profile(capacity: int, n_stall: int, device) -> Profile:
                    torch.zeros(HPA_MAX_STALL, dtype=torch.int64, device=device), 0, n_stall, cap)
 
 
+def _structure(b):
+    """hpa_structure over host copies of b's tables (returned to keep them alive)."""
+    arrs = dict(
+        range_lo=np.ascontiguousarray(b.range_lo, np.uint64), range_hi=np.ascontiguousarray(b.range_hi, np.uint64),
+        range_node=np.ascontiguousarray(b.range_node, np.uint32),
+        node_parent=np.ascontiguousarray(b.node_parent, np.uint32),
+        node_kind=np.ascontiguousarray(b.node_kind, np.uint8), node_func=np.ascontiguousarray(b.node_func, np.uint32),
+        cs_caller=np.ascontiguousarray(b.cs_caller, np.uint32), cs_callee=np.ascontiguousarray(b.cs_callee, np.uint32),
+        cs_node=np.ascontiguousarray(b.cs_node, np.uint32))
+    s = hpa_structure(arrs["range_lo"].shape[0], _ptr(arrs["range_lo"]), _ptr(arrs["range_hi"]),
+                      _ptr(arrs["range_node"]), arrs["node_parent"].shape[0], _ptr(arrs["node_parent"]),
+                      _ptr(arrs["node_kind"]), _ptr(arrs["node_func"]), int(b.n_funcs), arrs["cs_caller"].shape[0],
+                      _ptr(arrs["cs_caller"]), _ptr(arrs["cs_callee"]), _ptr(arrs["cs_node"]))
+    return s, arrs
+
+
+def validate_structure(b):
+    """hpa_validate_structure: (status, reason) of b's tables, on the host."""
+    L = lib()
+    s, _keep = _structure(b)
+    msg = C.create_string_buffer(256)
+    st = int(L.hpa_validate_structure(C.byref(s), msg, C.c_size_t(256)))
+    return st, msg.value.decode()
+
+
 class Hpa:
     """One library handle bound to a CUDA device and stream."""
 
@@ -319,17 +345,7 @@ class Hpa:
     # ---- structure
     def load_structure(self, b) -> int:
         """b: an object with numpy arrays range_lo/hi/node, node_parent/kind/func, cs_* (see synth.Binary)."""
-        arrs = dict(
-            range_lo=np.ascontiguousarray(b.range_lo, np.uint64), range_hi=np.ascontiguousarray(b.range_hi, np.uint64),
-            range_node=np.ascontiguousarray(b.range_node, np.uint32),
-            node_parent=np.ascontiguousarray(b.node_parent, np.uint32),
-            node_kind=np.ascontiguousarray(b.node_kind, np.uint8), node_func=np.ascontiguousarray(b.node_func, np.uint32),
-            cs_caller=np.ascontiguousarray(b.cs_caller, np.uint32), cs_callee=np.ascontiguousarray(b.cs_callee, np.uint32),
-            cs_node=np.ascontiguousarray(b.cs_node, np.uint32))
-        s = hpa_structure(arrs["range_lo"].shape[0], _ptr(arrs["range_lo"]), _ptr(arrs["range_hi"]),
-                          _ptr(arrs["range_node"]), arrs["node_parent"].shape[0], _ptr(arrs["node_parent"]),
-                          _ptr(arrs["node_kind"]), _ptr(arrs["node_func"]), int(b.n_funcs), arrs["cs_caller"].shape[0],
-                          _ptr(arrs["cs_caller"]), _ptr(arrs["cs_callee"]), _ptr(arrs["cs_node"]))
+        s, arrs = _structure(b)
         bid = C.c_uint32(0)
         self.check(self.L.hpa_load_structure(self.h, C.byref(s), C.byref(bid)))
         # structure-tree depth bounds the inclusive expansion
