@@ -193,6 +193,7 @@ using namespace hpa;
 
 extern "C" hpa_status hpa_bottom_up_view(hpa_handle* h, uint32_t binary_id, const hpa_profile* p,
                                          const hpa_cct_nodes* cct, hpa_bottom_up* out) {
+    hpa::Trace trace_("hpa.bottom_up_view");
     if (!h || !p || !cct || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     Binary* B = h->binary(binary_id);

@@ -341,6 +341,7 @@ __global__ void k_issue_rate(DerivedOut o) {
 using namespace hpa;
 
 extern "C" hpa_status hpa_derive_metrics(hpa_handle* h, const hpa_profile* const* ps, uint32_t P, hpa_derived* out) {
+    hpa::Trace trace_("hpa.derive_metrics");
     if (!h || !out || (P && !ps)) return HPA_E_INVALID_ARG;
     if (P == 0) return h->fail(HPA_E_INVALID_ARG, "no profiles");
     cudaSetDevice(h->device);

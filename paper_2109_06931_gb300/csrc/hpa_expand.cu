@@ -137,6 +137,7 @@ using namespace hpa;
 
 extern "C" hpa_status hpa_expand_gpucct(hpa_handle* h, uint32_t binary_id, const hpa_gpucct* g, uint32_t n_stall,
                                         uint32_t q, hpa_cct_tree* out) {
+    hpa::Trace trace_("hpa.expand_gpucct");
     if (!h || !g || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     Binary* B = h->binary(binary_id);

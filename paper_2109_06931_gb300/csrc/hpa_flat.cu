@@ -117,6 +117,7 @@ __global__ void k_flat_finish(FlatArgs a) {
 using namespace hpa;
 
 extern "C" hpa_status hpa_flat_profile(hpa_handle* h, uint32_t binary_id, const hpa_profile* p, hpa_profile* out) {
+    hpa::Trace trace_("hpa.flat_profile");
     if (!h || !p || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     Binary* B = h->binary(binary_id);

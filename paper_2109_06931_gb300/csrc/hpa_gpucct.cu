@@ -262,6 +262,7 @@ using namespace hpa;
 
 extern "C" hpa_status hpa_apportion_callgraph(hpa_handle* h, uint32_t binary_id, const hpa_profile* p,
                                               hpa_gpucct* out) {
+    hpa::Trace trace_("hpa.apportion_callgraph");
     if (!h || !p || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     Binary* B = h->binary(binary_id);

@@ -277,6 +277,7 @@ extern "C" hpa_status hpa_validate_structure(const hpa_structure* s, char* msg, 
 }
 
 extern "C" hpa_status hpa_load_structure(hpa_handle* h, const hpa_structure* s, uint32_t* binary_id) {
+    hpa::Trace trace_("hpa.load_structure");
     if (!h || !s || !binary_id) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     Binary* B = new Binary();
@@ -796,6 +797,7 @@ hpa_status hpa_handle::launch_graph(const std::vector<AggWork>& ws, size_t stage
 }
 
 extern "C" hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, const hpa_samples* in, hpa_profile* out) {
+    hpa::Trace trace_("hpa.attribute_samples");
     if (!h || !in || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     return h->aggregate(1, &binary_id, in, out);
@@ -804,6 +806,7 @@ extern "C" hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, c
 // every buffer of the call in one captured CUDA graph (cached per batch shape)
 extern "C" hpa_status hpa_attribute_batch(hpa_handle* h, uint32_t n, const uint32_t* ids, const hpa_samples* in,
                                           hpa_profile* outs) {
+    hpa::Trace trace_("hpa.attribute_batch");
     if (!h || (n && (!ids || !in || !outs))) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     return h->aggregate(n, ids, in, outs, true);
@@ -854,6 +857,7 @@ hpa_status hpa_handle::copies(const Copy* c, int n, cudaMemcpyKind kind) {
 
 extern "C" hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
                                                  hpa_profile* out) {
+    hpa::Trace trace_("hpa.attribute_samples_host");
     if (!h || !in || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     const uint64_t n = in->n;

@@ -4,10 +4,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hpa.h"
 #include "hpa_internal.h"
 
 namespace hpa {
+
+// An NVTX range around a library call (named "hpa.<call>"), so that traces
+// taken with Nsight tools show the library's calls over its kernels; without
+// a tool attached the calls are no-ops.
+struct Trace {
+    explicit Trace(const char* name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace&) = delete;
+    Trace& operator=(const Trace&) = delete;
+};
 
 // Device tables of a binary's static call graph (Section 6.3 steps 1 and 3),
 // shared by every context.

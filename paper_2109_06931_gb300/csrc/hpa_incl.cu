@@ -94,6 +94,7 @@ hpa_status hpa_handle::stage_single_output(AggWork& w, uint32_t bin, uint32_t n_
 
 extern "C" hpa_status hpa_propagate_inclusive(hpa_handle* h, uint32_t binary_id, const hpa_profile* p,
                                               hpa_profile* tree_out, const hpa_cct* cct, uint64_t* cct_out) {
+    hpa::Trace trace_("hpa.propagate_inclusive");
     if (!h || !p) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     Binary* B = h->binary(binary_id);

@@ -62,6 +62,7 @@ using namespace hpa;
 
 extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
                                                     hpa_profile* out) {
+    hpa::Trace trace_("hpa.attribute_samples_noalloc");
     if (!h || !in || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     Binary* B = h->binary(binary_id);

@@ -216,6 +216,7 @@ bool hpa_server::admit_and_launch() {
     }
     done_cv.notify_all();
     if (take.empty()) return false;
+    Trace trace_("hpa.server.batch");
     const double t_admit = now_s();
     Batch* b = new Batch();
     b->reqs = take;

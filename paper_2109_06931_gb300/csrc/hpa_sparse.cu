@@ -287,6 +287,7 @@ static hpa_status sp_stage(hpa_handle* h, const hpa_profile* const* ps, uint32_t
 }
 
 extern "C" hpa_status hpa_build_cms(hpa_handle* h, const hpa_profile* const* ps, uint32_t n_profiles, hpa_cms* out) {
+    hpa::Trace trace_("hpa.build_cms");
     if (!h || !ps || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     if (!out->counts || (out->cap_planes && (!out->plane_ctx || !out->plane_node)) || !out->plane_off ||
@@ -343,6 +344,7 @@ extern "C" hpa_status hpa_build_cms(hpa_handle* h, const hpa_profile* const* ps,
 }
 
 extern "C" hpa_status hpa_build_pms(hpa_handle* h, const hpa_profile* const* ps, uint32_t n_profiles, hpa_pms* out) {
+    hpa::Trace trace_("hpa.build_pms");
     if (!h || !ps || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     if (!out->counts || !out->prof_off || (out->cap_planes && (!out->plane_ctx || !out->plane_node)) ||

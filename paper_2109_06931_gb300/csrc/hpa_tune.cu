@@ -13,6 +13,7 @@ using namespace hpa;
 
 extern "C" hpa_status hpa_tune(hpa_handle* h, uint32_t binary_id, const hpa_samples* in, hpa_profile* out,
                                uint32_t reps, hpa_options* best, float* ms) {
+    hpa::Trace trace_("hpa.tune");
     if (!h || !in || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     if (reps == 0) reps = 2;

@@ -146,6 +146,7 @@ __global__ void k_un_finish(UnifyArgs a, hpa_cct_unified o) {
 using namespace hpa;
 
 extern "C" hpa_status hpa_unify_ccts(hpa_handle* h, const hpa_cct_nodes* ccts, uint32_t n, hpa_cct_unified* out) {
+    hpa::Trace trace_("hpa.unify_ccts");
     if (!h || !ccts || !out || n == 0) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
     if (!out->uid || !out->n_unified || (out->capacity && (!out->parent || !out->module || !out->offset)))
