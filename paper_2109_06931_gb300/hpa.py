@@ -231,6 +231,33 @@ class Profile:
         return (self.key_ctx[:k].cpu().numpy().view(np.uint32), self.key_node[:k].cpu().numpy().view(np.uint32),
                 self.key_stall[:k].cpu().numpy(), self.val[:k].cpu().numpy().view(np.uint64))
 
+    def save(self, path: str):
+        """Host dump of the sorted keys, totals and shape (.npz) -- a debugging
+        aid; load_profile() puts it back on a device."""
+        ctx, node, stall, val = self.numpy()
+        np.savez(path, key_ctx=ctx, key_node=node, key_stall=stall, val=val,
+                 total=self.total[: self.n_stall].cpu().numpy().view(np.uint64),
+                 unknown=self.unknown[: self.n_stall].cpu().numpy().view(np.uint64),
+                 shape=np.array([self.n_ctx, self.n_stall, self.n_nodes], np.int64))
+
+
+def load_profile(path: str, device) -> Profile:
+    """A profile written by Profile.save, on `device`."""
+    z = np.load(path)
+    n_ctx, n_stall, n_nodes = (int(x) for x in z["shape"])
+    k = int(z["val"].shape[0])
+    p = new_profile(max(1, k), n_stall, device)
+    if k:
+        p.key_ctx[:k] = torch.from_numpy(z["key_ctx"].view(np.int32))
+        p.key_node[:k] = torch.from_numpy(z["key_node"].view(np.int32))
+        p.key_stall[:k] = torch.from_numpy(z["key_stall"])
+        p.val[:k] = torch.from_numpy(z["val"].view(np.int64))
+    p.n_keys.fill_(k)
+    p.total[:n_stall] = torch.from_numpy(z["total"].view(np.int64))
+    p.unknown[:n_stall] = torch.from_numpy(z["unknown"].view(np.int64))
+    p.n_ctx, p.n_nodes = n_ctx, n_nodes
+    return p
+
 
 def new_profile(capacity: int, n_stall: int, device) -> Profile:
     cap = max(1, int(capacity))

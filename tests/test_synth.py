@@ -26,3 +26,4 @@ def test_tuple_samples_stay_on_their_tuples():
     keys = set(zip(s.ctx.numpy().tolist(), rng.tolist(), s.stall.numpy().tolist()))
     assert len(keys) <= 300
     assert np.all(s.pc.numpy().view(np.uint64) < b.range_hi[rng])
+
