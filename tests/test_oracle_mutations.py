@@ -35,6 +35,12 @@ MUTATIONS = [
     ("scc-excl-dropped", "for (uint32_t r = 0; r < n_stall; ++r) cex[comp[f]][r] += excl[f][r];",
      "for (uint32_t r = 0; r < n_stall; ++r) cex[comp[f]][r] = excl[f][r];",
      [lambda o: TA.test_golden(o, "gpucct_fig5.json")]),
+    ("issue-rate-of-stalls", "d->W[c] = (double)d->S_issued[c] / (double)d->S[c];",
+     "d->W[c] = (double)(d->S[c] - d->S_issued[c]) / (double)d->S[c];",
+     [lambda o: TI.test_derive_vs_numpy(o), lambda o: TI.test_derive_single_profile(o)]),
+    ("min-over-present-only", "for (uint32_t p = 0; p < P; ++p) { s += x[p]; lo = std::min(lo, x[p]); hi = std::max(hi, x[p]); }",
+     "for (uint32_t p = 0; p < P; ++p) { s += x[p]; if (x[p]) lo = std::min(lo, x[p]); hi = std::max(hi, x[p]); }",
+     [lambda o: TI.test_derive_vs_numpy(o)]),
     ("sample-std", "double sd = std::sqrt(ss / P);", "double sd = std::sqrt(ss / (P > 1 ? P - 1 : 1));",
      [lambda o: TI.test_derive_vs_numpy(o)]),
     ("incl-stops-below-func", "while (n != NO_PARENT) {\n            agg[Key(kctx[i], n, kstall[i])] += kval[i];",
