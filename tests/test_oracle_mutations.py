@@ -62,6 +62,14 @@ MUTATIONS = [
     ("bottom-up-skips-launch-site", "for (uint32_t c = kctx[i]; c != NO_PARENT && chain[i].size() <= levels; c = cct_parent[c])",
      "for (uint32_t c = cct_parent[kctx[i]]; c != NO_PARENT && chain[i].size() <= levels; c = cct_parent[c])",
      [lambda o: TB.test_hand_example(o), lambda o: TB.test_brute_force(o, 20, 16)]),
+    ("pms-plane-per-context", "if (first || p != pp || c != pc || nd != pn) {\n            o->plane_ctx.push_back(c); o->plane_node.push_back(nd); o->plane_off.push_back(o->val.size());\n            o->prof_off[p + 1]",
+     "if (first || p != pp || c != pc) {\n            o->plane_ctx.push_back(c); o->plane_node.push_back(nd); o->plane_off.push_back(o->val.size());\n            o->prof_off[p + 1]",
+     [lambda o: TS.test_hand_computed_pms(o), lambda o: TS.test_pms_reconstructs_every_profile(o)]),
+    ("pms-empty-profile-offsets", "for (uint32_t p = 1; p <= P; ++p) o->prof_off[p] = std::max(o->prof_off[p], o->prof_off[p - 1]);", "",
+     [lambda o: TS.test_hand_computed_pms(o), lambda o: TS.test_profiles_without_keys(o)]),
+    ("unify-root-under-node-0", "const uint32_t up = par == 0xFFFFFFFFu ? 0xFFFFFFFFu : u->uid[base[p] + par];",
+     "const uint32_t up = par == 0xFFFFFFFFu ? 0u : u->uid[base[p] + par];",
+     [lambda o: TU.test_hand_example(o), lambda o: TU.test_paths_are_kept(o)]),
     ("unify-ignores-parent", "const auto key = std::make_tuple(up, (uint32_t)module[i], offset[i]);",
      "const auto key = std::make_tuple(0u, (uint32_t)module[i], offset[i]);",
      [lambda o: TU.test_hand_example(o), lambda o: TU.test_paths_are_kept(o)]),

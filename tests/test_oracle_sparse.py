@@ -40,6 +40,20 @@ def test_hand_computed_pms(oracle_lib):
     assert p.metric_id.tolist() == [0, 2, 0, 1, 2, 1, 0] and p.val.tolist() == [5, 1, 4, 9, 6, 2, 8]
 
 
+def _empty():
+    z = np.zeros(0, np.uint32)
+    return oracle.KeyList(z, z, np.zeros(0, np.uint8), np.zeros(0, np.uint64))
+
+
+def test_profiles_without_keys(oracle_lib):
+    """An empty profile owns no plane (PMS: its offsets repeat) and no entry (CMS)."""
+    p = oracle.pms([keys(P0), _empty(), keys(P1), _empty()])
+    assert p.prof_off.tolist() == [0, 3, 3, 6, 6]
+    assert p.plane_ctx.tolist() == [0, 1, 2, 0, 1, 1] and p.val.tolist() == [5, 1, 4, 9, 6, 2, 8]
+    c = oracle.cms([_empty(), keys(P0), keys(P1)])
+    assert c.pid.tolist() == [1, 1, 2, 2, 1, 2, 1] and c.val.tolist() == [5, 1, 6, 2, 4, 8, 9]
+
+
 def _profiles():
     b = synth.PLAIN.binary()
     out = []
