@@ -62,6 +62,18 @@ def test_structure_inclusive_brute(oracle_lib):
         assert got[key] == v
     # no key is invented: every output node is an ancestor-or-self of a sampled node
     assert len(got) >= len(ex)
+    # UNKNOWN keys pass through unchanged (no function, no ancestors) ...
+    unknown = {key: v for key, v in ex.items() if key[1] == U}
+    assert unknown and all(got.get(key) == v for key, v in unknown.items())
+    # ... so per (ctx, stall) the function nodes and UNKNOWN together hold every sample
+    funcs = set(int(x) for x in B.func_node)
+    tot_in, tot_out = defaultdict(int), defaultdict(int)
+    for (c, n, r), v in ex.items():
+        tot_in[(c, r)] += v
+    for (c, n, r), v in got.items():
+        if n == U or n in funcs:
+            tot_out[(c, r)] += v
+    assert tot_in == tot_out
 
 
 def test_cct_inclusive(oracle_lib):

@@ -26,6 +26,14 @@ MUTATIONS = [
      [lambda o: TT.test_golden_fixture(o)]),
     ("no-unknown-total", "if (node == UNKNOWN) out->unknown[stall[i]] += c;", "",
      [lambda o: TT.test_golden_fixture(o)]),
+    ("lower-bound-search", "const uint64_t* it = std::upper_bound(range_lo, range_lo + n_ranges, pc[i]);",
+     "const uint64_t* it = std::lower_bound(range_lo, range_lo + n_ranges, pc[i]);",
+     [lambda o: TT.test_golden_fixture(o)]),
+    ("count-ignored", "uint64_t c = count ? count[i] : 1;", "uint64_t c = 1;",
+     [lambda o: TT.test_golden_fixture(o)]),
+    ("unknown-dropped-from-inclusive", "if (n == UNKNOWN) { agg[Key(kctx[i], n, kstall[i])] += kval[i]; continue; }",
+     "if (n == UNKNOWN) continue;",
+     [lambda o: TI.test_structure_inclusive_brute(o)]),
     ("step2-no-callers", "if (!inZ[h] && !in_edges[h].empty() && !measured_in[h]) { inZ[h] = 1; work.push_back(h); }", "",
      [lambda o: TA.test_golden(o, "gpucct_fig5.json")]),
     ("ratio-of-tail", "double ratio = W[h] > 0.0 ? wt[e] / W[h] : 0.0;", "double ratio = W[v] > 0.0 ? wt[e] / W[v] : 0.0;",
