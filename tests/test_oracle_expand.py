@@ -18,10 +18,14 @@ def setup(binary, n, n_ctx, seed, q_ctx):
     return keys, g
 
 
-@pytest.fixture(scope="module")
-def plain():
+def plain_bin():
     b = synth.PLAIN.binary()
     return (b,) + setup(b, 300_000, 4, 21, [0, 3])
+
+
+@pytest.fixture(scope="module")
+def plain():
+    return plain_bin()
 
 
 def test_each_nodes_scales_sum_to_one(oracle_lib, plain):
@@ -138,3 +142,17 @@ def test_paths_by_depth_first_enumeration(oracle_lib, plain):
                 stack.append((h, sc * r))
     got = collections.Counter((int(v), round(s, 12)) for v, s in zip(t.cnode, t.scale))
     assert got == found
+    # the links: a child's parent comes before it, its call site leads from the
+    # parent's condensed node to its own, and its scale is the parent's times
+    # that call site's ratio
+    NP = 0xFFFFFFFF
+    for i in range(len(t.cnode)):
+        p, e = int(t.parent[i]), int(t.edge[i])
+        if p == NP:
+            assert e == NP and t.scale[i] == 1.0
+            continue
+        assert p < i
+        assert int(g.cnode_of_func[b.cs_caller[e]]) == int(t.cnode[p])
+        assert int(g.cnode_of_func[b.cs_callee[e]]) == int(t.cnode[i])
+        r = a[e, -1] / inc[int(t.cnode[i]), -1]
+        assert abs(t.scale[i] - t.scale[p] * r) <= 1e-12 * t.scale[i]

@@ -58,6 +58,15 @@ MUTATIONS = [
      [lambda o: TI.test_cct_inclusive(o)]),
     ("expand-no-product", "const double sc = t->scale[i] * r;", "const double sc = r;",
      [lambda o: TX.test_ratios_are_call_site_weights(o, 1)]),
+    ("expand-budget-off-by-one", "if (t->cnode.size() >= budget) { t->truncated = 1; return; }",
+     "if (t->cnode.size() + 1 >= budget) { t->truncated = 1; return; }",
+     [lambda o: TX.test_budget_gives_a_prefix(o, TX.plain_bin())]),
+    ("expand-parent-is-level-start", "if (sc > 0.0) add((uint32_t)i, h, e, sc);",
+     "if (sc > 0.0) add((uint32_t)begin, h, e, sc);",
+     [lambda o: TX.test_paths_by_depth_first_enumeration(o, TX.plain_bin())]),
+    ("expand-keeps-zero-scale", "if (sc > 0.0) add((uint32_t)i, h, e, sc);", "add((uint32_t)i, h, e, sc);",
+     [lambda o: TX.test_paths_by_depth_first_enumeration(o, TX.plain_bin()),
+      lambda o: TX.test_each_nodes_scales_sum_to_one(o, TX.plain_bin())]),
     ("cms-profile-major-order", "m[std::make_tuple(kctx[i], knode[i], (uint32_t)kstall[i], kp[i])] = kval[i];",
      "m[std::make_tuple(kctx[i], knode[i], kp[i], (uint32_t)kstall[i])] = kval[i];",
      [lambda o: TS.test_hand_computed_cms(o), lambda o: TS.test_cms_reconstructs_every_profile(o)]),
