@@ -38,6 +38,14 @@ MUTATIONS = [
      [lambda o: TA.test_golden(o, "gpucct_fig5.json")]),
     ("ratio-of-tail", "double ratio = W[h] > 0.0 ? wt[e] / W[h] : 0.0;", "double ratio = W[v] > 0.0 ? wt[e] / W[v] : 0.0;",
      [lambda o: TA.test_golden(o, "gpucct_fig5.json"), lambda o: TA.test_path_enumeration(o, 1, False)]),
+    ("share-of-exclusive-cost", "double x = ratio * incl[h][r];", "double x = ratio * cex[h][r];",
+     [lambda o: TA.test_golden(o, "gpucct_fig5.json"), lambda o: TA.test_golden(o, "gpucct_diamond.json")]),
+    ("call-weight-one-stall", "if (call_of_node[knode[i]] >= 0) w[call_of_node[knode[i]]] += kval[i];",
+     "if (call_of_node[knode[i]] >= 0 && kstall[i] == 0) w[call_of_node[knode[i]]] += kval[i];",
+     [lambda o: TA.test_golden(o, "gpucct_fig5.json"), lambda o: TA.test_path_enumeration(o, 1, False)]),
+    ("fixup-without-samples", "if (S[f] > 0 && !in_edges[f].empty() && !measured_in[f]) { inZ[f] = 1; work.push_back(f); }",
+     "if (!in_edges[f].empty() && !measured_in[f]) { inZ[f] = 1; work.push_back(f); }",
+     [lambda o: TA.test_golden(o, "gpucct_fig5.json"), lambda o: TA.test_golden(o, "gpucct_diamond.json")]),
     ("no-fixup2", "if (cneed[v] && !cin[v].empty() && W[v] == 0.0) { inZ2[v] = 1; work.push_back(v); }", "",
      [lambda o: TA.test_golden(o, "gpucct_fig5.json")]),
     ("scc-excl-dropped", "for (uint32_t r = 0; r < n_stall; ++r) cex[comp[f]][r] += excl[f][r];",
@@ -79,6 +87,11 @@ MUTATIONS = [
     ("bottom-up-skips-launch-site", "for (uint32_t c = kctx[i]; c != NO_PARENT && chain[i].size() <= levels; c = cct_parent[c])",
      "for (uint32_t c = cct_parent[kctx[i]]; c != NO_PARENT && chain[i].size() <= levels; c = cct_parent[c])",
      [lambda o: TB.test_hand_example(o), lambda o: TB.test_brute_force(o, 20, 16)]),
+    ("cms-metric-runs-across-planes", "const bool new_metric = new_plane || r != ps;", "const bool new_metric = first || r != ps;",
+     [lambda o: TS.test_hand_computed_cms(o), lambda o: TS.test_cms_reconstructs_every_profile(o)]),
+    ("cms-plane-offsets-in-values", "if (new_plane) { o->plane_ctx.push_back(c); o->plane_node.push_back(nd); o->plane_off.push_back(o->metric_id.size()); }",
+     "if (new_plane) { o->plane_ctx.push_back(c); o->plane_node.push_back(nd); o->plane_off.push_back(o->val.size()); }",
+     [lambda o: TS.test_hand_computed_cms(o), lambda o: TS.test_cms_reconstructs_every_profile(o)]),
     ("pms-plane-per-context", "if (first || p != pp || c != pc || nd != pn) {\n            o->plane_ctx.push_back(c); o->plane_node.push_back(nd); o->plane_off.push_back(o->val.size());\n            o->prof_off[p + 1]",
      "if (first || p != pp || c != pc) {\n            o->plane_ctx.push_back(c); o->plane_node.push_back(nd); o->plane_off.push_back(o->val.size());\n            o->prof_off[p + 1]",
      [lambda o: TS.test_hand_computed_pms(o), lambda o: TS.test_pms_reconstructs_every_profile(o)]),
@@ -87,6 +100,15 @@ MUTATIONS = [
     ("unify-root-under-node-0", "const uint32_t up = par == 0xFFFFFFFFu ? 0xFFFFFFFFu : u->uid[base[p] + par];",
      "const uint32_t up = par == 0xFFFFFFFFu ? 0u : u->uid[base[p] + par];",
      [lambda o: TU.test_hand_example(o), lambda o: TU.test_paths_are_kept(o)]),
+    ("unify-ignores-module", "const auto key = std::make_tuple(up, (uint32_t)module[i], offset[i]);",
+     "const auto key = std::make_tuple(up, 0u, offset[i]);",
+     [lambda o: TU.test_hand_example(o), lambda o: TU.test_sites_differ_by_module(o)]),
+    ("bottom-up-one-site-short", "for (uint32_t c = kctx[i]; c != NO_PARENT && chain[i].size() <= levels; c = cct_parent[c])",
+     "for (uint32_t c = kctx[i]; c != NO_PARENT && chain[i].size() < levels; c = cct_parent[c])",
+     [lambda o: TB.test_hand_example(o), lambda o: TB.test_hand_example_cut(o)]),
+    ("bottom-up-stalls-merged", "cost[std::make_pair(id, (uint32_t)kstall[i])] += kval[i];",
+     "cost[std::make_pair(id, 0u)] += kval[i];",
+     [lambda o: TB.test_hand_example(o), lambda o: TB.test_brute_force(o, 20, 16)]),
     ("unify-ignores-parent", "const auto key = std::make_tuple(up, (uint32_t)module[i], offset[i]);",
      "const auto key = std::make_tuple(0u, (uint32_t)module[i], offset[i]);",
      [lambda o: TU.test_hand_example(o), lambda o: TU.test_paths_are_kept(o)]),

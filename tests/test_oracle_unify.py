@@ -25,6 +25,14 @@ def test_hand_example(oracle_lib):
     assert um.tolist() == [1, 1, 2, 3, 3, 1] and uo.tolist() == [10, 20, 5, 7, 7, 99]
 
 
+def test_sites_differ_by_module(oracle_lib):
+    # two call sites at one offset in different load modules are different sites
+    A = cct([(NP, 1, 10), (0, 1, 5), (0, 2, 5)])
+    B = cct([(NP, 1, 10), (0, 2, 5)])
+    uid, up, um, uo = oracle.unify([A, B])
+    assert uid.tolist() == [0, 1, 2, 0, 2] and um.tolist() == [1, 1, 2] and uo.tolist() == [10, 5, 5]
+
+
 def test_copies_unify_to_the_original(oracle_lib):
     c = synth.make_profile_ccts(5, 3000, 20, 1, 1.0)[0]
     uid, up, um, uo = oracle.unify([c, c, c])
