@@ -42,9 +42,9 @@ def workload(name: str):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per sample of
-# the kernel that dominates each phase, from one ncu capture of the 2e7-sample
-# case (profiles/k_leaf_plain-large-20M.md), keyed by a
-# hash of the kernel sources it was taken on: a changed kernel reports null.
+# the kernel that dominates each phase, from one ncu capture of the leaf kernel
+# on the 2e7-sample case of the large workload, keyed by a hash of the kernel
+# sources it was taken on: a changed kernel reports null.
 KERNEL_SOURCES = ("hpa_leaf.cu", "hpa_dev.cuh", "hpa_internal.h")     # the leaf kernel's sources
 TRAFFIC = {
     "leaf sort/reduce": {"kernel": "k_leaf", "bytes_per_sample": 15.46, "sources": "24660ecbb8e32a3f"},
@@ -115,22 +115,44 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_rate(w, B, target_s: float, max_n: int):
-    """Samples/s of the oracle on the first n samples of the workload."""
+def cpu_oracle_rate(w, B, target_s: float, max_n: int, dev=None):
+    """Samples/s of the oracle on the first n samples of the workload (n sized
+    for about target_s seconds).  Returns (rate, n, seconds, the oracle's keys,
+    the samples).  With dev the samples are generated there and copied to the
+    host, so that the same slice can be run on the GPU for a parity check."""
     import oracle
     oracle.build()
     n = 1_000_000
-    S = w.samples(B, device="cpu", n=n)
+    S = w.samples(B, device=dev or "cpu", n=n)
     t = time.perf_counter()
     oracle.attribute_samples(B, S)
     est = max(time.perf_counter() - t, 1e-3) / n
     n = int(min(max_n, max(n, target_s / est)))
-    S = w.samples(B, device="cpu", n=n)
+    S = w.samples(B, device=dev or "cpu", n=n)
+    Sh = synth.Samples(S.pc.cpu(), S.ctx.cpu(), S.stall.cpu(), None if S.count is None else S.count.cpu(),
+                       S.n_ctx, S.n_stall)
     t = time.perf_counter()
-    k = oracle.attribute_samples(B, S)
+    k = oracle.attribute_samples(B, Sh)
     dt = time.perf_counter() - t
     assert k.status == 0
-    return n / dt, n, dt
+    return n / dt, n, dt, k, S
+
+
+def parity_against_oracle(h, bid, S, ref) -> dict:
+    """Bit-exact comparison of the library's profile of S with the oracle's
+    keys and totals of the same samples."""
+    from paper_2109_06931_gb300 import hpa as H
+    out = H.new_profile(S.n, S.n_stall, S.pc.device)
+    h.attribute_samples(bid, S, out=out)
+    h.sync()
+    got = out.numpy()
+    same = out.count() == len(ref) and all(
+        np.array_equal(g, r) for g, r in zip(got, (ref.ctx, ref.node, ref.stall, ref.val)))
+    S_ = len(ref.total)
+    same = same and np.array_equal(out.total[:S_].cpu().numpy().view(np.uint64), ref.total) and \
+        np.array_equal(out.unknown[:S_].cpu().numpy().view(np.uint64), ref.unknown)
+    return {"checked_samples": int(S.n), "keys": len(ref), "bit_exact": bool(same),
+            "compared": "every key, value, per-stall total and UNKNOWN total"}
 
 
 def timed(stream, fn, reps=3):
@@ -224,7 +246,7 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     return out
 
 
-def run_serving(args, world, rank, local):
+def serving_result(args, world, rank, local):
     """Open-loop serving (hpa_server_*): Poisson arrivals at --rate requests/s
     for --duration s, sizes log-uniform over [10^3, 10^7] samples, 16 resident
     binaries.  Request payloads are slices of pinned per-binary sample pools
@@ -343,22 +365,26 @@ def run_serving(args, world, rank, local):
              "form": "one hpa_attribute_samples_host call per request, arrival order"}
     total = int(sizes.sum())
     keys = int(small[:, 0].sum())
+    return {
+        "metric": METRIC, "value": total * world / wall, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving", "rate_per_s": args.rate, "duration_s": args.duration,
+                   "requests": n_req, "binaries": n_bin, "samples": total, "sizes": "log-uniform [1e3, 1e7]",
+                   "admission_cap_gib": args.serve_mem_gb, "offered_samples_per_s": total / args.duration},
+        "latency_ms": {"p50": stats["p50_ms"], "p99": stats["p99_ms"], "max": stats["max_ms"],
+                       "mean": stats["mean_ms"], "measured": "submit -> keys in host arrays"},
+        "submit_lag_ms": {"p50": float(np.percentile(lag, 50) * 1e3), "p99": float(np.percentile(lag, 99) * 1e3)},
+        "server": {k: stats[k] for k in ("completed", "rejected", "batches", "busy_s")},
+        "plain": plain,
+        "e2e": {"value": total * world / wall, "unit": UNIT,
+                "h2d_bytes_per_step": 17 * total, "d2h_bytes_per_step": 17 * keys + 8 * (1 + 2 * 16) * n_req}}
+
+
+def run_serving(args, world, rank, local):
+    r = serving_result(args, world, rank, local)
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": total * world / wall, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0,
-            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "serving", "rate_per_s": args.rate, "duration_s": args.duration,
-                       "requests": n_req, "binaries": n_bin, "samples": total, "sizes": "log-uniform [1e3, 1e7]",
-                       "admission_cap_gib": args.serve_mem_gb, "offered_samples_per_s": total / args.duration},
-            "latency_ms": {"p50": stats["p50_ms"], "p99": stats["p99_ms"], "max": stats["max_ms"],
-                           "mean": stats["mean_ms"], "measured": "submit -> keys in host arrays"},
-            "submit_lag_ms": {"p50": float(np.percentile(lag, 50) * 1e3), "p99": float(np.percentile(lag, 99) * 1e3)},
-            "server": {k: stats[k] for k in ("completed", "rejected", "batches", "busy_s")},
-            "plain": plain,
-            "e2e": {"value": total * world / wall, "unit": UNIT,
-                    "h2d_bytes_per_step": 17 * total, "d2h_bytes_per_step": 17 * keys + 8 * (1 + 2 * 16) * n_req}}),
-              flush=True)
+        print(json.dumps(r), flush=True)
 
 
 def bind_near_gpu(dev_index: int):
@@ -460,7 +486,7 @@ def run_reference(args, world, rank):
     import oracle
     oracle.build()
     # one bounded sample per step, sized for about args.ref_step_s seconds
-    rate, _, _ = cpu_oracle_rate(w, B, 1.0, 2_000_000)
+    rate, _, _, _, _ = cpu_oracle_rate(w, B, 1.0, 2_000_000)
     n = int(min(w.n_samples, max(10_000, rate * args.ref_step_s)))
     S = w.samples(B, device="cpu", n=n)
     for _ in range(args.warmup):
@@ -481,9 +507,11 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, world, rank, local):
+def batched_result(args, world, rank, local, workload: str, steps: int, warmup: int, cpu_seconds: float):
     """Batched form (256 uneven buffers, 8 binaries, one graph launch per
-    step) against the plain form (one hpa_attribute_samples per buffer)."""
+    step; or 64 buffers over 10^6 tuples each) against the plain form (one
+    hpa_attribute_samples per buffer), with a bit-exact check of the batch's
+    smallest buffers against the oracle."""
     from paper_2109_06931_gb300 import hpa as H
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -491,7 +519,7 @@ def run_batched(args, world, rank, local):
     h = H.Hpa(local, stream=stream, sort_mode=args.sort_mode, partition=not args.no_part,
               small_leaves=args.small_leaves, leaf_hash=args.leaf_hash)
     extra = {}
-    if args.workload == "many-ctx":
+    if workload == "many-ctx":
         # 64 buffers of tuple samples over a 2x10^6-node merged CCT, one binary
         w = synth.MANY_CTX
         n_each = max(1, args.samples // w.n_buffers) if args.samples else w.n_samples
@@ -521,7 +549,7 @@ def run_batched(args, world, rank, local):
         big = int(np.argmax([b.n for b in bufs]))
         chosen, cand_ms = h.tune(bids[big], bufs[big], out=outs[big])
         tuned = dict(chosen, on_buffer=big, candidates_ms=[round(t, 3) for t in cand_ms])
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         h.attribute_batch(bids, bufs, outs)
     h.sync()
     K = sum(o.count() for o in outs)
@@ -529,34 +557,34 @@ def run_batched(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     l0 = h.launches()
-    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     with Clocks(local) as clk:
         e0.record(stream)
         marks[0].record(stream)
-        for k in range(args.steps):
+        for k in range(steps):
             h.attribute_batch(bids, bufs, outs)
             marks[k + 1].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
     h.sync()
     launches = h.launches() - l0
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
-    step_ms = step_stats([marks[k].elapsed_time(marks[k + 1]) for k in range(args.steps)])
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
+    step_ms = step_stats([marks[k].elapsed_time(marks[k + 1]) for k in range(steps)])
     # plain form: one launch sequence per buffer
     for _ in range(1):
         for bid, b, o in zip(bids, bufs, outs):
             h.attribute_samples(bid, b, out=o)
     h.sync()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for bid, b, o in zip(bids, bufs, outs):
             h.attribute_samples(bid, b, out=o)
     e1.record(stream)
     torch.cuda.synchronize()
     h.sync()
-    ms_plain = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    ms_plain = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
     rows = None
-    if args.workload == "many-ctx" and not args.no_rows:
+    if workload == "many-ctx" and not args.no_rows:
         # inclusive propagation of one buffer's keys over the 2x10^6-node CCT
         par = torch.from_numpy(w.cct().view(np.int32)).to(dev)
         torch.cuda.synchronize()
@@ -566,7 +594,7 @@ def run_batched(args, world, rank, local):
                                   "bytes_per_launch": 2 * int(par.shape[0]) * 8 * outs[0].n_stall}}
     # per-phase kernel times of the batched call (timing replaces graph replay)
     h.set_phase_timing(True)
-    for _ in range(args.steps):
+    for _ in range(steps):
         h.attribute_batch(bids, bufs, outs)
     h.sync()
     ph, calls = h.phase_times()
@@ -576,16 +604,18 @@ def run_batched(args, world, rank, local):
     path_bytes = 17 * N + 17 * K
     ach = path_bytes / (ms / 1e3) / 1e9
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    parity = None
+    if rank == 0 and cpu_seconds > 0:
         bin_of = [bins[i % len(bins)] for i in range(len(bufs))]
-        rate, n_cpu, dt_cpu, used = batched_cpu_rate(bin_of, bufs, args.cpu_seconds)
+        rate, n_cpu, dt_cpu, used, parity = batched_cpu_rate(bin_of, bufs, cpu_seconds, outs)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{used} smallest buffers, the last cut to fit ({n_cpu} samples, {dt_cpu:.1f} s); "
                          f"the rate applies per sample of the whole batch", **host_info()}
+    res = None
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": N * world / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        res = {
+            "metric": METRIC, "value": N * world / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": w.name, "buffers": len(bufs), "binaries": len(bins), "samples": N, "keys": K,
                        "form": "batched, one CUDA graph launch per step",
@@ -595,19 +625,32 @@ def run_batched(args, world, rank, local):
             "path_roofline": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                               "peak_kind": peak_kind, "algorithmic_bytes_per_step": path_bytes,
                               "frac_of_nominal": ach / NOMINAL_HBM_GBS},
-            "step_ms": step_ms, "cpu_baseline": cpu,
-            "phases_ms": ph, "clocks": clk.summary(), "gpu_launches": int(launches), "rows": rows}), flush=True)
+            "step_ms": step_ms, "cpu_baseline": cpu, "parity": parity,
+            "phases_ms": ph, "clocks": clk.summary(), "gpu_launches": int(launches), "rows": rows}
     h.close()
+    return res
 
 
-def batched_cpu_rate(bin_of, bufs, seconds: float):
+def run_batched(args, world, rank, local):
+    r = batched_result(args, world, rank, local, args.workload, args.steps, args.warmup,
+                       0.0 if args.no_cpu else args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(r), flush=True)
+
+
+
+
+def batched_cpu_rate(bin_of, bufs, seconds: float, outs=None):
     """Samples/s of the oracle on a bounded subset of a batch: buffers in
     increasing size, the last one cut so that the oracle runs about
-    `seconds`.  Returns (rate, samples, seconds, buffers used)."""
+    `seconds`.  With outs (the batch's device profiles) every whole buffer
+    the oracle ran is compared with its batched result, key by key.  Returns
+    (rate, samples, seconds, buffers used, parity summary or None)."""
     import oracle
     oracle.build()
     order = sorted(range(len(bufs)), key=lambda i: bufs[i].n)
     done_n, t_total, used = 0, 0.0, 0
+    checked, checked_n, exact = 0, 0, True
     for i in order:
         if t_total >= seconds:
             break
@@ -622,7 +665,21 @@ def batched_cpu_rate(bin_of, bufs, seconds: float):
         assert k.status == 0
         done_n += n
         used += 1
-    return done_n / max(t_total, 1e-9), done_n, t_total, used
+        if outs is not None and n == b.n:
+            o = outs[i]
+            got = o.numpy()
+            ok = o.count() == len(k) and all(np.array_equal(g, r) for g, r in zip(got, (k.ctx, k.node, k.stall, k.val)))
+            S_ = len(k.total)
+            ok = ok and np.array_equal(o.total[:S_].cpu().numpy().view(np.uint64), k.total) and \
+                np.array_equal(o.unknown[:S_].cpu().numpy().view(np.uint64), k.unknown)
+            exact = exact and bool(ok)
+            checked += 1
+            checked_n += n
+    parity = None
+    if outs is not None:
+        parity = {"buffers_checked": checked, "checked_samples": checked_n, "bit_exact": exact,
+                  "compared": "every key, value, per-stall total and UNKNOWN total of the batched result"}
+    return done_n / max(t_total, 1e-9), done_n, t_total, used, parity
 
 
 def main():
@@ -645,11 +702,13 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the apportion / inclusive / derive rows")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
-    ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--plain-seconds", type=float, default=5.0,
                     help="serving: seconds of the same arrivals replayed as one call per request")
     ap.add_argument("--serve-mem-gb", type=int, default=60, help="serving: admission pool (GiB)")
     ap.add_argument("--ref-step-s", type=float, default=4.0)
+    ap.add_argument("--no-extra-rows", action="store_true",
+                    help="skip the batched, many-contexts and serving rows of the default (1-GPU) run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
@@ -801,9 +860,30 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        rate, n_cpu, dt_cpu = cpu_oracle_rate(w, B, args.cpu_seconds, 20_000_000)
+        rate, n_cpu, dt_cpu, ref, S_cpu = cpu_oracle_rate(w, B, args.cpu_seconds, 20_000_000, dev)
+        torch.cuda.synchronize()
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n_cpu} samples of {w.name} ({dt_cpu:.1f} s)", **host_info()}
+               "sample": f"first {n_cpu} samples of {w.name} ({dt_cpu:.1f} s)", **host_info(),
+               "parity": parity_against_oracle(h, bid, S_cpu, ref)}
+        del S_cpu
+
+    # the metric's other half at one GPU: the batched forms against one call
+    # per buffer, and serving with p50 / p99 latency, each in its own process
+    # state (the large workload's buffers are freed first)
+    extra_rows = None
+    if world == 1 and not args.no_rows and not args.no_extra_rows:
+        h.close()
+        out = S = None
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        extra_rows = {}
+        for name, key in (("batched", "batched"), ("many-ctx", "many_ctx")):
+            extra_rows[key] = batched_result(args, world, rank, local, name, min(args.steps, 5), 3,
+                                             0.0 if args.no_cpu else 8.0)
+            torch.cuda.empty_cache()
+        extra_rows["serving"] = serving_result(args, world, rank, local)
+        torch.cuda.empty_cache()
+        rows = dict(rows or {}, **extra_rows)
 
     if rank == 0:
         line = {
@@ -829,7 +909,8 @@ def main():
             "rows": rows,
         }
         print(json.dumps(line), flush=True)
-    h.close()
+    if extra_rows is None:
+        h.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -120,6 +120,9 @@ typedef struct {
     uint32_t n_scc;          /* non-trivial SCCs (>= 2 functions or a self-call)                */
     uint32_t cdag_levels;    /* levels of the condensed DAG                                      */
     uint64_t n_ranges;
+    uint32_t max_depth;      /* depth of the deepest structure node (FUNC nodes have depth 0); a
+                                key expands into at most max_depth + 1 inclusive records          */
+    uint32_t reserved;
 } hpa_binary_info;
 
 /* One buffer of PC samples (Section 4.2: instruction address, stall reason,
@@ -307,19 +310,27 @@ hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, const hpa_sa
 hpa_status hpa_attribute_samples_host(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
                                       hpa_profile* out);
 
-/* hpa_attribute_samples for callers that cannot allocate device memory
- * while they analyse samples -- for example code running during CUDA stream
- * capture (allocation is not allowed there) or inside a runtime that owns
- * the GPU's memory pool.  The paper has no counterpart: this is a property
- * of the library, not of the method.  Same arguments, same results; in and
- * out are DEVICE arrays owned by the caller as for hpa_attribute_samples.
- * The call takes its scratch from one fixed 48 MiB array that the library
- * reserves on every GPU that loads it (about 1.5 million samples with counts
- * per call); a call that needs more returns HPA_E_INVALID_ARG and does
- * nothing.  It calls no cudaMalloc / cudaFree.  The first call on a device
- * looks up the array's device address; make that first call before any
- * stream capture.  All calls on a device share the array: calls that overlap
- * on the GPU (different streams or handles without synchronisation) race.  */
+/* hpa_attribute_samples for callers that must not allocate device memory
+ * while they analyse samples.  Examples: a measurement tool that runs inside
+ * the application it observes, whose device memory belongs to the
+ * application's own caching allocator (an allocation by the tool would change
+ * the footprint it is measuring, and may fail because the pool has taken the
+ * free memory); a serving loop that shares the GPU with other work, where
+ * cudaFree would synchronise the whole device.  The paper has no counterpart:
+ * this is a property of the library, not of the method.  Same arguments and
+ * same keys as hpa_attribute_samples; in and out are DEVICE arrays owned by
+ * the caller.  The handle's leaf_capacity, leaf_ranking, leaf_hash and
+ * small_leaves options apply as there; contexts are always grouped by
+ * per-context cursors (grouping is ignored).  Scratch comes from one fixed
+ * 48 MiB array that the library declares in device memory, present on every
+ * GPU that loads the library until the process exits (about 1.5 million
+ * samples with counts per call); a call that would need more returns
+ * HPA_E_INVALID_ARG and enqueues nothing.  The call makes no cudaMalloc or
+ * cudaFree.  Its first call on a device looks up the array's device address
+ * (once per device, under a lock); make that first call before any stream
+ * capture.  All calls on a device share the array and leave their contents
+ * in it: calls that overlap on the GPU (different streams or handles without
+ * synchronisation between them) race and corrupt each other's results.     */
 hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t binary_id, const hpa_samples* in,
                                          hpa_profile* out);
 

@@ -24,6 +24,9 @@
 // (ctx, node, stall).
 
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <tuple>
 #include <type_traits>
 
 #include "hpa_bulk.cuh"
@@ -82,6 +85,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, 
         pre += v[i];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = part[nb];
+}
+
+void set_smem_limit(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void*, int, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(std::make_tuple(fn, dev, bytes))) return;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+        done.insert(std::make_tuple(fn, dev, bytes));
 }
 
 size_t scan_tmp_words(uint64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 2; }
@@ -937,11 +951,7 @@ void launch_finalize(const AggWork& w, cudaStream_t s, uint64_t* launches) {
 
 void launch_big_partition(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
     constexpr size_t smem = ((1u << BIG_FINE_MAX_LOG) + 1) * 4;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_big_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    set_smem_limit((const void*)k_big_partition, (int)smem);
     k_big_partition<<<sms * 3, BIG_THREADS, smem, s>>>(w);
     *launches += 1;
 }
@@ -953,11 +963,7 @@ static void run_finish(const AggWork& w, cudaStream_t s, int sms, uint64_t* laun
     if (ev) cudaEventRecord(ev[4], s);
     scan_u32(w.leaf_d, w.leaf_d, w.L_max, w.scan_tmp, s, launches);
     const size_t emit_smem = w.emit_totals ? ((size_t)256 << w.sb) * 8 : 0;
-    static bool emit_attr = false;
-    if (!emit_attr) {
-        cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * HPA_MAX_STALL_DEV * 8);
-        emit_attr = true;
-    }
+    set_smem_limit((const void*)k_emit, 256 * HPA_MAX_STALL_DEV * 8);
     k_emit<<<sms * 8, 256, emit_smem, s>>>(w);
     launch_finalize(w, s, launches);
     *launches += 1;
@@ -976,13 +982,11 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
     if (w.part_mode) {
         const size_t csm = (size_t)w.part_ctx_max * 4;
         const size_t ssm = part_scatter_smem(w.part_ctx_max);
-        static bool attr = false;
-        if (!attr) {
+        {
             const int mx = (int)PART_CTX_MAX * 4, mxs = (int)part_scatter_smem(PART_CTX_MAX);
-            cudaFuncSetAttribute(k_part_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-            cudaFuncSetAttribute(k_part_scatter<true, PSC_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs);
-            cudaFuncSetAttribute(k_part_scatter<false, PSC_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs);
-            attr = true;
+            set_smem_limit((const void*)k_part_hist, mx);
+            set_smem_limit((const void*)k_part_scatter<true, PSC_U>, mxs);
+            set_smem_limit((const void*)k_part_scatter<false, PSC_U>, mxs);
         }
         const int pb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * 2));
         const int psb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * PSC_MIN_BLOCKS));
@@ -1019,7 +1023,7 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
         const size_t hsm = (size_t)HIST_SMEM_MAX * 4;
         const int per_sm = 2;
         const int hist_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_tiles, (uint64_t)sms * per_sm));
-        cudaFuncSetAttribute(k_grp_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        set_smem_limit((const void*)k_grp_hist, (int)hsm);
         k_grp_hist<<<hist_blocks, 256, hsm, s>>>(w);
         *launches += 1;
         run_plan(w, s, sms, launches, false);

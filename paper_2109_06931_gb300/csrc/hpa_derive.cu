@@ -433,7 +433,7 @@ extern "C" hpa_status hpa_derive_metrics(hpa_handle* h, const hpa_profile* const
     launch_big_partition(w, s, sms, &h->launches);
     using Sort = PackedRadix<DS_THREADS, DS_CAP, uint64_t>;
     const size_t smem = std::max(sizeof(typename Sort::Smem), (size_t)DS_WIN * 44);
-    cudaFuncSetAttribute(k_leaf_stats<DS_THREADS, DS_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem_limit((const void*)k_leaf_stats<DS_THREADS, DS_CAP>, (int)smem);
     k_leaf_stats<DS_THREADS, DS_CAP><<<sms * 2, DS_THREADS, smem, s>>>(w, A);
     scan_u32(w.leaf_d, w.leaf_d, w.L_max, w.scan_tmp, s, &h->launches);
     k_emit_stats<<<sms * 8, 256, 0, s>>>(w, A, o);

@@ -481,6 +481,8 @@ extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary
         info->n_nodes = B->n_nodes; info->n_funcs = B->n_funcs; info->n_calls = B->n_calls;
         info->n_cnodes = B->n_cnodes; info->n_scc = B->n_scc; info->cdag_levels = B->cdag_levels;
         info->n_ranges = B->n_ranges;
+        info->max_depth = B->max_depth;
+        info->reserved = 0;
     }
     if (cnode_of_func) std::copy(B->cnode_of_func.begin(), B->cnode_of_func.end(), cnode_of_func);
     return HPA_OK;

@@ -134,6 +134,12 @@ constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_EPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_EPT;
 
+// Raise the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device.  The attribute belongs to one device, so it is set once per
+// (kernel, device) and remembered under a lock (calls may come from several
+// host threads and handles on several devices).
+void set_smem_limit(const void* fn, int bytes);
+
 // device-wide exclusive scan of n uint32 values (in place allowed);
 // out[n] receives the total.  tmp needs scan_tmp_words(n) words.
 size_t scan_tmp_words(uint64_t n);

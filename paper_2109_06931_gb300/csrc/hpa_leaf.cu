@@ -483,12 +483,7 @@ template <int THREADS, int CAP, bool HAS_CNT, typename V, bool HASH>
 static void launch_leaf(const AggWork& w, cudaStream_t s, int sms, int per_sm, uint32_t n_lo = 0,
                         uint32_t n_hi = 0xFFFFFFFFu) {
     using Cfg = LeafCfg<THREADS, CAP, HAS_CNT, V, HASH>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_leaf<THREADS, CAP, HAS_CNT, V, HASH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg::SMEM);
-        attr_set = true;
-    }
+    set_smem_limit((const void*)k_leaf<THREADS, CAP, HAS_CNT, V, HASH>, (int)Cfg::SMEM);
     k_leaf<THREADS, CAP, HAS_CNT, V, HASH><<<sms * per_sm, THREADS, Cfg::SMEM, s>>>(w, n_lo, n_hi);
 }
 

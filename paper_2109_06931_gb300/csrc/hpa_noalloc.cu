@@ -1,20 +1,21 @@
 // hpa_attribute_samples_noalloc: the attribution + aggregation call for
 // callers that must not allocate device memory during the call.
 //
-// Some callers cannot call cudaMalloc at the point where they analyse
-// samples: code that runs while a stream is being captured into a CUDA graph
-// (allocation calls are not allowed there), runtimes that hand the GPU's
-// memory to their own pool and forbid other allocations, or tools attached
-// to an application whose memory must not change under them.  This entry
-// point takes its scratch from one fixed array that the library declares at
-// file scope; it calls no cudaMalloc, cudaFree or other allocating routine.
-// The kernels are the same ones hpa_attribute_samples launches.
+// Who cannot allocate: a measurement tool running inside the application it
+// observes, where the application's caching allocator holds the device memory
+// (an allocation by the tool would change the footprint under measurement and
+// may fail outright), and a serving loop sharing the GPU with other work,
+// where cudaFree synchronises the whole device.  This entry point takes its
+// scratch from one fixed array declared at file scope in device memory and
+// calls no cudaMalloc, cudaFree or other allocating routine.  The kernels are
+// the same ones hpa_attribute_samples launches.
 //
 // The array is NOALLOC_SCRATCH_BYTES (48 MiB) on every GPU that loads this
 // library, for as long as the process lives.  All calls on one device share
-// it: two calls that overlap on the GPU (on different streams or handles
-// without synchronisation between them) race and corrupt each other's
-// results.  Each call clears the parts that must start at zero.
+// it and it keeps the last call's contents: two calls that overlap on the GPU
+// (on different streams or handles without synchronisation between them)
+// race and corrupt each other's results.  Each call clears the parts that
+// must start at zero.
 
 #include <algorithm>
 #include <mutex>
@@ -79,7 +80,10 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
     const uint32_t sb = ceil_log2_u64(s.n_stall);
     const uint32_t nb = ceil_log2_u64((uint64_t)B->n_nodes + 1);
     if (nb + sb > 32) return h->fail(HPA_E_INVALID_ARG, "(n_nodes + 1) * 2^stall_bits exceeds 2^32");
-    const uint32_t cap = (N / G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL;
+    if (h->opt.leaf_capacity && h->opt.leaf_capacity != LEAF_CAP_SMALL && h->opt.leaf_capacity != LEAF_CAP_LARGE)
+        return h->fail(HPA_E_INVALID_ARG, "leaf_capacity must be 0, %u or %u", LEAF_CAP_SMALL, LEAF_CAP_LARGE);
+    const uint32_t cap = h->opt.leaf_capacity ? h->opt.leaf_capacity
+                                              : ((N / G >= LEAF_CAP_SMALL / 2) ? LEAF_CAP_LARGE : LEAF_CAP_SMALL);
     const uint64_t L_max = G + 6 * (N / cap + 1) + 9;
 
     AggWork w{};
@@ -89,6 +93,9 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
     w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt; w.val64 = false;
     w.emit_totals = 1;
     w.timeout_iters = h->opt.timeout_iters;
+    w.sort_mode = std::min<uint32_t>(h->opt.leaf_ranking, 3);
+    w.leaf_hash = h->opt.leaf_hash;
+    w.small_leaves = h->opt.small_leaves == 2 || (h->opt.small_leaves == 0 && N < 64 * G);
     w.n_tiles = (N + TILE - 1) / TILE;
     BufDev* d_buf = nullptr;
     uint64_t* d_tile = nullptr;

@@ -46,7 +46,7 @@ class hpa_structure(C.Structure):
 class hpa_binary_info(C.Structure):
     _fields_ = [("n_nodes", C.c_uint32), ("n_funcs", C.c_uint32), ("n_calls", C.c_uint32),
                 ("n_cnodes", C.c_uint32), ("n_scc", C.c_uint32), ("cdag_levels", C.c_uint32),
-                ("n_ranges", C.c_uint64)]
+                ("n_ranges", C.c_uint64), ("max_depth", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class hpa_samples(C.Structure):
@@ -375,16 +375,10 @@ class Hpa:
         s, arrs = _structure(b)
         bid = C.c_uint32(0)
         self.check(self.L.hpa_load_structure(self.h, C.byref(s), C.byref(bid)))
-        # structure-tree depth bounds the inclusive expansion
-        par = arrs["node_parent"]
-        depth = np.zeros(par.shape[0], np.int64)
-        cur = np.arange(par.shape[0])
-        alive = par[cur] != HPA_NO_PARENT
-        while alive.any():
-            depth[alive] += 1
-            cur = np.where(alive, par[np.minimum(cur, par.shape[0] - 1)], cur)
-            alive = alive & (par[np.minimum(cur, par.shape[0] - 1)] != HPA_NO_PARENT)
-        self._depth[int(bid.value)] = int(depth.max()) if depth.size else 0
+        # the structure-tree depth (computed by the library at load) bounds the inclusive expansion
+        info = hpa_binary_info()
+        self.check(self.L.hpa_binary_info_get(self.h, bid, C.byref(info), None))
+        self._depth[int(bid.value)] = int(info.max_depth)
         return int(bid.value)
 
     def unload_structure(self, bid: int):

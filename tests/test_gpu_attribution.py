@@ -382,3 +382,66 @@ def test_unaligned_sample_arrays(H, plain, n_ctx, counts, off):
                       S.n_ctx, S.n_stall)
     out = run(H, bid, T)
     assert_same_keys(out, oracle.attribute_samples(B, T))
+
+
+def test_headline_regime_two_level_and_big_groups(H, large_bin):
+    """The regime of the large workload: the large binary, more contexts than
+    one partition pass takes (4,500: buckets of contexts, then each bucket by
+    context), about 10^4 records per context with uint32 counts (so leaves
+    hold up to 10,240 records and sort 26-bit keys) and 45 contexts three
+    times that size, split into fine bins after the second pass.  Every key
+    of a context depends only on that context's samples, so the oracle
+    recomputes a subset of contexts (the 45 big ones and 100 others) from
+    their samples alone and those keys must match bit for bit; the per-stall
+    totals are checked against direct sums of the counts, the UNKNOWN totals
+    against the UNKNOWN keys, and the whole key list for canonical order."""
+    B, bid = large_bin
+    n_ctx = 4500
+    wts = np.ones(n_ctx)
+    big = synth.np_below(41, 1, np.arange(45), n_ctx).astype(np.int64)
+    wts[big] = 3.0
+    n = int(10_000 * wts.sum())
+    S = synth.make_samples(41, B, n, n_ctx, 0.9, counts=True, device="cuda", ctx_weights=wts)
+    out = run(H, bid, S)
+    K = out.count()
+    kc, kn, ks, kv = out.numpy()
+    # canonical order, no zero sums, totals
+    key = (kc.astype(np.uint64) << np.uint64(37)) | (kn.astype(np.uint64) << np.uint64(5)) | ks.astype(np.uint64)
+    assert K > 0.5 * n and np.all(key[1:] > key[:-1]) and np.all(kv > 0)
+    cnt = S.count.cpu().numpy().astype(np.uint64)
+    st = S.stall.cpu().numpy()
+    total = np.bincount(st, weights=cnt.astype(np.float64), minlength=16).astype(np.uint64)
+    assert np.array_equal(out.total[:16].cpu().numpy().view(np.uint64), total)
+    assert int(kv.sum(dtype=np.uint64)) == int(cnt.sum(dtype=np.uint64))
+    unk = np.bincount(ks[kn == 0xFFFFFFFF], weights=kv[kn == 0xFFFFFFFF].astype(np.float64), minlength=16)
+    assert np.array_equal(out.unknown[:16].cpu().numpy().view(np.uint64), unk.astype(np.uint64))
+    # the oracle on a subset of contexts
+    rest = np.setdiff1d(np.arange(n_ctx), big)
+    pick = np.union1d(big, rest[synth.np_below(41, 2, np.arange(100), rest.shape[0]).astype(np.int64)])
+    cpu_ctx = S.ctx.cpu().numpy()
+    sel = np.isin(cpu_ctx, pick)
+    sub = synth.Samples(S.pc.cpu()[sel], S.ctx.cpu()[sel], S.stall.cpu()[sel], S.count.cpu()[sel], n_ctx, 16)
+    ref = oracle.attribute_samples(B, sub)
+    keep = np.isin(kc, pick)
+    assert int(keep.sum()) == len(ref)
+    for name, g, r in zip(("ctx", "node", "stall", "val"), (kc[keep], kn[keep], ks[keep], kv[keep]),
+                          (ref.ctx, ref.node, ref.stall, ref.val)):
+        assert np.array_equal(g, r), f"{name} differs from the oracle"
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs two visible GPUs")
+def test_two_devices_in_one_process(plain):
+    """Handles on two devices of one process: the raised shared-memory
+    limits of the aggregation kernels belong to each device, so the second
+    device must get them too (a 10,240-record leaf needs about 197 KB)."""
+    from paper_2109_06931_gb300 import hpa
+    B, _ = plain
+    for dev in (0, 1):
+        h = hpa.Hpa(dev, leaf_capacity=10240)
+        bid = h.load_structure(B)
+        S = synth.make_samples(13, B, 400_000, 20, 1.1, counts=True, device=f"cuda:{dev}")
+        out = h.attribute_samples(bid, S)
+        h.sync()
+        assert_same_keys(out, oracle.attribute_samples(B, S))
+        h.close()

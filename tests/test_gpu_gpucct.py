@@ -50,8 +50,14 @@ def _gold_binary(g):
         cs_node=np.array(cs["node"], np.uint32)), lo
 
 
-@pytest.mark.parametrize("name", ["gpucct_fig5.json", "gpucct_selfcall.json"])
+@pytest.mark.parametrize("name", ["gpucct_fig5.json", "gpucct_selfcall.json", "gpucct_diamond.json",
+                                  "gpucct_two_cycle.json", "gpucct_scc_two_callers.json"])
 def test_golden(H, name):
+    """Hand-computed fixtures: the step-2 fix-up on A->B and an SCC (the
+    worked example of Section 6.3), a self-call, a diamond with and without
+    sampled call sites at the join, two functions calling each other, and an
+    SCC entered from two callers with two stall reasons.  The GPU result is
+    compared with the hand-computed values and with the oracle."""
     g = json.load(open(os.path.join(GOLD, name)))
     B, lo = _gold_binary(g)
     bid = H.load_structure(B)
@@ -67,6 +73,16 @@ def test_golden(H, name):
     H.sync()
     ref = oracle.apportion(B, g["n_stall"], oracle.attribute_samples(B, S), np.array(g["req_ctx"], np.uint32))
     check(res, ref)
+    # the hand-computed values themselves (sparse rows per context in the fixture)
+    hand = types.SimpleNamespace(incl=np.zeros(ref.incl.shape), a=np.zeros(ref.a.shape),
+                                 flags=np.zeros(ref.flags.shape, ref.flags.dtype))
+    for q, c in enumerate(g["req_ctx"]):
+        for v, row in g["expected_incl"][str(c)].items():
+            hand.incl[q, int(v)] = row
+        for e, row in g["expected_a"][str(c)].items():
+            hand.a[q, int(e)] = row
+        hand.flags[q] = g["expected_flags"][str(c)]
+    check(res, hand)
 
 
 def test_plain_workload(H):

@@ -1,10 +1,11 @@
-"""hpa_attribute_samples_noalloc, the entry point for callers that cannot
-allocate device memory during the call (stream capture, runtimes that own the
-GPU's memory pool): on two calls in a row it must give exactly what
-hpa_attribute_samples gives (counts are exact, so the comparison is
-bit-exact), and it must refuse a call whose scratch exceeds its fixed array.
-This file is collected last so that a failure here leaves every other test
-already run."""
+"""hpa_attribute_samples_noalloc, the entry point for callers that must not
+allocate device memory while they analyse samples (a tool inside the
+application it measures, whose caching allocator owns the device memory; a
+serving loop where cudaFree would synchronise the whole GPU).  On two calls in
+a row it must give exactly what hpa_attribute_samples gives (counts are exact,
+so the comparison is bit-exact), and it must refuse a call whose scratch
+exceeds its fixed array.  This file is collected last so that a failure here
+leaves every other test already run."""
 import numpy as np
 import pytest
 
