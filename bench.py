@@ -183,6 +183,24 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     info, _ = h.binary_info(bid)
     out["apportion"] = {"ms": ms, "contexts": len(req), "cnodes": info.n_cnodes, "calls": info.n_calls,
                         "contexts_per_s": len(req) / (ms / 1e3)}
+    # every context's GPU calling context tree in one call (sparse rows)
+    res = h.apportion_all(bid, prof)
+    h.sync()
+    nrows, nedges = res["caps"]
+    ms = timed(stream, lambda: (h.apportion_all(bid, prof, out=res), h.sync()), reps=2)
+    M = prof.n_stall + 1
+    out_b = nrows * (4 + 4 * M) + nedges * (4 + 4 + 1)
+    in_b = 17 * K
+    peak, _ = peaks()
+    out["apportion_all"] = {"ms": ms, "contexts": w.n_ctx, "node_rows": nrows, "edge_rows": nedges,
+                            "contexts_per_s": w.n_ctx / (ms / 1e3), "bytes_per_launch": in_b + out_b,
+                            "roofline": {"bound": "hbm", "achieved": (in_b + out_b) / (ms / 1e3) / 1e9,
+                                         "peak": peak, "unit": "GB/s",
+                                         "frac": (in_b + out_b) / (ms / 1e3) / 1e9 / peak,
+                                         "bytes": "17 B per key read; per node row 4 B id + 4 B per stall column "
+                                                  "and total; per call-site row 4 B id, 4 B ratio, 1 B flags"}}
+    del res
+    torch.cuda.empty_cache()
     par = torch.from_numpy(w.cct().view(np.int32)).to(dev)
     torch.cuda.synchronize()  # inputs are made on torch's stream, the handle runs on its own
     ms = timed(stream, lambda: (h.propagate_inclusive(bid, prof, tree=False, cct_parent=par), h.sync()))
@@ -697,6 +715,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip hpa_tune (use the per-call default configuration)")
     ap.add_argument("--small-leaves", type=int, default=0, help="0 automatic, 1 never, 2 always")
     ap.add_argument("--leaf-hash", type=int, default=0, help="0 sort, 1 hash (with --no-tune)")
+    ap.add_argument("--leaf-emit", type=int, default=0,
+                    help="0 leaves write their keys when their offset is ready, 1 a separate pass always")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the apportion / inclusive / derive rows")
@@ -738,7 +758,8 @@ def main():
     N = S.n
     stream = torch.cuda.Stream(dev)
     h = H.Hpa(local, stream=stream, cursor_shift=args.cursor_shift, sort_mode=args.sort_mode,
-              partition=not args.no_part, small_leaves=args.small_leaves, leaf_hash=args.leaf_hash)
+              partition=not args.no_part, small_leaves=args.small_leaves, leaf_hash=args.leaf_hash,
+              leaf_emit=args.leaf_emit)
     bid = h.load_structure(B)
     out = H.new_profile(N, S.n_stall, dev)
     h.reserve(N, S.n_ctx)
@@ -786,8 +807,10 @@ def main():
     in_b = 17 if has_cnt else 13
     rec_b = 8 if has_cnt else 4
     # algorithmic bytes per launch of each phase (per-unit figures x units)
+    # (the leaves write the final 17-byte keys themselves; "emit" is then the
+    # scan of the leaves' key counts and the per-buffer key count)
     algo = {"hist+plan": 4 * N, "attribute+scatter": (in_b + rec_b) * N, "big-split": 0,
-            "leaf sort/reduce": rec_b * N + 12 * K, "emit": 12 * K + 17 * K}
+            "leaf sort/reduce": rec_b * N + 17 * K, "emit": 0}
     dom = max(ph, key=ph.get)
     peak, peak_kind = peaks()
     ach = algo[dom] / (ph[dom] / 1e3) / 1e9 if ph[dom] > 0 else 0.0

@@ -81,6 +81,10 @@ typedef struct {
                                1 = shared-memory hash table first, then a sort of the
                                distinct keys (falls back to the sort for a leaf with too
                                many distinct keys); pays off when samples repeat keys     */
+    uint32_t leaf_emit;     /* placement of the output keys: 0 = a leaf writes its keys
+                               itself when the keys of the leaves before it are counted
+                               (else a separate pass places them), 1 = always a
+                               separate pass after the leaves                            */
 } hpa_options;
 
 /* Program structure of one GPU binary (Section 5).  HOST arrays, copied into
@@ -179,6 +183,41 @@ typedef struct {
     uint8_t* flags;
 } hpa_gpucct;
 
+/* GPU calling context trees of EVERY launch context of a profile (Section
+ * 6.3, steps 1-4) as sparse rows: in each context only the condensed nodes
+ * with a nonzero inclusive cost and the call sites with a nonzero share --
+ * the part of the call graph above the context's sampled functions.  DEVICE
+ * arrays, rows of context c at [node_off[c], node_off[c+1]) and
+ * [edge_off[c], edge_off[c+1]), contexts in order:
+ *   node_off[n_ctx + 1], edge_off[n_ctx + 1]  (may be NULL)
+ *   node_id[cap_nodes]              condensed node, ascending within a context
+ *   incl[cap_nodes][n_stall + 1]    its inclusive cost (last column: total)
+ *   edge_id[cap_edges]              call site, ascending within a context
+ *   ratio[cap_edges]                r(e) = w(e) / W(callee's condensed node);
+ *                                   the share is a(e) = r(e) * incl(that node)
+ *   a[cap_edges][n_stall + 1]       that share, or NULL: not written
+ *   flags[cap_edges]                HPA_EDGE_FIXUP / HPA_EDGE_FIXUP2 bits
+ *   counts[2]                       device uint64: rows written (nodes, call
+ *                                   sites), or -- with HPA_E_CAPACITY from
+ *                                   hpa_sync -- the rows needed
+ * Entries without a row are exactly zero; a call site without a row has no
+ * flags, apart from HPA_EDGE_INTRA_SCC (and HPA_EDGE_FIXUP) on the call sites
+ * inside a recursive SCC, which never get rows.  Capacities both 0 ask for
+ * the row counts only (no error; the costs are not computed then).          */
+typedef struct {
+    uint64_t cap_nodes;
+    uint64_t cap_edges;
+    uint64_t* node_off;
+    uint32_t* node_id;
+    float* incl;
+    uint64_t* edge_off;
+    uint32_t* edge_id;
+    float* ratio;
+    float* a;
+    uint8_t* flags;
+    uint64_t* counts;
+} hpa_gpucct_all;
+
 /* One context's GPU calling context tree materialised as a tree (Section
  * 6.3, step 4: apportioning the condensed call graph equals splitting it
  * into a tree whose call paths carry the product of the call-site ratios).
@@ -232,6 +271,25 @@ typedef struct {
     float* W;                /* [n_ctx] */
     float* frac;             /* [n_ctx][n_stall] */
 } hpa_derived;
+
+/* Warp issue rate and stall shares per (launch context, function) (Section
+ * 7: W = (S - S_stall) / S, read per kernel and per function).  DEVICE
+ * arrays of `capacity` rows, ascending by (ctx, func), one row per pair
+ * with samples (UNKNOWN samples belong to no function and are left out):
+ * S = samples of the function in the context, S_issued = those whose stall
+ * reason is in the handle's issued_mask, W = S_issued / S, frac[row][r] =
+ * share of S in stall reason r (may be NULL).  *n_rows (device uint64): rows
+ * written, or -- with HPA_E_CAPACITY from hpa_sync -- the rows needed.       */
+typedef struct {
+    uint64_t capacity;
+    uint32_t* ctx;
+    uint32_t* func;
+    uint64_t* S;
+    uint64_t* S_issued;
+    float* W;
+    float* frac;          /* [capacity][n_stall] */
+    uint64_t* n_rows;
+} hpa_issue_rows;
 
 /* ---- handle ------------------------------------------------------------- */
 
@@ -367,6 +425,21 @@ hpa_status hpa_tune(hpa_handle* h, uint32_t binary_id, const hpa_samples* in, hp
  * from FP64 accumulation of exact integer counts.                            */
 hpa_status hpa_apportion_callgraph(hpa_handle* h, uint32_t binary_id, const hpa_profile* p,
                                    hpa_gpucct* out);
+
+/* The same reconstruction (Section 6.3, steps 1-4) for every launch context
+ * 0..p->n_ctx-1 of the profile in one call, as sparse rows (hpa_gpucct_all).
+ * Inclusive costs are summed in double-float arithmetic from exact integer
+ * counts and rounded once to FP32 per stored value.  Errors at hpa_sync:
+ * HPA_E_CAPACITY (counts holds the rows needed; rows of the contexts that
+ * fit may be written), HPA_E_INVALID_ARG (a key outside the binary).        */
+hpa_status hpa_apportion_all(hpa_handle* h, uint32_t binary_id, const hpa_profile* p, hpa_gpucct_all* out);
+
+/* Warp issue rate and stall shares per (launch context, function) of a
+ * profile of this binary (Section 7; see hpa_issue_rows).  The keys are
+ * regrouped by (context, function, stall) with exact 64-bit sums; each row's
+ * W and shares are rounded once to FP32.  A key outside the binary (node or
+ * stall) fails the call at hpa_sync with HPA_E_INVALID_SAMPLE.               */
+hpa_status hpa_issue_by_function(hpa_handle* h, uint32_t binary_id, const hpa_profile* p, hpa_issue_rows* out);
 
 /* Inclusive metrics (Section 6.1, statistic generation).
  *  tree_out (may be NULL): for every key of p, its value is added to its node

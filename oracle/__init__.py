@@ -78,6 +78,12 @@ def load(path: str):
     L.orc_inclusive_cct.argtypes = [u32, vp, u32, u64, vp, vp, vp, vp]
     L.orc_derive.restype = vp
     L.orc_derive.argtypes = [u32, vp, vp, vp, vp, vp, u32, u32, u32]
+    L.orc_issue_by_function.restype = vp
+    L.orc_issue_by_function.argtypes = [u32, vp, u32, u32, u64, vp, vp, vp, vp]
+    L.orc_issue_status.restype = i32; L.orc_issue_status.argtypes = [vp]
+    L.orc_issue_size.restype = u64; L.orc_issue_size.argtypes = [vp]
+    L.orc_issue_fetch.argtypes = [vp] * 7
+    L.orc_issue_free.argtypes = [vp]
     L.orc_apportion.restype = vp
     L.orc_apportion.argtypes = [u32, vp, u32, u32, vp, vp, vp, u32, u64, vp, vp, vp, vp, u32, vp]
     for name in ("orc_status", "orc_apportion_status"):
@@ -212,6 +218,32 @@ def derive(profiles, n_ctx: int, n_stall: int, issued_mask: int = 1) -> Derived:
     L.orc_derive_free(h)
     del ks
     return d
+
+
+@dataclass
+class IssueRows:
+    ctx: np.ndarray        # uint32[n]
+    func: np.ndarray       # uint32[n]
+    S: np.ndarray          # uint64[n]
+    S_issued: np.ndarray   # uint64[n]
+    W: np.ndarray          # float64[n]
+    frac: np.ndarray       # float64[n, n_stall]
+    status: int = 0
+
+
+def issue_by_function(node_func, n_stall: int, keys: KeyList, issued_mask: int = 1) -> IssueRows:
+    """Warp issue rate and stall shares per (context, function) (Section 7)."""
+    L = lib()
+    nf = _c(node_func, np.uint32)
+    k = [_c(keys.ctx, np.uint32), _c(keys.node, np.uint32), _c(keys.stall, np.uint8), _c(keys.val, np.uint64)]
+    h = L.orc_issue_by_function(nf.shape[0], _p(nf), n_stall, issued_mask, k[0].shape[0], *[_p(x) for x in k])
+    st = L.orc_issue_status(h)
+    n = L.orc_issue_size(h)
+    r = IssueRows(np.empty(n, np.uint32), np.empty(n, np.uint32), np.empty(n, np.uint64), np.empty(n, np.uint64),
+                  np.empty(n, np.float64), np.empty((n, n_stall), np.float64), st)
+    L.orc_issue_fetch(h, _p(r.ctx), _p(r.func), _p(r.S), _p(r.S_issued), _p(r.W), _p(r.frac))
+    L.orc_issue_free(h)
+    return r
 
 
 @dataclass

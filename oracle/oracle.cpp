@@ -16,7 +16,8 @@
 //                 context tree (inclusive metrics).
 //   Section 6.3   GPU calling context tree, steps 1-4 (call-graph weights,
 //                 zero-weight fix-up, SCC collapse, gprof-style splitting).
-//   Section 7     warp issue rate W = (S - S_stall) / S.
+//   Section 7     warp issue rate W = (S - S_stall) / S, per context and per
+//                 (context, function).
 // Readings of points the paper leaves open are stated where they are used.
 //
 // Floating point is double precision throughout; counts are exact uint64.
@@ -250,6 +251,49 @@ void* orc_derive(uint32_t P, const uint64_t* nkeys, const uint32_t* const* kctx,
             d->frac[(size_t)c * n_stall + r] = (double)per[(size_t)c * n_stall + r] / (double)d->S[c];
     }
     return d;
+}
+
+// O5 per function: warp issue rate and stall shares per (launch context,
+// function) (Section 7 reads W per kernel and per function).  A key counts
+// toward (its context, the function of its node); UNKNOWN keys belong to no
+// function and are left out.  S = all counts of the pair, S_issued = those
+// whose stall reason is in issued_mask, W = S_issued / S, frac[r] = the share
+// of S in stall reason r.  One row per pair with S > 0, ascending by
+// (context, function).
+struct IssueRows {
+    std::vector<uint32_t> ctx, func;
+    std::vector<uint64_t> S, S_issued;
+    std::vector<double> W, frac;
+    int status = OK;
+};
+
+void* orc_issue_by_function(uint32_t n_nodes, const uint32_t* node_func, uint32_t n_stall, uint32_t issued_mask,
+                            uint64_t k, const uint32_t* kctx, const uint32_t* knode, const uint8_t* kstall,
+                            const uint64_t* kval) {
+    IssueRows* o = new IssueRows();
+    std::map<std::pair<uint32_t, uint32_t>, std::vector<uint64_t>> per;   // (ctx, func) -> count per stall
+    for (uint64_t i = 0; i < k; ++i) {
+        if (knode[i] == UNKNOWN) continue;
+        if (knode[i] >= n_nodes || kstall[i] >= n_stall) { o->status = INVALID_ARG; return o; }
+        std::vector<uint64_t>& v = per[std::make_pair(kctx[i], node_func[knode[i]])];
+        if (v.empty()) v.assign(n_stall, 0);
+        v[kstall[i]] += kval[i];
+    }
+    for (auto& kv : per) {
+        uint64_t S = 0, issued = 0;
+        for (uint32_t r = 0; r < n_stall; ++r) {
+            S += kv.second[r];
+            if (r < 32 && ((issued_mask >> r) & 1u)) issued += kv.second[r];
+        }
+        if (S == 0) continue;
+        o->ctx.push_back(kv.first.first);
+        o->func.push_back(kv.first.second);
+        o->S.push_back(S);
+        o->S_issued.push_back(issued);
+        o->W.push_back((double)issued / (double)S);
+        for (uint32_t r = 0; r < n_stall; ++r) o->frac.push_back((double)kv.second[r] / (double)S);
+    }
+    return o;
 }
 
 // ---------------------------------------------------------------------------
@@ -752,6 +796,20 @@ void orc_derive_fetch(void* p, uint32_t* ctx, uint32_t* node, uint8_t* stall, ui
     for (size_t i = 0; i < d->frac.size(); ++i) frac[i] = d->frac[i];
 }
 void orc_derive_free(void* p) { delete (Derived*)p; }
+
+int orc_issue_status(void* p) { return ((IssueRows*)p)->status; }
+uint64_t orc_issue_size(void* p) { return ((IssueRows*)p)->S.size(); }
+void orc_issue_fetch(void* p, uint32_t* ctx, uint32_t* func, uint64_t* S, uint64_t* S_issued, double* W,
+                     double* frac) {
+    IssueRows* o = (IssueRows*)p;
+    std::copy(o->ctx.begin(), o->ctx.end(), ctx);
+    std::copy(o->func.begin(), o->func.end(), func);
+    std::copy(o->S.begin(), o->S.end(), S);
+    std::copy(o->S_issued.begin(), o->S_issued.end(), S_issued);
+    std::copy(o->W.begin(), o->W.end(), W);
+    std::copy(o->frac.begin(), o->frac.end(), frac);
+}
+void orc_issue_free(void* p) { delete (IssueRows*)p; }
 
 int orc_apportion_status(void* p) { return ((GpuCct*)p)->status; }
 uint32_t orc_apportion_V(void* p) { return ((GpuCct*)p)->V; }

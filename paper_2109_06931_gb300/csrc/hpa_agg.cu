@@ -252,9 +252,11 @@ __global__ void k_leaves(AggWork w) {
 
 // ------------------------------------------------------------------ K9a: attribute
 // U samples per thread: the structure node of each PC (Section 4.2) through
-// the direct-answer directory, with a short forward walk over the sorted
-// ranges where a directory bucket straddles several ranges.  Only these
-// loads are dependent, so U lookups per thread stay in flight.
+// the direct-answer directory, with a short forward walk over the table
+// entries where a directory bucket straddles several of them (the entry
+// holding the bucket start and the next one are loaded together; the last
+// entry, at the span, ends every walk).  Only these loads are dependent, so
+// U lookups per thread stay in flight.
 template <int U>
 __device__ __forceinline__ void lookup_nodes(const DevBinary& bin, const uint64_t (&pc)[U], const bool (&ok)[U],
                                              uint32_t (&nd)[U], uint64_t keep) {
@@ -274,10 +276,14 @@ __device__ __forceinline__ void lookup_nodes(const DevBinary& bin, const uint64_
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (nd[u] & DIR_SEARCH) {
-            uint32_t i = nd[u] & ~DIR_SEARCH;
-            uint4 r = ld_keep4(&bin.rng[i], keep);
-            while (r.y <= off[u] && i + 1 < bin.n_ranges) r = ld_keep4(&bin.rng[++i], keep);
-            nd[u] = (r.x <= off[u] && off[u] < r.y) ? r.z : bin.n_nodes;
+            uint32_t j = nd[u] & ~DIR_SEARCH;
+            uint2 cur = ld_keep2(&bin.ent[j], keep), nx = ld_keep2(&bin.ent[j + 1], keep);
+            while (nx.x <= off[u]) {
+                cur = nx;
+                ++j;
+                nx = ld_keep2(&bin.ent[j + 1], keep);
+            }
+            nd[u] = cur.y;
         }
     }
 }
@@ -547,7 +553,10 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
                 if (ok[u]) rk[u] = atomicAdd(&th[cx[u] >> shift], 1u);
             __syncthreads();
             if (threadIdx.x == 0 && staged(t0 + PART_TILE)) issue(t0 + PART_TILE);
-            const uint32_t tot = block_scan_array<uint32_t, PSC_THREADS, PSC_SCAN_EPT>(th, (int)nbin, sw);
+            // one counter per thread when the bins fit (the two-level path's buckets)
+            const uint32_t tot = nbin <= (uint32_t)PSC_THREADS
+                                     ? block_scan_array<uint32_t, PSC_THREADS, 1>(th, (int)nbin, sw)
+                                     : block_scan_array<uint32_t, PSC_THREADS, PSC_SCAN_EPT>(th, (int)nbin, sw);
             if (threadIdx.x == 0) th[nbin] = tot;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -809,7 +818,8 @@ __global__ void __launch_bounds__(BIG_THREADS, 2) k_big_partition(AggWork w) {
 
 // ------------------------------------------------------------------ K13: emit
 // Leaves are in key order, so leaf_out (the scanned run counts) places every
-// key.  With emit_totals, the per-stall totals and UNKNOWN totals of each
+// key (of every leaf, or with fused leaves of those that left their keys in
+// tmp_key / tmp_val).  With emit_totals, the per-stall totals and UNKNOWN totals of each
 // buffer are summed here over its keys (every valid record lies in exactly
 // one key): per-thread slots in shared memory, flushed when the CTA moves to
 // another buffer.
@@ -850,6 +860,7 @@ __global__ void __launch_bounds__(256) k_emit(AggWork w) {
     for (uint32_t l = blockIdx.x; l < n_leaves; l += gridDim.x) {
         const uint32_t d = leaf_out[l + 1] - leaf_out[l];
         if (d == 0) continue;                             // uniform across the block
+        if (w.fuse_emit && (w.leaf_look[l] & LOOK_DIRECT)) continue;   // the leaf wrote its keys itself
         const uint32_t info = w.leaf_info[l];
         const uint32_t b = info >> 8;
         const BufDev& B = w.bufs[b];
@@ -956,17 +967,28 @@ void launch_big_partition(const AggWork& w, cudaStream_t s, int sms, uint64_t* l
     *launches += 1;
 }
 
-static void run_finish(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
+// Leaves write the final keys themselves (fused) when one leaf kernel takes
+// every leaf of the call and the records carry 32-bit counts or none;
+// otherwise they leave their keys in tmp_key / tmp_val for k_emit.
+static bool can_fuse(const AggWork& w) {
+    return w.leaf_look && w.leaf_ticket && !w.val64 && !w.small_leaves && !w.emit_separate;
+}
+
+static void run_finish(const AggWork& w_in, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
+    AggWork w = w_in;
+    w.fuse_emit = can_fuse(w) ? 1u : 0u;
     launch_big_partition(w, s, sms, launches);
     if (ev) cudaEventRecord(ev[3], s);
     launch_leaves(w, s, sms, launches);
     if (ev) cudaEventRecord(ev[4], s);
     scan_u32(w.leaf_d, w.leaf_d, w.L_max, w.scan_tmp, s, launches);
+    // keys left in tmp_key / tmp_val (every leaf, or the fused leaves that
+    // did not wait for their offset) are placed by k_emit
     const size_t emit_smem = w.emit_totals ? ((size_t)256 << w.sb) * 8 : 0;
     set_smem_limit((const void*)k_emit, 256 * HPA_MAX_STALL_DEV * 8);
     k_emit<<<sms * 8, 256, emit_smem, s>>>(w);
-    launch_finalize(w, s, launches);
     *launches += 1;
+    launch_finalize(w, s, launches);
     if (ev) cudaEventRecord(ev[5], s);
 }
 
@@ -974,6 +996,8 @@ void clear_work(const AggWork& w, cudaStream_t s) {
     cudaMemsetAsync(w.grp_hist, 0, sizeof(uint32_t) * ((size_t)w.G + 1), s);
     cudaMemsetAsync(w.leaf_d, 0, sizeof(uint32_t) * ((size_t)w.L_max + 1), s);
     cudaMemsetAsync(w.buf_bad, 0, sizeof(unsigned long long) * w.n_buf, s);
+    if (w.leaf_look) cudaMemsetAsync(w.leaf_look, 0, sizeof(unsigned long long) * w.L_max, s);
+    if (w.leaf_ticket) cudaMemsetAsync(w.leaf_ticket, 0, sizeof(uint32_t), s);
 }
 
 void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
@@ -1077,6 +1101,10 @@ __global__ void k_expand_scatter(AggWork w, ExpandSrc x) {
             n = x.parent[n];
         }
     }
+}
+
+void run_group_tail(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches) {
+    run_finish(w, s, sms, launches, nullptr);
 }
 
 void run_expand_aggregate(const AggWork& w, const ExpandSrc& x, cudaStream_t s, int sms, uint64_t* launches) {

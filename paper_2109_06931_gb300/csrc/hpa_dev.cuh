@@ -23,39 +23,30 @@ __device__ __forceinline__ void raise_status(DevStatus* st, int32_t code, int32_
 }
 
 // Program structure of one binary as the attribution kernels read it.
-//   rng[i] = {lo - pc_base, hi - pc_base, node, 0}, sorted, disjoint.
-//   dir[b], for the bucket [b << dshift, (b + 1) << dshift) of offsets:
-//     the node of the one range that covers the whole bucket, or n_nodes
-//     when no range touches it (UNKNOWN), or DIR_SEARCH | i with i the first
-//     range whose hi lies beyond the bucket start.
-// A PC p belongs to range i iff lo_i <= p < hi_i (half-open); ranges are
-// disjoint, so the only candidate is the first range with hi > p.
+//   ent[j] = {lo_j, node_j} (offsets from pc_base): entry j covers
+//     [lo_j, lo_{j+1}); the ranges in order, a gap between two ranges as an
+//     entry of node n_nodes (UNKNOWN), and a last entry at `span` that only
+//     ends the one before it.  8 bytes per entry, so that the table stays in L2.
+//   dir[b], for the bucket [b << dshift, (b + 1) << dshift) of offsets: the
+//     node of the one entry that covers the whole bucket, or DIR_SEARCH | j
+//     with j the entry that holds the bucket's start.
+// A PC p belongs to range i iff lo_i <= p < hi_i (half-open); the entries
+// tile [0, span), so p lies in exactly one of them.
 constexpr uint32_t DIR_SEARCH = 0x80000000u;
-constexpr uint64_t DIR_MAX_ENTRIES = 16ull << 20;   // 64 MB directory at most
+constexpr uint64_t DIR_MAX_ENTRIES = 8ull << 20;    // 32 MB directory at most
+constexpr uint64_t DIR_PER_ENTRY = 4;               // directory buckets per table entry, at most
+constexpr uint64_t DIR_MIN_ENTRIES = 1ull << 20;    // small binaries still get 2^20 buckets
 
 struct DevBinary {
     uint64_t pc_base;
     uint64_t span;          // range_hi[R-1] - pc_base (< 2^32)
     uint32_t dshift;
     uint32_t n_dir;
-    uint32_t n_ranges;
+    uint32_t n_ent;         // table entries, the last one at span
     uint32_t n_nodes;       // M: UNKNOWN is coded as node M inside subkeys
     const uint32_t* dir;
-    const uint4* rng;
+    const uint2* ent;
 };
-
-// Section 4.2 / Section 5: the structure node of one PC (M if none).
-__device__ __forceinline__ uint32_t attribute_pc(const DevBinary& b, uint64_t pc) {
-    const uint64_t off64 = pc - b.pc_base;    // wraps to a huge value below the segment
-    if (off64 >= b.span) return b.n_nodes;
-    const uint32_t off = (uint32_t)off64;
-    const uint32_t e = __ldg(&b.dir[off >> b.dshift]);
-    if (!(e & DIR_SEARCH)) return e;
-    uint32_t i = e & ~DIR_SEARCH;
-    uint4 r = __ldg(&b.rng[i]);
-    while (r.y <= off && i + 1 < b.n_ranges) r = __ldg(&b.rng[++i]);
-    return (r.x <= off && off < r.y) ? r.z : b.n_nodes;
-}
 
 // asynchronous global -> shared copies (cp.async, sm_80+)
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -87,16 +78,25 @@ __device__ __forceinline__ uint32_t ld_keep(const uint32_t* a, uint64_t pol) {
     asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
     return v;
 }
-__device__ __forceinline__ uint4 ld_keep4(const uint4* a, uint64_t pol) {
-    uint4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(pol));
+__device__ __forceinline__ uint2 ld_keep2(const uint2* a, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(a), "l"(pol));
     return v;
 }
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T* a) { return __ldcs(a); }
 __device__ __forceinline__ void st_stream(uint2* a, uint2 v) { __stcs(a, v); }
 __device__ __forceinline__ void st_stream(uint32_t* a, uint32_t v) { __stcs(a, v); }
+
+// release / acquire accesses at GPU scope (look-back words between CTAs)
+__device__ __forceinline__ void st_release_u64(unsigned long long* a, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* a) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -165,6 +165,43 @@ __device__ __forceinline__ T block_scan_array(T* a, int n, T* sw) {
     }
     __syncthreads();
     return tot;
+}
+
+__host__ __device__ inline uint32_t ceil_log2_u64(uint64_t x) {
+    uint32_t b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+// Exclusive scan, in place, of n counters in shared memory, walked by each
+// warp over a contiguous chunk 32 entries per row (lane l reads entry
+// row * 32 + l: no bank conflicts), then offset by the warps before it.
+// `sw` holds >= 33 words.  Every thread of the block must call it.
+template <int THREADS>
+__device__ __forceinline__ void block_scan_rows(uint32_t* a, int n, uint32_t* sw) {
+    constexpr int W = THREADS / 32;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int per = max(32, ((n + W - 1) / W + 31) & ~31);
+    const int a0 = min(n, warp * per), a1 = min(n, a0 + per);
+    uint32_t carry = 0;
+    for (int base = a0; base < a1; base += 32) {
+        const int i = base + lane;
+        const uint32_t v = i < a1 ? a[i] : 0u;
+        const uint32_t inc = warp_inclusive_scan(v);
+        if (i < a1) a[i] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) sw[warp] = carry;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < W ? sw[lane] : 0u;
+        const uint32_t inc = warp_inclusive_scan(v);
+        if (lane < W) sw[lane] = inc - v;
+    }
+    __syncthreads();
+    const uint32_t off = sw[warp];
+    for (int i = a0 + lane; i < a1; i += 32) a[i] += off;
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -258,23 +295,32 @@ struct BlockRadix {
     }
 };
 
-// Block-wide stable LSD radix sort of packed elements: E = uint64_t holds
+// Block-wide LSD radix sort of packed elements: E = uint64_t holds
 // (value << 32 | key) -- the memory image of a {key, value} record, so records
-// are copied into shared memory verbatim -- and E = uint32_t a key alone.  Digits are at most 9 bits
-// (a 26-bit key takes 3 passes); passes and digit width follow the key width.
-// Counter rows are padded by one word so the digit-major scan is free of bank
-// conflicts.  Stable ranking as in BlockRadix (warp-contiguous chunks, equal
-// digits of a 32-element row found by __match_any_sync or by ballots).
+// are copied into shared memory verbatim -- and E = uint32_t a key alone.
+// Elements with equal keys may come out in any order (every caller sums or
+// merges them), so the first pass, over the lowest digit, need not be
+// stable: it is a counting sort with block-wide counters and shared-memory
+// atomics over up to U1 bits (13 with 16 warps).  The remaining bits are
+// sorted by stable passes of at most 9-bit digits: each warp owns a
+// contiguous chunk and walks it 32 elements at a time in order; lanes with
+// equal digits are found by __match_any_sync or by ballots, counted in the
+// warp's own counter row (rows padded by one word so the digit-major scan is
+// free of bank conflicts).  A 26-bit key takes one 13-bit counting pass and
+// two stable passes of 7 and 6 bits.
 template <int THREADS, int CAP, typename E>
 struct PackedRadix {
     static constexpr int W = THREADS / 32;
     static constexpr int MAXB = 9, MAXBINS = 1 << MAXB, ROW = MAXBINS + 1;
     static constexpr int MAX_EPT = (MAXBINS * W + THREADS - 1) / THREADS;
     static constexpr int RPT = (CAP + THREADS - 1) / THREADS;   // 32-element rows per warp at most
+    static constexpr int CNT_WORDS = W * ROW;
+    // widest first-pass digit whose block-wide counters fit the counter rows
+    static constexpr int U1 = CNT_WORDS >= 8192 ? 13 : (CNT_WORDS >= 4096 ? 12 : (CNT_WORDS >= 2048 ? 11 : 10));
 
     struct Smem {
         E el[2][CAP];
-        uint32_t cnt[W * ROW];
+        uint32_t cnt[CNT_WORDS];
         uint32_t sw[33];
     };
 
@@ -297,19 +343,45 @@ struct PackedRadix {
         return m;
     }
 
-    // Ranking within a 32-element row: lanes with equal digits are found
-    // with __match_any_sync (executed on the ADU), or with one ballot per
-    // digit bit (ALU).  match: 0 = by digit width, 1 = __match_any_sync,
-    // 2 = ballots, 3 = the two alternately by row, so that the ADU and ALU
-    // pipes share the work.  Measured on GB300 for 9-bit digits (26-bit
-    // keys): alternating 9 % faster than ballots, ballots 2 % faster than
-    // __match_any_sync; for narrower digits __match_any_sync is fastest.
+    // First pass: counting sort of el[0][0..n) by the low b1 bits into
+    // el[1] (block-wide counters, atomics; the order of equal digits is free).
+    __device__ static void counting_pass(Smem& s, int n, int b1) {
+        const int nb = 1 << b1;
+        const uint32_t m1 = (uint32_t)nb - 1u;
+        uint32_t* c = s.cnt;
+        for (int i = threadIdx.x; i < nb; i += THREADS) c[i] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += THREADS) atomicAdd(&c[key_of(s.el[0][i]) & m1], 1u);
+        __syncthreads();
+        block_scan_rows<THREADS>(c, nb, s.sw);
+        for (int i = threadIdx.x; i < n; i += THREADS) {
+            const E e = s.el[0][i];
+            const uint32_t p = atomicAdd(&c[key_of(e) & m1], 1u);
+            s.el[1][p] = e;
+        }
+        __syncthreads();
+    }
+
+    // Ranking within a 32-element row of a stable pass: lanes with equal
+    // digits are found with __match_any_sync (executed on the ADU), or with
+    // one ballot per digit bit (ALU).  match: 0 = by digit width (alternating
+    // for 9-bit digits, __match_any_sync for narrower ones), 1 =
+    // __match_any_sync, 2 = ballots, 3 = the two alternately by row, so that
+    // the ADU and ALU pipes share the work.
+    // Sorts s.el[0][0..n) by the low `bits` bits of the key; returns the
+    // buffer index (0 or 1) that holds the result.
     __device__ static int sort(Smem& s, int n, int bits, int match = 0) {
-        if (bits <= 0) return 0;
+        if (bits <= 0 || n <= 1) return 0;
         const int warp = threadIdx.x >> 5;
         const int lane = lane_id();
-        const int passes = (bits + MAXB - 1) / MAXB;
-        const int rb = (bits + passes - 1) / passes;
+        // first pass: wide enough for the leaf's size, at most U1 bits
+        const int b1 = min(bits, min(U1, max(8, (int)ceil_log2_u64((uint64_t)n) + 1)));
+        counting_pass(s, n, b1);
+        int cur = 1;
+        const int rem = bits - b1;
+        if (rem <= 0) return cur;
+        const int passes = (rem + MAXB - 1) / MAXB;
+        const int rb = (rem + passes - 1) / passes;
         const int bins = 1 << rb;
         const int total = bins * W;
         const int ept = (total + THREADS - 1) / THREADS;
@@ -318,10 +390,9 @@ struct PackedRadix {
         const int hi = min(n, lo + chunk);
         const bool ballots = match == 2;
         const bool alternate = match == 3 || (match == 0 && rb >= MAXB);
-        int cur = 0;
-        for (int shift = 0; shift < bits; shift += rb) {
+        for (int shift = b1; shift < bits; shift += rb) {
             const uint32_t dmask = (1u << min(rb, bits - shift)) - 1;
-            for (int i = threadIdx.x; i < W * ROW; i += THREADS) s.cnt[i] = 0;
+            for (int i = threadIdx.x; i < total; i += THREADS) s.cnt[(i >> rb) * ROW + (i & (bins - 1))] = 0;
             __syncthreads();
             uint32_t* row = s.cnt + warp * ROW;
             // pass A: each element's rank among the equal digits before it in
@@ -390,11 +461,5 @@ struct PackedRadix {
         return cur;
     }
 };
-
-__host__ __device__ inline uint32_t ceil_log2_u64(uint64_t x) {
-    uint32_t b = 0;
-    while ((1ull << b) < x) ++b;
-    return b;
-}
 
 }  // namespace hpa

@@ -126,7 +126,7 @@ Binary* hpa_handle::binary(uint32_t id) {
 extern "C" hpa_status hpa_create(hpa_handle** out, int device, void* cuda_stream, const hpa_options* opt) {
     if (!out) return HPA_E_INVALID_ARG;
     *out = nullptr;
-    if (opt && (opt->leaf_hash > 1 || opt->small_leaves > 2 || opt->leaf_ranking > 3 || opt->grouping > 1 ||
+    if (opt && (opt->leaf_hash > 1 || opt->leaf_emit > 1 || opt->small_leaves > 2 || opt->leaf_ranking > 3 || opt->grouping > 1 ||
                 opt->cursor_pad > 7 ||
                 (opt->leaf_capacity && opt->leaf_capacity != LEAF_CAP_SMALL && opt->leaf_capacity != LEAF_CAP_LARGE)))
         return HPA_E_INVALID_ARG;
@@ -176,6 +176,7 @@ hpa_handle::~hpa_handle() {
     if (host_io) cudaFree(host_io);
     if (pinned_io) cudaFreeHost(pinned_io);
     if (cct_scratch) cudaFree(cct_scratch);
+    if (aux_scratch) cudaFree(aux_scratch);
 }
 
 extern "C" hpa_status hpa_destroy(hpa_handle* h) {
@@ -426,40 +427,48 @@ static hpa_status load_binary(hpa_handle* h, const hpa_structure* s, Binary* B) 
     if (vst) return h->fail(vst, "%s", msg);
     const uint64_t base = s->range_lo[0];
     const uint64_t span = s->range_hi[R - 1] - base;
+    if (M >= DIR_SEARCH) return h->fail(HPA_E_INVALID_TABLE, "n_nodes must be < 2^31");
     B->n_nodes = M; B->n_funcs = F; B->n_calls = E; B->n_ranges = R; B->max_depth = max_depth;
-    // attribution tables: ranges as offsets from the segment base, and a
-    // bucket directory (at most DIR_MAX_ENTRIES buckets of 2^dshift bytes).
-    // An entry answers directly when its bucket lies inside one range (the
-    // range's node) or touches no range (n_nodes, i.e. UNKNOWN); otherwise it
-    // holds DIR_SEARCH | first range whose hi lies beyond the bucket start.
+    // attribution tables: the ranges as entries {lo, node} of offsets from the
+    // segment base with each gap between two ranges as an entry of node M
+    // (UNKNOWN) and a last entry at the span; and a bucket directory of at
+    // most DIR_PER_ENTRY buckets per entry (at least DIR_MIN_ENTRIES, at most
+    // DIR_MAX_ENTRIES) of 2^dshift bytes each.  A directory entry answers
+    // directly when its bucket lies inside one table entry (that entry's
+    // node), otherwise it holds DIR_SEARCH | the entry holding the bucket start.
+    std::vector<uint2> ent;
+    ent.reserve(R + R / 4 + 2);
+    for (uint64_t i = 0; i < R; ++i) {
+        ent.push_back(make_uint2((uint32_t)(s->range_lo[i] - base), s->range_node[i]));
+        if (i + 1 < R && s->range_hi[i] < s->range_lo[i + 1]) ent.push_back(make_uint2((uint32_t)(s->range_hi[i] - base), M));
+    }
+    ent.push_back(make_uint2((uint32_t)span, M));
+    const uint64_t n_ent = ent.size();
+    const uint64_t dir_cap = std::min<uint64_t>(DIR_MAX_ENTRIES, std::max<uint64_t>(DIR_PER_ENTRY * n_ent, DIR_MIN_ENTRIES));
     uint32_t dshift = 4;
-    while (dshift < 31 && (span >> dshift) + 1 > DIR_MAX_ENTRIES) ++dshift;
+    while (dshift < 31 && (span >> dshift) + 1 > dir_cap) ++dshift;
     const uint64_t n_dir = (span >> dshift) + 1;
-    std::vector<uint4> rng(R);
-    for (uint64_t i = 0; i < R; ++i)
-        rng[i] = make_uint4((uint32_t)(s->range_lo[i] - base), (uint32_t)(s->range_hi[i] - base), s->range_node[i], 0);
     std::vector<uint32_t> dir(n_dir + 1);
     {
-        uint64_t i = 0;
+        uint64_t j = 0;
         for (uint64_t b = 0; b <= n_dir; ++b) {
             const uint64_t start = b << dshift, end = start + (1ull << dshift);
-            while (i < R && rng[i].y <= start) ++i;
-            if (i < R && rng[i].x <= start && rng[i].y >= end) dir[b] = rng[i].z;
-            else if (i == R || rng[i].x >= end) dir[b] = M;
-            else dir[b] = DIR_SEARCH | (uint32_t)i;
+            if (start >= span) { dir[b] = M; continue; }
+            while (j + 1 < n_ent && ent[j + 1].x <= start) ++j;
+            dir[b] = (ent[j + 1].x >= end) ? ent[j].y : (DIR_SEARCH | (uint32_t)j);
         }
     }
     hpa_status st;
-    uint4* d_rng; uint32_t* d_dir;
-    if ((st = upload(h, B, rng, &d_rng)) || (st = upload(h, B, dir, &d_dir))) return st;
+    uint2* d_ent; uint32_t* d_dir;
+    if ((st = upload(h, B, ent, &d_ent)) || (st = upload(h, B, dir, &d_dir))) return st;
     B->dev.pc_base = base;
     B->dev.span = span;
     B->dev.dshift = dshift;
     B->dev.n_dir = (uint32_t)n_dir;
-    B->dev.n_ranges = (uint32_t)R;
+    B->dev.n_ent = (uint32_t)n_ent;
     B->dev.n_nodes = M;
     B->dev.dir = d_dir;
-    B->dev.rng = d_rng;
+    B->dev.ent = d_ent;
     // host copies kept for the other analyses
     B->node_parent.assign(s->node_parent, s->node_parent + M);
     B->node_kind.assign(s->node_kind, s->node_kind + M);
@@ -514,6 +523,8 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
         w.leaf_grp0 = c.take<uint32_t>(L_max);
         w.leaf_info = c.take<uint32_t>(L_max);
         w.leaf_d = c.take<uint32_t>(L_max + 1);
+        w.leaf_look = c.take<unsigned long long>(L_max);
+        w.leaf_ticket = c.take<uint32_t>(1);
         w.buf_first_leaf = c.take<uint32_t>(n + 1);
         w.buf_bad = c.take<unsigned long long>(n);
         const bool pair = has_cnt && !val64;
@@ -709,6 +720,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         w.timeout_iters = opt.timeout_iters;
         w.small_leaves = opt.small_leaves == 2 || (opt.small_leaves == 0 && u.N < 64 * u.G);
         w.leaf_hash = opt.leaf_hash;
+        w.emit_separate = opt.leaf_emit;
         if (u.mode) {
             w.part_mode = u.mode;
             w.part_ctx_max = u.nbin_max;

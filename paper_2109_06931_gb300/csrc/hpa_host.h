@@ -129,6 +129,8 @@ struct hpa_handle {
     uint64_t graph_replays = 0;
     void* cct_scratch = nullptr;
     size_t cct_cap = 0;
+    void* aux_scratch = nullptr;  // intermediate keys of analyses built on the aggregation
+    size_t aux_cap = 0;
     // phase timing
     bool timing = false;
     std::vector<std::vector<cudaEvent_t>> ev_pool, ev_pending;

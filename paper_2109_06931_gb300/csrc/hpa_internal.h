@@ -100,7 +100,20 @@ struct AggWork {
     uint32_t small_leaves;        // leaves of <= SMALL_LEAF_CAP records go to the small-leaf kernel
     uint32_t leaf_hash;           // leaves aggregate in a shared-memory hash table before sorting
     uint32_t timeout_iters;       // polls of a bounded device wait (0 = 1 << 22)
+    // fused leaves: each leaf writes its keys to the output arrays itself, at
+    // an offset found by a look-back over the leaves before it (k_emit is
+    // then not launched); leaves are taken in index order from leaf_ticket
+    uint32_t fuse_emit;
+    uint32_t emit_separate;          // 1: never fused (every leaf goes through k_emit)
+    unsigned long long* leaf_look;   // [L_max] look-back words (zeroed per call)
+    uint32_t* leaf_ticket;           // [1] next leaf to take (zeroed per call)
 };
+
+// look-back words of fused leaves: a count (AGG) or an inclusive prefix
+// (INCL) in the low bits; DIRECT marks a leaf that wrote its keys itself
+constexpr unsigned long long LOOK_AGG = 1ull << 62, LOOK_INCL = 1ull << 63, LOOK_DIRECT = 1ull << 61,
+                             LOOK_VAL = (1ull << 61) - 1;
+constexpr uint32_t LOOK_QUICK = 2;       // polls a fused leaf makes before it leaves its keys to k_emit
 
 constexpr int TILE = 4096;            // samples per tile of the sample-reading kernels
 constexpr uint32_t HPA_MAX_STALL_DEV = 32;
@@ -166,6 +179,10 @@ struct ExpandSrc {
     uint32_t n_ctx;
 };
 void run_expand_aggregate(const AggWork& w, const ExpandSrc& x, cudaStream_t s, int sms, uint64_t* launches);
+
+// the aggregation's tail after the records are grouped: big-group split,
+// leaves, key placement and the per-buffer key counts
+void run_group_tail(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
 
 // zero every buffer's per-stall totals (device-side, so a captured graph
 // reads the current descriptors)

@@ -11,7 +11,10 @@
 //   dense: a leaf of more than CAP records (one fine bin of a big group, at
 //         most one window of 8192 subkeys wide) is summed in dense windows.
 // Results go to tmp_key / tmp_val at the leaf's start, in key order, with
-// the number of keys in leaf_d.
+// the number of keys in leaf_d -- or, for fused leaves (fuse_emit), straight
+// to the buffer's output arrays at the offset that a look-back over the
+// leaves before it gives, with the per-stall and UNKNOWN totals summed on
+// the way (the work k_emit does otherwise).
 
 #include <algorithm>
 #include <type_traits>
@@ -45,8 +48,101 @@ struct LeafCfg {
     using HSort = PackedRadix<THREADS, DMAX, uint64_t>;
     static constexpr size_t HASH_BYTES = (PACKED && HASH) ? (size_t)TS * 12 + sizeof(typename HSort::Smem) : 0;
     static constexpr size_t SMEM_SD = SORT_BYTES > DENSE_BYTES ? SORT_BYTES : DENSE_BYTES;
-    static constexpr size_t SMEM = SMEM_SD > HASH_BYTES ? SMEM_SD : HASH_BYTES;
+    static constexpr size_t SMEM_WORK = SMEM_SD > HASH_BYTES ? SMEM_SD : HASH_BYTES;
+    // fused leaves (packed records, leaf kernels other than the small-leaf
+    // one): per-warp per-stall totals and the UNKNOWN totals follow the work area
+    static constexpr bool CAN_FUSE = PACKED && CAP > SMALL_LEAF_CAP;
+    static constexpr int ACC_WORDS = (THREADS / 32 + 1) * (int)HPA_MAX_STALL_DEV;
+    static constexpr size_t SMEM = CAN_FUSE ? ((SMEM_WORK + 15) & ~(size_t)15) + (size_t)ACC_WORDS * 8 : SMEM_WORK;
 };
+
+// Look-back over the leaves of one buffer (fused leaves).  Leaf l publishes
+// its key count, adds up the counts of the leaves before it, walking back
+// until a leaf whose inclusive prefix is published (the buffer's first leaf
+// publishes one at once), and publishes its own inclusive prefix.  Leaves
+// are taken in index order from a counter, so every leaf waited for has been
+// taken by a running CTA that never waits for a later leaf.
+//   try:    waits at most `quick` polls; on success the leaf's prefix is
+//           published with LOOK_DIRECT (its keys go straight to the output);
+//           otherwise only its count is published, its keys go to tmp_key /
+//           tmp_val for k_emit, and `finish` completes the walk afterwards,
+//           so that a slow leaf delays the leaves after it by at most `quick`
+//           polls instead of holding them all (a convoy);
+//   finish: bounded by timeout_iters polls; on a timeout the status becomes
+//           HPA_E_TIMEOUT and the prefix is published as if the missing
+//           counts were zero, so that no CTA waits forever.
+
+// walk back from leaf l - 1 summing counts until an inclusive prefix; false
+// if `limit` polls pass first (the sum so far is then incomplete)
+__device__ bool leaf_walk(const AggWork& w, uint32_t l, uint32_t first, uint32_t limit, unsigned long long* prefix) {
+    unsigned long long sum = 0;
+    uint32_t j = l - 1, polls = 0;
+    for (;;) {
+        const unsigned long long st = ld_acquire_u64(&w.leaf_look[j]);
+        if (st & LOOK_INCL) { sum += st & LOOK_VAL; break; }
+        if (st & LOOK_AGG) {
+            sum += st & LOOK_VAL;
+            if (j == first) break;
+            --j;
+            continue;
+        }
+        if (++polls > limit) { *prefix = sum; return false; }
+        if (limit > LOOK_QUICK) __nanosleep(64);
+    }
+    *prefix = sum;
+    return true;
+}
+
+__device__ bool leaf_lookback_try(const AggWork& w, uint32_t l, uint32_t first, uint32_t cnt,
+                                  unsigned long long* base) {
+    if (l == first) {
+        st_release_u64(&w.leaf_look[l], LOOK_INCL | LOOK_DIRECT | cnt);
+        *base = 0;
+        return true;
+    }
+    st_release_u64(&w.leaf_look[l], LOOK_AGG | cnt);
+    unsigned long long prefix;
+    if (!leaf_walk(w, l, first, LOOK_QUICK, &prefix)) return false;
+    st_release_u64(&w.leaf_look[l], LOOK_INCL | LOOK_DIRECT | (prefix + cnt));
+    *base = prefix;
+    return true;
+}
+
+__device__ void leaf_lookback_finish(const AggWork& w, uint32_t l, uint32_t first, uint32_t cnt) {
+    unsigned long long prefix;
+    if (!leaf_walk(w, l, first, w.timeout_iters ? w.timeout_iters : (1u << 22), &prefix))
+        raise_status(w.status, 7 /* HPA_E_TIMEOUT */, 11);
+    st_release_u64(&w.leaf_look[l], LOOK_INCL | (prefix + cnt));
+}
+
+// Where a fused leaf's keys go: the buffer's output arrays from `base`, the
+// context of group-tag 0, UNKNOWN coded as node M, and the subkey layout.
+struct LeafOut {
+    uint32_t* key_ctx;
+    uint32_t* key_node;
+    uint8_t* key_stall;
+    unsigned long long* val;
+    uint64_t capacity;
+    uint32_t gctx0, M, sbits, sb;
+};
+
+// One key of a fused leaf: its per-stall total (this warp's row of counters)
+// and UNKNOWN total, and the four output arrays when it is within capacity.
+__device__ __forceinline__ void fused_put(const LeafOut& o, uint64_t base, unsigned long long* acc,
+                                          unsigned long long* unk, uint32_t pos, uint32_t k, unsigned long long v) {
+    const uint32_t smask = o.sbits >= 32 ? 0xFFFFFFFFu : ((1u << o.sbits) - 1);
+    const uint32_t sub = k & smask, node = sub >> o.sb, stall = sub & ((1u << o.sb) - 1);
+    atomicAdd(&acc[stall], v);
+    if (node == o.M) atomicAdd(&unk[stall], v);
+    const uint64_t p = base + pos;
+    if (p < o.capacity) {
+        const uint32_t gl = o.sbits >= 32 ? 0u : (k >> o.sbits);
+        __stcs(&o.key_ctx[p], o.gctx0 + gl);
+        __stcs(&o.key_node[p], node == o.M ? UNKNOWN : node);
+        o.key_stall[p] = (uint8_t)stall;
+        __stcs(&o.val[p], v);
+    }
+}
 
 // Runs of equal keys in a sorted shared-memory array, reduced warp-striped:
 // warp w owns a contiguous chunk and walks it 32 elements per row (lane l
@@ -66,10 +162,11 @@ __device__ __forceinline__ unsigned long long val_at(const V* vals, int i) {
 // type (32-bit when the leaf's values cannot overflow it).  A run's partial
 // sum in a row is the row's inclusive prefix minus the prefix just before the
 // run's head (found with a ballot), so one plain scan serves every run.
-template <typename T, typename KA, typename VA>
+// put(write, position, key, sum) is called by every lane of the warp
+// together; lanes with `write` store one key.
+template <typename T, typename KA, typename VA, typename PUT>
 __device__ __forceinline__ uint32_t warp_runs(KA K, VA Vf, int n, int w0, int w1,
-                                              int run0, T carry, int mode, uint32_t nz_base,
-                                              uint32_t* out_key, unsigned long long* out_val) {
+                                              int run0, T carry, int mode, uint32_t nz_base, PUT put) {
     const int lane = lane_id();
     int run = run0;
     uint32_t nz = nz_base, nz_count = 0;
@@ -77,7 +174,12 @@ __device__ __forceinline__ uint32_t warp_runs(KA K, VA Vf, int n, int w0, int w1
         const int i = base + lane;
         const bool ok = i < w1;
         const uint32_t k = ok ? K(i) : 0u;
-        const bool h = ok && (i == 0 || K(i - 1) != k);
+        // neighbours from the adjacent lanes; the row's edge lanes load theirs
+        uint32_t kp = __shfl_up_sync(0xffffffffu, k, 1);
+        if (lane == 0 && i > 0) kp = K(i - 1);
+        uint32_t kn = __shfl_down_sync(0xffffffffu, k, 1);
+        if ((lane == 31 || i + 1 >= w1) && i + 1 < n) kn = K(i + 1);
+        const bool h = ok && (i == 0 || kp != k);
         const T v = ok ? (T)Vf(i) : T(0);
         const uint32_t hb = __ballot_sync(0xffffffffu, h);
         T p = v;
@@ -91,16 +193,12 @@ __device__ __forceinline__ uint32_t warp_runs(KA K, VA Vf, int n, int w0, int w1
         const T ph = __shfl_sync(0xffffffffu, p, hpos > 0 ? hpos - 1 : 0);
         const T sum = le ? (hpos > 0 ? p - ph : p) : p + carry;
         const int rid = run + __popc(le);
-        const bool end = ok && (i == n - 1 || K(i + 1) != k);
+        const bool end = ok && (i == n - 1 || kn != k);
         if (mode == 0) {
-            if (end) { out_key[rid] = k; out_val[rid] = (unsigned long long)sum; }
+            put(end, (uint32_t)rid, k, (unsigned long long)sum);
         } else {
             const uint32_t nzb = __ballot_sync(0xffffffffu, end && sum != 0);
-            if (mode == 2 && end && sum != 0) {
-                const uint32_t pos = nz + __popc(nzb & lanemask_lt());
-                out_key[pos] = k;
-                out_val[pos] = (unsigned long long)sum;
-            }
+            if (mode == 2) put(end && sum != 0, nz + __popc(nzb & lanemask_lt()), k, (unsigned long long)sum);
             nz += __popc(nzb);
             nz_count += __popc(nzb);
         }
@@ -126,7 +224,9 @@ __device__ __forceinline__ RunSum<T> warp_run_summary(KA K, VA Vf, int w0, int w
         const int i = base + lane;
         const bool ok = i < w1;
         const uint32_t k = ok ? K(i) : 0u;
-        const bool h = ok && (i == 0 || K(i - 1) != k);
+        uint32_t kp = __shfl_up_sync(0xffffffffu, k, 1);
+        if (lane == 0 && i > 0) kp = K(i - 1);
+        const bool h = ok && (i == 0 || kp != k);
         const T v = ok ? (T)Vf(i) : T(0);
         const uint32_t hb = __ballot_sync(0xffffffffu, h);
         r.heads += __popc(hb);
@@ -143,11 +243,12 @@ __device__ __forceinline__ RunSum<T> warp_run_summary(KA K, VA Vf, int w0, int w
 // Runs of one leaf: per-warp summaries, a block-level (segmented) scan over
 // the warps, then every warp writes its runs; keys with a zero sum are
 // dropped by a compacting second walk (only when a zero value exists).
-// Returns the number of keys written at out_key / out_val.
-template <typename T, int W, typename KA, typename VA>
-__device__ uint32_t leaf_runs(KA Kc, VA Vc, int n, int w0, int w1, bool any_zero, uint32_t* out_key,
-                              unsigned long long* out_val, uint32_t* s_run0, uint32_t* s_nz, T* s_carry,
-                              uint32_t* s_tot) {
+// pre(n_out) is called by every thread once the number of keys is known and
+// before any key is written (fused leaves find their output offset there).
+// Returns the number of keys written.
+template <typename T, int W, typename KA, typename VA, typename PRE, typename PUT>
+__device__ uint32_t leaf_runs(KA Kc, VA Vc, int n, int w0, int w1, bool any_zero, PRE pre, PUT put,
+                              uint32_t* s_run0, uint32_t* s_nz, T* s_carry, uint32_t* s_tot) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const RunSum<T> rc = warp_run_summary<T>(Kc, Vc, w0, w1);
     if (lane == 0) { s_run0[warp] = rc.heads; s_carry[warp] = rc.tail; s_nz[warp] = rc.has_head; }
@@ -170,9 +271,11 @@ __device__ uint32_t leaf_runs(KA Kc, VA Vc, int n, int w0, int w1, bool any_zero
     const int run0 = (int)s_run0[warp] - 1;
     const T carry = s_carry[warp];
     if (!any_zero) {
-        warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 0, 0, out_key, out_val);
+        pre(n_out);
+        warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 0, 0, put);
     } else {
-        const uint32_t nzc = warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 1, 0, nullptr, nullptr);
+        auto none = [](bool, uint32_t, uint32_t, unsigned long long) {};
+        const uint32_t nzc = warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 1, 0, none);
         __syncthreads();
         if (lane == 0) s_nz[warp] = nzc;
         __syncthreads();
@@ -183,7 +286,8 @@ __device__ uint32_t leaf_runs(KA Kc, VA Vc, int n, int w0, int w1, bool any_zero
         }
         __syncthreads();
         n_out = *s_tot;
-        warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 2, s_nz[warp], out_key, out_val);
+        pre(n_out);
+        warp_runs<T>(Kc, Vc, n, w0, w1, run0, carry, 2, s_nz[warp], put);
     }
     __syncthreads();
     return n_out;
@@ -205,15 +309,113 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
     __shared__ uint32_t s_any_zero, s_tot;
     __shared__ uint32_t s_hd, s_abort;
     __shared__ unsigned long long s_spec;
+    __shared__ uint32_t s_leaf, s_direct;
+    __shared__ unsigned long long s_base;
     const uint32_t n_leaves = w.item_nleaf[w.G];
     const uint32_t* seg = w.grp_hist;
     const int warp = threadIdx.x >> 5, lane = lane_id();
 
-    for (uint32_t l = blockIdx.x; l < n_leaves; l += gridDim.x) {
+    // fused leaves: taken in index order from the ticket counter; per-warp
+    // per-stall totals and UNKNOWN totals in shared memory, flushed to the
+    // buffer's totals when the CTA moves on to another buffer and at the end
+    const bool fuse = Cfg::CAN_FUSE && w.fuse_emit != 0;
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw + ((Cfg::SMEM_WORK + 15) & ~(size_t)15));
+    unsigned long long* unk = acc + W * HPA_MAX_STALL_DEV;
+    uint32_t cur_b = 0xFFFFFFFFu;
+    if constexpr (Cfg::CAN_FUSE) {
+        if (fuse)
+            for (int i = threadIdx.x; i < Cfg::ACC_WORDS; i += THREADS) acc[i] = 0;
+    }
+    auto flush = [&]() {
+        __syncthreads();
+        if (cur_b != 0xFFFFFFFFu && w.emit_totals) {
+            const BufDev& B = w.bufs[cur_b];
+            for (uint32_t r = threadIdx.x; r < HPA_MAX_STALL_DEV; r += THREADS) {
+                unsigned long long t = 0;
+                for (int x = 0; x < W; ++x) { t += acc[x * HPA_MAX_STALL_DEV + r]; acc[x * HPA_MAX_STALL_DEV + r] = 0; }
+                const unsigned long long u = unk[r];
+                unk[r] = 0;
+                if (t && B.total) atomicAdd((unsigned long long*)&B.total[r], t);
+                if (u && B.unknown) atomicAdd((unsigned long long*)&B.unknown[r], u);
+            }
+        }
+        __syncthreads();
+    };
+    auto next_leaf = [&](uint32_t l) -> uint32_t {
+        if (!fuse) return l + gridDim.x;
+        __syncthreads();                                   // every thread has read s_leaf
+        if (threadIdx.x == 0) s_leaf = atomicAdd(w.leaf_ticket, 1u);
+        __syncthreads();
+        return s_leaf;
+    };
+
+    for (uint32_t l = fuse ? next_leaf(0) : blockIdx.x; l < n_leaves; l = next_leaf(l)) {
         const uint32_t start = w.leaf_start[l], end = w.leaf_end[l];
         const uint32_t info = w.leaf_info[l];
         const uint32_t n = end - start;
         if (n < n_lo || n > n_hi) continue;               // another leaf kernel's size class
+        // fused leaves: the buffer's output arrays; keys of a buffer with
+        // invalid samples are not written (the call fails as a whole)
+        LeafOut lo_{};
+        uint32_t first = 0;
+        bool skip = true;
+        if constexpr (Cfg::CAN_FUSE) {
+            if (fuse) {
+                const uint32_t b = info >> 8;
+                if (b != cur_b) {
+                    flush();
+                    cur_b = b;
+                }
+                const BufDev& B = w.bufs[b];
+                first = w.buf_first_leaf[b];
+                skip = w.buf_bad[b] != 0;
+                lo_ = LeafOut{B.key_ctx, B.key_node, B.key_stall, (unsigned long long*)B.val, B.capacity,
+                              w.leaf_grp0[l] - B.grp_base, w.bins[B.bin].n_nodes, w.sbits, w.sb};
+            }
+        }
+        // pre: the output offset of this leaf if its predecessors have (nearly)
+        // published theirs (thread 0 looks back, every thread waits for it);
+        // s_direct says whether the keys go straight to the output
+        auto pre = [&](uint32_t n_keys) {
+            if constexpr (Cfg::CAN_FUSE) {
+                if (fuse) {
+                    if (threadIdx.x == 0) {
+                        unsigned long long b = 0;
+                        s_direct = leaf_lookback_try(w, l, first, n_keys, &b) ? 1u : 0u;
+                        s_base = b;
+                    }
+                    __syncthreads();
+                }
+            }
+        };
+        // after the keys are written: a leaf that left them to k_emit completes its look-back
+        auto post = [&](uint32_t n_keys) {
+            if constexpr (Cfg::CAN_FUSE) {
+                if (fuse && !s_direct && threadIdx.x == 0) leaf_lookback_finish(w, l, first, n_keys);
+            }
+        };
+        unsigned long long* acc_w = acc + warp * HPA_MAX_STALL_DEV;
+        auto put_fused = [&](bool wr, uint32_t pos, uint32_t k, unsigned long long v) {
+            if constexpr (Cfg::CAN_FUSE) {
+                if (!wr) return;
+                if (s_direct) {
+                    if (!skip) fused_put(lo_, s_base, acc_w, unk, pos, k, v);
+                } else {
+                    w.tmp_key[start + pos] = k;
+                    w.tmp_val[start + pos] = v;
+                }
+            }
+        };
+        // fused leaves whose path left its keys at tmp_key / tmp_val + start:
+        // copied to the output when the offset is ready, else left to k_emit
+        auto copy_fused = [&](uint32_t n_keys) {
+            __syncthreads();
+            pre(n_keys);
+            if (s_direct)
+                for (uint32_t i = threadIdx.x; i < n_keys; i += THREADS)
+                    put_fused(true, i, w.tmp_key[start + i], (unsigned long long)w.tmp_val[start + i]);
+            post(n_keys);
+        };
         const bool second = info & 1u;
         const uint2* src_pair = second ? w.rec2_pair : w.rec_pair;
         const uint32_t* src_sub = second ? w.rec2_sub : w.rec_sub;
@@ -228,6 +430,8 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
             }
         };
         if (n == 0) {
+            pre(0);
+            post(0);
             if (threadIdx.x == 0) w.leaf_d[l] = 0;
             continue;
         }
@@ -334,6 +538,7 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
                         const int hc = HS::sort(HM, (int)D, (int)(w.sbits + gbits), (int)w.sort_mode);
                         for (uint32_t j = threadIdx.x; j < D; j += THREADS) put(j, HM.el[hc][j]);
                     }
+                    if (fuse) copy_fused(D);
                     if (threadIdx.x == 0) w.leaf_d[l] = D;
                     __syncthreads();
                     continue;
@@ -408,13 +613,27 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
             const bool wide = __syncthreads_or(vmax > (0xFFFFFFFFull / (unsigned long long)n));
             uint32_t* ok_ = w.tmp_key + start;
             unsigned long long* ov = (unsigned long long*)(w.tmp_val + start);
+            auto put_tmp = [&](bool wr, uint32_t pos, uint32_t k, unsigned long long v) {
+                if (wr) { ok_[pos] = k; ov[pos] = v; }
+            };
             uint32_t n_out;
-            if (!wide)
-                n_out = leaf_runs<uint32_t, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, ok_, ov, s_run0, s_nz,
-                                               reinterpret_cast<uint32_t*>(s_carry), &s_tot);
-            else
-                n_out = leaf_runs<unsigned long long, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, ok_, ov, s_run0,
-                                                         s_nz, s_carry, &s_tot);
+            if (fuse) {
+                if (!wide)
+                    n_out = leaf_runs<uint32_t, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, pre, put_fused, s_run0,
+                                                   s_nz, reinterpret_cast<uint32_t*>(s_carry), &s_tot);
+                else
+                    n_out = leaf_runs<unsigned long long, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, pre, put_fused,
+                                                             s_run0, s_nz, s_carry, &s_tot);
+                post(n_out);
+            } else {
+                auto no_pre = [](uint32_t) {};
+                if (!wide)
+                    n_out = leaf_runs<uint32_t, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, no_pre, put_tmp, s_run0,
+                                                   s_nz, reinterpret_cast<uint32_t*>(s_carry), &s_tot);
+                else
+                    n_out = leaf_runs<unsigned long long, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, no_pre, put_tmp,
+                                                             s_run0, s_nz, s_carry, &s_tot);
+            }
             if (threadIdx.x == 0) w.leaf_d[l] = n_out;
             __syncthreads();
         } else if constexpr (Cfg::DENSE) {
@@ -473,9 +692,13 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
                 out += tot;
                 __syncthreads();
             }
+            if (fuse) copy_fused(out);
             if (threadIdx.x == 0) w.leaf_d[l] = out;
             __syncthreads();
         }
+    }
+    if constexpr (Cfg::CAN_FUSE) {
+        if (fuse) flush();
     }
 }
 

@@ -95,6 +95,7 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
     w.timeout_iters = h->opt.timeout_iters;
     w.sort_mode = std::min<uint32_t>(h->opt.leaf_ranking, 3);
     w.leaf_hash = h->opt.leaf_hash;
+    w.emit_separate = h->opt.leaf_emit;
     w.small_leaves = h->opt.small_leaves == 2 || (h->opt.small_leaves == 0 && N < 64 * G);
     w.n_tiles = (N + TILE - 1) / TILE;
     BufDev* d_buf = nullptr;
@@ -114,6 +115,8 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
         w.leaf_grp0 = c.take<uint32_t>(L_max);
         w.leaf_info = c.take<uint32_t>(L_max);
         w.leaf_d = c.take<uint32_t>(L_max + 1);
+        w.leaf_look = c.take<unsigned long long>(L_max);
+        w.leaf_ticket = c.take<uint32_t>(1);
         w.buf_first_leaf = c.take<uint32_t>(2);
         w.buf_bad = c.take<unsigned long long>(1);
         w.rec_sub = has_cnt ? nullptr : c.take<uint32_t>(N + 1);

@@ -33,7 +33,7 @@ vp, u8p, u32p, u64p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_uint32), C
 class hpa_options(C.Structure):
     _fields_ = [("issued_mask", C.c_uint32), ("leaf_capacity", C.c_uint32), ("timeout_iters", C.c_uint32),
                 ("cursor_pad", C.c_uint32), ("leaf_ranking", C.c_uint32), ("grouping", C.c_uint32),
-                ("small_leaves", C.c_uint32), ("leaf_hash", C.c_uint32)]
+                ("small_leaves", C.c_uint32), ("leaf_hash", C.c_uint32), ("leaf_emit", C.c_uint32)]
 
 
 class hpa_structure(C.Structure):
@@ -62,6 +62,17 @@ class hpa_profile(C.Structure):
 
 class hpa_gpucct(C.Structure):
     _fields_ = [("n_req", C.c_uint32), ("req_ctx", vp), ("incl", vp), ("a", vp), ("flags", vp)]
+
+
+class hpa_gpucct_all(C.Structure):
+    _fields_ = [("cap_nodes", C.c_uint64), ("cap_edges", C.c_uint64), ("node_off", vp), ("node_id", vp),
+                ("incl", vp), ("edge_off", vp), ("edge_id", vp), ("ratio", vp), ("a", vp), ("flags", vp),
+                ("counts", vp)]
+
+
+class hpa_issue_rows(C.Structure):
+    _fields_ = [("capacity", C.c_uint64), ("ctx", vp), ("func", vp), ("S", vp), ("S_issued", vp), ("W", vp),
+                ("frac", vp), ("n_rows", vp)]
 
 
 class hpa_cct(C.Structure):
@@ -121,7 +132,7 @@ class hpa_derived(C.Structure):
 EXPORTS = ["hpa_create", "hpa_destroy", "hpa_last_error", "hpa_sync", "hpa_reserve", "hpa_kernel_launches",
            "hpa_load_structure", "hpa_unload_structure", "hpa_binary_info_get", "hpa_attribute_samples",
            "hpa_attribute_samples_host", "hpa_attribute_batch", "hpa_apportion_callgraph",
-           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_set_phase_timing", "hpa_phase_times",
+           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_apportion_all", "hpa_issue_by_function", "hpa_set_phase_timing", "hpa_phase_times",
            "hpa_attribute_samples_noalloc", "hpa_server_create", "hpa_server_submit", "hpa_server_poll",
            "hpa_server_stats_get", "hpa_server_destroy"]
 PHASES = ["hist+plan", "attribute+scatter", "big-split", "leaf sort/reduce", "emit"]
@@ -167,6 +178,8 @@ def lib(build_if_needed: bool = True):
         L.hpa_tune.argtypes = [H, C.c_uint32, C.POINTER(hpa_samples), C.POINTER(hpa_profile), C.c_uint32,
                                C.POINTER(hpa_options), vp]
         L.hpa_apportion_callgraph.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_gpucct)]
+        L.hpa_apportion_all.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_gpucct_all)]
+        L.hpa_issue_by_function.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_issue_rows)]
         L.hpa_propagate_inclusive.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile),
                                               C.POINTER(hpa_cct), vp]
         L.hpa_derive_metrics.argtypes = [H, C.POINTER(C.POINTER(hpa_profile)), C.c_uint32, C.POINTER(hpa_derived)]
@@ -298,7 +311,7 @@ class Hpa:
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, issued_mask: int = 1,
                  leaf_capacity: int = 0, cursor_shift: int | None = None,
                  sort_mode: int | None = None, partition: bool = True, small_leaves: int = 0,
-                 leaf_hash: int = 0, timeout_iters: int = 0):
+                 leaf_hash: int = 0, timeout_iters: int = 0, leaf_emit: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("hpa needs a CUDA device; there is no CPU implementation")
         self.L = lib()
@@ -314,6 +327,7 @@ class Hpa:
             opt.grouping = 1
         opt.small_leaves = small_leaves
         opt.leaf_hash = leaf_hash
+        opt.leaf_emit = leaf_emit
         st = self.L.hpa_create(C.byref(self.h), device, C.c_void_p(self.stream.cuda_stream), C.byref(opt))
         if st:
             raise HpaError(st, "hpa_create failed")
@@ -472,6 +486,63 @@ class Hpa:
         self.check(self.L.hpa_apportion_callgraph(self.h, bid, C.byref(pc), C.byref(g)))
         self._keep = [req]
         return incl, a, flags
+
+    def apportion_all(self, bid: int, p: Profile, shares: bool = False, caps=None, out=None):
+        """hpa_apportion_all: GPU calling context trees of every context of p as
+        sparse rows.  Two calls: the first (capacities 0) asks for the row
+        counts, the second fills arrays of that size (caps=(nodes, edges) skips
+        the first).  Returns a dict of device tensors: node_off, node_id,
+        incl [rows, S+1], edge_off, edge_id, ratio, flags, a (with shares) and
+        counts."""
+        d = self.device
+        M = p.n_stall + 1
+        pc = p.c()
+        if out is not None:                        # the arrays of an earlier call, reused
+            shares = out["a"] is not None
+            g = hpa_gpucct_all(out["caps"][0], out["caps"][1], _ptr(out["node_off"]), _ptr(out["node_id"]),
+                               _ptr(out["incl"]), _ptr(out["edge_off"]), _ptr(out["edge_id"]), _ptr(out["ratio"]),
+                               _ptr(out["a"]) if shares else None, _ptr(out["flags"]), _ptr(out["counts"]))
+            self.check(self.L.hpa_apportion_all(self.h, bid, C.byref(pc), C.byref(g)))
+            return out
+        counts = torch.zeros(2, dtype=torch.int64, device=d)
+        if caps is None:
+            g = hpa_gpucct_all(0, 0, None, None, None, None, None, None, None, None, _ptr(counts))
+            self.check(self.L.hpa_apportion_all(self.h, bid, C.byref(pc), C.byref(g)))
+            self.sync()
+            caps = tuple(int(x) for x in counts.tolist())
+        cn, ce = caps
+        out = dict(node_off=torch.empty(p.n_ctx + 1, dtype=torch.int64, device=d),
+                   node_id=torch.empty(max(cn, 1), dtype=torch.int32, device=d),
+                   incl=torch.empty((max(cn, 1), M), dtype=torch.float32, device=d),
+                   edge_off=torch.empty(p.n_ctx + 1, dtype=torch.int64, device=d),
+                   edge_id=torch.empty(max(ce, 1), dtype=torch.int32, device=d),
+                   ratio=torch.empty(max(ce, 1), dtype=torch.float32, device=d),
+                   flags=torch.empty(max(ce, 1), dtype=torch.uint8, device=d),
+                   a=torch.empty((max(ce, 1), M), dtype=torch.float32, device=d) if shares else None,
+                   counts=counts, caps=(cn, ce))
+        g = hpa_gpucct_all(cn, ce, _ptr(out["node_off"]), _ptr(out["node_id"]), _ptr(out["incl"]),
+                           _ptr(out["edge_off"]), _ptr(out["edge_id"]), _ptr(out["ratio"]),
+                           _ptr(out["a"]) if shares else None, _ptr(out["flags"]), _ptr(counts))
+        self.check(self.L.hpa_apportion_all(self.h, bid, C.byref(pc), C.byref(g)))
+        return out
+
+    def issue_by_function(self, bid: int, p: Profile, capacity: int | None = None):
+        """hpa_issue_by_function: warp issue rate and stall shares per (context,
+        function).  Returns a dict of device tensors (ctx, func, S, S_issued,
+        W, frac [rows, S], n_rows); capacity defaults to the key count."""
+        d = self.device
+        cap = p.capacity if capacity is None else capacity
+        out = dict(ctx=torch.empty(max(cap, 1), dtype=torch.int32, device=d),
+                   func=torch.empty(max(cap, 1), dtype=torch.int32, device=d),
+                   S=torch.empty(max(cap, 1), dtype=torch.int64, device=d),
+                   S_issued=torch.empty(max(cap, 1), dtype=torch.int64, device=d),
+                   W=torch.empty(max(cap, 1), dtype=torch.float32, device=d),
+                   frac=torch.empty((max(cap, 1), p.n_stall), dtype=torch.float32, device=d),
+                   n_rows=torch.zeros(1, dtype=torch.int64, device=d))
+        o = hpa_issue_rows(cap, *[_ptr(out[k]) for k in ("ctx", "func", "S", "S_issued", "W", "frac", "n_rows")])
+        pc = p.c()
+        self.check(self.L.hpa_issue_by_function(self.h, bid, C.byref(pc), C.byref(o)))
+        return out
 
     def expand_gpucct(self, bid: int, res, req_ctx, n_stall: int, q: int, budget: int):
         """hpa_expand_gpucct on an apportion_callgraph result `res` = (incl, a, flags)

@@ -47,7 +47,8 @@ def test_library_loads_and_binding_types():
 
 
 @pytest.mark.parametrize("field,value", [("leaf_capacity", 5000), ("leaf_ranking", 4), ("grouping", 2),
-                                         ("cursor_pad", 8), ("small_leaves", 3), ("leaf_hash", 2)])
+                                         ("cursor_pad", 8), ("small_leaves", 3), ("leaf_hash", 2),
+                                         ("leaf_emit", 2)])
 def test_create_rejects_invalid_options(field, value):
     """Option checks come before any device call, so they hold without a GPU."""
     import ctypes
@@ -68,8 +69,9 @@ def test_struct_layouts_match_header():
 #include <stdio.h>
 #include "hpa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hpa_options), sizeof(hpa_structure), sizeof(hpa_samples),
-         sizeof(hpa_profile), sizeof(hpa_gpucct), sizeof(hpa_cct), sizeof(hpa_derived), sizeof(hpa_binary_info));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hpa_options), sizeof(hpa_structure), sizeof(hpa_samples),
+         sizeof(hpa_profile), sizeof(hpa_gpucct), sizeof(hpa_cct), sizeof(hpa_derived), sizeof(hpa_binary_info),
+         sizeof(hpa_gpucct_all), sizeof(hpa_issue_rows));
   return 0;
 }
 '''
@@ -81,5 +83,5 @@ int main(void) {
         subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (H.hpa_options, H.hpa_structure, H.hpa_samples, H.hpa_profile, H.hpa_gpucct,
-                                       H.hpa_cct, H.hpa_derived, H.hpa_binary_info)]
+                                       H.hpa_cct, H.hpa_derived, H.hpa_binary_info, H.hpa_gpucct_all, H.hpa_issue_rows)]
     assert sizes == mine

@@ -86,3 +86,31 @@ def test_derive_hot_keys_many_profiles(H):
     assert np.array_equal(out["sum"][:k].cpu().numpy().view(np.uint64), ref.sum)
     close(out["std"][:k].cpu().numpy(), ref.std)
     close(out["cov"][:k].cpu().numpy(), ref.cov)
+
+
+@pytest.mark.parametrize("wl,n,n_ctx", [("plain", 300_000, 500), ("large", 2_000_000, 20_000)])
+def test_issue_by_function(H, wl, n, n_ctx):
+    """Warp issue rate and stall shares per (context, function) (Section 7)
+    against the oracle: rows, S and S_issued exact, W and shares within 1e-5;
+    a too-small capacity reports the rows needed."""
+    from paper_2109_06931_gb300 import hpa
+    w = synth.PLAIN if wl == "plain" else synth.LARGE
+    B = w.binary()
+    bid = H.load_structure(B)
+    S = synth.make_samples(77, B, n, n_ctx, w.zipf_s, counts=True, device="cuda")
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    r = H.issue_by_function(bid, p)
+    H.sync()
+    ref = oracle.issue_by_function(B.node_func, 16, oracle.attribute_samples(B, S), 0b11)
+    k = int(r["n_rows"].item())
+    assert k == len(ref.S)
+    assert np.array_equal(r["ctx"][:k].cpu().numpy().view(np.uint32), ref.ctx)
+    assert np.array_equal(r["func"][:k].cpu().numpy().view(np.uint32), ref.func)
+    assert np.array_equal(r["S"][:k].cpu().numpy().view(np.uint64), ref.S)
+    assert np.array_equal(r["S_issued"][:k].cpu().numpy().view(np.uint64), ref.S_issued)
+    close(r["W"][:k].cpu().numpy(), ref.W)
+    close(r["frac"][:k].cpu().numpy().ravel(), ref.frac.ravel())
+    H.issue_by_function(bid, p, capacity=k - 1)
+    st, _ = H.sync_status()
+    assert st == hpa.HPA_E_CAPACITY

@@ -112,3 +112,144 @@ def test_recursive_sccs_large_graph(H):
     res = H.apportion_callgraph(bid, p, req)
     H.sync()
     check(res, oracle.apportion(B, 16, oracle.attribute_samples(B, S), req))
+
+
+# ---- every context in one call (hpa_apportion_all): sparse rows
+
+def _rel_check(got, exp, what):
+    zero = exp == 0
+    assert (got[zero] == 0).all(), f"{what}: nonzero where the oracle is exactly zero"
+    err = np.abs(got[~zero] - exp[~zero]) / np.abs(exp[~zero])
+    assert err.size == 0 or err.max() <= RTOL, f"{what}: max rel err {err.max()}"
+
+
+def check_all(res, ref, req, B, cof):
+    """Rows of the contexts `req` against the oracle's dense result for them:
+    every row within 1e-5, every entry without a row exactly zero in the
+    oracle, node and call-site ids ascending, flags exact."""
+    noff = res["node_off"].cpu().numpy()
+    eoff = res["edge_off"].cpu().numpy()
+    nid = res["node_id"].cpu().numpy().view(np.uint32)
+    incl = res["incl"].cpu().numpy()
+    eid = res["edge_id"].cpu().numpy().view(np.uint32)
+    ratio = res["ratio"].cpu().numpy()
+    flags = res["flags"].cpu().numpy()
+    a = res["a"].cpu().numpy() if res["a"] is not None else None
+    callee = np.asarray(B.cs_callee, np.int64)
+    caller = np.asarray(B.cs_caller, np.int64)
+    cof = np.asarray(cof, np.int64)
+    intra = cof[caller] == cof[callee]
+    assert np.all(np.diff(noff) >= 0) and np.all(np.diff(eoff) >= 0)
+    for q, c in enumerate(req):
+        rows = slice(int(noff[c]), int(noff[c + 1]))
+        ids = nid[rows].astype(np.int64)
+        assert np.all(np.diff(ids) > 0)
+        got = np.zeros_like(ref.incl[q])
+        got[ids] = incl[rows]
+        _rel_check(got, ref.incl[q], f"incl of context {c}")
+        er = slice(int(eoff[c]), int(eoff[c + 1]))
+        es = eid[er].astype(np.int64)
+        assert np.all(np.diff(es) > 0) and not intra[es].any()
+        gotA = np.zeros_like(ref.a[q])
+        gotA[es] = ratio[er, None].astype(np.float64) * got[cof[callee[es]]]
+        _rel_check(gotA, ref.a[q], f"r(e) * incl(head) of context {c}")
+        if a is not None:
+            gotA2 = np.zeros_like(ref.a[q])
+            gotA2[es] = a[er]
+            _rel_check(gotA2, ref.a[q], f"shares of context {c}")
+        gotF = np.zeros(ref.flags.shape[1], np.uint8)
+        gotF[es] = flags[er]
+        assert np.array_equal(gotF[~intra], ref.flags[q][~intra]), f"flags of context {c}"
+
+
+@pytest.mark.parametrize("name", ["gpucct_fig5.json", "gpucct_selfcall.json", "gpucct_diamond.json",
+                                  "gpucct_two_cycle.json", "gpucct_scc_two_callers.json"])
+def test_all_contexts_golden(H, name):
+    """Every context of the hand-computed fixtures in one call, with and
+    without the shares themselves."""
+    g = json.load(open(os.path.join(GOLD, name)))
+    B, lo = _gold_binary(g)
+    bid = H.load_structure(B)
+    info, cof = H.binary_info(bid)
+    ks = np.array(g["keys"], np.uint64)
+    n_ctx = max(g["req_ctx"]) + 1
+    S = samples_from_numpy(lo[ks[:, 1].astype(np.int64)], ks[:, 0], ks[:, 2], ks[:, 3], n_ctx, g["n_stall"])
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    req = np.arange(n_ctx, dtype=np.uint32)
+    ref = oracle.apportion(B, g["n_stall"], oracle.attribute_samples(B, S), req)
+    for shares in (False, True):
+        res = H.apportion_all(bid, p, shares=shares)
+        H.sync()
+        check_all(res, ref, req, B, cof)
+
+
+def test_all_contexts_plain_workload(H):
+    """All 500 contexts of the plain workload (2,000 functions, 4,000 call
+    sites) in one call, every context against the oracle."""
+    w = synth.PLAIN
+    B = w.binary()
+    bid = H.load_structure(B)
+    _, cof = H.binary_info(bid)
+    S = w.samples(B, device="cuda")
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    res = H.apportion_all(bid, p, shares=True)
+    H.sync()
+    keys = oracle.attribute_samples(B, S)
+    for lo_c in range(0, 500, 125):
+        req = np.arange(lo_c, lo_c + 125, dtype=np.uint32)
+        check_all(res, oracle.apportion(B, 16, keys, req), req, B, cof)
+
+
+def test_all_contexts_large_graph(H):
+    """The large binary (120,000 call sites, 50 recursive SCCs) with 20,000
+    contexts: sampled contexts against the oracle, and every context's rows
+    against the per-context GPU result of hpa_apportion_callgraph for 64
+    contexts spread over the range."""
+    w = synth.LARGE
+    B = w.binary()
+    bid = H.load_structure(B)
+    _, cof = H.binary_info(bid)
+    S = w.samples(B, device="cuda", n=4_000_000)
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    res = H.apportion_all(bid, p)
+    H.sync()
+    req = np.array([0, 1, 777, 12_345, 19_999], np.uint32)
+    check_all(res, oracle.apportion(B, 16, oracle.attribute_samples(B, S), req), req, B, cof)
+    req = np.linspace(0, w.n_ctx - 1, 64).astype(np.uint32)
+    incl, a, flags = H.apportion_callgraph(bid, p, req)
+    H.sync()
+    dense = types.SimpleNamespace(incl=incl.cpu().numpy().astype(np.float64), a=a.cpu().numpy().astype(np.float64),
+                                  flags=flags.cpu().numpy())
+    noff = res["node_off"].cpu().numpy()
+    nid = res["node_id"].cpu().numpy().view(np.uint32)
+    rows = res["incl"].cpu().numpy()
+    for q, c in enumerate(req):
+        got = np.zeros_like(dense.incl[q])
+        got[nid[noff[c]:noff[c + 1]].astype(np.int64)] = rows[noff[c]:noff[c + 1]]
+        np.testing.assert_allclose(got, dense.incl[q], rtol=2e-5, atol=0)
+
+
+def test_all_contexts_capacity_and_empty(H):
+    """Capacities 0 return the row counts only; too small a capacity is
+    HPA_E_CAPACITY with the counts needed; contexts without samples have no
+    rows."""
+    from paper_2109_06931_gb300 import hpa
+    w = synth.PLAIN
+    B = w.binary()
+    bid = H.load_structure(B)
+    S = synth.make_samples(3, B, 50_000, 900, 1.1, device="cuda")
+    S.ctx.clamp_(max=599)                      # contexts 600..899 stay empty
+    p = H.attribute_samples(bid, S)
+    H.sync()
+    res = H.apportion_all(bid, p)
+    H.sync()
+    need = [int(x) for x in res["counts"].tolist()]
+    noff = res["node_off"].cpu().numpy()
+    assert need[0] > 0 and need[1] > 0 and noff[-1] == need[0]
+    assert np.all(noff[600:] == need[0])
+    small = H.apportion_all(bid, p, caps=(need[0] - 1, need[1]))
+    st, _ = H.sync_status()
+    assert st == hpa.HPA_E_CAPACITY and [int(x) for x in small["counts"].tolist()] == need

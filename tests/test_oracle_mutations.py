@@ -14,6 +14,7 @@ import test_oracle_bottom_up as TB
 import test_oracle_expand as TX
 import test_oracle_flat as TF
 import test_oracle_inclusive_derive as TI
+import test_oracle_issue as TW
 import test_oracle_sparse as TS
 import test_oracle_unify as TU
 
@@ -54,6 +55,18 @@ MUTATIONS = [
     ("issue-rate-of-stalls", "d->W[c] = (double)d->S_issued[c] / (double)d->S[c];",
      "d->W[c] = (double)(d->S[c] - d->S_issued[c]) / (double)d->S[c];",
      [lambda o: TI.test_derive_vs_numpy(o), lambda o: TI.test_derive_single_profile(o)]),
+    ("issue-by-function-stalled-share", "o->W.push_back((double)issued / (double)S);",
+     "o->W.push_back((double)(S - issued) / (double)S);",
+     [lambda o: TW.test_hand_example(o, 0b001, [5 / 8, 2 / 8, 0.0, 1 / 2])]),
+    ("issue-by-function-keyed-by-node", "std::vector<uint64_t>& v = per[std::make_pair(kctx[i], node_func[knode[i]])];",
+     "std::vector<uint64_t>& v = per[std::make_pair(kctx[i], knode[i])];",
+     [lambda o: TW.test_hand_example(o, 0b001, [5 / 8, 2 / 8, 0.0, 1 / 2])]),
+    ("issue-by-function-first-reason-only", "if (r < 32 && ((issued_mask >> r) & 1u)) issued += kv.second[r];",
+     "if (r == 0) issued += kv.second[r];",
+     [lambda o: TW.test_hand_example(o, 0b101, [1.0, 2 / 8, 0.0, 1.0])]),
+    ("issue-by-function-unknown-as-function", "if (knode[i] == UNKNOWN) continue;\n        if (knode[i] >= n_nodes",
+     "if (knode[i] >= n_nodes",
+     [lambda o: TW.test_hand_example(o, 0b001, [5 / 8, 2 / 8, 0.0, 1 / 2])]),
     ("min-over-present-only", "for (uint32_t p = 0; p < P; ++p) { s += x[p]; lo = std::min(lo, x[p]); hi = std::max(hi, x[p]); }",
      "for (uint32_t p = 0; p < P; ++p) { s += x[p]; if (x[p]) lo = std::min(lo, x[p]); hi = std::max(hi, x[p]); }",
      [lambda o: TI.test_derive_vs_numpy(o)]),
