@@ -716,7 +716,7 @@ def main():
     ap.add_argument("--small-leaves", type=int, default=0, help="0 automatic, 1 never, 2 always")
     ap.add_argument("--leaf-hash", type=int, default=0, help="0 sort, 1 hash (with --no-tune)")
     ap.add_argument("--leaf-emit", type=int, default=0,
-                    help="0 leaves write their keys when their offset is ready, 1 a separate pass always")
+                    help="0 a separate pass places the keys, 1 leaves write theirs when their offset is ready")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the apportion / inclusive / derive rows")
@@ -807,10 +807,8 @@ def main():
     in_b = 17 if has_cnt else 13
     rec_b = 8 if has_cnt else 4
     # algorithmic bytes per launch of each phase (per-unit figures x units)
-    # (the leaves write the final 17-byte keys themselves; "emit" is then the
-    # scan of the leaves' key counts and the per-buffer key count)
     algo = {"hist+plan": 4 * N, "attribute+scatter": (in_b + rec_b) * N, "big-split": 0,
-            "leaf sort/reduce": rec_b * N + 17 * K, "emit": 0}
+            "leaf sort/reduce": rec_b * N + 12 * K, "emit": 12 * K + 17 * K}
     dom = max(ph, key=ph.get)
     peak, peak_kind = peaks()
     ach = algo[dom] / (ph[dom] / 1e3) / 1e9 if ph[dom] > 0 else 0.0

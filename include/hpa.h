@@ -81,10 +81,10 @@ typedef struct {
                                1 = shared-memory hash table first, then a sort of the
                                distinct keys (falls back to the sort for a leaf with too
                                many distinct keys); pays off when samples repeat keys     */
-    uint32_t leaf_emit;     /* placement of the output keys: 0 = a leaf writes its keys
-                               itself when the keys of the leaves before it are counted
-                               (else a separate pass places them), 1 = always a
-                               separate pass after the leaves                            */
+    uint32_t leaf_emit;     /* placement of the output keys: 0 = a separate pass after the
+                               leaves, 1 = a leaf writes its keys itself when the keys of
+                               the leaves before it are already counted (the others are
+                               left to the separate pass)                                */
 } hpa_options;
 
 /* Program structure of one GPU binary (Section 5).  HOST arrays, copied into

@@ -720,7 +720,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
         w.timeout_iters = opt.timeout_iters;
         w.small_leaves = opt.small_leaves == 2 || (opt.small_leaves == 0 && u.N < 64 * u.G);
         w.leaf_hash = opt.leaf_hash;
-        w.emit_separate = opt.leaf_emit;
+        w.emit_separate = opt.leaf_emit == 0 ? 1u : 0u;
         if (u.mode) {
             w.part_mode = u.mode;
             w.part_ctx_max = u.nbin_max;

@@ -95,7 +95,7 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
     w.timeout_iters = h->opt.timeout_iters;
     w.sort_mode = std::min<uint32_t>(h->opt.leaf_ranking, 3);
     w.leaf_hash = h->opt.leaf_hash;
-    w.emit_separate = h->opt.leaf_emit;
+    w.emit_separate = h->opt.leaf_emit == 0 ? 1u : 0u;
     w.small_leaves = h->opt.small_leaves == 2 || (h->opt.small_leaves == 0 && N < 64 * G);
     w.n_tiles = (N + TILE - 1) / TILE;
     BufDev* d_buf = nullptr;

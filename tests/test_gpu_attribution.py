@@ -445,3 +445,19 @@ def test_two_devices_in_one_process(plain):
         h.sync()
         assert_same_keys(out, oracle.attribute_samples(B, S))
         h.close()
+
+
+@pytest.mark.parametrize("n_ctx,counts", [(20_000, True), (300, False), (7, True)])
+def test_leaves_writing_their_own_keys(large_bin, plain, n_ctx, counts):
+    """leaf_emit = 1: a leaf whose predecessors have published their key
+    counts writes its keys straight to the output (look-back over leaves),
+    the others go through the separate pass; same keys and totals."""
+    from paper_2109_06931_gb300 import hpa
+    B, _ = large_bin if n_ctx > 1000 else plain
+    h = hpa.Hpa(0, leaf_emit=1)
+    bid = h.load_structure(B)
+    S = synth.make_samples(61, B, 1_500_000, n_ctx, 0.9, counts=counts, device="cuda")
+    out = h.attribute_samples(bid, S)
+    h.sync()
+    assert_same_keys(out, oracle.attribute_samples(B, S))
+    h.close()
