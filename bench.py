@@ -525,6 +525,48 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def plain_small_row(local, steps: int = 50):
+    """The small plain profile (10^6 samples, 500 contexts, no counts): the
+    time per call when calls of one shape repeat (the library then replays a
+    captured graph of the pipeline), the kernels per call, and a bit-exact
+    check of the result against the oracle."""
+    from paper_2109_06931_gb300 import hpa as H
+    import oracle
+    dev = torch.device("cuda", local)
+    w = synth.PLAIN
+    B = w.binary()
+    S = w.samples(B, device=dev)
+    stream = torch.cuda.Stream(dev)
+    h = H.Hpa(local, stream=stream)
+    bid = h.load_structure(B)
+    out = H.new_profile(S.n, S.n_stall, dev)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        h.attribute_samples(bid, S, out=out)
+    h.sync()
+    l0 = h.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        h.attribute_samples(bid, S, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    h.sync()
+    ms = e0.elapsed_time(e1) / steps
+    kernels = (h.launches() - l0) / steps
+    oracle.build()
+    parity = parity_against_oracle(h, bid, S, oracle.attribute_samples(B, S))
+    K = out.count()
+    peak, _ = peaks()
+    path = 13 * S.n + 17 * K
+    h.close()
+    return {"workload": w.name, "samples": S.n, "keys": K, "ms": ms, "samples_per_s": S.n / (ms / 1e3),
+            "kernels_per_call": kernels, "form": "repeated calls of one shape (graph replays)",
+            "path_roofline": {"achieved": path / (ms / 1e3) / 1e9, "frac": path / (ms / 1e3) / 1e9 / peak,
+                              "unit": "GB/s", "algorithmic_bytes_per_step": path},
+            "parity": parity}
+
+
 def batched_result(args, world, rank, local, workload: str, steps: int, warmup: int, cpu_seconds: float):
     """Batched form (256 uneven buffers, 8 binaries, one graph launch per
     step; or 64 buffers over 10^6 tuples each) against the plain form (one
@@ -625,7 +667,14 @@ def batched_result(args, world, rank, local, workload: str, steps: int, warmup: 
     parity = None
     if rank == 0 and cpu_seconds > 0:
         bin_of = [bins[i % len(bins)] for i in range(len(bufs))]
-        rate, n_cpu, dt_cpu, used, parity = batched_cpu_rate(bin_of, bufs, cpu_seconds, outs)
+        def gpu_slice(i, n):
+            b = bufs[i]
+            sl = synth.Samples(b.pc[:n], b.ctx[:n], b.stall[:n], None if b.count is None else b.count[:n],
+                               b.n_ctx, b.n_stall)
+            o = h.attribute_samples(bids[i], sl)
+            h.sync()
+            return o
+        rate, n_cpu, dt_cpu, used, parity = batched_cpu_rate(bin_of, bufs, cpu_seconds, outs, gpu_slice)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{used} smallest buffers, the last cut to fit ({n_cpu} samples, {dt_cpu:.1f} s); "
                          f"the rate applies per sample of the whole batch", **host_info()}
@@ -658,7 +707,7 @@ def run_batched(args, world, rank, local):
 
 
 
-def batched_cpu_rate(bin_of, bufs, seconds: float, outs=None):
+def batched_cpu_rate(bin_of, bufs, seconds: float, outs=None, gpu_slice=None):
     """Samples/s of the oracle on a bounded subset of a batch: buffers in
     increasing size, the last one cut so that the oracle runs about
     `seconds`.  With outs (the batch's device profiles) every whole buffer
@@ -683,8 +732,9 @@ def batched_cpu_rate(bin_of, bufs, seconds: float, outs=None):
         assert k.status == 0
         done_n += n
         used += 1
-        if outs is not None and n == b.n:
-            o = outs[i]
+        if outs is not None and (n == b.n or gpu_slice is not None):
+            # a buffer cut to the time budget is compared with the GPU's profile of the same slice
+            o = outs[i] if n == b.n else gpu_slice(i, n)
             got = o.numpy()
             ok = o.count() == len(k) and all(np.array_equal(g, r) for g, r in zip(got, (k.ctx, k.node, k.stall, k.val)))
             S_ = len(k.total)
@@ -897,7 +947,8 @@ def main():
         out = S = None
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        extra_rows = {}
+        extra_rows = {"plain_1M": plain_small_row(local)}
+        torch.cuda.empty_cache()
         for name, key in (("batched", "batched"), ("many-ctx", "many_ctx")):
             extra_rows[key] = batched_result(args, world, rank, local, name, min(args.steps, 5), 3,
                                              0.0 if args.no_cpu else 8.0)

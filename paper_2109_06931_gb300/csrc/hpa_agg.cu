@@ -24,9 +24,8 @@
 // (ctx, node, stall).
 
 #include <algorithm>
+#include <map>
 #include <mutex>
-#include <set>
-#include <tuple>
 #include <type_traits>
 
 #include "hpa_bulk.cuh"
@@ -89,18 +88,49 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, 
 
 void set_smem_limit(const void* fn, int bytes) {
     static std::mutex mu;
-    static std::set<std::tuple<const void*, int, int>> done;
+    static std::map<std::pair<const void*, int>, int> limit;   // largest limit set per (kernel, device)
+    if (bytes <= 48 * 1024) return;                             // within the default limit
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
-    if (done.count(std::make_tuple(fn, dev, bytes))) return;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
-        done.insert(std::make_tuple(fn, dev, bytes));
+    int& cur = limit[std::make_pair(fn, dev)];
+    if (bytes <= cur) return;                                   // the limit only ever grows
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess) cur = bytes;
+    else cudaGetLastError();
+}
+
+// short arrays: one CTA scans them in one launch
+constexpr int SCAN_SMALL_THREADS = 1024, SCAN_SMALL_EPT = 16;
+constexpr uint64_t SCAN_SMALL_MAX = (uint64_t)SCAN_SMALL_THREADS * SCAN_SMALL_EPT;
+
+__global__ void __launch_bounds__(SCAN_SMALL_THREADS) k_scan_small(const uint32_t* in, uint32_t* out, uint32_t n) {
+    __shared__ uint32_t sw[33];
+    const uint32_t base = threadIdx.x * SCAN_SMALL_EPT;
+    uint32_t v[SCAN_SMALL_EPT];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_SMALL_EPT; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t tot;
+    uint32_t pre = block_exclusive_scan<uint32_t, SCAN_SMALL_THREADS>(sum, sw, &tot);
+#pragma unroll
+    for (int i = 0; i < SCAN_SMALL_EPT; ++i) {
+        if (base + i < n) out[base + i] = pre;
+        pre += v[i];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
 }
 
 size_t scan_tmp_words(uint64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 2; }
 
 void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cudaStream_t s, uint64_t* launches) {
+    if (n <= SCAN_SMALL_MAX) {
+        k_scan_small<<<1, SCAN_SMALL_THREADS, 0, s>>>(in, out, (uint32_t)n);
+        *launches += 1;
+        return;
+    }
     const uint32_t nb = (uint32_t)std::max<uint64_t>(1, (n + SCAN_TILE - 1) / SCAN_TILE);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, tmp);
     k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb);
@@ -871,6 +901,7 @@ __global__ void __launch_bounds__(256) k_emit(AggWork w) {
         const uint32_t g0 = w.leaf_grp0[l];
         const uint64_t o0 = (uint64_t)leaf_out[l] - leaf_out[w.buf_first_leaf[b]];
         const uint32_t gctx0 = g0 - B.grp_base;
+        const bool narrow = w.tmp_v32 && !w.leaf_wide[l];        // 32-bit sums in tmp_v32
         // EMIT_U keys per thread loaded before any is processed: more bytes in flight
         for (uint32_t i0 = tid; i0 < d; i0 += EMIT_U * 256) {
             uint32_t kk[EMIT_U];
@@ -880,7 +911,8 @@ __global__ void __launch_bounds__(256) k_emit(AggWork w) {
                 const uint32_t i = i0 + u * 256;
                 if (i < d) {
                     kk[u] = __ldcs(&w.tmp_key[start + i]);
-                    vv[u] = __ldcs((const unsigned long long*)&w.tmp_val[start + i]);
+                    vv[u] = narrow ? (unsigned long long)__ldcs(&w.tmp_v32[start + i])
+                                   : __ldcs((const unsigned long long*)&w.tmp_val[start + i]);
                 }
             }
 #pragma unroll

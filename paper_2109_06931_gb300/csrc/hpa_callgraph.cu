@@ -141,6 +141,10 @@ hpa_status build_callgraph(hpa_handle* h, Binary* B) {
     csr(F, B->cs_callee, eids, fin_off, fin_edge);
     std::vector<uint32_t> node_cs(M, 0xFFFFFFFFu);
     for (uint32_t e = 0; e < E; ++e) node_cs[B->cs_node[e]] = e;
+    std::vector<uint32_t> cs_head(E);
+    for (uint32_t e = 0; e < E; ++e) cs_head[e] = cof[B->cs_callee[e]];
+    std::vector<uint32_t> level_of(V, 0);
+    for (uint32_t v = 0; v < V; ++v) level_of[v] = live[v] ? height[v] : 0;
 
     B->n_cnodes = V;
     B->n_scc = (uint32_t)nt.size();
@@ -149,7 +153,7 @@ hpa_status build_callgraph(hpa_handle* h, Binary* B) {
     DevCallGraph& g = B->cg;
     g.F = F; g.E = E; g.V = V; g.n_levels = n_levels; g.M = M;
     hpa_status st;
-    uint32_t *p0, *p1, *p2, *p3, *p4, *p5, *p6, *p7, *p8, *p9, *p10, *p11, *p12, *p13;
+    uint32_t *p0, *p1, *p2, *p3, *p4, *p5, *p6, *p7, *p8, *p9, *p10, *p11, *p12, *p13, *p14, *p15;
     uint8_t *q0, *q1;
     if ((st = upload(h, B, B->node_func, &p0)) || (st = upload(h, B, node_cs, &p1)) ||
         (st = upload(h, B, B->cs_caller, &p2)) || (st = upload(h, B, B->cs_callee, &p3)) ||
@@ -158,11 +162,13 @@ hpa_status build_callgraph(hpa_handle* h, Binary* B) {
         (st = upload(h, B, cout_off, &p9)) || (st = upload(h, B, cout_edge, &p10)) ||
         (st = upload(h, B, cout_head, &p13)) ||
         (st = upload(h, B, level_off, &p11)) || (st = upload(h, B, level_node, &p12)) ||
-        (st = upload(h, B, intra, &q0)) || (st = upload(h, B, live, &q1)))
+        (st = upload(h, B, intra, &q0)) || (st = upload(h, B, live, &q1)) ||
+        (st = upload(h, B, cs_head, &p14)) || (st = upload(h, B, level_of, &p15)))
         return st;
     g.node_func = p0; g.node_cs = p1; g.cs_caller = p2; g.cs_callee = p3; g.cnode_of_func = p4;
     g.fin_off = p5; g.fin_edge = p6; g.cin_off = p7; g.cin_edge = p8; g.cout_off = p9; g.cout_edge = p10; g.cout_head = p13;
     g.level_off = p11; g.level_node = p12; g.edge_intra = q0; g.cnode_live = q1;
+    g.cs_head = p14; g.level_of = p15;
     uint32_t* par;
     if ((st = upload(h, B, B->node_parent, &par))) return st;
     B->d_node_parent = par;

@@ -3,24 +3,29 @@
 // inclusive cost is not zero and the call sites whose share is not zero --
 // the part of the call graph above the context's sampled functions.
 //
-// One CTA per context at a time, contexts taken in order from a counter:
+// Contexts are taken in order from a counter, several CTAs per SM, one
+// context per CTA at a time; every step walks the context's own part of the
+// graph, never the whole graph:
 //  step 1  the context's keys give the exclusive cost of each condensed node
-//          (exact 64-bit sums per stall reason) and the measured weight of
-//          each call site (samples at its call instruction, all stall
-//          reasons); a per-CTA list of the touched call sites resets them;
+//          (exact 64-bit sums per stall reason, rows zeroed through a list of
+//          the nodes with samples) and the measured weight of each call site
+//          (samples at its call instruction, all stall reasons; reset through
+//          a list of the touched call sites);
 //  step 2  functions with samples and no measured incoming weight get weight
 //          1 on every incoming call site, repeated through their callers that
-//          have no measured incoming weight (frontier-parallel closure);
+//          have no measured incoming weight (a breadth-first queue);
 //  step 3  static condensation (Tarjan at load); a condensed node with cost or
 //          a member in the step-2 closure whose incoming weight is still zero
 //          gets the same rule on the condensed graph (FIXUP2);
-//  rows    a condensed node has a nonzero inclusive cost iff it has cost
-//          itself or an outgoing call site of nonzero weight into a node with
-//          nonzero inclusive cost (found level by level, sinks first); the
-//          rows of the context are those nodes and those call sites, in id
-//          order; a look-back over the contexts gives their offsets;
-//  step 4  level by level, one thread per (node, stall column):
-//          incl(v) = excl(v) + sum_e r(e) * incl(head(e)), r(e) = w(e) / W(head),
+//  rows    a bitmap marks the call sites of nonzero weight; the nodes of
+//          nonzero inclusive cost are those reachable upward from the nodes
+//          with samples through such call sites (a breadth-first search that
+//          also fixes each node's incoming weight W, each call site's ratio
+//          w / W and its row bit); rows in id order come from the bitmaps'
+//          popcounts, their offsets from a look-back over the contexts;
+//  step 4  level by level (nodes bucketed by level with a counting sort), one
+//          thread per (node, stall column):
+//          incl(v) = excl(v) + sum_e r(e) * incl(head(e)),
 //          accumulated in double-float arithmetic (error-free products and
 //          sums of float pairs) from the float rows of the heads, which are the
 //          output rows themselves; each stored value is rounded once to float.
@@ -36,6 +41,7 @@ namespace hpa {
 // barrier and a chain of dependent loads per level) overlap another's work
 constexpr int GALL_THREADS = 256;
 constexpr int GALL_PER_SM = 4;
+constexpr size_t GALL_SMEM_MAX = 48 * 1024;   // bitmaps in shared memory up to this size, else in the slot
 
 // per-node / per-function flags of one context (u32 words, atomicOr)
 enum : uint32_t {
@@ -44,29 +50,27 @@ enum : uint32_t {
     GF_Z = 4,        // function: in the step-2 closure
     GC_NEED = 8,     // condensed node: cost or a member in the step-2 closure
     GC_Z2 = 16,      // condensed node: in the FIXUP2 closure
-    GC_EXCL = 32,    // condensed node: exclusive cost (keys with a value)
-    GC_CLOS = 64     // condensed node: nonzero inclusive cost
+    GC_EXCL = 32     // condensed node: exclusive cost (keys with a value)
 };
 
 struct GallSlot {
     uint32_t* flags;             // [V]
-    uint32_t* rowmap;            // [V] row of a node within its context
     unsigned long long* wmeas;   // [E] measured call-site weights (reset through `touched`)
     uint32_t* touched;           // [E]
     unsigned long long* excl;    // [V][S] rows of GC_EXCL nodes
-    unsigned long long* Wc;      // [V] incoming weight of GC_CLOS nodes
-    float* ratio;                // [E] r(e) of the context's edge rows
-    uint8_t* wpos;               // [E] w(e) > 0 after steps 2 and 3, by call site
-    uint8_t* wpos_c;             // [E] the same in cout order
-    uint32_t* front[2];          // [max(F, V)]
-    // the step-4 sweep's lists: nodes with nonzero inclusive cost in level
-    // order, each with its active out-edges (ratio, row of the head)
-    uint32_t* cl_node;           // [V]
-    uint32_t* cl_off;            // [n_levels + 1]
-    uint32_t* ce_off;            // [V + 1]
+    float* ratio;                // [E] r(e) of the context's call-site rows
+    uint32_t* q_has;             // [F] functions with samples
+    uint32_t* q_z;               // [F] step-2 closure (breadth-first queue)
+    uint32_t* q_need;            // [V] nodes with cost or a member in the closure
+    uint32_t* q_z2;              // [V] FIXUP2 closure
+    uint32_t* q_excl;            // [V] nodes with samples
+    uint32_t* q_clos;            // [V] nodes of nonzero inclusive cost (breadth-first queue)
+    uint32_t* cl_node;           // [V] the same in level order
+    uint32_t* cl_row;            // [V] their rows
+    uint32_t* ce_off;            // [V + 1] active out-edges of cl_node[k]
     float* ce_ratio;             // [E]
     uint32_t* ce_hrow;           // [E]
-    uint32_t* pos_pre;           // [V + 1] prefix counts over level positions
+    uint32_t* bits;              // bitmaps when they do not fit shared memory
 };
 
 struct GallArgs {
@@ -81,13 +85,39 @@ struct GallArgs {
     const uint64_t* ctx_start;       // [n_ctx + 1] first key of each context
     hpa_gpucct_all out;
     unsigned long long* look_n;      // [n_ctx] look-back words (node rows)
-    unsigned long long* look_e;      // [n_ctx] look-back words (edge rows)
+    unsigned long long* look_e;      // [n_ctx] look-back words (call-site rows)
     uint32_t* ticket;
     char* slots;
     size_t slot_bytes;
+    uint32_t smem_bits;              // bitmaps in dynamic shared memory (else in the slot)
     uint32_t timeout_iters;
     DevStatus* status;
 };
+
+// bitmaps of one context: call sites of nonzero weight, call-site rows,
+// nodes of nonzero inclusive cost, the prefix of the node bitmap's popcounts,
+// and the per-level counters of the sweep lists
+struct GallBits {
+    uint32_t *wpos, *erow, *clos, *npre, *lev;
+    uint32_t we, wv;                 // words per call-site / node bitmap
+};
+
+__host__ __device__ inline size_t gall_bits_words(const DevCallGraph& g) {
+    const size_t we = ((size_t)g.E + 31) / 32 + 1, wv = ((size_t)g.V + 31) / 32 + 1;
+    return 2 * we + 2 * wv + g.n_levels + 2;
+}
+
+__device__ inline GallBits gall_bits(const DevCallGraph& g, uint32_t* base) {
+    GallBits b;
+    b.we = (g.E + 31) / 32 + 1;
+    b.wv = (g.V + 31) / 32 + 1;
+    b.wpos = base;
+    b.erow = b.wpos + b.we;
+    b.clos = b.erow + b.we;
+    b.npre = b.clos + b.wv;
+    b.lev = b.npre + b.wv;
+    return b;
+}
 
 __host__ __device__ inline size_t gall_layout(const DevCallGraph& g, uint32_t S, char* base, GallSlot* s) {
     size_t off = 0;
@@ -97,25 +127,24 @@ __host__ __device__ inline size_t gall_layout(const DevCallGraph& g, uint32_t S,
         off += bytes;
         return p;
     };
-    const size_t FV = g.F > g.V ? g.F : g.V;
     GallSlot t;
     t.flags = (uint32_t*)take((size_t)g.V * 4);
-    t.rowmap = (uint32_t*)take((size_t)g.V * 4);
     t.wmeas = (unsigned long long*)take((size_t)g.E * 8 + 8);
     t.touched = (uint32_t*)take((size_t)g.E * 4 + 4);
     t.excl = (unsigned long long*)take((size_t)g.V * S * 8);
-    t.Wc = (unsigned long long*)take((size_t)g.V * 8);
     t.ratio = (float*)take((size_t)g.E * 4 + 4);
-    t.wpos = (uint8_t*)take((size_t)g.E + 4);
-    t.wpos_c = (uint8_t*)take((size_t)g.E + 4);
-    t.front[0] = (uint32_t*)take(FV * 4);
-    t.front[1] = (uint32_t*)take(FV * 4);
+    t.q_has = (uint32_t*)take((size_t)g.F * 4 + 4);
+    t.q_z = (uint32_t*)take((size_t)g.F * 4 + 4);
+    t.q_need = (uint32_t*)take((size_t)g.V * 4 + 4);
+    t.q_z2 = (uint32_t*)take((size_t)g.V * 4 + 4);
+    t.q_excl = (uint32_t*)take((size_t)g.V * 4 + 4);
+    t.q_clos = (uint32_t*)take((size_t)g.V * 4 + 4);
     t.cl_node = (uint32_t*)take((size_t)g.V * 4 + 4);
-    t.cl_off = (uint32_t*)take((size_t)g.n_levels * 4 + 8);
+    t.cl_row = (uint32_t*)take((size_t)g.V * 4 + 4);
     t.ce_off = (uint32_t*)take((size_t)g.V * 4 + 8);
     t.ce_ratio = (float*)take((size_t)g.E * 4 + 4);
     t.ce_hrow = (uint32_t*)take((size_t)g.E * 4 + 4);
-    t.pos_pre = (uint32_t*)take((size_t)g.V * 4 + 8);
+    t.bits = (uint32_t*)take(gall_bits_words(g) * 4);
     if (s) *s = t;
     return (off + 255) & ~size_t(255);
 }
@@ -132,9 +161,9 @@ __global__ void k_ctx_bounds(const uint32_t* key_ctx, const uint64_t* n_keys, ui
     }
 }
 
-// the look-back of the fused leaves, over contexts: publish this context's
-// row count, add up the counts before it until a published inclusive prefix
-// (context 0 publishes one at once); bounded waits
+// look-back over contexts: publish this context's row count, add up the
+// counts before it until a published inclusive prefix (context 0 publishes
+// one at once); bounded waits
 constexpr unsigned long long GL_AGG = 1ull << 62, GL_INCL = 1ull << 63, GL_VAL = (1ull << 62) - 1;
 
 __device__ unsigned long long ctx_lookback(unsigned long long* look, uint32_t c, unsigned long long cnt,
@@ -186,13 +215,15 @@ __device__ __forceinline__ void df_from_u64(unsigned long long x, float& hi, flo
     lo = __ll2float_rn(r);
 }
 
-// weight of call site e after steps 2 and 3 (external edges only)
-__device__ __forceinline__ unsigned long long w2_of(const DevCallGraph& g, const GallSlot& T, uint32_t e) {
-    const unsigned long long w = T.wmeas[e];
-    if (w) return w;
-    const uint32_t f = g.cs_callee[e];
-    if (T.flags[f] & GF_Z) return 1ull;
-    return (T.flags[g.cnode_of_func[f]] & GC_Z2) ? 1ull : 0ull;
+__device__ __forceinline__ bool bit_get(const uint32_t* b, uint32_t i) { return (b[i >> 5] >> (i & 31)) & 1u; }
+// sets bit i; true if it was already set
+__device__ __forceinline__ bool bit_set(uint32_t* b, uint32_t i) {
+    const uint32_t m = 1u << (i & 31);
+    return (atomicOr(&b[i >> 5], m) & m) != 0;
+}
+// row of node v: nodes of nonzero inclusive cost before it in id order
+__device__ __forceinline__ uint32_t node_rank(const GallBits& B, uint32_t v) {
+    return B.npre[v >> 5] + __popc(B.clos[v >> 5] & ((1u << (v & 31)) - 1u));
 }
 
 // zero incoming weight before FIXUP2 (measured weights and the step-2 closure)
@@ -205,27 +236,15 @@ __device__ __forceinline__ bool w_zero_step2(const DevCallGraph& g, const GallSl
     return true;
 }
 
-// Block-wide exclusive prefix counts of pred over the items [0, n), in id
-// order: each thread takes a contiguous chunk; put(i, prefix) for every item
-// (all = true) or only for the items satisfying pred.  Returns the count.
-template <bool ALL, typename P, typename PUT>
-__device__ uint32_t block_prefix(uint32_t n, P pred, PUT put, uint32_t* sw) {
-    const uint32_t per = (n + GALL_THREADS - 1) / GALL_THREADS;
-    const uint32_t a = min(n, threadIdx.x * per), b = min(n, a + per);
-    uint32_t c = 0;
-    for (uint32_t i = a; i < b; ++i) c += pred(i) ? 1u : 0u;
-    uint32_t tot;
-    uint32_t r = block_exclusive_scan<uint32_t, GALL_THREADS>(c, sw, &tot);
-    for (uint32_t i = a; i < b; ++i) {
-        const bool p = pred(i);
-        if (ALL || p) put(i, r);
-        r += p ? 1u : 0u;
-    }
-    return tot;
+// weight of external call site e after steps 2 and 3
+__device__ __forceinline__ unsigned long long w2_of(const GallSlot& T, const GallBits& B, uint32_t e) {
+    const unsigned long long w = T.wmeas[e];
+    return w ? w : (bit_get(B.wpos, e) ? 1ull : 0ull);
 }
 
 // Block-wide exclusive prefix sums of cnt(i) over the items [0, n), in id
-// order: put(i, sum of cnt over the items before i).  Returns the total.
+// order (each thread a contiguous chunk): put(i, sum of cnt over the items
+// before i).  Returns the total.
 template <typename CNT, typename PUT>
 __device__ uint32_t block_prefix_sum(uint32_t n, CNT cnt, PUT put, uint32_t* sw) {
     const uint32_t per = (n + GALL_THREADS - 1) / GALL_THREADS;
@@ -241,18 +260,35 @@ __device__ uint32_t block_prefix_sum(uint32_t n, CNT cnt, PUT put, uint32_t* sw)
     return tot;
 }
 
+// Level-synchronous breadth-first processing of a queue: q[0, *s_n) holds the
+// first level (set before the call); visit(x, push) may append with push(y).
+template <typename VISIT>
+__device__ void block_bfs(uint32_t* q, uint32_t* s_n, VISIT visit) {
+    uint32_t lo = 0;
+    for (;;) {
+        __syncthreads();
+        const uint32_t hi = *s_n;
+        __syncthreads();                       // every thread has read *s_n before anyone pushes
+        if (hi == lo) break;
+        for (uint32_t k = lo + threadIdx.x; k < hi; k += GALL_THREADS)
+            visit(q[k], [&](uint32_t y) { q[atomicAdd(s_n, 1u)] = y; });
+        lo = hi;
+    }
+}
+
 __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallArgs A) {
     const DevCallGraph& g = A.g;
+    extern __shared__ __align__(16) uint32_t gsm[];
     __shared__ uint32_t sw[33];
-    __shared__ uint32_t s_c, s_cnt[2], s_ntouch;
+    __shared__ uint32_t s_c, s_ntouch, s_nhas, s_nz, s_nneed, s_nz2, s_nexcl, s_nclos;
     __shared__ unsigned long long s_nbase, s_ebase;
     GallSlot T;
     gall_layout(g, A.S, A.slots + (size_t)blockIdx.x * A.slot_bytes, &T);
+    const GallBits B = gall_bits(g, A.smem_bits ? gsm : T.bits);
     const uint32_t tid = threadIdx.x;
     const uint32_t S = A.S, M = A.M;
     const uint32_t limit = A.timeout_iters ? A.timeout_iters : (1u << 22);
     const hpa_gpucct_all& O = A.out;
-    const uint32_t n_pos = g.level_off[g.n_levels];     // live condensed nodes, in level order
     // every slot starts with no touched call site
     for (uint32_t e = tid; e < g.E; e += GALL_THREADS) T.wmeas[e] = 0;
     __syncthreads();
@@ -266,7 +302,8 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
         if (k1 > k0) {
             // ---- step 1
             for (uint32_t v = tid; v < g.V; v += GALL_THREADS) T.flags[v] = 0;
-            if (tid == 0) s_ntouch = 0;
+            for (uint32_t i = tid; i < 2 * B.we + B.wv; i += GALL_THREADS) B.wpos[i] = 0;   // wpos, erow, clos
+            if (tid == 0) { s_ntouch = 0; s_nhas = 0; s_nz = 0; s_nneed = 0; s_nz2 = 0; s_nexcl = 0; s_nclos = 0; }
             __syncthreads();
             for (uint64_t i = k0 + tid; i < k1; i += GALL_THREADS) {
                 const uint32_t n = A.key_node[i];
@@ -276,17 +313,21 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                 const unsigned long long v = A.key_val[i];
                 if (!v) continue;
                 const uint32_t f = g.node_func[n];
-                atomicOr(&T.flags[f], GF_HAS);
-                atomicOr(&T.flags[g.cnode_of_func[f]], GC_EXCL);
+                if (!(atomicOr(&T.flags[f], GF_HAS) & GF_HAS)) T.q_has[atomicAdd(&s_nhas, 1u)] = f;
+                const uint32_t cv = g.cnode_of_func[f];
+                if (!(atomicOr(&T.flags[cv], GC_EXCL) & GC_EXCL)) T.q_excl[atomicAdd(&s_nexcl, 1u)] = cv;
                 const uint32_t e = g.node_cs[n];
                 if (e != UNKNOWN && atomicAdd(&T.wmeas[e], v) == 0ull) T.touched[atomicAdd(&s_ntouch, 1u)] = e;
             }
             __syncthreads();
-            const uint32_t ntouch = s_ntouch;
-            for (uint32_t v = tid; v < g.V; v += GALL_THREADS)
-                if (T.flags[v] & GC_EXCL)
-                    for (uint32_t r = 0; r < S; ++r) T.excl[(size_t)v * S + r] = 0;
-            for (uint32_t t = tid; t < ntouch; t += GALL_THREADS) atomicOr(&T.flags[g.cs_callee[T.touched[t]]], GF_MEAS);
+            const uint32_t ntouch = s_ntouch, nhas = s_nhas, nexcl = s_nexcl;
+            for (uint32_t k = tid; k < nexcl; k += GALL_THREADS)
+                for (uint32_t r = 0; r < S; ++r) T.excl[(size_t)T.q_excl[k] * S + r] = 0;
+            for (uint32_t t = tid; t < ntouch; t += GALL_THREADS) {
+                const uint32_t e = T.touched[t];
+                atomicOr(&T.flags[g.cs_callee[e]], GF_MEAS);
+                if (!g.edge_intra[e]) bit_set(B.wpos, e);
+            }
             __syncthreads();
             for (uint64_t i = k0 + tid; i < k1; i += GALL_THREADS) {
                 const uint32_t n = A.key_node[i];
@@ -295,94 +336,77 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                 atomicAdd(&T.excl[(size_t)g.cnode_of_func[g.node_func[n]] * S + r], (unsigned long long)A.key_val[i]);
             }
             // ---- step 2: zero-weight fix-up, closure through callers
-            if (tid == 0) s_cnt[0] = 0;
-            __syncthreads();
-            for (uint32_t f = tid; f < g.F; f += GALL_THREADS) {
-                const uint32_t fl = T.flags[f];
-                if ((fl & GF_HAS) && !(fl & GF_MEAS) && g.fin_off[f + 1] > g.fin_off[f]) {
-                    atomicOr(&T.flags[f], GF_Z);
-                    T.front[0][atomicAdd(&s_cnt[0], 1u)] = f;
-                }
+            for (uint32_t k = tid; k < nhas; k += GALL_THREADS) {
+                const uint32_t f = T.q_has[k];
+                if (!(T.flags[f] & GF_MEAS) && g.fin_off[f + 1] > g.fin_off[f] &&
+                    !(atomicOr(&T.flags[f], GF_Z) & GF_Z))
+                    T.q_z[atomicAdd(&s_nz, 1u)] = f;
             }
-            __syncthreads();
-            int cur = 0;
-            for (;;) {
-                const uint32_t cnt = s_cnt[cur];
-                if (cnt == 0) break;
-                if (tid == 0) s_cnt[cur ^ 1] = 0;
-                __syncthreads();
-                for (uint32_t k = tid; k < cnt; k += GALL_THREADS) {
-                    const uint32_t f = T.front[cur][k];
-                    for (uint32_t j = g.fin_off[f]; j < g.fin_off[f + 1]; ++j) {
-                        const uint32_t h = g.cs_caller[g.fin_edge[j]];
-                        if (g.fin_off[h + 1] > g.fin_off[h] && !(T.flags[h] & GF_MEAS) &&
-                            !(atomicOr(&T.flags[h], GF_Z) & GF_Z))
-                            T.front[cur ^ 1][atomicAdd(&s_cnt[cur ^ 1], 1u)] = h;
-                    }
+            block_bfs(T.q_z, &s_nz, [&](uint32_t f, auto push) {
+                for (uint32_t j = g.fin_off[f]; j < g.fin_off[f + 1]; ++j) {
+                    const uint32_t e = g.fin_edge[j];
+                    if (!g.edge_intra[e]) bit_set(B.wpos, e);           // weight 1 (FIXUP)
+                    const uint32_t h = g.cs_caller[e];
+                    if (g.fin_off[h + 1] > g.fin_off[h] && !(T.flags[h] & GF_MEAS) &&
+                        !(atomicOr(&T.flags[h], GF_Z) & GF_Z))
+                        push(h);
                 }
-                __syncthreads();
-                cur ^= 1;
-            }
+            });
             // ---- step 3: FIXUP2 on the condensed graph
-            for (uint32_t f = tid; f < g.F; f += GALL_THREADS)
-                if (T.flags[f] & (GF_HAS | GF_Z)) atomicOr(&T.flags[g.cnode_of_func[f]], GC_NEED);
-            if (tid == 0) s_cnt[0] = 0;
-            __syncthreads();
-            for (uint32_t v = tid; v < g.V; v += GALL_THREADS)
-                if (g.cnode_live[v] && (T.flags[v] & GC_NEED) && g.cin_off[v + 1] > g.cin_off[v] &&
-                    w_zero_step2(g, T, v)) {
-                    atomicOr(&T.flags[v], GC_Z2);
-                    T.front[0][atomicAdd(&s_cnt[0], 1u)] = v;
-                }
-            __syncthreads();
-            cur = 0;
-            for (;;) {
-                const uint32_t cnt = s_cnt[cur];
-                if (cnt == 0) break;
-                if (tid == 0) s_cnt[cur ^ 1] = 0;
-                __syncthreads();
-                for (uint32_t k = tid; k < cnt; k += GALL_THREADS) {
-                    const uint32_t v = T.front[cur][k];
-                    for (uint32_t j = g.cin_off[v]; j < g.cin_off[v + 1]; ++j) {
-                        const uint32_t u = g.cnode_of_func[g.cs_caller[g.cin_edge[j]]];
-                        if (g.cin_off[u + 1] > g.cin_off[u] && !(T.flags[u] & GC_Z2) && w_zero_step2(g, T, u) &&
-                            !(atomicOr(&T.flags[u], GC_Z2) & GC_Z2))
-                            T.front[cur ^ 1][atomicAdd(&s_cnt[cur ^ 1], 1u)] = u;
-                    }
-                }
-                __syncthreads();
-                cur ^= 1;
+            const uint32_t nz = s_nz;
+            for (uint32_t k = tid; k < nhas + nz; k += GALL_THREADS) {
+                const uint32_t cv = g.cnode_of_func[k < nhas ? T.q_has[k] : T.q_z[k - nhas]];
+                if (!(atomicOr(&T.flags[cv], GC_NEED) & GC_NEED)) T.q_need[atomicAdd(&s_nneed, 1u)] = cv;
             }
-            // ---- call sites of nonzero weight (by id and in cout order)
-            for (uint32_t e = tid; e < g.E; e += GALL_THREADS)
-                T.wpos[e] = (!g.edge_intra[e] && w2_of(g, T, e)) ? 1 : 0;
             __syncthreads();
-            for (uint32_t j = tid; j < g.cout_off[g.V]; j += GALL_THREADS) T.wpos_c[j] = T.wpos[g.cout_edge[j]];
-            __syncthreads();
-            // ---- nodes with nonzero inclusive cost, level by level (sinks first)
-            for (uint32_t lev = 0; lev < g.n_levels; ++lev) {
-                for (uint32_t k = g.level_off[lev] + tid; k < g.level_off[lev + 1]; k += GALL_THREADS) {
-                    const uint32_t v = g.level_node[k];
-                    bool clos = (T.flags[v] & GC_EXCL) != 0;
-                    for (uint32_t j = g.cout_off[v]; !clos && j < g.cout_off[v + 1]; ++j)
-                        clos = T.wpos_c[j] && (T.flags[g.cout_head[j]] & GC_CLOS);
-                    if (clos) atomicOr(&T.flags[v], GC_CLOS);
-                }
-                __syncthreads();
+            const uint32_t nneed = s_nneed;
+            for (uint32_t k = tid; k < nneed; k += GALL_THREADS) {
+                const uint32_t v = T.q_need[k];
+                if (g.cin_off[v + 1] > g.cin_off[v] && w_zero_step2(g, T, v) && !(atomicOr(&T.flags[v], GC_Z2) & GC_Z2))
+                    T.q_z2[atomicAdd(&s_nz2, 1u)] = v;
             }
-            // ---- rows: nodes and call sites in id order, incoming weights
-            auto node_row = [&](uint32_t v) { return g.cnode_live[v] && (T.flags[v] & GC_CLOS); };
-            n_rows = block_prefix<false>(g.V, node_row, [&](uint32_t v, uint32_t r) { T.rowmap[v] = r; }, sw);
-            auto edge_row = [&](uint32_t e) {
-                return T.wpos[e] && (T.flags[g.cnode_of_func[g.cs_callee[e]]] & GC_CLOS);
-            };
-            n_edges = block_prefix<false>(g.E, edge_row, [](uint32_t, uint32_t) {}, sw);
-            for (uint32_t v = tid; v < g.V; v += GALL_THREADS)
-                if (node_row(v)) {
-                    unsigned long long W = 0;
-                    for (uint32_t j = g.cin_off[v]; j < g.cin_off[v + 1]; ++j) W += w2_of(g, T, g.cin_edge[j]);
-                    T.Wc[v] = W;
+            block_bfs(T.q_z2, &s_nz2, [&](uint32_t v, auto push) {
+                for (uint32_t j = g.cin_off[v]; j < g.cin_off[v + 1]; ++j) {
+                    const uint32_t e = g.cin_edge[j];
+                    bit_set(B.wpos, e);                                  // weight 1 (FIXUP2)
+                    const uint32_t u = g.cnode_of_func[g.cs_caller[e]];
+                    if (g.cin_off[u + 1] > g.cin_off[u] && !(T.flags[u] & GC_Z2) && w_zero_step2(g, T, u) &&
+                        !(atomicOr(&T.flags[u], GC_Z2) & GC_Z2))
+                        push(u);
                 }
+            });
+            // ---- nodes of nonzero inclusive cost: upward from the nodes with
+            // samples through call sites of nonzero weight; on the way each
+            // node's incoming weight, its call sites' ratios and row bits
+            for (uint32_t k = tid; k < nexcl; k += GALL_THREADS) {
+                const uint32_t v = T.q_excl[k];
+                bit_set(B.clos, v);
+                T.q_clos[k] = v;
+            }
+            if (tid == 0) s_nclos = nexcl;
+            block_bfs(T.q_clos, &s_nclos, [&](uint32_t v, auto push) {
+                unsigned long long W = 0;
+                for (uint32_t j = g.cin_off[v]; j < g.cin_off[v + 1]; ++j) W += w2_of(T, B, g.cin_edge[j]);
+                if (!W) return;
+                const float Wf = __ull2float_rn(W);
+                for (uint32_t j = g.cin_off[v]; j < g.cin_off[v + 1]; ++j) {
+                    const uint32_t e = g.cin_edge[j];
+                    const unsigned long long w = w2_of(T, B, e);
+                    if (!w) continue;
+                    T.ratio[e] = __fdiv_rn(__ull2float_rn(w), Wf);   // correctly rounded below 2^24
+                    bit_set(B.erow, e);
+                    const uint32_t u = g.cnode_of_func[g.cs_caller[e]];
+                    if (!bit_set(B.clos, u)) push(u);
+                }
+            });
+            // ---- row counts and the node rows' popcount prefix
+            n_rows = block_prefix_sum(B.wv, [&](uint32_t i) -> uint32_t { return __popc(B.clos[i]); },
+                                      [&](uint32_t i, uint32_t r) { B.npre[i] = r; }, sw);
+            uint32_t ne = 0;
+            for (uint32_t i = tid; i < B.we; i += GALL_THREADS) ne += __popc(B.erow[i]);
+            uint32_t tot;
+            block_exclusive_scan<uint32_t, GALL_THREADS>(ne, sw, &tot);
+            n_edges = tot;
         }
         // ---- offsets of this context's rows
         if (tid == 0) {
@@ -405,58 +429,71 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
         }
         const bool fits = k1 > k0 && nb + n_rows <= O.cap_nodes && eb + n_edges <= O.cap_edges;
         if (fits) {
-            // ---- node and edge rows
-            for (uint32_t v = tid; v < g.V; v += GALL_THREADS)
-                if (g.cnode_live[v] && (T.flags[v] & GC_CLOS)) O.node_id[nb + T.rowmap[v]] = v;
-            auto edge_row = [&](uint32_t e) {
-                return T.wpos[e] && (T.flags[g.cnode_of_func[g.cs_callee[e]]] & GC_CLOS);
-            };
-            block_prefix<false>(g.E, edge_row,
-                                [&](uint32_t e, uint32_t r) {
-                                    const uint32_t f = g.cs_callee[e], h = g.cnode_of_func[f];
-                                    const unsigned long long w = w2_of(g, T, e), W = T.Wc[h];
-                                    const float q = __fdiv_rn(__ull2float_rn(w), __ull2float_rn(W));
-                                    T.ratio[e] = q;
-                                    O.edge_id[eb + r] = e;
-                                    O.ratio[eb + r] = q;
-                                    uint8_t fl = 0;
-                                    if (T.flags[f] & GF_Z) fl |= HPA_EDGE_FIXUP;
-                                    if (T.flags[h] & GC_Z2) fl |= HPA_EDGE_FIXUP2;
-                                    O.flags[eb + r] = fl;
-                                },
-                                sw);
-            // ---- sweep lists: nonzero nodes in level order, their active out-edges
-            const uint32_t n_cl = block_prefix<true>(
-                n_pos, [&](uint32_t k) { return (T.flags[g.level_node[k]] & GC_CLOS) != 0; },
-                [&](uint32_t k, uint32_t r) {
-                    T.pos_pre[k] = r;
-                    const uint32_t v = g.level_node[k];
-                    if (T.flags[v] & GC_CLOS) T.cl_node[r] = v;
-                },
-                sw);
-            if (tid == 0) T.pos_pre[n_pos] = n_cl;
+            // ---- node rows (bitmap order = id order)
+            for (uint32_t i = tid; i < B.wv; i += GALL_THREADS) {
+                uint32_t m = B.clos[i], r = B.npre[i];
+                while (m) {
+                    const uint32_t b = __ffs(m) - 1;
+                    m &= m - 1;
+                    O.node_id[nb + r++] = i * 32 + b;
+                }
+            }
+            // ---- call-site rows in id order
+            block_prefix_sum(B.we, [&](uint32_t i) -> uint32_t { return __popc(B.erow[i]); },
+                             [&](uint32_t i, uint32_t r) {
+                                 uint32_t m = B.erow[i];
+                                 while (m) {
+                                     const uint32_t b = __ffs(m) - 1;
+                                     m &= m - 1;
+                                     const uint32_t e = i * 32 + b, f = g.cs_callee[e], h = g.cs_head[e];
+                                     O.edge_id[eb + r] = e;
+                                     O.ratio[eb + r] = T.ratio[e];
+                                     uint8_t fl = 0;
+                                     if (T.flags[f] & GF_Z) fl |= HPA_EDGE_FIXUP;
+                                     if (T.flags[h] & GC_Z2) fl |= HPA_EDGE_FIXUP2;
+                                     O.flags[eb + r] = fl;
+                                     ++r;
+                                 }
+                             },
+                             sw);
+            // ---- sweep lists: the nodes bucketed by level, their active out-edges
+            for (uint32_t l = tid; l <= g.n_levels; l += GALL_THREADS) B.lev[l] = 0;
             __syncthreads();
-            for (uint32_t lev = tid; lev <= g.n_levels; lev += GALL_THREADS) T.cl_off[lev] = T.pos_pre[g.level_off[lev]];
+            const uint32_t ncl = n_rows;
+            for (uint32_t k = tid; k < ncl; k += GALL_THREADS) atomicAdd(&B.lev[g.level_of[T.q_clos[k]]], 1u);
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t run = 0;
+                for (uint32_t l = 0; l <= g.n_levels; ++l) { const uint32_t x = B.lev[l]; B.lev[l] = run; run += x; }
+            }
+            __syncthreads();
+            for (uint32_t k = tid; k < ncl; k += GALL_THREADS) {
+                const uint32_t v = T.q_clos[k];
+                const uint32_t p = atomicAdd(&B.lev[g.level_of[v]], 1u);
+                T.cl_node[p] = v;
+                T.cl_row[p] = node_rank(B, v);
+            }
+            __syncthreads();
+            // (B.lev[l] now holds the end of level l, which is where level l + 1 starts)
             const uint32_t n_ce = block_prefix_sum(
-                n_cl,
+                ncl,
                 [&](uint32_t k) -> uint32_t {
                     const uint32_t v = T.cl_node[k];
                     uint32_t a = 0;
-                    for (uint32_t j = g.cout_off[v]; j < g.cout_off[v + 1]; ++j)
-                        a += (T.wpos_c[j] && (T.flags[g.cout_head[j]] & GC_CLOS)) ? 1u : 0u;
+                    for (uint32_t j = g.cout_off[v]; j < g.cout_off[v + 1]; ++j) a += bit_get(B.erow, g.cout_edge[j]);
                     return a;
                 },
                 [&](uint32_t k, uint32_t r) { T.ce_off[k] = r; }, sw);
-            if (tid == 0) T.ce_off[n_cl] = n_ce;
+            if (tid == 0) T.ce_off[ncl] = n_ce;
             __syncthreads();
-            for (uint32_t k = tid; k < n_cl; k += GALL_THREADS) {
+            for (uint32_t k = tid; k < ncl; k += GALL_THREADS) {
                 const uint32_t v = T.cl_node[k];
                 uint32_t o = T.ce_off[k];
                 for (uint32_t j = g.cout_off[v]; j < g.cout_off[v + 1]; ++j) {
-                    const uint32_t hd = g.cout_head[j];
-                    if (T.wpos_c[j] && (T.flags[hd] & GC_CLOS)) {
-                        T.ce_ratio[o] = T.ratio[g.cout_edge[j]];
-                        T.ce_hrow[o] = T.rowmap[hd];
+                    const uint32_t e = g.cout_edge[j];
+                    if (bit_get(B.erow, e)) {
+                        T.ce_ratio[o] = T.ratio[e];
+                        T.ce_hrow[o] = node_rank(B, g.cout_head[j]);
                         ++o;
                     }
                 }
@@ -465,7 +502,7 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
             // ---- step 4: level by level, one thread per (node, stall column)
             float* incl = O.incl + (size_t)nb * M;
             for (uint32_t lev = 0; lev < g.n_levels; ++lev) {
-                const uint32_t c0 = T.cl_off[lev], nk = T.cl_off[lev + 1] - c0;
+                const uint32_t c0 = lev ? B.lev[lev - 1] : 0u, nk = B.lev[lev] - c0;
                 for (uint32_t it = tid; it < nk * M; it += GALL_THREADS) {
                     const uint32_t k = c0 + it / M, r = it % M;
                     const uint32_t v = T.cl_node[k];
@@ -490,7 +527,7 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                         for (int u = 0; u < 4; ++u)
                             if (j + u < e1) df_add_prod(hi, lo, q[u], x[u]);
                     }
-                    incl[(size_t)T.rowmap[v] * M + r] = __fadd_rn(hi, lo);
+                    incl[(size_t)T.cl_row[k] * M + r] = __fadd_rn(hi, lo);
                 }
                 __syncthreads();
             }
@@ -499,8 +536,7 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                 for (uint64_t it = tid; it < (uint64_t)n_edges * M; it += GALL_THREADS) {
                     const uint32_t row = (uint32_t)(it / M), r = (uint32_t)(it % M);
                     const uint32_t e = O.edge_id[eb + row];
-                    const uint32_t hd = g.cnode_of_func[g.cs_callee[e]];
-                    O.a[(eb + row) * M + r] = __fmul_rn(T.ratio[e], incl[(size_t)T.rowmap[hd] * M + r]);
+                    O.a[(eb + row) * M + r] = __fmul_rn(T.ratio[e], incl[(size_t)node_rank(B, g.cs_head[e]) * M + r]);
                 }
             }
         }
@@ -543,6 +579,8 @@ extern "C" hpa_status hpa_apportion_all(hpa_handle* h, uint32_t binary_id, const
     A.timeout_iters = h->opt.timeout_iters;
     A.status = h->d_status;
     A.slot_bytes = gall_layout(g, A.S, nullptr, nullptr);
+    const size_t bits_bytes = gall_bits_words(g) * 4;
+    A.smem_bits = bits_bytes <= GALL_SMEM_MAX ? 1u : 0u;
     const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(p->n_ctx, (uint32_t)h->sms * GALL_PER_SM));
     // scratch: per-CTA slots, then context starts, look-back words and the ticket
     Carve probe{nullptr};
@@ -566,7 +604,9 @@ extern "C" hpa_status hpa_apportion_all(hpa_handle* h, uint32_t binary_id, const
     cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), s);
     const int bb = (int)std::max<uint64_t>(1, std::min<uint64_t>((p->capacity + 256) / 256, (uint64_t)h->sms * 8));
     k_ctx_bounds<<<bb, 256, 0, s>>>(p->key_ctx, p->n_keys, p->capacity, p->n_ctx, start);
-    k_gpucct_all<<<grid, GALL_THREADS, 0, s>>>(A);
+    const size_t dsm = A.smem_bits ? bits_bytes : 0;
+    if (dsm) set_smem_limit((const void*)k_gpucct_all, (int)dsm);
+    k_gpucct_all<<<grid, GALL_THREADS, dsm, s>>>(A);
     h->launches += 2;
     return h->cuda(cudaGetLastError(), "apportion (every context) launch");
 }

@@ -501,7 +501,7 @@ extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary
 // Scratch layout of one aggregation over N records in G groups (n_buf buffers).
 hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n, uint32_t cap, uint32_t sb,
                                   uint32_t sbits, bool has_cnt, bool val64, uint64_t staged, uint64_t cnt_words,
-                                  uint64_t seg_words, uint64_t cnt2_words) {
+                                  uint64_t seg_words, uint64_t cnt2_words, bool narrow_tmp) {
     const uint64_t N2 = std::max(N, staged);   // the second record buffer also stages samples in tile order
     const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
     w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
@@ -538,6 +538,8 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
         w.rec2_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
         w.tmp_key = c.take<uint32_t>(N + 1);
         w.tmp_val = c.take<uint64_t>(N + 1);
+        w.tmp_v32 = narrow_tmp ? c.take<uint32_t>(N + 1) : nullptr;
+        w.leaf_wide = narrow_tmp ? c.take<uint8_t>(L_max + 1) : nullptr;
         w.part_cnt = cnt_words ? c.take<uint32_t>(cnt_words) : nullptr;
         w.seg_chunk = seg_words ? c.take<uint32_t>(seg_words) : nullptr;
         w.cnt2 = cnt2_words ? c.take<uint32_t>(cnt2_words) : nullptr;
@@ -649,7 +651,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     }
     AggWork w0{};
     hpa_status st = carve_work(w0, N_max, G_max, n_max, cap_min, sb, sbits_max, has_cnt, false, staged_max,
-                               cnt_words_max, seg_words_max, cnt2_words_max);
+                               cnt_words_max, seg_words_max, cnt2_words_max, true);
     if (st) return st;
 
     // descriptors: every buffer's BufDev, then per sub-batch its prefix arrays
@@ -810,11 +812,21 @@ hpa_status hpa_handle::launch_graph(const std::vector<AggWork>& ws, size_t stage
     return st;
 }
 
+// A call with the shape of the call before it (binary, samples, contexts,
+// stall reasons, counts or not) replays a captured CUDA graph of the whole
+// pipeline (cached per shape, as for batches): repeated calls on buffers of
+// one size then pay neither the host's launches nor their gaps.  A call of a
+// new shape runs kernel by kernel, so sizes that change from call to call
+// never pay for a capture.
 extern "C" hpa_status hpa_attribute_samples(hpa_handle* h, uint32_t binary_id, const hpa_samples* in, hpa_profile* out) {
     hpa::Trace trace_("hpa.attribute_samples");
     if (!h || !in || !out) return HPA_E_INVALID_ARG;
     cudaSetDevice(h->device);
-    return h->aggregate(1, &binary_id, in, out);
+    uint64_t shape = mix64(mix64(mix64(0x5EEDull, binary_id), in->n), in->n_ctx);
+    shape = mix64(mix64(shape, in->n_stall), in->count ? 1u : 0u);
+    const bool repeat = shape == h->last_plain_shape && !h->capturing();
+    h->last_plain_shape = shape;
+    return h->aggregate(1, &binary_id, in, out, repeat);
 }
 
 // every buffer of the call in one captured CUDA graph (cached per batch shape)

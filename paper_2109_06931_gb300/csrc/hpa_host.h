@@ -41,6 +41,8 @@ struct DevCallGraph {
     const uint32_t* level_node;
     const uint8_t* edge_intra;   // [E] 1 if the edge lies inside one SCC
     const uint8_t* cnode_live;   // [V] 0 for rows of functions inside a non-trivial SCC
+    const uint32_t* cs_head;     // [E] condensed node of each call site's callee
+    const uint32_t* level_of;    // [V] level (height) of each live condensed node
 };
 
 struct Binary {
@@ -127,6 +129,7 @@ struct hpa_handle {
     struct Copy { void* dst; const void* src; size_t bytes; };
     hpa_status copies(const Copy* c, int n, cudaMemcpyKind kind);
     uint64_t graph_replays = 0;
+    uint64_t last_plain_shape = 0;   // shape of the previous hpa_attribute_samples call
     void* cct_scratch = nullptr;
     size_t cct_cap = 0;
     void* aux_scratch = nullptr;  // intermediate keys of analyses built on the aggregation
@@ -157,7 +160,8 @@ struct hpa_handle {
                           uint32_t sbits, bool has_cnt, bool val64, uint64_t staged = 0,
                           uint64_t cnt_words = 0,    // part counters incl. the scan total (0: none)
                           uint64_t seg_words = 0,    // bucket segments + 2 (two-level partition; 0: none)
-                          uint64_t cnt2_words = 0);  // second-pass counters incl. the scan total
+                          uint64_t cnt2_words = 0,   // second-pass counters incl. the scan total
+                          bool narrow_tmp = false);  // 32-bit leaf sums where they fit (tmp_v32)
     // descriptors of single-output pipelines (expansion, union) in the staging area
     hpa_status stage_single_output(hpa::AggWork& w, uint32_t bin, uint32_t n_ctx, const hpa_profile& out);
 };

@@ -75,6 +75,8 @@ struct AggWork {
     uint2* rec2_pair;      // [N]
     uint32_t* tmp_key;     // [N]
     uint64_t* tmp_val;     // [N]
+    uint32_t* tmp_v32;     // [N] 32-bit sums of leaves whose sums all stay below 2^32 (may be null)
+    uint8_t* leaf_wide;    // [L_max] 1: the leaf's sums are in tmp_val, 0: in tmp_v32
     uint32_t* scan_tmp;    // device-wide scan partials
     const BufDev* bufs;    // [n_buf]
     const uint64_t* buf_tile;     // [n_buf + 1] tile prefix
@@ -147,10 +149,11 @@ constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_EPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_EPT;
 
-// Raise the dynamic shared-memory limit of kernel `fn` to `bytes` on the
-// current device.  The attribute belongs to one device, so it is set once per
-// (kernel, device) and remembered under a lock (calls may come from several
-// host threads and handles on several devices).
+// Raise the dynamic shared-memory limit of kernel `fn` to at least `bytes`
+// on the current device.  The attribute belongs to one device; the largest
+// limit set per (kernel, device) is remembered under a lock (calls may come
+// from several host threads and handles on several devices), and a limit is
+// never lowered, so launches of any smaller size stay valid.
 void set_smem_limit(const void* fn, int bytes);
 
 // device-wide exclusive scan of n uint32 values (in place allowed);
