@@ -901,7 +901,6 @@ __global__ void __launch_bounds__(256) k_emit(AggWork w) {
         const uint32_t g0 = w.leaf_grp0[l];
         const uint64_t o0 = (uint64_t)leaf_out[l] - leaf_out[w.buf_first_leaf[b]];
         const uint32_t gctx0 = g0 - B.grp_base;
-        const bool narrow = w.tmp_v32 && !w.leaf_wide[l];        // 32-bit sums in tmp_v32
         // EMIT_U keys per thread loaded before any is processed: more bytes in flight
         for (uint32_t i0 = tid; i0 < d; i0 += EMIT_U * 256) {
             uint32_t kk[EMIT_U];
@@ -911,8 +910,7 @@ __global__ void __launch_bounds__(256) k_emit(AggWork w) {
                 const uint32_t i = i0 + u * 256;
                 if (i < d) {
                     kk[u] = __ldcs(&w.tmp_key[start + i]);
-                    vv[u] = narrow ? (unsigned long long)__ldcs(&w.tmp_v32[start + i])
-                                   : __ldcs((const unsigned long long*)&w.tmp_val[start + i]);
+                    vv[u] = __ldcs((const unsigned long long*)&w.tmp_val[start + i]);
                 }
             }
 #pragma unroll

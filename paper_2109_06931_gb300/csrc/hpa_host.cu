@@ -501,7 +501,7 @@ extern "C" hpa_status hpa_binary_info_get(hpa_handle* h, uint32_t id, hpa_binary
 // Scratch layout of one aggregation over N records in G groups (n_buf buffers).
 hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n, uint32_t cap, uint32_t sb,
                                   uint32_t sbits, bool has_cnt, bool val64, uint64_t staged, uint64_t cnt_words,
-                                  uint64_t seg_words, uint64_t cnt2_words, bool narrow_tmp) {
+                                  uint64_t seg_words, uint64_t cnt2_words) {
     const uint64_t N2 = std::max(N, staged);   // the second record buffer also stages samples in tile order
     const uint64_t L_max = G + 6 * (N / cap + 1) + n + 8;   // items + sub-bins of big groups
     w.G = (uint32_t)G; w.n_buf = n; w.cap = cap; w.q = cap / 2; w.sb = sb; w.sbits = sbits;
@@ -538,8 +538,6 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
         w.rec2_v64 = val64 ? c.take<uint64_t>(N + 1) : nullptr;
         w.tmp_key = c.take<uint32_t>(N + 1);
         w.tmp_val = c.take<uint64_t>(N + 1);
-        w.tmp_v32 = narrow_tmp ? c.take<uint32_t>(N + 1) : nullptr;
-        w.leaf_wide = narrow_tmp ? c.take<uint8_t>(L_max + 1) : nullptr;
         w.part_cnt = cnt_words ? c.take<uint32_t>(cnt_words) : nullptr;
         w.seg_chunk = seg_words ? c.take<uint32_t>(seg_words) : nullptr;
         w.cnt2 = cnt2_words ? c.take<uint32_t>(cnt2_words) : nullptr;
@@ -651,7 +649,7 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     }
     AggWork w0{};
     hpa_status st = carve_work(w0, N_max, G_max, n_max, cap_min, sb, sbits_max, has_cnt, false, staged_max,
-                               cnt_words_max, seg_words_max, cnt2_words_max, true);
+                               cnt_words_max, seg_words_max, cnt2_words_max);
     if (st) return st;
 
     // descriptors: every buffer's BufDev, then per sub-batch its prefix arrays

@@ -160,8 +160,7 @@ struct hpa_handle {
                           uint32_t sbits, bool has_cnt, bool val64, uint64_t staged = 0,
                           uint64_t cnt_words = 0,    // part counters incl. the scan total (0: none)
                           uint64_t seg_words = 0,    // bucket segments + 2 (two-level partition; 0: none)
-                          uint64_t cnt2_words = 0,   // second-pass counters incl. the scan total
-                          bool narrow_tmp = false);  // 32-bit leaf sums where they fit (tmp_v32)
+                          uint64_t cnt2_words = 0);  // second-pass counters incl. the scan total
     // descriptors of single-output pipelines (expansion, union) in the staging area
     hpa_status stage_single_output(hpa::AggWork& w, uint32_t bin, uint32_t n_ctx, const hpa_profile& out);
 };

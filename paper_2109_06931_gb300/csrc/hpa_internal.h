@@ -75,8 +75,6 @@ struct AggWork {
     uint2* rec2_pair;      // [N]
     uint32_t* tmp_key;     // [N]
     uint64_t* tmp_val;     // [N]
-    uint32_t* tmp_v32;     // [N] 32-bit sums of leaves whose sums all stay below 2^32 (may be null)
-    uint8_t* leaf_wide;    // [L_max] 1: the leaf's sums are in tmp_val, 0: in tmp_v32
     uint32_t* scan_tmp;    // device-wide scan partials
     const BufDev* bufs;    // [n_buf]
     const uint64_t* buf_tile;     // [n_buf + 1] tile prefix

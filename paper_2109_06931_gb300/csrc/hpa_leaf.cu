@@ -10,8 +10,7 @@
 //         falls back to the sort;
 //   dense: a leaf of more than CAP records (one fine bin of a big group, at
 //         most one window of 8192 subkeys wide) is summed in dense windows.
-// Results go to tmp_key / tmp_val (or tmp_v32 when every sum of the leaf is
-// below 2^32, marked in leaf_wide) at the leaf's start, in key order, with
+// Results go to tmp_key / tmp_val at the leaf's start, in key order, with
 // the number of keys in leaf_d -- or, for fused leaves (fuse_emit), straight
 // to the buffer's output arrays at the offset that a look-back over the
 // leaves before it gives, with the per-stall and UNKNOWN totals summed on
@@ -355,7 +354,6 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
         const uint32_t info = w.leaf_info[l];
         const uint32_t n = end - start;
         if (n < n_lo || n > n_hi) continue;               // another leaf kernel's size class
-        if (w.tmp_v32 && threadIdx.x == 0) w.leaf_wide[l] = 1;   // 64-bit values unless set below
         // fused leaves: the buffer's output arrays; keys of a buffer with
         // invalid samples are not written (the call fails as a whole)
         LeafOut lo_{};
@@ -618,11 +616,7 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
             auto put_tmp = [&](bool wr, uint32_t pos, uint32_t k, unsigned long long v) {
                 if (wr) { ok_[pos] = k; ov[pos] = v; }
             };
-            // sums below 2^32 leave 8-byte keys (key, 32-bit value) for k_emit
-            uint32_t* ov32 = w.tmp_v32 ? w.tmp_v32 + start : nullptr;
-            auto put_tmp32 = [&](bool wr, uint32_t pos, uint32_t k, unsigned long long v) {
-                if (wr) { ok_[pos] = k; ov32[pos] = (uint32_t)v; }
-            };
+
             uint32_t n_out;
             if (fuse) {
                 if (!wide)
@@ -634,11 +628,7 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
                 post(n_out);
             } else {
                 auto no_pre = [](uint32_t) {};
-                if (!wide && ov32) {
-                    n_out = leaf_runs<uint32_t, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, no_pre, put_tmp32, s_run0,
-                                                   s_nz, reinterpret_cast<uint32_t*>(s_carry), &s_tot);
-                    if (threadIdx.x == 0) w.leaf_wide[l] = 0;
-                } else if (!wide)
+                if (!wide)
                     n_out = leaf_runs<uint32_t, W>(Kc, Vc, (int)n, w0, w1, s_any_zero != 0, no_pre, put_tmp, s_run0,
                                                    s_nz, reinterpret_cast<uint32_t*>(s_carry), &s_tot);
                 else
