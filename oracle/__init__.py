@@ -80,6 +80,11 @@ def load(path: str):
     L.orc_derive.argtypes = [u32, vp, vp, vp, vp, vp, u32, u32, u32]
     L.orc_issue_by_function.restype = vp
     L.orc_issue_by_function.argtypes = [u32, vp, u32, u32, u64, vp, vp, vp, vp]
+    L.orc_ratio.restype = vp
+    L.orc_ratio.argtypes = [u32, u32, vp, vp, vp, vp, vp]
+    L.orc_ratio_size.restype = u64; L.orc_ratio_size.argtypes = [vp]
+    L.orc_ratio_fetch.argtypes = [vp] * 7
+    L.orc_ratio_free.argtypes = [vp]
     L.orc_issue_status.restype = i32; L.orc_issue_status.argtypes = [vp]
     L.orc_issue_size.restype = u64; L.orc_issue_size.argtypes = [vp]
     L.orc_issue_fetch.argtypes = [vp] * 7
@@ -243,6 +248,33 @@ def issue_by_function(node_func, n_stall: int, keys: KeyList, issued_mask: int =
                   np.empty(n, np.float64), np.empty((n, n_stall), np.float64), st)
     L.orc_issue_fetch(h, _p(r.ctx), _p(r.func), _p(r.S), _p(r.S_issued), _p(r.W), _p(r.frac))
     L.orc_issue_free(h)
+    return r
+
+
+@dataclass
+class RatioRows:
+    ctx: np.ndarray        # uint32[n]
+    node: np.ndarray       # uint32[n]
+    stall: np.ndarray      # uint8[n]
+    num: np.ndarray        # uint64[n]
+    den: np.ndarray        # uint64[n]
+    ratio: np.ndarray      # float64[n] (NaN where den = 0)
+
+
+def ratio(num_profiles, den_profiles) -> RatioRows:
+    """Ratio of two raw metrics, each summed over its group of profiles (Section 4.5)."""
+    L = lib()
+    profiles = list(num_profiles) + list(den_profiles)
+    ks = [[_c(p.ctx, np.uint32), _c(p.node, np.uint32), _c(p.stall, np.uint8), _c(p.val, np.uint64)] for p in profiles]
+    nk = np.array([k[0].shape[0] for k in ks] or [0], np.uint64)
+    ptrs = [np.array([k[j].ctypes.data for k in ks] or [0], np.uint64) for j in range(4)]
+    h = L.orc_ratio(len(num_profiles), len(den_profiles), _p(nk), *[_p(x) for x in ptrs])
+    n = L.orc_ratio_size(h)
+    r = RatioRows(np.empty(n, np.uint32), np.empty(n, np.uint32), np.empty(n, np.uint8), np.empty(n, np.uint64),
+                  np.empty(n, np.uint64), np.empty(n, np.float64))
+    L.orc_ratio_fetch(h, _p(r.ctx), _p(r.node), _p(r.stall), _p(r.num), _p(r.den), _p(r.ratio))
+    L.orc_ratio_free(h)
+    del ks
     return r
 
 

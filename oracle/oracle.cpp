@@ -10,7 +10,9 @@
 //                 it becomes a GPU-instruction node under the kernel's context.
 //   Section 4.5   a raw metric is the sum of all measured values of a kind
 //                 in a context; post-mortem derived metrics are sum, min,
-//                 mean, max, std. deviation and coefficient of variation.
+//                 mean, max, std. deviation and coefficient of variation;
+//                 a per-invocation quantity is the ratio of two summed raw
+//                 metrics.
 //   Section 5     instructions map to lines, loops, inlined code, functions.
 //   Section 6.1   statistic generation propagates values up the calling
 //                 context tree (inclusive metrics).
@@ -292,6 +294,42 @@ void* orc_issue_by_function(uint32_t n_nodes, const uint32_t* node_func, uint32_
         o->S_issued.push_back(issued);
         o->W.push_back((double)issued / (double)S);
         for (uint32_t r = 0; r < n_stall; ++r) o->frac.push_back((double)kv.second[r] / (double)S);
+    }
+    return o;
+}
+
+// O5 ratio of raw metrics (Section 4.5: a quantity known once per kernel
+// invocation, such as its registers, is recovered from two raw metrics that
+// are summed over threads and ranks like any other -- the quantity summed
+// over invocations and the number of invocations -- by dividing the sums).
+// Profiles 0 .. P_num - 1 are the numerator group, the next P_den the
+// denominator group.  Per key (context, node, stall) of the union of both
+// groups: num = the sum of the numerator group's values (0 where absent),
+// den = the same over the denominator group, ratio = num / den (NaN when
+// den = 0).  One row per key, ascending.
+struct RatioRows {
+    std::vector<uint32_t> ctx, node, stall;
+    std::vector<uint64_t> num, den;
+    std::vector<double> ratio;
+};
+
+void* orc_ratio(uint32_t P_num, uint32_t P_den, const uint64_t* nkeys, const uint32_t* const* kctx,
+                const uint32_t* const* knode, const uint8_t* const* kstall, const uint64_t* const* kval) {
+    RatioRows* o = new RatioRows();
+    std::map<Key, std::pair<uint64_t, uint64_t>> u;   // key -> (numerator sum, denominator sum)
+    for (uint32_t p = 0; p < P_num + P_den; ++p)
+        for (uint64_t i = 0; i < nkeys[p]; ++i) {
+            std::pair<uint64_t, uint64_t>& v = u[Key(kctx[p][i], knode[p][i], kstall[p][i])];
+            if (p < P_num) v.first += kval[p][i];
+            else v.second += kval[p][i];
+        }
+    for (auto& kv : u) {
+        o->ctx.push_back(std::get<0>(kv.first));
+        o->node.push_back(std::get<1>(kv.first));
+        o->stall.push_back(std::get<2>(kv.first));
+        o->num.push_back(kv.second.first);
+        o->den.push_back(kv.second.second);
+        o->ratio.push_back(kv.second.second == 0 ? NAN : (double)kv.second.first / (double)kv.second.second);
     }
     return o;
 }
@@ -796,6 +834,21 @@ void orc_derive_fetch(void* p, uint32_t* ctx, uint32_t* node, uint8_t* stall, ui
     for (size_t i = 0; i < d->frac.size(); ++i) frac[i] = d->frac[i];
 }
 void orc_derive_free(void* p) { delete (Derived*)p; }
+
+uint64_t orc_ratio_size(void* p) { return ((RatioRows*)p)->num.size(); }
+void orc_ratio_fetch(void* p, uint32_t* ctx, uint32_t* node, uint8_t* stall, uint64_t* num, uint64_t* den,
+                     double* ratio) {
+    RatioRows* o = (RatioRows*)p;
+    for (size_t i = 0; i < o->num.size(); ++i) {
+        ctx[i] = o->ctx[i];
+        node[i] = o->node[i];
+        stall[i] = (uint8_t)o->stall[i];
+        num[i] = o->num[i];
+        den[i] = o->den[i];
+        ratio[i] = o->ratio[i];
+    }
+}
+void orc_ratio_free(void* p) { delete (RatioRows*)p; }
 
 int orc_issue_status(void* p) { return ((IssueRows*)p)->status; }
 uint64_t orc_issue_size(void* p) { return ((IssueRows*)p)->S.size(); }

@@ -15,6 +15,7 @@ import test_oracle_expand as TX
 import test_oracle_flat as TF
 import test_oracle_inclusive_derive as TI
 import test_oracle_issue as TW
+import test_oracle_ratio as TR
 import test_oracle_sparse as TS
 import test_oracle_unify as TU
 
@@ -67,6 +68,18 @@ MUTATIONS = [
     ("issue-by-function-unknown-as-function", "if (knode[i] == UNKNOWN) continue;\n        if (knode[i] >= n_nodes",
      "if (knode[i] >= n_nodes",
      [lambda o: TW.test_hand_example(o, 0b001, [5 / 8, 2 / 8, 0.0, 1 / 2])]),
+    ("ratio-first-denominator-in-numerator", "if (p < P_num) v.first += kval[p][i];",
+     "if (p <= P_num) v.first += kval[p][i];",
+     [lambda o: TR.test_hand_example(o)]),
+    ("ratio-inverted", "(double)kv.second.first / (double)kv.second.second);",
+     "(double)kv.second.second / (double)kv.second.first);",
+     [lambda o: TR.test_hand_example(o)]),
+    ("ratio-zero-denominator-as-zero", "o->ratio.push_back(kv.second.second == 0 ? NAN :",
+     "o->ratio.push_back(kv.second.second == 0 ? 0.0 :",
+     [lambda o: TR.test_hand_example(o)]),
+    ("ratio-last-thread-only", "if (p < P_num) v.first += kval[p][i];\n            else v.second += kval[p][i];",
+     "if (p < P_num) v.first = kval[p][i];\n            else v.second = kval[p][i];",
+     [lambda o: TR.test_hand_example(o)]),
     ("min-over-present-only", "for (uint32_t p = 0; p < P; ++p) { s += x[p]; lo = std::min(lo, x[p]); hi = std::max(hi, x[p]); }",
      "for (uint32_t p = 0; p < P; ++p) { s += x[p]; if (x[p]) lo = std::min(lo, x[p]); hi = std::max(hi, x[p]); }",
      [lambda o: TI.test_derive_vs_numpy(o)]),
