@@ -291,6 +291,27 @@ typedef struct {
     uint64_t* n_rows;
 } hpa_issue_rows;
 
+/* Ratio of two raw metrics per key (Section 4.5: a quantity known once per
+ * kernel invocation, such as its registers, is recovered by dividing two raw
+ * metrics that were summed over threads and ranks like any other: the
+ * quantity summed over invocations, and the count of invocations).  DEVICE
+ * arrays of `capacity` rows, ascending by (ctx, node, stall), one row per key
+ * of the union of the numerator and the denominator profiles: num = the sum
+ * of the numerator profiles' values of the key, den = the same over the
+ * denominator profiles (0 where absent), ratio = num / den computed in FP64
+ * and rounded once to FP32, NaN where den = 0.  *n_keys (device uint64): rows
+ * written, or -- with HPA_E_CAPACITY from hpa_sync -- the rows needed.       */
+typedef struct {
+    uint64_t capacity;
+    uint32_t* key_ctx;
+    uint32_t* key_node;
+    uint8_t* key_stall;
+    uint64_t* num;
+    uint64_t* den;
+    float* ratio;
+    uint64_t* n_keys;
+} hpa_ratio_rows;
+
 /* ---- handle ------------------------------------------------------------- */
 
 /* Create a handle on CUDA device `device` that enqueues on `cuda_stream`
@@ -440,6 +461,15 @@ hpa_status hpa_apportion_all(hpa_handle* h, uint32_t binary_id, const hpa_profil
  * W and shares are rounded once to FP32.  A key outside the binary (node or
  * stall) fails the call at hpa_sync with HPA_E_INVALID_SAMPLE.               */
 hpa_status hpa_issue_by_function(hpa_handle* h, uint32_t binary_id, const hpa_profile* p, hpa_issue_rows* out);
+
+/* Ratio of two raw metrics (Section 4.5; see hpa_ratio_rows) over profiles of
+ * this binary: num[0..n_num) are the numerator group, den[0..n_den) the
+ * denominator group (HOST arrays of profile descriptors with DEVICE data;
+ * either group may be empty, not both).  Sums are exact (64-bit).  A key
+ * outside the binary or the profiles' n_ctx / n_stall fails the call at
+ * hpa_sync with HPA_E_INVALID_SAMPLE.                                         */
+hpa_status hpa_ratio_of_sums(hpa_handle* h, uint32_t binary_id, const hpa_profile* const* num, uint32_t n_num,
+                             const hpa_profile* const* den, uint32_t n_den, hpa_ratio_rows* out);
 
 /* Inclusive metrics (Section 6.1, statistic generation).
  *  tree_out (may be NULL): for every key of p, its value is added to its node

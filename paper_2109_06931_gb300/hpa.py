@@ -75,6 +75,11 @@ class hpa_issue_rows(C.Structure):
                 ("frac", vp), ("n_rows", vp)]
 
 
+class hpa_ratio_rows(C.Structure):
+    _fields_ = [("capacity", C.c_uint64), ("key_ctx", vp), ("key_node", vp), ("key_stall", vp), ("num", vp),
+                ("den", vp), ("ratio", vp), ("n_keys", vp)]
+
+
 class hpa_cct(C.Structure):
     _fields_ = [("n_nodes", C.c_uint32), ("parent", vp)]
 
@@ -132,7 +137,7 @@ class hpa_derived(C.Structure):
 EXPORTS = ["hpa_create", "hpa_destroy", "hpa_last_error", "hpa_sync", "hpa_reserve", "hpa_kernel_launches",
            "hpa_load_structure", "hpa_unload_structure", "hpa_binary_info_get", "hpa_attribute_samples",
            "hpa_attribute_samples_host", "hpa_attribute_batch", "hpa_apportion_callgraph",
-           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_apportion_all", "hpa_issue_by_function", "hpa_set_phase_timing", "hpa_phase_times",
+           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_apportion_all", "hpa_issue_by_function", "hpa_ratio_of_sums", "hpa_set_phase_timing", "hpa_phase_times",
            "hpa_attribute_samples_noalloc", "hpa_server_create", "hpa_server_submit", "hpa_server_poll",
            "hpa_server_stats_get", "hpa_server_destroy"]
 PHASES = ["hist+plan", "attribute+scatter", "big-split", "leaf sort/reduce", "emit"]
@@ -180,6 +185,8 @@ def lib(build_if_needed: bool = True):
         L.hpa_apportion_callgraph.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_gpucct)]
         L.hpa_apportion_all.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_gpucct_all)]
         L.hpa_issue_by_function.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_issue_rows)]
+        L.hpa_ratio_of_sums.argtypes = [H, C.c_uint32, C.POINTER(C.POINTER(hpa_profile)), C.c_uint32,
+                                        C.POINTER(C.POINTER(hpa_profile)), C.c_uint32, C.POINTER(hpa_ratio_rows)]
         L.hpa_propagate_inclusive.argtypes = [H, C.c_uint32, C.POINTER(hpa_profile), C.POINTER(hpa_profile),
                                               C.POINTER(hpa_cct), vp]
         L.hpa_derive_metrics.argtypes = [H, C.POINTER(C.POINTER(hpa_profile)), C.c_uint32, C.POINTER(hpa_derived)]
@@ -681,6 +688,29 @@ class Hpa:
         arr = (C.POINTER(hpa_profile) * P)(*[C.pointer(c) for c in cps])
         self.check(self.L.hpa_derive_metrics(self.h, arr, P, C.byref(o)))
         self._keep = [cps, arr]
+        return out
+
+    def ratio_of_sums(self, bid: int, num, den, capacity: int | None = None):
+        """hpa_ratio_of_sums: per key, the numerator profiles' sum over the
+        denominator profiles' sum (Section 4.5).  Returns a dict of device
+        tensors (ctx, node, stall, num, den, ratio, n); capacity defaults to
+        the profiles' key counts added up."""
+        num, den = list(num), list(den)
+        cap = capacity if capacity is not None else max(1, sum(p.count() for p in num + den))
+        d = self.device
+        out = dict(ctx=torch.empty(cap, dtype=torch.int32, device=d), node=torch.empty(cap, dtype=torch.int32, device=d),
+                   stall=torch.empty(cap, dtype=torch.uint8, device=d), num=torch.empty(cap, dtype=torch.int64, device=d),
+                   den=torch.empty(cap, dtype=torch.int64, device=d), ratio=torch.empty(cap, dtype=torch.float32, device=d),
+                   n=torch.zeros(1, dtype=torch.int64, device=d))
+        o = hpa_ratio_rows(cap, *[_ptr(out[k]) for k in ("ctx", "node", "stall", "num", "den", "ratio", "n")])
+        groups = []
+        for ps in (num, den):
+            cps = [p.c() for p in ps]
+            for c, p in zip(cps, ps):
+                c.capacity = p.count()
+            groups.append((cps, (C.POINTER(hpa_profile) * max(1, len(cps)))(*[C.pointer(c) for c in cps])))
+        self.check(self.L.hpa_ratio_of_sums(self.h, bid, groups[0][1], len(num), groups[1][1], len(den), C.byref(o)))
+        self._keep = groups
         return out
 
     def max_depth(self, bid: int) -> int:

@@ -69,9 +69,9 @@ def test_struct_layouts_match_header():
 #include <stdio.h>
 #include "hpa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hpa_options), sizeof(hpa_structure), sizeof(hpa_samples),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hpa_options), sizeof(hpa_structure), sizeof(hpa_samples),
          sizeof(hpa_profile), sizeof(hpa_gpucct), sizeof(hpa_cct), sizeof(hpa_derived), sizeof(hpa_binary_info),
-         sizeof(hpa_gpucct_all), sizeof(hpa_issue_rows));
+         sizeof(hpa_gpucct_all), sizeof(hpa_issue_rows), sizeof(hpa_ratio_rows));
   return 0;
 }
 '''
@@ -83,5 +83,6 @@ int main(void) {
         subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (H.hpa_options, H.hpa_structure, H.hpa_samples, H.hpa_profile, H.hpa_gpucct,
-                                       H.hpa_cct, H.hpa_derived, H.hpa_binary_info, H.hpa_gpucct_all, H.hpa_issue_rows)]
+                                       H.hpa_cct, H.hpa_derived, H.hpa_binary_info, H.hpa_gpucct_all, H.hpa_issue_rows,
+                                       H.hpa_ratio_rows)]
     assert sizes == mine

@@ -114,3 +114,80 @@ def test_issue_by_function(H, wl, n, n_ctx):
     H.issue_by_function(bid, p, capacity=k - 1)
     st, _ = H.sync_status()
     assert st == hpa.HPA_E_CAPACITY
+
+
+def _gpu_profile(rows, n_ctx, n_stall, n_nodes):
+    """A device profile holding the given (ctx, node, stall, value) keys, sorted."""
+    import torch
+    from paper_2109_06931_gb300 import hpa
+    a = np.array(sorted(rows), dtype=np.uint64).reshape(-1, 4)
+    k = a.shape[0]
+    t = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x.astype(dt)).view(
+        {np.uint32: np.int32, np.uint64: np.int64, np.uint8: np.uint8}[dt]), device="cuda")
+    return hpa.Profile(t(a[:, 0], np.uint32), t(a[:, 1], np.uint32), t(a[:, 2], np.uint8), t(a[:, 3], np.uint64),
+                       torch.tensor([k], dtype=torch.int64, device="cuda"),
+                       torch.zeros(n_stall, dtype=torch.int64, device="cuda"),
+                       torch.zeros(n_stall, dtype=torch.int64, device="cuda"), n_ctx, n_stall, max(k, 1), n_nodes)
+
+
+def _check_ratio(r, ref):
+    k = int(r["n"].item())
+    assert k == len(ref.num)
+    assert np.array_equal(r["ctx"][:k].cpu().numpy().view(np.uint32), ref.ctx)
+    assert np.array_equal(r["node"][:k].cpu().numpy().view(np.uint32), ref.node)
+    assert np.array_equal(r["stall"][:k].cpu().numpy(), ref.stall)
+    assert np.array_equal(r["num"][:k].cpu().numpy().view(np.uint64), ref.num)
+    assert np.array_equal(r["den"][:k].cpu().numpy().view(np.uint64), ref.den)
+    # FP64 quotient rounded once to FP32 on both sides: equal bit for bit
+    got = r["ratio"][:k].cpu().numpy()
+    exp = ref.ratio.astype(np.float32)
+    assert np.array_equal(np.isnan(got), np.isnan(exp))
+    assert np.array_equal(got[~np.isnan(got)], exp[~np.isnan(exp)])
+    return k
+
+
+def test_ratio_hand_example(H):
+    """Registers per invocation from registers summed over invocations and the
+    invocation counts of two ranks (Section 4.5), hand-computed: 96 / 3 = 32,
+    200 / 5 = 40, NaN without a count, 0 without registers, UNKNOWN 9 / 3."""
+    import test_oracle_ratio as TR
+    B = synth.PLAIN.binary()
+    bid = H.load_structure(B)
+    M = int(B.node_func.shape[0])
+    num = [_gpu_profile(p, 5, 2, M) for p in TR.NUM]
+    den = [_gpu_profile(p, 5, 2, M) for p in TR.DEN]
+    r = H.ratio_of_sums(bid, num, den)
+    H.sync()
+    k = int(r["n"].item())
+    assert k == 5
+    assert r["ctx"][:k].tolist() == [0, 1, 2, 3, 4]
+    assert r["node"][:k].cpu().numpy().view(np.uint32).tolist() == [3, 3, 5, 1, 0xFFFFFFFF]
+    assert r["num"][:k].tolist() == [96, 200, 7, 0, 9] and r["den"][:k].tolist() == [3, 5, 0, 4, 3]
+    q = r["ratio"][:k].cpu().numpy()
+    assert q[0] == 32.0 and q[1] == 40.0 and np.isnan(q[2]) and q[3] == 0.0 and q[4] == 3.0
+    ref = oracle.ratio([TR._keys(oracle, p) for p in TR.NUM], [TR._keys(oracle, p) for p in TR.DEN])
+    _check_ratio(r, ref)
+
+
+@pytest.mark.parametrize("wl,P_num,P_den,n,n_ctx", [("plain", 1, 1, 200_000, 300), ("plain", 3, 2, 100_000, 40),
+                                                    ("plain", 2, 0, 50_000, 7), ("large", 2, 2, 1_000_000, 20_000)])
+def test_ratio_of_sums(H, wl, P_num, P_den, n, n_ctx):
+    """Ratio of two raw metrics per key against the oracle: keys, both sums
+    exact, the FP32 ratio equal; a too-small capacity reports the rows needed."""
+    from paper_2109_06931_gb300 import hpa
+    w = synth.PLAIN if wl == "plain" else synth.LARGE
+    B = w.binary()
+    bid = H.load_structure(B)
+    gp, cp = [], []
+    for p in range(P_num + P_den):
+        S = synth.make_samples(500 + p, B, n // (1 + p % 3), n_ctx, w.zipf_s, counts=(p % 2 == 0), device="cuda")
+        gp.append(H.attribute_samples(bid, S))
+        cp.append(oracle.attribute_samples(B, S))
+    H.sync()
+    r = H.ratio_of_sums(bid, gp[:P_num], gp[P_num:])
+    H.sync()
+    ref = oracle.ratio(cp[:P_num], cp[P_num:])
+    k = _check_ratio(r, ref)
+    H.ratio_of_sums(bid, gp[:P_num], gp[P_num:], capacity=k - 1)
+    st, _ = H.sync_status()
+    assert st == hpa.HPA_E_CAPACITY
