@@ -342,6 +342,13 @@ hpa_status hpa_reserve(hpa_handle* h, uint64_t max_samples, uint64_t max_groups)
 hpa_status hpa_wait_flag(hpa_handle* h, const uint32_t* flag, uint32_t value);
 /* Number of kernels the handle has launched so far. */
 uint64_t hpa_kernel_launches(hpa_handle* h);
+/* How this library was built: bit 0 (HPA_BUILD_CHECKED) set in the
+ * bounds-checked flavour (compiled with -DHPA_CHECKED), in which every index
+ * that a kernel computes from counters, scans or data is checked against the
+ * array it indexes; a violation skips the access and makes the call fail at
+ * hpa_sync with HPA_E_INTERNAL (the detail names the site).  No handle needed. */
+#define HPA_BUILD_CHECKED 1u
+uint32_t hpa_build_flags(void);
 /* Per-phase timing of the aggregation pipeline with CUDA events recorded on
  * the handle's stream between its kernels (enable != 0 starts a fresh
  * accumulation; 0 stops).  Phases: 0 group histogram and plan, 1 attribute +

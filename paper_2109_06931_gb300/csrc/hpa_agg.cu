@@ -289,7 +289,7 @@ __global__ void k_leaves(AggWork w) {
 // U lookups per thread stay in flight.
 template <int U>
 __device__ __forceinline__ void lookup_nodes(const DevBinary& bin, const uint64_t (&pc)[U], const bool (&ok)[U],
-                                             uint32_t (&nd)[U], uint64_t keep) {
+                                             uint32_t (&nd)[U], uint64_t keep, DevStatus* st) {
     uint32_t off[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -299,21 +299,35 @@ __device__ __forceinline__ void lookup_nodes(const DevBinary& bin, const uint64_
             const uint64_t o = pc[u] - bin.pc_base;
             if (o < bin.span) {
                 off[u] = (uint32_t)o;
-                nd[u] = ld_keep(&bin.dir[off[u] >> bin.dshift], keep);
+                // site 111: directory entry
+                if (in_bounds(st, off[u] >> bin.dshift, bin.n_dir, 111))
+                    nd[u] = ld_keep(&bin.dir[off[u] >> bin.dshift], keep);
             }
+        }
+    }
+    // the first two entries of every walk are loaded for all U lookups
+    // before any walk goes on, so that the U second-level loads overlap
+    uint2 cur[U], nx[U];
+    uint32_t j[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (nd[u] & DIR_SEARCH) {
+            j[u] = nd[u] & ~DIR_SEARCH;
+            if (!in_bounds(st, j[u] + 1, bin.n_ent, 112)) { nd[u] = bin.n_nodes; continue; }   // site 112: interval entry
+            cur[u] = ld_keep2(&bin.ent[j[u]], keep);
+            nx[u] = ld_keep2(&bin.ent[j[u] + 1], keep);
         }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (nd[u] & DIR_SEARCH) {
-            uint32_t j = nd[u] & ~DIR_SEARCH;
-            uint2 cur = ld_keep2(&bin.ent[j], keep), nx = ld_keep2(&bin.ent[j + 1], keep);
-            while (nx.x <= off[u]) {
-                cur = nx;
-                ++j;
-                nx = ld_keep2(&bin.ent[j + 1], keep);
+            while (nx[u].x <= off[u]) {
+                cur[u] = nx[u];
+                ++j[u];
+                if (!in_bounds(st, j[u] + 1, bin.n_ent, 112)) break;
+                nx[u] = ld_keep2(&bin.ent[j[u] + 1], keep);
             }
-            nd[u] = cur.y;
+            nd[u] = cur[u].y;
         }
     }
 }
@@ -349,7 +363,7 @@ __global__ void __launch_bounds__(256, 4) k_attribute(AggWork w) {
                     if (HAS_CNT && B.count) cnt[u] = ld_stream(&B.count[i]);
                 }
             }
-            lookup_nodes<U>(bin, pc, ok, nd, keep);
+            lookup_nodes<U>(bin, pc, ok, nd, keep, w.status);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (!ok[u]) continue;
@@ -398,6 +412,7 @@ __global__ void __launch_bounds__(256) k_scatter(AggWork w) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (c[u] >= n_ctx) continue;
+                if (!in_bounds(w.status, slot[u], w.n_rec, 101)) continue;   // site 101: record slot
                 if (HAS_CNT) w.rec_pair[slot[u]] = r[u];
                 else w.rec_sub[slot[u]] = r[u].x;
             }
@@ -577,7 +592,7 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
                     ok[u] = cx[u] < n_ctx;                  // counted as invalid by k_part_hist
                 }
             }
-            lookup_nodes<U>(bin, pc, ok, nd, keep);
+            lookup_nodes<U>(bin, pc, ok, nd, keep, w.status);
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (ok[u]) rk[u] = atomicAdd(&th[cx[u] >> shift], 1u);
@@ -594,6 +609,7 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
                 const bool bad_stall = st[u] >= B.n_stall;
                 const uint32_t sub = bad_stall ? 0u : ((nd[u] << w.sb) | st[u]);
                 const uint32_t q = th[cx[u] >> shift] + rk[u];
+                if (!in_bounds(w.status, q, PART_TILE, 102)) continue;     // site 102: tile stage
                 srec[q] = make_uint2(sub, bad_stall ? 0u : cnt[u]);
                 sbin[q] = (uint16_t)(two ? ((cx[u] >> shift) << 8 | (cx[u] & dmask)) : cx[u]);
                 bad += bad_stall;
@@ -603,6 +619,7 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
                 const uint32_t sb = sbin[j];
                 const uint32_t c = two ? sb >> 8 : sb;
                 const uint32_t dst = cur[c] + (j - th[c]);
+                if (!in_bounds(w.status, dst, w.n_rec, 103)) continue;     // site 103: record destination
                 if (two) {
                     if (HAS_CNT) w.rec2_pair[dst] = srec[j];
                     else w.rec2_sub[dst] = srec[j].x;
@@ -734,6 +751,7 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part2_scatter(AggWork w) {
             for (int u = 0; u < U; ++u) {
                 if (dg[u] == 0xFFFFFFFFu) continue;
                 const uint32_t q = th[dg[u]] + rk[u];
+                if (!in_bounds(w.status, q, PART_TILE, 104)) continue;     // site 104: tile stage
                 srec[q] = r[u];
                 sdig[q] = (uint8_t)dg[u];
             }
@@ -741,6 +759,7 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part2_scatter(AggWork w) {
             for (uint32_t i = threadIdx.x; i < tot; i += PART_THREADS) {
                 const uint32_t d = sdig[i];
                 const uint32_t dst = cur[d] + (i - th[d]);
+                if (!in_bounds(w.status, dst, w.n_rec, 105)) continue;     // site 105: record destination
                 if (HAS_CNT) w.rec_pair[dst] = srec[i];
                 else w.rec_sub[dst] = srec[i].x;
             }
@@ -834,6 +853,7 @@ __global__ void __launch_bounds__(BIG_THREADS, 2) k_big_partition(AggWork w) {
                 const uint32_t i = i0 + u * BIG_THREADS;
                 if (i >= s1) break;
                 const uint32_t p = s0 + atomicAdd(&off[r[u].x >> shift], 1u);
+                if (!in_bounds(w.status, p, s1, 106)) continue;              // site 106: big-group record
                 if (pair) {
                     w.rec2_pair[p] = r[u];
                 } else {
@@ -909,8 +929,13 @@ __global__ void __launch_bounds__(256) k_emit(AggWork w) {
             for (int u = 0; u < EMIT_U; ++u) {
                 const uint32_t i = i0 + u * 256;
                 if (i < d) {
-                    kk[u] = __ldcs(&w.tmp_key[start + i]);
-                    vv[u] = __ldcs((const unsigned long long*)&w.tmp_val[start + i]);
+                    if (in_bounds(w.status, (uint64_t)start + i, w.n_rec, 110)) {   // site 110: leaf key
+                        kk[u] = __ldcs(&w.tmp_key[start + i]);
+                        vv[u] = __ldcs((const unsigned long long*)&w.tmp_val[start + i]);
+                    } else {
+                        kk[u] = 0;
+                        vv[u] = 0;
+                    }
                 }
             }
 #pragma unroll

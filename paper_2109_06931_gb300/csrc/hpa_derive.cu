@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_leaf_stats(AggWork w, DeriveArgs
                 }
                 __syncthreads();
             }
-            const int cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
+            const int cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits), 0, w.status);
             const uint64_t* el = S.el[cur];
             const int c0 = threadIdx.x * EPT, c1 = min((int)n, c0 + EPT);
             uint32_t heads = 0;

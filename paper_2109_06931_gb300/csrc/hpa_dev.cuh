@@ -22,6 +22,23 @@ __device__ __forceinline__ void raise_status(DevStatus* st, int32_t code, int32_
     if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
 }
 
+// Bounds-checked build (compiled with -DHPA_CHECKED): an index that a kernel
+// computes from counters, scans or data is checked against the size of the
+// array it indexes before the access; out of range, the caller skips the
+// access and the status records HPA_E_INTERNAL with `where` = the site's
+// number (100 + n, listed where each check stands) -- never a trap.  In the
+// normal build the check is the constant true and compiles away.
+__device__ __forceinline__ bool in_bounds(DevStatus* st, uint64_t i, uint64_t n, int32_t site) {
+#ifdef HPA_CHECKED
+    if (i < n) return true;
+    if (st) raise_status(st, 8 /* HPA_E_INTERNAL */, site);
+    return false;
+#else
+    (void)st; (void)i; (void)n; (void)site;
+    return true;
+#endif
+}
+
 // Program structure of one binary as the attribution kernels read it.
 //   ent[j] = {lo_j, node_j} (offsets from pc_base): entry j covers
 //     [lo_j, lo_{j+1}); the ranges in order, a gap between two ranges as an
@@ -345,7 +362,7 @@ struct PackedRadix {
 
     // First pass: counting sort of el[0][0..n) by the low b1 bits into
     // el[1] (block-wide counters, atomics; the order of equal digits is free).
-    __device__ static void counting_pass(Smem& s, int n, int b1) {
+    __device__ static void counting_pass(Smem& s, int n, int b1, DevStatus* st) {
         const int nb = 1 << b1;
         const uint32_t m1 = (uint32_t)nb - 1u;
         uint32_t* c = s.cnt;
@@ -357,7 +374,7 @@ struct PackedRadix {
         for (int i = threadIdx.x; i < n; i += THREADS) {
             const E e = s.el[0][i];
             const uint32_t p = atomicAdd(&c[key_of(e) & m1], 1u);
-            s.el[1][p] = e;
+            if (in_bounds(st, p, (uint64_t)n, 107)) s.el[1][p] = e;      // site 107: counting-pass position
         }
         __syncthreads();
     }
@@ -370,13 +387,13 @@ struct PackedRadix {
     // the ADU and ALU pipes share the work.
     // Sorts s.el[0][0..n) by the low `bits` bits of the key; returns the
     // buffer index (0 or 1) that holds the result.
-    __device__ static int sort(Smem& s, int n, int bits, int match = 0) {
+    __device__ static int sort(Smem& s, int n, int bits, int match = 0, DevStatus* st = nullptr) {
         if (bits <= 0 || n <= 1) return 0;
         const int warp = threadIdx.x >> 5;
         const int lane = lane_id();
         // first pass: wide enough for the leaf's size, at most U1 bits
         const int b1 = min(bits, min(U1, max(8, (int)ceil_log2_u64((uint64_t)n) + 1)));
-        counting_pass(s, n, b1);
+        counting_pass(s, n, b1, st);
         int cur = 1;
         const int rem = bits - b1;
         if (rem <= 0) return cur;
@@ -452,7 +469,8 @@ struct PackedRadix {
                 const int i = lo + r * 32 + lane;
                 if (i < hi) {
                     const uint32_t d = (key_of(x[r]) >> shift) & dmask;
-                    s.el[cur ^ 1][row[d] + rk[r]] = x[r];
+                    const uint32_t p = row[d] + rk[r];
+                    if (in_bounds(st, p, (uint64_t)n, 108)) s.el[cur ^ 1][p] = x[r];   // site 108: stable-pass position
                 }
             }
             __syncthreads();

@@ -263,7 +263,7 @@ __device__ uint32_t block_prefix_sum(uint32_t n, CNT cnt, PUT put, uint32_t* sw)
 // Level-synchronous breadth-first processing of a queue: q[0, *s_n) holds the
 // first level (set before the call); visit(x, push) may append with push(y).
 template <typename VISIT>
-__device__ void block_bfs(uint32_t* q, uint32_t* s_n, VISIT visit) {
+__device__ void block_bfs(uint32_t* q, uint32_t* s_n, uint32_t cap, DevStatus* st, VISIT visit) {
     uint32_t lo = 0;
     for (;;) {
         __syncthreads();
@@ -271,7 +271,10 @@ __device__ void block_bfs(uint32_t* q, uint32_t* s_n, VISIT visit) {
         __syncthreads();                       // every thread has read *s_n before anyone pushes
         if (hi == lo) break;
         for (uint32_t k = lo + threadIdx.x; k < hi; k += GALL_THREADS)
-            visit(q[k], [&](uint32_t y) { q[atomicAdd(s_n, 1u)] = y; });
+            visit(q[k], [&](uint32_t y) {
+                const uint32_t at = atomicAdd(s_n, 1u);
+                if (in_bounds(st, at, cap, 116)) q[at] = y;             // site 116: breadth-first queue
+            });
         lo = hi;
     }
 }
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                     !(atomicOr(&T.flags[f], GF_Z) & GF_Z))
                     T.q_z[atomicAdd(&s_nz, 1u)] = f;
             }
-            block_bfs(T.q_z, &s_nz, [&](uint32_t f, auto push) {
+            block_bfs(T.q_z, &s_nz, g.F, A.status, [&](uint32_t f, auto push) {
                 for (uint32_t j = g.fin_off[f]; j < g.fin_off[f + 1]; ++j) {
                     const uint32_t e = g.fin_edge[j];
                     if (!g.edge_intra[e]) bit_set(B.wpos, e);           // weight 1 (FIXUP)
@@ -365,7 +368,7 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                 if (g.cin_off[v + 1] > g.cin_off[v] && w_zero_step2(g, T, v) && !(atomicOr(&T.flags[v], GC_Z2) & GC_Z2))
                     T.q_z2[atomicAdd(&s_nz2, 1u)] = v;
             }
-            block_bfs(T.q_z2, &s_nz2, [&](uint32_t v, auto push) {
+            block_bfs(T.q_z2, &s_nz2, g.V, A.status, [&](uint32_t v, auto push) {
                 for (uint32_t j = g.cin_off[v]; j < g.cin_off[v + 1]; ++j) {
                     const uint32_t e = g.cin_edge[j];
                     bit_set(B.wpos, e);                                  // weight 1 (FIXUP2)
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                 T.q_clos[k] = v;
             }
             if (tid == 0) s_nclos = nexcl;
-            block_bfs(T.q_clos, &s_nclos, [&](uint32_t v, auto push) {
+            block_bfs(T.q_clos, &s_nclos, g.V, A.status, [&](uint32_t v, auto push) {
                 unsigned long long W = 0;
                 for (uint32_t j = g.cin_off[v]; j < g.cin_off[v + 1]; ++j) W += w2_of(T, B, g.cin_edge[j]);
                 if (!W) return;
@@ -446,6 +449,8 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                                      const uint32_t b = __ffs(m) - 1;
                                      m &= m - 1;
                                      const uint32_t e = i * 32 + b, f = g.cs_callee[e], h = g.cs_head[e];
+                                     // site 114: call-site row
+                                     if (!in_bounds(A.status, eb + r, O.cap_edges, 114)) break;
                                      O.edge_id[eb + r] = e;
                                      O.ratio[eb + r] = T.ratio[e];
                                      uint8_t fl = 0;
@@ -470,6 +475,7 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
             for (uint32_t k = tid; k < ncl; k += GALL_THREADS) {
                 const uint32_t v = T.q_clos[k];
                 const uint32_t p = atomicAdd(&B.lev[g.level_of[v]], 1u);
+                if (!in_bounds(A.status, p, ncl, 113)) continue;               // site 113: sweep list
                 T.cl_node[p] = v;
                 T.cl_row[p] = node_rank(B, v);
             }
@@ -527,7 +533,8 @@ __global__ void __launch_bounds__(GALL_THREADS, GALL_PER_SM) k_gpucct_all(GallAr
                         for (int u = 0; u < 4; ++u)
                             if (j + u < e1) df_add_prod(hi, lo, q[u], x[u]);
                     }
-                    incl[(size_t)T.cl_row[k] * M + r] = __fadd_rn(hi, lo);
+                    if (in_bounds(A.status, T.cl_row[k], ncl, 115))          // site 115: node row
+                        incl[(size_t)T.cl_row[k] * M + r] = __fadd_rn(hi, lo);
                 }
                 __syncthreads();
             }

@@ -190,6 +190,14 @@ extern "C" const char* hpa_last_error(hpa_handle* h) { return h ? h->err.c_str()
 
 extern "C" uint64_t hpa_kernel_launches(hpa_handle* h) { return h ? h->launches : 0; }
 
+extern "C" uint32_t hpa_build_flags(void) {
+#ifdef HPA_CHECKED
+    return HPA_BUILD_CHECKED;
+#else
+    return 0u;
+#endif
+}
+
 cudaEvent_t* hpa_handle::phase_events(bool new_call) {
     std::vector<cudaEvent_t> v;
     if (!ev_pool.empty()) {
@@ -258,6 +266,7 @@ extern "C" hpa_status hpa_sync(hpa_handle* h, uint64_t* bad) {
         const char* what = ds.code == HPA_E_INVALID_SAMPLE ? "invalid sample records"
                          : ds.code == HPA_E_CAPACITY ? "output capacity too small (n_keys holds the size needed)"
                          : ds.code == HPA_E_TIMEOUT ? "a bounded device wait gave up"
+                         : ds.code == HPA_E_INTERNAL ? "internal invariant violated (detail >= 100: the index check that failed)"
                          : "device error";
         return h->fail(ds.code, "%s (detail %d, bad records %llu)", what, ds.where, (unsigned long long)ds.bad);
     }
@@ -512,6 +521,7 @@ hpa_status hpa_handle::carve_work(AggWork& w, uint64_t N, uint64_t G, uint32_t n
     if (((G + 1) << w.cur_shift) > (64ull << 20)) w.cur_shift = 0;
     w.sort_mode = std::min<uint32_t>(opt.leaf_ranking, 3);
     w.L_max = (uint32_t)L_max; w.has_cnt = has_cnt || val64; w.val64 = val64;
+    w.n_rec = N;
     auto layout = [&](Carve& c) {
         w.grp_hist = c.take<uint32_t>(G + 1);
         w.grp_cursor = c.take<uint32_t>((G + 1) << w.cur_shift);

@@ -75,6 +75,7 @@ struct AggWork {
     uint2* rec2_pair;      // [N]
     uint32_t* tmp_key;     // [N]
     uint64_t* tmp_val;     // [N]
+    uint64_t n_rec;        // N: entries of each record array above
     uint32_t* scan_tmp;    // device-wide scan partials
     const BufDev* bufs;    // [n_buf]
     const uint64_t* buf_tile;     // [n_buf + 1] tile prefix

@@ -170,6 +170,8 @@ __device__ __forceinline__ uint32_t warp_runs(KA K, VA Vf, int n, int w0, int w1
     const int lane = lane_id();
     int run = run0;
     uint32_t nz = nz_base, nz_count = 0;
+    // two rows at a time: their scans are independent, only the carry links them
+#pragma unroll 2
     for (int base = w0; base < w1; base += 32) {
         const int i = base + lane;
         const bool ok = i < w1;
@@ -220,6 +222,8 @@ template <typename T, typename KA, typename VA>
 __device__ __forceinline__ RunSum<T> warp_run_summary(KA K, VA Vf, int w0, int w1) {
     const int lane = lane_id();
     RunSum<T> r{0, T(0), 0};
+    // two rows at a time: their scans are independent, only the carry links them
+#pragma unroll 2
     for (int base = w0; base < w1; base += 32) {
         const int i = base + lane;
         const bool ok = i < w1;
@@ -535,7 +539,7 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
                             put(r, e);
                         }
                     } else {
-                        const int hc = HS::sort(HM, (int)D, (int)(w.sbits + gbits), (int)w.sort_mode);
+                        const int hc = HS::sort(HM, (int)D, (int)(w.sbits + gbits), (int)w.sort_mode, w.status);
                         for (uint32_t j = threadIdx.x; j < D; j += THREADS) put(j, HM.el[hc][j]);
                     }
                     if (fuse) copy_fused(D);
@@ -590,7 +594,7 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
             }
             __syncthreads();
             int cur;
-            if constexpr (Cfg::PACKED || Cfg::IDX) cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits), (int)w.sort_mode);
+            if constexpr (Cfg::PACKED || Cfg::IDX) cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits), (int)w.sort_mode, w.status);
             else cur = Sort::sort(S, (int)n, (int)(w.sbits + gbits));
             auto Kc = [&S, cur](int i) -> uint32_t {
                 if constexpr (Cfg::PACKED || Cfg::IDX) return Sort::key_of(S.el[cur][i]);
@@ -614,7 +618,8 @@ k_leaf(AggWork w, uint32_t n_lo, uint32_t n_hi) {
             uint32_t* ok_ = w.tmp_key + start;
             unsigned long long* ov = (unsigned long long*)(w.tmp_val + start);
             auto put_tmp = [&](bool wr, uint32_t pos, uint32_t k, unsigned long long v) {
-                if (wr) { ok_[pos] = k; ov[pos] = v; }
+                // site 109: a key of the leaf's runs
+                if (wr && in_bounds(w.status, pos, n, 109)) { ok_[pos] = k; ov[pos] = v; }
             };
 
             uint32_t n_out;

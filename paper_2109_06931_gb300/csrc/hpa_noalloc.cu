@@ -144,6 +144,7 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
     w.buf_grp = d_grp;
     w.bins = h->d_bins;
     w.status = h->d_status;
+    w.n_rec = N;
     BufDev d{};
     d.pc = s.pc; d.ctx = s.ctx; d.stall = s.stall; d.count = s.count; d.n = s.n;
     d.tile_base = 0; d.n_ctx = s.n_ctx; d.n_stall = s.n_stall; d.grp_base = 0; d.bin = binary_id;

@@ -17,6 +17,7 @@ from . import build as _build
 
 HPA_OK, HPA_E_INVALID_ARG, HPA_E_INVALID_TABLE, HPA_E_INVALID_SAMPLE = 0, 1, 2, 3
 HPA_E_CAPACITY, HPA_E_OOM, HPA_E_CUDA, HPA_E_TIMEOUT, HPA_E_INTERNAL = 4, 5, 6, 7, 8
+HPA_BUILD_CHECKED = 1
 HPA_PENDING = 9
 HPA_UNKNOWN_NODE = 0xFFFFFFFF
 HPA_NO_PARENT = 0xFFFFFFFF
@@ -137,23 +138,26 @@ class hpa_derived(C.Structure):
 EXPORTS = ["hpa_create", "hpa_destroy", "hpa_last_error", "hpa_sync", "hpa_reserve", "hpa_kernel_launches",
            "hpa_load_structure", "hpa_unload_structure", "hpa_binary_info_get", "hpa_attribute_samples",
            "hpa_attribute_samples_host", "hpa_attribute_batch", "hpa_apportion_callgraph",
-           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_apportion_all", "hpa_issue_by_function", "hpa_ratio_of_sums", "hpa_set_phase_timing", "hpa_phase_times",
+           "hpa_propagate_inclusive", "hpa_derive_metrics", "hpa_apportion_all", "hpa_issue_by_function", "hpa_ratio_of_sums", "hpa_build_flags", "hpa_set_phase_timing", "hpa_phase_times",
            "hpa_attribute_samples_noalloc", "hpa_server_create", "hpa_server_submit", "hpa_server_poll",
            "hpa_server_stats_get", "hpa_server_destroy"]
 PHASES = ["hist+plan", "attribute+scatter", "big-split", "leaf sort/reduce", "emit"]
 
-_lib = None
+_libs = {}
 
 
-def lib(build_if_needed: bool = True):
-    """Load libhpa.so (building it first if needed)."""
-    global _lib
-    if _lib is None:
-        path = _build.LIB
+def lib(build_if_needed: bool = True, checked: bool | None = None):
+    """Load libhpa.so (building it first if needed); checked=True loads the
+    bounds-checked flavour libhpa_checked.so instead (default: the
+    HPA_CHECKED environment variable)."""
+    if checked is None:
+        checked = os.environ.get("HPA_CHECKED", "0") not in ("", "0")
+    if checked not in _libs:
+        path = _build.lib_path(checked)
         if build_if_needed:
-            path = _build.build()
+            path = _build.build(checked=checked)
         if not os.path.exists(path):
-            raise RuntimeError(f"libhpa.so not built at {path}")
+            raise RuntimeError(f"{os.path.basename(path)} not built at {path}")
         L = C.CDLL(path)
         H = vp
         L.hpa_create.argtypes = [C.POINTER(H), C.c_int, vp, C.POINTER(hpa_options)]
@@ -163,6 +167,8 @@ def lib(build_if_needed: bool = True):
         L.hpa_sync.argtypes = [H, u64p]
         L.hpa_reserve.argtypes = [H, C.c_uint64, C.c_uint64]
         L.hpa_kernel_launches.argtypes = [H]
+        L.hpa_build_flags.argtypes = []
+        L.hpa_build_flags.restype = C.c_uint32
         L.hpa_kernel_launches.restype = C.c_uint64
         L.hpa_load_structure.argtypes = [H, C.POINTER(hpa_structure), u32p]
         L.hpa_validate_structure.argtypes = [C.POINTER(hpa_structure), C.c_char_p, C.c_size_t]
@@ -201,8 +207,8 @@ def lib(build_if_needed: bool = True):
         for f in EXPORTS:
             if f not in ("hpa_last_error", "hpa_kernel_launches"):
                 getattr(L, f).restype = C.c_int32
-        _lib = L
-    return _lib
+        _libs[checked] = L
+    return _libs[checked]
 
 
 class HpaError(RuntimeError):
@@ -318,10 +324,10 @@ class Hpa:
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, issued_mask: int = 1,
                  leaf_capacity: int = 0, cursor_shift: int | None = None,
                  sort_mode: int | None = None, partition: bool = True, small_leaves: int = 0,
-                 leaf_hash: int = 0, timeout_iters: int = 0, leaf_emit: int = 0):
+                 leaf_hash: int = 0, timeout_iters: int = 0, leaf_emit: int = 0, checked: bool | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("hpa needs a CUDA device; there is no CPU implementation")
-        self.L = lib()
+        self.L = lib(checked=checked)
         self.device = torch.device("cuda", device)
         self.stream = stream or torch.cuda.current_stream(self.device)
         self.h = C.c_void_p()

@@ -31,6 +31,19 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def test_bounds_checked_flavour_exports_the_same_symbols():
+    """libhpa_checked.so (-DHPA_CHECKED) is the same boundary with index
+    checks compiled in; hpa_build_flags tells the two apart."""
+    from paper_2109_06931_gb300 import build
+    from paper_2109_06931_gb300 import hpa as H
+    lib = build.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (hpa_[a-z_]+)", out))
+    assert not [n for n in declared() if n not in exported]
+    assert H.lib(checked=True).hpa_build_flags() == H.HPA_BUILD_CHECKED
+    assert H.lib(checked=False).hpa_build_flags() == 0
+
+
 def test_library_loads_and_binding_types():
     import ctypes
     from paper_2109_06931_gb300 import hpa as H
