@@ -99,12 +99,16 @@ void set_smem_limit(const void* fn, int bytes) {
     else cudaGetLastError();
 }
 
-// short arrays: one CTA scans them in one launch
+// Arrays of up to SCAN_ONE_CTA_MAX entries: one CTA scans them in one launch
+// (where the three-kernel scan pays three launch gaps).  A single CTA is
+// latency-bound beyond that: 1.4-2.4 x 10^5 entries took 0.13-0.6 ms in one
+// CTA, 16,384 at a time, against a few microseconds for the three kernels.
 constexpr int SCAN_SMALL_THREADS = 1024, SCAN_SMALL_EPT = 16;
-constexpr uint64_t SCAN_SMALL_MAX = (uint64_t)SCAN_SMALL_THREADS * SCAN_SMALL_EPT;
+constexpr uint64_t SCAN_ONE_CTA_MAX = (uint64_t)SCAN_SMALL_THREADS * SCAN_SMALL_EPT;
 
-__global__ void __launch_bounds__(SCAN_SMALL_THREADS) k_scan_small(const uint32_t* in, uint32_t* out, uint32_t n) {
-    __shared__ uint32_t sw[33];
+// exclusive scan of in[0, n), n <= SCAN_ONE_CTA_MAX, into out[0, n) by one
+// CTA of SCAN_SMALL_THREADS threads, the total in out[n] (in == out allowed)
+__device__ void cta_scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* sw) {
     const uint32_t base = threadIdx.x * SCAN_SMALL_EPT;
     uint32_t v[SCAN_SMALL_EPT];
     uint32_t sum = 0;
@@ -123,10 +127,15 @@ __global__ void __launch_bounds__(SCAN_SMALL_THREADS) k_scan_small(const uint32_
     if (threadIdx.x == 0) out[n] = tot;
 }
 
+__global__ void __launch_bounds__(SCAN_SMALL_THREADS) k_scan_small(const uint32_t* in, uint32_t* out, uint32_t n) {
+    __shared__ uint32_t sw[33];
+    cta_scan_u32(in, out, n, sw);
+}
+
 size_t scan_tmp_words(uint64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 2; }
 
 void scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cudaStream_t s, uint64_t* launches) {
-    if (n <= SCAN_SMALL_MAX) {
+    if (n <= SCAN_ONE_CTA_MAX) {
         k_scan_small<<<1, SCAN_SMALL_THREADS, 0, s>>>(in, out, (uint32_t)n);
         *launches += 1;
         return;
@@ -215,10 +224,13 @@ __global__ void __launch_bounds__(256) k_grp_hist(AggWork w) {
 }
 
 // ------------------------------------------------------------------ K3..K8: items and leaves
-__global__ void k_item_flags(AggWork w) {
+// Each step is a loop over groups or items from `i0` in steps of `step`:
+// one thread per element across a grid (the kernels below), or the threads
+// of one CTA (k_plan_one, for calls with few groups).
+__device__ __forceinline__ void item_flags_range(const AggWork& w, uint32_t i0, uint32_t step) {
     const uint32_t* seg = w.grp_hist;
     const uint32_t span_mask = (w.span_log >= 32) ? 0xFFFFFFFFu : ((1u << w.span_log) - 1);
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < w.G; g += gridDim.x * blockDim.x) {
+    for (uint32_t g = i0; g < w.G; g += step) {
         const uint32_t s0 = seg[g];
         uint32_t f = 0;
         if (g == 0) {
@@ -239,15 +251,15 @@ __global__ void k_item_flags(AggWork w) {
     }
 }
 
-__global__ void k_items(AggWork w) {
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < w.G; g += gridDim.x * blockDim.x)
+__device__ __forceinline__ void items_range(const AggWork& w, uint32_t i0, uint32_t step) {
+    for (uint32_t g = i0; g < w.G; g += step)
         if (w.item_id[g + 1] != w.item_id[g]) w.item_grp0[w.item_id[g]] = g;
 }
 
-__global__ void k_items_size(AggWork w) {
+__device__ __forceinline__ void items_size_range(const AggWork& w, uint32_t i0, uint32_t step) {
     const uint32_t n_items = w.item_id[w.G];
     const uint32_t* seg = w.grp_hist;
-    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < w.G; it += gridDim.x * blockDim.x) {
+    for (uint32_t it = i0; it < w.G; it += step) {
         uint32_t nl = 0;
         if (it < n_items) {
             const uint32_t g0 = w.item_grp0[it];
@@ -259,11 +271,11 @@ __global__ void k_items_size(AggWork w) {
     }
 }
 
-__global__ void k_leaves(AggWork w) {
+__device__ __forceinline__ void leaves_range(const AggWork& w, uint32_t i0, uint32_t step) {
     const uint32_t n_items = w.item_id[w.G];
     const uint32_t* seg = w.grp_hist;
     const uint32_t* leaf_base = w.item_nleaf;
-    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < n_items; it += gridDim.x * blockDim.x) {
+    for (uint32_t it = i0; it < n_items; it += step) {
         const uint32_t g0 = w.item_grp0[it];
         const uint32_t g1 = (it + 1 < n_items) ? w.item_grp0[it + 1] : w.G;
         const uint32_t n = seg[g1] - seg[g0];
@@ -277,7 +289,51 @@ __global__ void k_leaves(AggWork w) {
             w.leaf_info[l] = b << 8;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) w.buf_first_leaf[w.n_buf] = leaf_base[w.G];
+    if (i0 == 0) w.buf_first_leaf[w.n_buf] = leaf_base[w.G];
+}
+
+// group offsets (exclusive) from the scanned part counts (partition path, part_mode 1)
+__device__ __forceinline__ void part_seg_range(const AggWork& w, uint32_t i0, uint32_t step) {
+    for (uint32_t g = i0; g <= w.G; g += step) {
+        if (g == w.G) { w.grp_hist[g] = w.part_cnt[w.n_cnt]; continue; }
+        const uint32_t b = upper_index<uint32_t>(w.buf_grp, w.n_buf, g);
+        const BufDev& B = w.bufs[b];
+        const uint64_t parts = w.buf_part[b + 1] - w.buf_part[b];
+        w.grp_hist[g] = w.part_cnt[B.cnt_base + (uint64_t)(g - B.grp_base) * parts];
+    }
+}
+
+#define HPA_GRID_RANGE blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x
+__global__ void k_item_flags(AggWork w) { item_flags_range(w, HPA_GRID_RANGE); }
+__global__ void k_items(AggWork w) { items_range(w, HPA_GRID_RANGE); }
+__global__ void k_items_size(AggWork w) { items_size_range(w, HPA_GRID_RANGE); }
+__global__ void k_leaves(AggWork w) { leaves_range(w, HPA_GRID_RANGE); }
+__global__ void k_part_seg(AggWork w) { part_seg_range(w, HPA_GRID_RANGE); }
+#undef HPA_GRID_RANGE
+
+// The whole plan in one CTA (calls with fewer than SCAN_ONE_CTA_MAX groups,
+// so that each of its scans is one CTA's): group offsets (from the part
+// counts, or a scan of the group histogram), item flags, their scan, items,
+// leaf slots per item, their scan, leaves -- one launch for seven.
+constexpr uint32_t PLAN_ONE_CTA_MAX = (uint32_t)SCAN_ONE_CTA_MAX - 1;
+
+__global__ void __launch_bounds__(SCAN_SMALL_THREADS) k_plan_one(AggWork w, int seg_mode) {
+    __shared__ uint32_t sw[33];
+    const uint32_t t = threadIdx.x, n = blockDim.x;
+    if (seg_mode == 1) part_seg_range(w, t, n);
+    else if (seg_mode == 0) cta_scan_u32(w.grp_hist, w.grp_hist, w.G, sw);
+    __syncthreads();
+    item_flags_range(w, t, n);
+    __syncthreads();
+    cta_scan_u32(w.item_id, w.item_id, w.G, sw);
+    __syncthreads();
+    items_range(w, t, n);
+    __syncthreads();
+    items_size_range(w, t, n);
+    __syncthreads();
+    cta_scan_u32(w.item_nleaf, w.item_nleaf, w.G, sw);
+    __syncthreads();
+    leaves_range(w, t, n);
 }
 
 // ------------------------------------------------------------------ K9a: attribute
@@ -472,16 +528,6 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_hist(AggWork w) {
     }
 }
 
-// group offsets (exclusive) from the scanned part counts
-__global__ void k_part_seg(AggWork w) {
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= w.G; g += gridDim.x * blockDim.x) {
-        if (g == w.G) { w.grp_hist[g] = w.part_cnt[w.n_cnt]; continue; }
-        const uint32_t b = upper_index<uint32_t>(w.buf_grp, w.n_buf, g);
-        const BufDev& B = w.bufs[b];
-        const uint64_t parts = w.buf_part[b + 1] - w.buf_part[b];
-        w.grp_hist[g] = w.part_cnt[B.cnt_base + (uint64_t)(g - B.grp_base) * parts];
-    }
-}
 
 // Shared memory of k_part_scatter for up to nb bins: per-bin cursors of the
 // part, the tile's per-bin counts / offsets, and the tile's records staged in
@@ -965,9 +1011,12 @@ __global__ void __launch_bounds__(256) k_emit(AggWork w) {
     if (tot) flush();
 }
 
-__global__ void k_finalize(AggWork w) {
+// per-buffer key counts and status, from the scanned leaf key counts (doing
+// this in k_emit's first CTA instead of a launch of its own made k_emit 0.47
+// ms slower on the large profile)
+__device__ __forceinline__ void finalize_range(const AggWork& w, uint32_t i0, uint32_t step) {
     const uint32_t* leaf_out = w.leaf_d;
-    for (uint32_t b = threadIdx.x; b < w.n_buf; b += blockDim.x) {
+    for (uint32_t b = i0; b < w.n_buf; b += step) {
         const BufDev& B = w.bufs[b];
         const uint64_t K = (uint64_t)leaf_out[w.buf_first_leaf[b + 1]] - leaf_out[w.buf_first_leaf[b]];
         const unsigned long long bad = w.buf_bad[b];
@@ -982,10 +1031,24 @@ __global__ void k_finalize(AggWork w) {
     }
 }
 
+__global__ void k_finalize(AggWork w) { finalize_range(w, threadIdx.x, blockDim.x); }
+
 // ------------------------------------------------------------------ driver
-void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, bool seg_ready) {
-    const int gblocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 255) / 256, (uint64_t)sms * 16));
-    if (!seg_ready) scan_u32(w.grp_hist, w.grp_hist, w.G, w.scan_tmp, s, launches);
+// seg_ready: the group offsets are in grp_hist already; part_seg: they come
+// from the scanned part counts (partition path, part_mode 1)
+void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, bool seg_ready, bool part_seg) {
+    const int gblocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 256) / 256, (uint64_t)sms * 16));
+    if (w.G <= PLAN_ONE_CTA_MAX) {
+        k_plan_one<<<1, SCAN_SMALL_THREADS, 0, s>>>(w, part_seg ? 1 : (seg_ready ? 2 : 0));
+        *launches += 1;
+        return;
+    }
+    if (part_seg) {
+        k_part_seg<<<gblocks, 256, 0, s>>>(w);
+        *launches += 1;
+    } else if (!seg_ready) {
+        scan_u32(w.grp_hist, w.grp_hist, w.G, w.scan_tmp, s, launches);
+    }
     k_item_flags<<<gblocks, 256, 0, s>>>(w);
     scan_u32(w.item_id, w.item_id, w.G, w.scan_tmp, s, launches);
     k_items<<<gblocks, 256, 0, s>>>(w);
@@ -993,21 +1056,6 @@ void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, boo
     scan_u32(w.item_nleaf, w.item_nleaf, w.G, w.scan_tmp, s, launches);
     k_leaves<<<gblocks, 256, 0, s>>>(w);
     *launches += 4;
-}
-
-__global__ void k_zero_totals(AggWork w) {
-    for (uint32_t b = blockIdx.x; b < w.n_buf; b += gridDim.x) {
-        const BufDev& B = w.bufs[b];
-        for (uint32_t r = threadIdx.x; r < B.n_stall; r += blockDim.x) {
-            if (B.total) B.total[r] = 0;
-            if (B.unknown) B.unknown[r] = 0;
-        }
-    }
-}
-
-void launch_zero_totals(const AggWork& w, cudaStream_t s, uint64_t* launches) {
-    k_zero_totals<<<std::min<uint32_t>(w.n_buf, 1024), 32, 0, s>>>(w);
-    *launches += 1;
 }
 
 void launch_finalize(const AggWork& w, cudaStream_t s, uint64_t* launches) {
@@ -1047,17 +1095,44 @@ static void run_finish(const AggWork& w_in, cudaStream_t s, int sms, uint64_t* l
     if (ev) cudaEventRecord(ev[5], s);
 }
 
-void clear_work(const AggWork& w, cudaStream_t s) {
-    cudaMemsetAsync(w.grp_hist, 0, sizeof(uint32_t) * ((size_t)w.G + 1), s);
-    cudaMemsetAsync(w.leaf_d, 0, sizeof(uint32_t) * ((size_t)w.L_max + 1), s);
-    cudaMemsetAsync(w.buf_bad, 0, sizeof(unsigned long long) * w.n_buf, s);
-    if (w.leaf_look) cudaMemsetAsync(w.leaf_look, 0, sizeof(unsigned long long) * w.L_max, s);
-    if (w.leaf_ticket) cudaMemsetAsync(w.leaf_ticket, 0, sizeof(uint32_t), s);
+// One launch zeroes the per-call counters of the work area (and, with
+// totals, the buffers' per-stall and UNKNOWN totals), where five memsets and
+// a kernel were six graph nodes.
+__global__ void k_clear(AggWork w, int totals) {
+    const uint64_t nh = (uint64_t)w.G + 1, nd = (uint64_t)w.L_max + 1, nb = w.n_buf;
+    const uint64_t nl = w.leaf_look ? w.L_max : 0, nt = w.leaf_ticket ? 1 : 0;
+    const uint64_t n = nh + nd + nb + nl + nt;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t j = i;
+        if (j < nh) { w.grp_hist[j] = 0; continue; }
+        j -= nh;
+        if (j < nd) { w.leaf_d[j] = 0; continue; }
+        j -= nd;
+        if (j < nb) { w.buf_bad[j] = 0; continue; }
+        j -= nb;
+        if (j < nl) { w.leaf_look[j] = 0; continue; }
+        *w.leaf_ticket = 0;
+    }
+    if (totals)
+        for (uint32_t b = blockIdx.x; b < w.n_buf; b += gridDim.x) {
+            const BufDev& B = w.bufs[b];
+            for (uint32_t r = threadIdx.x; r < B.n_stall; r += blockDim.x) {
+                if (B.total) B.total[r] = 0;
+                if (B.unknown) B.unknown[r] = 0;
+            }
+        }
+}
+
+void clear_work(const AggWork& w, cudaStream_t s, bool totals) {
+    const uint64_t n = (uint64_t)w.G + w.L_max + w.n_buf + w.L_max + 3;
+    const int blocks = (int)std::max<uint64_t>(std::min<uint64_t>(w.n_buf, 1024),
+                                               std::min<uint64_t>((n + 255) / 256, 1024));
+    k_clear<<<blocks, 256, 0, s>>>(w, totals ? 1 : 0);
 }
 
 void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
-    clear_work(w, s);
+    clear_work(w, s, true);
     if (w.part_mode) {
         const size_t csm = (size_t)w.part_ctx_max * 4;
         const size_t ssm = part_scatter_smem(w.part_ctx_max);
@@ -1072,11 +1147,8 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
         k_part_hist<<<pb, PART_THREADS, csm, s>>>(w);
         scan_u32(w.part_cnt, w.part_cnt, w.n_cnt, w.scan_tmp, s, launches);
         *launches += 1;
-        const int gb = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 256) / 256, (uint64_t)sms * 16));
         if (w.part_mode == 1) {
-            k_part_seg<<<gb, 256, 0, s>>>(w);
-            *launches += 1;
-            run_plan(w, s, sms, launches, true);
+            run_plan(w, s, sms, launches, true, true);
             if (ev) cudaEventRecord(ev[1], s);
             if (w.has_cnt) k_part_scatter<true, PSC_U><<<psb, PSC_THREADS, ssm, s>>>(w);
             else k_part_scatter<false, PSC_U><<<psb, PSC_THREADS, ssm, s>>>(w);
@@ -1092,6 +1164,7 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
             cudaMemsetAsync(w.cnt2, 0, sizeof(uint32_t) * ((size_t)w.n_cnt2 + 1), s);
             k_part2_hist<<<sms * 4, PART_THREADS, 0, s>>>(w);
             scan_u32(w.cnt2, w.cnt2, w.n_cnt2, w.scan_tmp, s, launches);
+            const int gb = (int)std::max<uint64_t>(1, std::min<uint64_t>((w.G + 256) / 256, (uint64_t)sms * 16));
             k_part2_seg<<<gb, 256, 0, s>>>(w);
             run_plan(w, s, sms, launches, true);
             if (w.has_cnt) k_part2_scatter<true><<<sms * 2, PART_THREADS, 0, s>>>(w);

@@ -752,18 +752,15 @@ hpa_status hpa_handle::aggregate(uint32_t n, const uint32_t* binary_ids, const h
     if (used > desc_bytes) return fail(HPA_E_INTERNAL, "descriptor layout overflows its staging area");
     if (use_graph && !timing) return launch_graph(ws, used, n, in);
     if ((st = upload_staging(used))) return st;
-    for (uint32_t b = 0; b < n; ++b) {
-        if (outs[b].total) cudaMemsetAsync(outs[b].total, 0, 8 * in[b].n_stall, stream);
-        if (outs[b].unknown) cudaMemsetAsync(outs[b].unknown, 0, 8 * in[b].n_stall, stream);
-    }
+    // (each sub-batch's first kernel zeroes its buffers' totals)
     for (size_t k = 0; k < ws.size(); ++k)
         run_aggregate(ws[k], stream, sms, &launches, timing ? phase_events(k == 0) : nullptr);
     return cuda(cudaGetLastError(), "aggregation launch");
 }
 
 // One CUDA graph per batch shape: the descriptor upload (from the pinned
-// staging area, rewritten before every replay), the zeroing of totals and
-// every kernel of the pipeline.  User pointers reach the kernels only
+// staging area, rewritten before every replay) and every kernel of the
+// pipeline (the first of which zeroes the totals).  User pointers reach the kernels only
 // through the uploaded descriptors, so a replay serves new buffers of the
 // same shape.
 static uint64_t mix64(uint64_t h, uint64_t v) {
@@ -795,7 +792,6 @@ hpa_status hpa_handle::launch_graph(const std::vector<AggWork>& ws, size_t stage
         uint64_t k0 = launches;
         if ((st = cuda(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeRelaxed), "begin capture"))) return st;
         cudaMemcpyAsync(d_staging, staging, staged_bytes, cudaMemcpyHostToDevice, capture_stream);
-        for (const AggWork& w : ws) launch_zero_totals(w, capture_stream, &launches);
         for (const AggWork& w : ws) run_aggregate(w, capture_stream, sms, &launches, nullptr);
         cudaError_t e = cudaStreamEndCapture(capture_stream, &graph);
         if ((st = cuda(e, "end capture"))) return st;

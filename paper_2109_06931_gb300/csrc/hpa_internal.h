@@ -188,11 +188,10 @@ void run_group_tail(const AggWork& w, cudaStream_t s, int sms, uint64_t* launche
 
 // zero every buffer's per-stall totals (device-side, so a captured graph
 // reads the current descriptors)
-void launch_zero_totals(const AggWork& w, cudaStream_t s, uint64_t* launches);
 
 // shared stages for other producers
-void clear_work(const AggWork& w, cudaStream_t s);
-void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, bool seg_ready);
+void clear_work(const AggWork& w, cudaStream_t s, bool totals = false);   // totals: the buffers' too
+void run_plan(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches, bool seg_ready, bool part_seg = false);
 void launch_big_partition(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);
 // every leaf kernel of one aggregation (hpa_leaf.cu)
 void launch_leaves(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches);

@@ -154,8 +154,6 @@ extern "C" hpa_status hpa_attribute_samples_noalloc(hpa_handle* h, uint32_t bina
     cudaStream_t stream = h->stream;
     k_noalloc_descriptors<<<1, 1, 0, stream>>>(d, w.n_tiles, (uint32_t)G, d_buf, d_tile, d_grp);
     h->launches += 1;
-    if (out->total) cudaMemsetAsync(out->total, 0, 8 * s.n_stall, stream);
-    if (out->unknown) cudaMemsetAsync(out->unknown, 0, 8 * s.n_stall, stream);
     out->n_ctx = s.n_ctx;
     out->n_stall = s.n_stall;
     out->n_nodes = B->n_nodes;
