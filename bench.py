@@ -234,6 +234,9 @@ def measure_rows(h, bid, B, w, prof, stream, dev):
     kk = sum(p.count() for p in profs)
     ms = timed(stream, lambda: (h.derive_metrics(profs), h.sync()), reps=2)
     out["derive"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
+    # ratio of raw metrics: two profiles over the other two
+    ms = timed(stream, lambda: (h.ratio_of_sums(bid, profs[:2], profs[2:]), h.sync()), reps=2)
+    out["ratio"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}
     # sparse layouts of the same profiles (context-major and profile-major)
     ms = timed(stream, lambda: (h.build_cms(profs), h.sync()), reps=2)
     out["cms"] = {"ms": ms, "profiles": len(profs), "keys_in": kk, "keys_per_s": kk / (ms / 1e3)}

@@ -37,12 +37,12 @@
 
 namespace hpa {
 
-// two contexts per SM, so that one context's level-synchronous steps (a
-// barrier and a chain of dependent loads per level) overlap another's work
-// (on 2,000 contexts of 10^4 keys: 512 x 2 took 40.6 ms, 256 x 4 45.4 ms,
-// 128 x 8 72.9 ms)
-constexpr int GALL_THREADS = 512;
-constexpr int GALL_PER_SM = 2;
+// one context per SM at a time, its level-synchronous steps (a barrier and a
+// chain of dependent loads per level) spread over 1,024 threads (on 2,000
+// contexts of 10^4 keys: 1,024 x 1 took 39.0 ms, 512 x 2 40.6 ms, 256 x 4
+// 45.4 ms, 128 x 8 72.9 ms)
+constexpr int GALL_THREADS = 1024;
+constexpr int GALL_PER_SM = 1;
 constexpr size_t GALL_SMEM_MAX = 48 * 1024;   // bitmaps in shared memory up to this size, else in the slot
 
 // per-node / per-function flags of one context (u32 words, atomicOr)
