@@ -568,6 +568,7 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
     uint2* srec = reinterpret_cast<uint2*>(psm + PSC_STAGE + (((size_t)nbmax * 4 + ((size_t)nbmax + 1) * 4 + 7) & ~(size_t)7));
     uint16_t* sbin = reinterpret_cast<uint16_t*>(srec + PART_TILE);
     const uint64_t keep = policy_evict_last();
+    const uint64_t once = policy_evict_first();      // samples and records pass through L2 once: the tables stay
     const uint32_t limit = w.timeout_iters ? w.timeout_iters : (1u << 22);
     if (threadIdx.x == 0) { mbar_init(&bar); s_abort = 0; }
     uint32_t phase = 0;
@@ -596,10 +597,10 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
         auto issue = [&](uint64_t t) {                  // one thread; every thread is done with the stage
             fence_proxy_async();
             mbar_expect_tx(&bar, PART_TILE * (cnt_in ? 8u + 4u + 1u + 4u : 8u + 4u + 1u));
-            bulk_g2s(spc, B.pc + t, PART_TILE * 8, &bar);
-            bulk_g2s(sctx, B.ctx + t, PART_TILE * 4, &bar);
-            bulk_g2s(sst, B.stall + t, PART_TILE, &bar);
-            if (cnt_in) bulk_g2s(scnt, B.count + t, PART_TILE * 4, &bar);
+            bulk_g2s_hint(spc, B.pc + t, PART_TILE * 8, &bar, once);
+            bulk_g2s_hint(sctx, B.ctx + t, PART_TILE * 4, &bar, once);
+            bulk_g2s_hint(sst, B.stall + t, PART_TILE, &bar, once);
+            if (cnt_in) bulk_g2s_hint(scnt, B.count + t, PART_TILE * 4, &bar, once);
         };
         if (threadIdx.x == 0 && staged(i0)) issue(i0);
         uint32_t bad = 0;
@@ -667,9 +668,9 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
                 const uint32_t dst = cur[c] + (j - th[c]);
                 if (!in_bounds(w.status, dst, w.n_rec, 103)) continue;     // site 103: record destination
                 if (two) {
-                    if (HAS_CNT) w.rec2_pair[dst] = srec[j];
-                    else w.rec2_sub[dst] = srec[j].x;
-                    w.rec2_dig[dst] = (uint8_t)sb;
+                    if (HAS_CNT) __stcs((unsigned long long*)&w.rec2_pair[dst], *(const unsigned long long*)&srec[j]);
+                    else __stcs(&w.rec2_sub[dst], srec[j].x);
+                    __stcs((signed char*)&w.rec2_dig[dst], (signed char)(uint8_t)sb);
                 } else {
                     if (HAS_CNT) w.rec_pair[dst] = srec[j];
                     else w.rec_sub[dst] = srec[j].x;
