@@ -672,8 +672,8 @@ __global__ void __launch_bounds__(PSC_THREADS, PSC_MIN_BLOCKS) k_part_scatter(Ag
                     else __stcs(&w.rec2_sub[dst], srec[j].x);
                     __stcs((signed char*)&w.rec2_dig[dst], (signed char)(uint8_t)sb);
                 } else {
-                    if (HAS_CNT) w.rec_pair[dst] = srec[j];
-                    else w.rec_sub[dst] = srec[j].x;
+                    if (HAS_CNT) __stcs((unsigned long long*)&w.rec_pair[dst], *(const unsigned long long*)&srec[j]);
+                    else __stcs(&w.rec_sub[dst], srec[j].x);
                 }
             }
             __syncthreads();
@@ -807,8 +807,8 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part2_scatter(AggWork w) {
                 const uint32_t d = sdig[i];
                 const uint32_t dst = cur[d] + (i - th[d]);
                 if (!in_bounds(w.status, dst, w.n_rec, 105)) continue;     // site 105: record destination
-                if (HAS_CNT) w.rec_pair[dst] = srec[i];
-                else w.rec_sub[dst] = srec[i].x;
+                if (HAS_CNT) __stcs((unsigned long long*)&w.rec_pair[dst], *(const unsigned long long*)&srec[i]);
+                else __stcs(&w.rec_sub[dst], srec[i].x);
             }
             __syncthreads();
             for (uint32_t d = threadIdx.x; d < nd; d += PART_THREADS) cur[d] += th[d + 1] - th[d];
