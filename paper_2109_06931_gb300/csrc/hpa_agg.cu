@@ -1090,10 +1090,10 @@ static void run_finish(const AggWork& w_in, cudaStream_t s, int sms, uint64_t* l
     // did not wait for their offset) are placed by k_emit
     const size_t emit_smem = w.emit_totals ? ((size_t)256 << w.sb) * 8 : 0;
     set_smem_limit((const void*)k_emit, 256 * HPA_MAX_STALL_DEV * 8);
-    // leaves in small portions: up to 64 CTAs per SM, never more than the leaf
-    // table's size (on the large profile 64 per SM took 1.006 ms, 32 1.056, 16
-    // 1.14, 8 1.19)
-    const int eg = (int)std::max<uint64_t>((uint64_t)sms * 8, std::min<uint64_t>((uint64_t)sms * 64, w.L_max));
+    // leaves in small portions: up to 128 CTAs per SM, never more than the leaf
+    // table's size (on the large profile 128 per SM took 0.983 ms, 64 1.005, 32
+    // 1.056, 16 1.14, 8 1.19)
+    const int eg = (int)std::max<uint64_t>((uint64_t)sms * 8, std::min<uint64_t>((uint64_t)sms * 128, w.L_max));
     k_emit<<<eg, 256, emit_smem, s>>>(w);
     *launches += 1;
     launch_finalize(w, s, launches);
@@ -1147,7 +1147,8 @@ void run_aggregate(const AggWork& w, cudaStream_t s, int sms, uint64_t* launches
             set_smem_limit((const void*)k_part_scatter<true, PSC_U>, mxs);
             set_smem_limit((const void*)k_part_scatter<false, PSC_U>, mxs);
         }
-        const int pb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * 2));
+        // up to 8 histogram CTAs per SM, one part each (2 per SM: 0.09 ms more on the large profile)
+        const int pb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * 8));
         const int psb = (int)std::max<uint64_t>(1, std::min<uint64_t>(w.n_parts, (uint64_t)sms * PSC_MIN_BLOCKS));
         k_part_hist<<<pb, PART_THREADS, csm, s>>>(w);
         scan_u32(w.part_cnt, w.part_cnt, w.n_cnt, w.scan_tmp, s, launches);
